@@ -1,0 +1,44 @@
+"""The whole CPU ExactSim query: Algorithm 1 with Algorithm 2 as its D estimator.
+
+Test infrastructure only (see ``oracle/__init__.py``).  It runs the steps in the
+paper's order -- L, hop vectors, allocation, walk pairs, D^, reverse
+accumulation -- from ``linearization`` (NumPy/SciPy FP64) and ``walks`` (C,
+OpenMP).  This is also the plain multithreaded CPU ExactSim the benchmark times.
+
+Pinned by: max_v |s(v) - S(u, v)| <= eps against the Power Method on small
+graphs, and the pins of its parts.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import linearization as lin
+from . import walks
+
+
+@dataclass
+class QueryResult:
+    s: np.ndarray
+    H: np.ndarray
+    pi: np.ndarray
+    R: np.ndarray
+    nonmeet: np.ndarray
+    D: np.ndarray
+    L: int
+    R_b: float
+    pair_steps: int
+
+
+def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
+          kappa: float | None = None, mode: str = "pi2", threads: int = 0) -> QueryResult:
+    L = lin.levels(c, eps)
+    H = lin.hop_vectors(n, in_rowptr, in_col, u, c, L)
+    pi = lin.ppr(H)
+    R_b = lin.sample_base(n, c, eps, kappa)
+    R = lin.allocate(pi, R_b, mode)
+    nonmeet, steps = walks.walk_pairs(n, in_rowptr, in_col, R, c, seed, threads)
+    D = lin.dhat(nonmeet, R)
+    s = lin.reverse(n, in_rowptr, in_col, H, D, c)
+    return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
