@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: single-source SimRank top-k queries/s on one GB300 (ExactSim, arXiv:2004.03493).
+
+Workload (default "cl100k"): directed Chung-Lu power-law graph, n = 100,000,
+m = 1,000,000, in/out Pareto weights with exponent 2.1 (graph seed 1);
+c = 0.6, eps = 1e-6, ten seeded sources (uniform over nodes with din >= 1) run
+one at a time, top-50 each.  One step = those ten top-k queries, every step of
+the hot path (forward sweeps, allocation, walk pairs, reverse sweeps, top-k) on
+the GPU.  The graph is synthetic; the paper's datasets are not available.
+
+Timing: W warm-up steps, then K timed steps; the graph (8 MB) fits in L2, so
+L2 is flushed (a 512 MB write) before every timed step, outside the CUDA-event
+bracket of the step.  Under torchrun each rank is an independent replica with
+its own ten sources (the path has no exchange step); value = all queries of
+all ranks / max over ranks of the timed span.
+
+--impl reference times the CPU oracle (oracle/, FP64, OpenMP walk sampler) as it
+stands on the host cores: each step runs a bounded sample of one query (all
+sweeps, a fixed number of walk pairs) and the time is scaled to a full query.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "cl100k": dict(kind="chung_lu", n=100_000, m=1_000_000, gamma=2.1, graph_seed=1, c=0.6, eps=1e-6,
+                   sources=10, source_seed=7, k=50),
+    "er2000": dict(kind="erdos_renyi", n=2000, m=20_000, graph_seed=1, c=0.6, eps=1e-4, sources=1,
+                   source_seed=0, k=50),
+}
+METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6, top-50)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def make_graph(w):
+    import synth
+    if w["kind"] == "chung_lu":
+        return synth.chung_lu(w["n"], w["m"], gamma=w["gamma"], seed=w["graph_seed"])
+    return synth.erdos_renyi(w["n"], w["m"], seed=w["graph_seed"])
+
+
+def sources_for(w, rp, world, rank):
+    import synth
+    if w["kind"] == "erdos_renyi" and w["sources"] == 1:
+        return [0] * 1
+    allsrc = synth.random_sources(rp, w["sources"] * world, seed=w["source_seed"])
+    return [int(x) for x in allsrc[rank * w["sources"]:(rank + 1) * w["sources"]]]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0):
+    """Time one bounded sample of the CPU oracle query; return (seconds per full query, info)."""
+    from oracle import linearization as lin
+    from oracle import walks
+    c, eps = w["c"], w["eps"]
+    t0 = time.perf_counter()
+    L = lin.levels(c, eps)
+    H = lin.hop_vectors(n, rp, col, u, c, L)
+    pi = lin.ppr(H)
+    R_b = lin.sample_base(n, c, eps, kappa)
+    R = lin.allocate(pi, R_b, "pi2")
+    t_sweep_fwd = time.perf_counter() - t0
+    total = int(R.sum())
+    # bounded sample of the walk pairs: the same per-node proportions, scaled down
+    scale = min(1.0, pair_cap / max(total, 1))
+    R_s = np.floor(R.astype(np.float64) * scale).astype(np.uint64)
+    t1 = time.perf_counter()
+    nonmeet, steps = walks.walk_pairs(n, rp, col, R_s, c, 1, threads)
+    t_walk = time.perf_counter() - t1
+    D = lin.dhat(nonmeet, R_s)
+    t2 = time.perf_counter()
+    s = lin.reverse(n, rp, col, H, D, c)
+    lin.topk(s, w["k"], exclude=u)
+    t_rev = time.perf_counter() - t2
+    sampled = int(R_s.sum())
+    walk_full = t_walk * (total / max(sampled, 1))
+    return t_sweep_fwd + walk_full + t_rev, {"pairs_total": total, "pairs_sampled": sampled,
+                                             "t_sweeps_s": t_sweep_fwd + t_rev, "t_walk_sample_s": t_walk}
+
+
+def run_reference(args, w, rank, world):
+    """--impl reference: the CPU oracle on the host cores."""
+    if rank != 0:
+        return
+    from oracle import walks
+    walks.build()
+    n, rp, col = make_graph(w)
+    srcs = sources_for(w, rp, 1, 0)
+    cores = walks.max_threads()
+    per_query = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        u = srcs[i % len(srcs)]
+        t, info = cpu_reference_sample(w, n, rp, col, u, args.kappa, args.ref_pairs)
+        if i >= args.warmup:
+            per_query.append(t)
+    q_per_s = 1.0 / statistics.mean(per_query)
+    sample = (f"one query per step (sources cycled), all forward/reverse sweeps and allocation in full, "
+              f"{info['pairs_sampled']:.3g} of {info['pairs_total']:.3g} walk pairs (same per-node proportions), "
+              f"walk time scaled to the full pair count")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": q_per_s, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / q_per_s * w["sources"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, w),
+        "cpu_baseline": {"value": q_per_s, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": q_per_s, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, w):
+    return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
+            "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources_per_step": w["sources"],
+            "top_k": w["k"], "kappa": args.kappa, "alloc": "pi^2 (Lemma 4)",
+            "l2": "flushed (512 MB write) before each timed step", "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cl100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--kappa", type=float, default=0.05,
+                    help="sample constant: R_b = kappa ln(n) / eps^2 (<= 0: the paper's 6/(1-sqrt c)^4)")
+    ap.add_argument("--ref-pairs", type=float, default=2e8, help="walk pairs per CPU reference sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+
+    n, rp, col = make_graph(w)
+    srcs = sources_for(w, rp, world, rank)
+    c, eps, k = w["c"], w["eps"], w["k"]
+    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream)
+    ids = torch.empty(k, dtype=torch.int32, device=dev)
+    vals = torch.empty(k, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(step_idx, record):
+        for q, u in enumerate(srcs):
+            g.topk_device(u, c, eps, k, 1000 * step_idx + q, ids, vals)
+            if record is not None:
+                record.append(g.stats())
+
+    for i in range(args.warmup):
+        step(i, None)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    stats = []
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step(args.warmup + i, stats)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+
+    # end to end through the public host API (host outputs; results copied back every query)
+    host_ids = np.empty(k, dtype=np.int32)
+    host_vals = np.empty(k, dtype=np.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        for q, u in enumerate(srcs):
+            esim.esim_topk(g.handle, u, c, eps, 1000 * (args.warmup + i) + q, k, host_ids, host_vals)
+    e2e_s = time.perf_counter() - t0
+
+    t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_s = float(t[0]), float(t[1])
+    queries = args.steps * len(srcs) * world
+    value = queries / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel (the walk-pair sampler): pair-steps per second against
+    # the integer-issue limit of the Philox-4x32-10 block
+    steps_total = sum(s["pair_steps"] for s in stats)
+    ms_sample = sum(s["ms_sample"] for s in stats)
+    ms_phase = {p: sum(s[f"ms_{p}"] for s in stats) for p in ("forward", "allocate", "sample", "reverse", "topk")}
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    instr_per_step = 48.0
+    peak_steps = sm_count * 128 * sm_max * 1e6 / instr_per_step
+    achieved = steps_total / (ms_sample / 1000.0) if ms_sample > 0 else 0.0
+    sweep_bytes = 2 * (4 * len(col) + 4 * (n + 1)) + 3 * 8 * n  # per forward+reverse level pair
+    L = stats[0]["L"] if stats else 0
+    sweep_gbs = (len(stats) * L * sweep_bytes) / ((ms_phase["forward"] + ms_phase["reverse"]) / 1000.0) / 1e9 \
+        if stats else 0.0
+    launches = sum(s["launches"] for s in stats)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, w),
+        "clocks": clk,
+        "e2e": {"value": queries / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": len(srcs) * k * (4 + 8),
+                "note": "esim_topk with host output buffers; query parameters pass by value"},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "sample_pairs_kernel", "bound": "alu", "achieved": achieved / 1e9,
+                     "peak": peak_steps / 1e9, "unit": "G pair-steps/s", "frac": achieved / peak_steps,
+                     "traffic": None,
+                     "peak_source": f"{sm_count} SMs x 128 lanes x {sm_max:.0f} MHz ({pk_src}) / {instr_per_step:.0f} "
+                                    "instr per pair-step"},
+        "phases_ms": {p: v / max(len(stats), 1) for p, v in ms_phase.items()},
+        "walk": {"pairs_per_query": sum(s["sum_R"] for s in stats) / max(len(stats), 1),
+                 "pair_steps_per_s": achieved, "L": L},
+        "sweep_hbm_gbs": sweep_gbs,
+        "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import walks
+        walks.build()
+        t, info = cpu_reference_sample(w, n, rp, col, srcs[0], args.kappa, args.ref_pairs)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "queries/s", "cores": walks.max_threads(), "kind": "oracle",
+                                "sample": f"one query (u={srcs[0]}): sweeps in full, {info['pairs_sampled']:.3g} of "
+                                          f"{info['pairs_total']:.3g} walk pairs, walk time scaled"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * exactsim.h -- C ABI of the GB300 (sm_103a) ExactSim single-source SimRank library.
+ *
+ * Method: Wang, Wei, Yuan, Du, Wen, "Exact Single-Source SimRank Computation on
+ * Large Graphs" (SIGMOD 2020, arXiv:2004.03493).  A single-source query for
+ * node u returns s(v) ~ S(u, v) for every node v (Sec. 1); a top-k query returns
+ * the k nodes with the largest similarities (Sec. 1).  The query runs Algorithm 1
+ * (Basic ExactSim) with Algorithm 2 as its estimator of the diagonal correction
+ * D and the pi(k)^2 sample allocation of Lemma 4:
+ *
+ *   1. L = ceil(log_{1/c}(2/eps))                                   (Algorithm 1)
+ *   2. pi^0 = (1-sqrt c) e_u,  pi^l = sqrt(c) P pi^{l-1},  l = 1..L   (Algorithm 1)
+ *   3. pi = sum_l pi^l;  R(k) = ceil(R_b pi(k)^2),  R_b = kappa ln(n) / eps^2
+ *                                                  (Lemma 4; kappa = 6/(1-sqrt c)^4)
+ *   4. D^(k) = fraction of R(k) sqrt(c)-walk pairs from k that never meet
+ *                                                  (Algorithm 2, Eq. scwwalk)
+ *   5. s^0 = D^ pi^L / (1-sqrt c);  s^l = sqrt(c) P^T s^{l-1} + D^ pi^{L-l} / (1-sqrt c)
+ *      and s = s^L                                 (Algorithm 1, Eq. sL)
+ *   6. top-k of s, ordered (score desc, node id asc), the source excluded
+ *
+ * P is the reverse transition matrix of Sec. 2.2: P(i, j) = 1/din(j) for every
+ * in-neighbour i of j.  The graph is given as an in-edge CSR: row j lists the
+ * in-neighbours I(j) of node j.  A repeated in-edge counts with its multiplicity.
+ *
+ * Random numbers (the paper names none): Philox-4x32-10 (Salmon et al., SC'11)
+ * with key = (seed low 32 bits, seed high 32 bits) and counter (r_lo, r_hi, k, t)
+ * for pair r of node k at step t.  One call per step gives (w0, w1, w2, w3); with
+ * T = floor(sqrt(c) 2^32) walk A moves iff w0 < T and din > 0 and goes to
+ * in-neighbour number (w1 * din) >> 32; walk B likewise with w2, w3.  A pair ends
+ * as "no meeting" as soon as either walk stops, and as "meeting" when both move
+ * to the same node.  A pair still running after 65536 steps ends as "no meeting".
+ * A walk pair therefore depends only on (seed, k, r), not on the query.
+ *
+ * Conventions
+ *  - Every call returns an esim_status; ESIM_OK is 0.  On failure
+ *    esim_last_error() gives a message (thread-local, valid until the next call
+ *    on the same thread).
+ *  - "host" pointers are ordinary CPU memory owned by the caller.  "device"
+ *    pointers are CUDA global memory on the graph's device, owned by the caller.
+ *  - Whole-query calls (esim_query, esim_topk and their _device forms) return
+ *    after the work has finished on the GPU.  Step calls (esim_forward ...
+ *    esim_select_topk) only enqueue work on the graph's stream; call esim_sync
+ *    to wait and to collect device-side errors.
+ *  - No call falls back to the CPU.  Without a usable CUDA device every call
+ *    that needs one returns ESIM_ECUDA.
+ *  - Node ids are int32 in [0, n); n < 2^31 and m < 2^32.
+ */
+#ifndef EXACTSIM_H
+#define EXACTSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esim_graph esim_graph; /* opaque; owned by the library */
+
+typedef enum {
+    ESIM_OK = 0,
+    ESIM_EINVAL = -1,   /* an argument is out of range or inconsistent */
+    ESIM_ENOMEM = -2,   /* device or host allocation failed */
+    ESIM_ECUDA = -3,    /* a CUDA call failed, or no usable device */
+    ESIM_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+    ESIM_EBUDGET = -5,  /* the sum of R(k) exceeds the pair budget; no walks were run */
+    ESIM_ENOTSUP = -6   /* a size the library does not handle (e.g. k above the top-k limit) */
+} esim_status;
+
+/* Statistics of the last whole query on a graph handle. */
+typedef struct {
+    int32_t L;            /* depth ceil(log_{1/c}(2/eps)) */
+    int32_t launches;     /* kernels the library launched for the query */
+    double R_b;           /* kappa ln(n) / eps^2 */
+    double kappa;         /* the constant used */
+    double pi_norm2;      /* ||pi||^2 = sum_k pi(k)^2 */
+    uint64_t sum_R;       /* number of walk pairs, sum_k R(k) */
+    uint64_t pair_steps;  /* Philox calls made by the sampler (one per pair step) */
+    float ms_forward;     /* phase durations (CUDA events) when option "timing" is 1, else 0 */
+    float ms_allocate;
+    float ms_sample;
+    float ms_reverse;
+    float ms_topk;
+    float ms_total;
+} esim_query_stats;
+
+/* ------------------------------------------------------------------ library */
+
+/* Version string of the library. */
+const char* esim_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* esim_last_error(void);
+
+/* Parameters of Algorithm 1.  esim_levels returns L = ceil(log(2/eps)/log(1/c)),
+ * or -1 unless 0 < c < 1 and 0 < eps < 1.  esim_sample_base returns
+ * R_b = kappa * log(n) / (eps * eps), kappa <= 0 meaning the paper's
+ * 6 / ((1 - sqrt c)^4), or -1 on bad input.  esim_walk_threshold returns
+ * T = floor(sqrt(c) * 2^32). */
+int32_t esim_levels(double c, double eps);
+double esim_sample_base(int64_t n, double c, double eps, double kappa);
+uint32_t esim_walk_threshold(double c);
+
+/* ------------------------------------------------------------------ graph */
+
+/* Load a graph from a host in-edge CSR: in_rowptr[n+1] (in_rowptr[0] = 0,
+ * non-decreasing, in_rowptr[n] = m), in_col[m] with 0 <= in_col[p] < n.
+ * The library copies both arrays to the current CUDA device, builds the
+ * out-edge CSR (its transpose) and the row-split tables, and keeps them until
+ * esim_free_graph.  The caller may free its arrays after the call.
+ * Errors: ESIM_EINVAL (bad CSR, n < 1, n >= 2^31, m >= 2^32), ESIM_ENOMEM,
+ * ESIM_ECUDA. */
+esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* in_col, esim_graph** out);
+
+/* Release the graph and every device buffer the library holds for it. */
+void esim_free_graph(esim_graph* g);
+
+int64_t esim_num_nodes(const esim_graph* g);
+int64_t esim_num_edges(const esim_graph* g);
+
+/* Run the graph's work on `stream` (a cudaStream_t of the graph's device; NULL
+ * restores the library's own stream).  The library does not take ownership. */
+esim_status esim_set_stream(esim_graph* g, void* stream);
+
+/* Options (per graph handle):
+ *   "kappa"          sample constant; <= 0 means 6/(1-sqrt c)^4 (default 0)
+ *   "alloc"          0: R(k) = ceil(R_b pi(k)^2) (Lemma 4, default);
+ *                    1: R(k) = ceil(R_b pi(k)) (Algorithm 1, basic)
+ *   "exclude_source" 1: top-k leaves out the source (default); 0: keeps it
+ *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
+ *                    query returns ESIM_EBUDGET without running walks
+ *   "timing"         1: record per-phase CUDA event times in the stats
+ * Errors: ESIM_EINVAL for an unknown key or a bad value. */
+esim_status esim_set_option(esim_graph* g, const char* key, double value);
+esim_status esim_get_option(const esim_graph* g, const char* key, double* value);
+
+/* ------------------------------------------------------------------ queries */
+
+/* Single-source query of node u (Algorithm 1): s_out[n] (host) receives s(v)
+ * for every node v.  c and eps in (0, 1); seed selects the walk stream.
+ * Errors: ESIM_EINVAL, ESIM_EBUDGET, ESIM_ENOMEM, ESIM_ECUDA. */
+esim_status esim_query(esim_graph* g, int64_t u, double c, double eps, uint64_t seed, double* s_out);
+
+/* As esim_query, with s_dev[n] in device memory. */
+esim_status esim_query_device(esim_graph* g, int64_t u, double c, double eps, uint64_t seed, double* s_dev);
+
+/* Top-k query: the k nodes with the largest s(v), ordered (score desc, id asc),
+ * the source left out unless option "exclude_source" is 0.  ids_out[k] and
+ * scores_out[k] are host arrays.  If fewer than k nodes are eligible the
+ * remaining slots get id -1 and score 0.  1 <= k <= 4096, else ESIM_ENOTSUP
+ * (k > 4096) or ESIM_EINVAL (k < 1). */
+esim_status esim_topk(esim_graph* g, int64_t u, double c, double eps, uint64_t seed, int32_t k,
+                      int32_t* ids_out, double* scores_out);
+
+/* As esim_topk with device outputs. */
+esim_status esim_topk_device(esim_graph* g, int64_t u, double c, double eps, uint64_t seed, int32_t k,
+                             int32_t* ids_dev, double* scores_dev);
+
+/* Statistics of the last whole query on g. */
+esim_status esim_last_stats(const esim_graph* g, esim_query_stats* out);
+
+/* ------------------------------------------------------------------ steps
+ * The steps of the query, exposed for testing and composition.  All pointers
+ * are device pointers; all calls enqueue on the graph's stream. */
+
+/* Forward sweeps (Algorithm 1): hist[(L+1) * n] receives pi^0 .. pi^L, level l
+ * at hist + l*n.  0 <= u < n, 0 < c < 1, 0 <= L <= 4096. */
+esim_status esim_forward(esim_graph* g, int64_t u, double c, int32_t L, double* hist);
+
+/* Allocation (Lemma 4 / Algorithm 1): pi(k) = sum_{l=0..L} hist[l*n + k] added in
+ * level order; R(k) = ceil(R_b * (pi(k) * pi(k))) (mode 0) or ceil(R_b * pi(k))
+ * (mode 1); off[0] = 0, off[k+1] = off[k] + R(k).  pi_out may be NULL.
+ * R_out[n], off[n+1] (uint64).  A value of R_b * pi^2 at or above 2^63 makes
+ * esim_sync return ESIM_EBUDGET. */
+esim_status esim_allocate(esim_graph* g, const double* hist, int32_t L, double R_b, int32_t mode,
+                          double* pi_out, uint64_t* R_out, uint64_t* off);
+
+/* Walk pairs (Algorithm 2): nonmeet[n] (uint64) receives, for each k, how many
+ * of its off[k+1] - off[k] pairs never meet.  pair_steps (one uint64, may be
+ * NULL) receives the number of Philox calls.  If off[n] exceeds the option
+ * "pair_budget" no walk runs and esim_sync returns ESIM_EBUDGET. */
+esim_status esim_sample(esim_graph* g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
+                        uint64_t* pair_steps);
+
+/* D^(k) = nonmeet[k] / (off[k+1] - off[k]), 0 where the count is 0 (Algorithm 2). */
+esim_status esim_dhat(esim_graph* g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
+
+/* Reverse accumulation (Algorithm 1, Eq. sL) from hist[(L+1)*n] and D^[n]:
+ * s_out[n] = s^L. */
+esim_status esim_reverse(esim_graph* g, const double* hist, int32_t L, double c, const double* dhat,
+                         double* s_out);
+
+/* Top-k selection over scores[n] (device): ids_out[k], vals_out[k] (device),
+ * ordered (score desc, id asc); exclude = -1 keeps every node.  1 <= k <= 4096. */
+esim_status esim_select_topk(esim_graph* g, const double* scores, int64_t exclude, int32_t k,
+                             int32_t* ids_out, double* vals_out);
+
+/* Wait for the graph's stream; returns the first device-side error recorded
+ * since the last esim_sync (ESIM_EBUDGET, ESIM_ETIMEOUT) or ESIM_ECUDA. */
+esim_status esim_sync(esim_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXACTSIM_H */

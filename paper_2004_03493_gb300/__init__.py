@@ -1,0 +1,128 @@
+"""GB300-native ExactSim single-source SimRank (arXiv:2004.03493).
+
+The computation lives in the CUDA library ``_lib/libexactsim.so`` (C ABI in
+``include/exactsim.h``); this package is its Python binding.  ``Graph`` wraps a
+graph handle; the ``esim_*`` functions mirror the C entry points one to one.
+There is no CPU fallback: without the library or a CUDA device every call
+raises.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native
+from ._native import (  # noqa: F401
+    EsimError,
+    esim_allocate,
+    esim_dhat,
+    esim_forward,
+    esim_free_graph,
+    esim_get_option,
+    esim_last_error,
+    esim_last_stats,
+    esim_levels,
+    esim_load_graph,
+    esim_num_edges,
+    esim_num_nodes,
+    esim_query,
+    esim_query_device,
+    esim_reverse,
+    esim_sample,
+    esim_sample_base,
+    esim_select_topk,
+    esim_set_option,
+    esim_set_stream,
+    esim_sync,
+    esim_topk,
+    esim_topk_device,
+    esim_version,
+    esim_walk_threshold,
+)
+
+
+class Graph:
+    """A graph resident on the current CUDA device (in-edge CSR input)."""
+
+    def __init__(self, n: int, in_rowptr, in_col, **options):
+        self.n = int(n)
+        self.handle = esim_load_graph(self.n, in_rowptr, in_col)
+        self.m = esim_num_edges(self.handle)
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            esim_free_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, key: str, value: float):
+        esim_set_option(self.handle, key, value)
+
+    def get_option(self, key: str) -> float:
+        return esim_get_option(self.handle, key)
+
+    def set_stream(self, stream):
+        """Use a torch.cuda.Stream (or a raw cudaStream_t int, or None)."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        esim_set_stream(self.handle, ptr)
+
+    def query(self, u: int, c: float, eps: float, seed: int = 0) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float64)
+        esim_query(self.handle, u, c, eps, seed, out)
+        return out
+
+    def query_device(self, u: int, c: float, eps: float, seed: int, out):
+        esim_query_device(self.handle, u, c, eps, seed, out)
+        return out
+
+    def topk(self, u: int, c: float, eps: float, k: int, seed: int = 0):
+        ids = np.empty(k, dtype=np.int32)
+        vals = np.empty(k, dtype=np.float64)
+        esim_topk(self.handle, u, c, eps, seed, k, ids, vals)
+        return ids, vals
+
+    def topk_device(self, u: int, c: float, eps: float, k: int, seed: int, ids_out, vals_out):
+        esim_topk_device(self.handle, u, c, eps, seed, k, ids_out, vals_out)
+        return ids_out, vals_out
+
+    def stats(self) -> dict:
+        return esim_last_stats(self.handle)
+
+    # steps (device tensors)
+    def forward(self, u, c, L, hist):
+        esim_forward(self.handle, u, c, L, hist)
+
+    def allocate(self, hist, L, R_b, mode, pi_out, R_out, off):
+        esim_allocate(self.handle, hist, L, R_b, mode, pi_out, R_out, off)
+
+    def sample(self, off, c, seed, nonmeet, pair_steps=None):
+        esim_sample(self.handle, off, c, seed, nonmeet, pair_steps)
+
+    def dhat(self, nonmeet, off, out):
+        esim_dhat(self.handle, nonmeet, off, out)
+
+    def reverse(self, hist, L, c, dhat, s_out):
+        esim_reverse(self.handle, hist, L, c, dhat, s_out)
+
+    def select_topk(self, scores, exclude, k, ids_out, vals_out):
+        esim_select_topk(self.handle, scores, exclude, k, ids_out, vals_out)
+
+    def sync(self):
+        esim_sync(self.handle)
+
+
+def build(force: bool = False) -> str:
+    from .buildlib import build as _build
+    return _build(force=force)

@@ -1,0 +1,540 @@
+// C ABI of the library (include/exactsim.h): graph loading, options, the whole
+// query pipeline (Algorithm 1 with Algorithm 2 and the Lemma 4 allocation) and
+// the step entry points.
+#include "exactsim.h"
+#include "internal.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace esim;
+
+struct esim_graph {
+    Graph g;
+};
+
+namespace {
+
+thread_local std::string t_err;
+
+esim_status fail(esim_status st, const std::string& msg) {
+    t_err = msg;
+    return st;
+}
+
+esim_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(ESIM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ESIM_CUDA_TRY(expr, where)                        \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+void free_csr(DevCsr& c) {
+    cudaFree(c.rp);
+    cudaFree(c.col);
+    cudaFree(c.seg);
+    cudaFree(c.long_rows);
+    cudaFree(c.long_first);
+    c = DevCsr{};
+}
+
+int group_for(double avg_degree) {
+    if (avg_degree <= 3.0) return 2;
+    if (avg_degree <= 6.0) return 4;
+    if (avg_degree <= 12.0) return 8;
+    if (avg_degree <= 24.0) return 16;
+    return 32;
+}
+
+constexpr uint32_t kSegLen = 4096;
+
+// Upload a host CSR and build its row-split table.
+esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::vector<int32_t>& col, DevCsr& d) {
+    const int64_t m = (int64_t)rp[n];
+    d.group = group_for(n ? (double)m / (double)n : 1.0);
+    d.long_min = std::max<uint32_t>(256u, 32u * (uint32_t)d.group);
+    std::vector<Segment> seg;
+    std::vector<int32_t> long_rows, long_first;
+    for (int64_t r = 0; r < n; ++r) {
+        const uint32_t b = rp[r], e = rp[r + 1];
+        if (e - b < d.long_min) continue;
+        long_rows.push_back((int32_t)r);
+        long_first.push_back((int32_t)seg.size());
+        const uint32_t first = (uint32_t)seg.size();
+        for (uint32_t s = b; s < e; s += kSegLen) seg.push_back(Segment{(int32_t)r, s, std::min(e, s + kSegLen), first});
+    }
+    long_first.push_back((int32_t)seg.size());
+    d.nseg = (int64_t)seg.size();
+    d.nlong = (int64_t)long_rows.size();
+    cudaError_t e;
+    if ((e = dev_alloc(&d.rp, (size_t)n + 1)) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(rowptr)");
+    if ((e = dev_alloc(&d.col, (size_t)m)) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(col)");
+    if ((e = dev_alloc(&d.seg, seg.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(segments)");
+    if ((e = dev_alloc(&d.long_rows, long_rows.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(long rows)");
+    if ((e = dev_alloc(&d.long_first, long_first.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(long first)");
+    ESIM_CUDA_TRY(cudaMemcpy(d.rp, rp.data(), sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice), "upload rowptr");
+    if (m) ESIM_CUDA_TRY(cudaMemcpy(d.col, col.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice), "upload col");
+    if (!seg.empty())
+        ESIM_CUDA_TRY(cudaMemcpy(d.seg, seg.data(), sizeof(Segment) * seg.size(), cudaMemcpyHostToDevice), "upload segments");
+    if (!long_rows.empty())
+        ESIM_CUDA_TRY(cudaMemcpy(d.long_rows, long_rows.data(), sizeof(int32_t) * long_rows.size(), cudaMemcpyHostToDevice),
+                      "upload long rows");
+    ESIM_CUDA_TRY(cudaMemcpy(d.long_first, long_first.data(), sizeof(int32_t) * long_first.size(), cudaMemcpyHostToDevice),
+                  "upload long first");
+    return ESIM_OK;
+}
+
+void release(Graph& g) {
+    cudaSetDevice(g.device);
+    if (g.own_stream) cudaStreamSynchronize(g.own_stream);
+    free_csr(g.in);
+    free_csr(g.out);
+    cudaFree(g.status);
+    if (g.status_host) cudaFreeHost(g.status_host);
+    cudaFree(g.ws);
+    cudaFree(g.partial);
+    cudaFree(g.scan_part);
+    cudaFree(g.norm_part);
+    cudaFree(g.topk_ws);
+    for (auto& ev : g.ev)
+        if (ev) cudaEventDestroy(ev);
+    if (g.own_stream) cudaStreamDestroy(g.own_stream);
+    g = Graph{};
+}
+
+size_t topk_stage_offset(int64_t n) { return (topk_workspace_bytes(n) + 255) / 256 * 256; }
+
+bool valid_c_eps(double c, double eps) { return c > 0.0 && c < 1.0 && eps > 0.0 && eps < 1.0; }
+
+double kappa_of(const Graph& g, double c) {
+    if (g.kappa > 0.0) return g.kappa;
+    const double a = 1.0 - sqrt(c);
+    return 6.0 / (a * a * a * a);
+}
+
+// Query workspace layout (doubles / uint64, each n long unless noted).
+struct Ws {
+    double* hist;     // (L+1) n
+    double* xa;       // n (forward x, then reverse ping-pong)
+    double* xb;       // n
+    double* pi;       // n
+    uint64_t* R;      // n
+    uint64_t* off;    // n+1
+    uint64_t* nonmeet;// n
+    double* dhat;     // n
+    double* s;        // n
+};
+
+size_t ws_bytes_for(int64_t n, int32_t L) {
+    const size_t v = (size_t)n * 8;
+    return v * (size_t)(L + 1) + 8 * v + 8 + 8 * 256;
+}
+
+esim_status ensure_ws(Graph& g, int32_t L, Ws& w) {
+    const size_t need = ws_bytes_for(g.n, L);
+    if (need > g.ws_bytes) {
+        cudaStreamSynchronize(g.stream);
+        cudaFree(g.ws);
+        g.ws = nullptr;
+        g.ws_bytes = 0;
+        if (cudaMalloc(&g.ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ESIM_ENOMEM, "cudaMalloc(query workspace of " + std::to_string(need) + " bytes)");
+        }
+        g.ws_bytes = need;
+    }
+    const size_t n = (size_t)g.n;
+    double* p = (double*)g.ws;
+    w.hist = p;
+    p += n * (size_t)(L + 1);
+    w.xa = p; p += n;
+    w.xb = p; p += n;
+    w.pi = p; p += n;
+    w.R = (uint64_t*)p; p += n;
+    w.off = (uint64_t*)p; p += n + 1;
+    w.nonmeet = (uint64_t*)p; p += n;
+    w.dhat = p; p += n;
+    w.s = p;
+    return ESIM_OK;
+}
+
+esim_status check_graph(const esim_graph* h) {
+    if (!h) return fail(ESIM_EINVAL, "graph handle is NULL");
+    return ESIM_OK;
+}
+
+// Runs the whole query; s_dev may be NULL (the workspace holds s); k > 0 adds top-k.
+esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, double* s_dev, int32_t k,
+                      int32_t* ids_dev, double* vals_dev, double* s_host, int32_t* ids_host, double* vals_host) {
+    if (u < 0 || u >= g.n) return fail(ESIM_EINVAL, "source node out of range");
+    if (!valid_c_eps(c, eps)) return fail(ESIM_EINVAL, "need 0 < c < 1 and 0 < eps < 1");
+    if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    const int32_t L = esim_levels(c, eps);
+    const double kappa = kappa_of(g, c);
+    const double R_b = kappa * log((double)g.n) / (eps * eps);
+    Ws w;
+    esim_status st = ensure_ws(g, L, w);
+    if (st != ESIM_OK) return st;
+    double* s = s_dev ? s_dev : w.s;
+    if (g.timing)
+        for (auto& ev : g.ev)
+            if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
+    ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
+    if (g.timing) cudaEventRecord(g.ev[0], g.stream);
+    ESIM_CUDA_TRY(launch_forward(g, u, c, L, w.hist, w.xa, w.xb), "forward sweeps");
+    if (g.timing) cudaEventRecord(g.ev[1], g.stream);
+    ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
+    if (g.timing) cudaEventRecord(g.ev[2], g.stream);
+    ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr), "walk pairs");
+    if (g.timing) cudaEventRecord(g.ev[3], g.stream);
+    ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
+    ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
+    if (g.timing) cudaEventRecord(g.ev[4], g.stream);
+    if (k > 0) {
+        int32_t* ids = ids_dev;
+        double* vals = vals_dev;
+        if (!ids) {  // host outputs: stage behind the top-k workspace
+            char* stage = (char*)g.topk_ws + topk_stage_offset(g.n);
+            vals = (double*)stage;
+            ids = (int32_t*)(stage + sizeof(double) * kTopkMax);
+        }
+        ESIM_CUDA_TRY(launch_topk(g, s, g.exclude_source ? u : -1, k, ids, vals, g.topk_ws), "top-k");
+        if (ids_host) {
+            ESIM_CUDA_TRY(cudaMemcpyAsync(ids_host, ids, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, g.stream),
+                          "copy ids");
+            ESIM_CUDA_TRY(cudaMemcpyAsync(vals_host, vals, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, g.stream),
+                          "copy scores");
+        }
+    }
+    if (g.timing) cudaEventRecord(g.ev[5], g.stream);
+    if (s_host)
+        ESIM_CUDA_TRY(cudaMemcpyAsync(s_host, s, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
+                      "copy scores");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(g.status_host, g.status, sizeof(Status), cudaMemcpyDeviceToHost, g.stream),
+                  "copy status");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "query");
+    const Status hs = *g.status_host;
+    g.last_L = L;
+    // kernels launched: forward init + per level (rows [+ long rows]), 3 allocation
+    // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
+    g.last_launches = (1 + L * (1 + (g.out.nlong > 0 ? 1 : 0))) + 3 + 1 + 1 +
+                      (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0);
+    g.last_R_b = R_b;
+    g.last_kappa = kappa;
+    g.last_norm2 = hs.pi_norm2;
+    g.last_sum_R = hs.sum_R;
+    g.last_steps = hs.pair_steps;
+    for (float& x : g.last_ms) x = 0.f;
+    if (g.timing) {
+        for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
+        cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
+    }
+    if (hs.err & kErrBudget)
+        return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
+    if (hs.err & kErrTimeout) return fail(ESIM_ETIMEOUT, "device wait timed out");
+    return ESIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* esim_version(void) { return "exactsim-gb300 0.1 (sm_103a)"; }
+
+const char* esim_last_error(void) { return t_err.c_str(); }
+
+int32_t esim_levels(double c, double eps) {
+    if (!valid_c_eps(c, eps)) return -1;
+    return (int32_t)ceil(log(2.0 / eps) / log(1.0 / c));
+}
+
+double esim_sample_base(int64_t n, double c, double eps, double kappa) {
+    if (n < 1 || !valid_c_eps(c, eps)) return -1.0;
+    if (kappa <= 0.0) {
+        const double a = 1.0 - sqrt(c);
+        kappa = 6.0 / (a * a * a * a);
+    }
+    return kappa * log((double)n) / (eps * eps);
+}
+
+uint32_t esim_walk_threshold(double c) { return walk_threshold(c); }
+
+esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* in_col, esim_graph** out) {
+    if (!out) return fail(ESIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(ESIM_EINVAL, "need 1 <= n < 2^31");
+    if (!in_rowptr) return fail(ESIM_EINVAL, "in_rowptr is NULL");
+    if (in_rowptr[0] != 0) return fail(ESIM_EINVAL, "in_rowptr[0] must be 0");
+    for (int64_t j = 0; j < n; ++j)
+        if (in_rowptr[j + 1] < in_rowptr[j]) return fail(ESIM_EINVAL, "in_rowptr is not non-decreasing");
+    const int64_t m = in_rowptr[n];
+    if (m >= ((int64_t)1 << 32) - 4096) return fail(ESIM_EINVAL, "need m < 2^32 - 4096");
+    if (m > 0 && !in_col) return fail(ESIM_EINVAL, "in_col is NULL");
+    for (int64_t p = 0; p < m; ++p)
+        if (in_col[p] < 0 || (int64_t)in_col[p] >= n) return fail(ESIM_EINVAL, "in_col entry out of range");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice (no usable CUDA device)");
+    cudaDeviceProp prop;
+    ESIM_CUDA_TRY(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+
+    esim_graph* h = new (std::nothrow) esim_graph();
+    if (!h) return fail(ESIM_ENOMEM, "host allocation");
+    Graph& g = h->g;
+    g.device = dev;
+    g.sm_count = prop.multiProcessorCount;
+    g.n = n;
+    g.m = m;
+
+    // host: 32-bit in-CSR, and the out-CSR by a stable counting sort (rows of the
+    // out-CSR list targets j in increasing order)
+    std::vector<uint32_t> in_rp((size_t)n + 1), out_rp((size_t)n + 1, 0);
+    for (int64_t j = 0; j <= n; ++j) in_rp[j] = (uint32_t)in_rowptr[j];
+    std::vector<int32_t> in_c(in_col, in_col + m), out_c((size_t)m);
+    for (int64_t p = 0; p < m; ++p) out_rp[(size_t)in_col[p] + 1]++;
+    for (int64_t i = 0; i < n; ++i) out_rp[i + 1] += out_rp[i];
+    {
+        std::vector<uint32_t> cur(out_rp.begin(), out_rp.end() - 1);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t p = in_rowptr[j]; p < in_rowptr[j + 1]; ++p) out_c[cur[in_col[p]]++] = (int32_t)j;
+    }
+    esim_status st = upload_csr(n, in_rp, in_c, g.in);
+    if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out);
+    if (st != ESIM_OK) {
+        release(g);
+        delete h;
+        return st;
+    }
+    const int64_t nb = allocate_blocks(n);
+    const size_t npart = (size_t)std::max<int64_t>(1, std::max(g.in.nseg, g.out.nseg));
+    bool ok = dev_alloc(&g.status, 1) == cudaSuccess && cudaMallocHost((void**)&g.status_host, sizeof(Status)) == cudaSuccess &&
+              dev_alloc(&g.partial, npart) == cudaSuccess && dev_alloc(&g.scan_part, (size_t)nb) == cudaSuccess &&
+              dev_alloc(&g.norm_part, 2 * (size_t)nb) == cudaSuccess &&
+              cudaMalloc(&g.topk_ws, topk_stage_offset(n) + (sizeof(double) + sizeof(int32_t)) * kTopkMax) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(g);
+        delete h;
+        return fail(ESIM_ENOMEM, "device allocation for graph workspace");
+    }
+    g.scan_blocks = nb;
+    g.stream = g.own_stream;
+    cudaMemset(g.status, 0, sizeof(Status));
+    *out = h;
+    return ESIM_OK;
+}
+
+void esim_free_graph(esim_graph* h) {
+    if (!h) return;
+    release(h->g);
+    delete h;
+}
+
+int64_t esim_num_nodes(const esim_graph* h) { return h ? h->g.n : -1; }
+int64_t esim_num_edges(const esim_graph* h) { return h ? h->g.m : -1; }
+
+esim_status esim_set_stream(esim_graph* h, void* stream) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    h->g.stream = stream ? (cudaStream_t)stream : h->g.own_stream;
+    return ESIM_OK;
+}
+
+esim_status esim_set_option(esim_graph* h, const char* key, double value) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!key) return fail(ESIM_EINVAL, "option key is NULL");
+    Graph& g = h->g;
+    const std::string k(key);
+    if (k == "kappa") {
+        if (!(value == value)) return fail(ESIM_EINVAL, "kappa is NaN");
+        g.kappa = value;
+    } else if (k == "alloc") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "alloc must be 0 (pi^2) or 1 (basic)");
+        g.alloc_mode = (int)value;
+    } else if (k == "exclude_source") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "exclude_source must be 0 or 1");
+        g.exclude_source = (int)value;
+    } else if (k == "pair_budget") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "pair_budget must be >= 0");
+        g.pair_budget = value;
+    } else if (k == "timing") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "timing must be 0 or 1");
+        g.timing = (int)value;
+    } else {
+        return fail(ESIM_EINVAL, "unknown option '" + k + "'");
+    }
+    return ESIM_OK;
+}
+
+esim_status esim_get_option(const esim_graph* h, const char* key, double* value) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!key || !value) return fail(ESIM_EINVAL, "NULL argument");
+    const Graph& g = h->g;
+    const std::string k(key);
+    if (k == "kappa") *value = g.kappa;
+    else if (k == "alloc") *value = g.alloc_mode;
+    else if (k == "exclude_source") *value = g.exclude_source;
+    else if (k == "pair_budget") *value = g.pair_budget;
+    else if (k == "timing") *value = g.timing;
+    else return fail(ESIM_EINVAL, "unknown option '" + k + "'");
+    return ESIM_OK;
+}
+
+esim_status esim_query(esim_graph* h, int64_t u, double c, double eps, uint64_t seed, double* s_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!s_out) return fail(ESIM_EINVAL, "s_out is NULL");
+    return run_query(h->g, u, c, eps, seed, nullptr, 0, nullptr, nullptr, s_out, nullptr, nullptr);
+}
+
+esim_status esim_query_device(esim_graph* h, int64_t u, double c, double eps, uint64_t seed, double* s_dev) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!s_dev) return fail(ESIM_EINVAL, "s_dev is NULL");
+    return run_query(h->g, u, c, eps, seed, s_dev, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+esim_status esim_topk(esim_graph* h, int64_t u, double c, double eps, uint64_t seed, int32_t k, int32_t* ids_out,
+                      double* scores_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
+    if (!ids_out || !scores_out) return fail(ESIM_EINVAL, "NULL output");
+    return run_query(h->g, u, c, eps, seed, nullptr, k, nullptr, nullptr, nullptr, ids_out, scores_out);
+}
+
+esim_status esim_topk_device(esim_graph* h, int64_t u, double c, double eps, uint64_t seed, int32_t k,
+                             int32_t* ids_dev, double* scores_dev) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
+    if (!ids_dev || !scores_dev) return fail(ESIM_EINVAL, "NULL output");
+    return run_query(h->g, u, c, eps, seed, nullptr, k, ids_dev, scores_dev, nullptr, nullptr, nullptr);
+}
+
+esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!out) return fail(ESIM_EINVAL, "out is NULL");
+    const Graph& g = h->g;
+    memset(out, 0, sizeof(*out));
+    out->L = g.last_L;
+    out->launches = g.last_launches;
+    out->R_b = g.last_R_b;
+    out->kappa = g.last_kappa;
+    out->pi_norm2 = g.last_norm2;
+    out->sum_R = g.last_sum_R;
+    out->pair_steps = g.last_steps;
+    out->ms_forward = g.last_ms[0];
+    out->ms_allocate = g.last_ms[1];
+    out->ms_sample = g.last_ms[2];
+    out->ms_reverse = g.last_ms[3];
+    out->ms_topk = g.last_ms[4];
+    out->ms_total = g.last_ms[5];
+    return ESIM_OK;
+}
+
+esim_status esim_forward(esim_graph* h, int64_t u, double c, int32_t L, double* hist) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (u < 0 || u >= g.n) return fail(ESIM_EINVAL, "source node out of range");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (!hist) return fail(ESIM_EINVAL, "hist is NULL");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    Ws w;
+    esim_status st = ensure_ws(g, 0, w);
+    if (st != ESIM_OK) return st;
+    ESIM_CUDA_TRY(launch_forward(g, u, c, L, hist, w.xa, w.xb), "forward sweeps");
+    return ESIM_OK;
+}
+
+esim_status esim_allocate(esim_graph* h, const double* hist, int32_t L, double R_b, int32_t mode, double* pi_out,
+                          uint64_t* R_out, uint64_t* off) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!hist || !R_out || !off) return fail(ESIM_EINVAL, "NULL argument");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (mode != 0 && mode != 1) return fail(ESIM_EINVAL, "mode must be 0 or 1");
+    if (!(R_b >= 0.0)) return fail(ESIM_EINVAL, "need R_b >= 0");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_allocate(g, hist, L, R_b, mode, pi_out, R_out, off), "allocation");
+    return ESIM_OK;
+}
+
+esim_status esim_sample(esim_graph* h, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
+                        uint64_t* pair_steps) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!off || !nonmeet) return fail(ESIM_EINVAL, "NULL argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_sample(g, off, c, seed, nonmeet, pair_steps), "walk pairs");
+    return ESIM_OK;
+}
+
+esim_status esim_dhat(esim_graph* h, const uint64_t* nonmeet, const uint64_t* off, double* dhat) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!nonmeet || !off || !dhat) return fail(ESIM_EINVAL, "NULL argument");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_dhat(g, nonmeet, off, dhat), "dhat");
+    return ESIM_OK;
+}
+
+esim_status esim_reverse(esim_graph* h, const double* hist, int32_t L, double c, const double* dhat, double* s_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!hist || !dhat || !s_out) return fail(ESIM_EINVAL, "NULL argument");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    Ws w;
+    esim_status st = ensure_ws(g, 0, w);
+    if (st != ESIM_OK) return st;
+    ESIM_CUDA_TRY(launch_reverse(g, hist, L, c, dhat, s_out, w.xa, w.xb), "reverse sweeps");
+    return ESIM_OK;
+}
+
+esim_status esim_select_topk(esim_graph* h, const double* scores, int64_t exclude, int32_t k, int32_t* ids_out,
+                             double* vals_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!scores || !ids_out || !vals_out) return fail(ESIM_EINVAL, "NULL argument");
+    if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
+    if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
+    if (exclude < -1 || exclude >= g.n) return fail(ESIM_EINVAL, "exclude out of range");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_topk(g, scores, exclude, k, ids_out, vals_out, g.topk_ws), "top-k");
+    return ESIM_OK;
+}
+
+esim_status esim_sync(esim_graph* h) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(g.status_host, g.status, sizeof(Status), cudaMemcpyDeviceToHost, g.stream),
+                  "copy status");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "stream synchronize");
+    const int err = g.status_host->err;
+    ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "stream synchronize");
+    if (err & kErrBudget) return fail(ESIM_EBUDGET, "pair budget exceeded or R(k) overflow");
+    if (err & kErrTimeout) return fail(ESIM_ETIMEOUT, "device wait timed out");
+    return ESIM_OK;
+}
+
+}  // extern "C"

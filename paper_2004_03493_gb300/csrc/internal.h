@@ -1,0 +1,103 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (that is include/exactsim.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace esim {
+
+// Device-side error bits, accumulated in Status::err.
+enum : int {
+    kErrBudget = 1,   // sum of R(k) above the pair budget, or R(k) overflow
+    kErrTimeout = 2,  // a bounded wait ran out
+};
+
+// Per-query device status block (one per graph handle).
+struct Status {
+    unsigned long long sum_R;
+    unsigned long long pair_steps;
+    double pi_norm2;
+    int err;
+    int pad;
+};
+
+// One segment of a long CSR row: entries [beg, end) of row `row`.
+struct Segment {
+    int32_t row;
+    uint32_t beg;
+    uint32_t end;
+    uint32_t first;  // index of the row's first segment (rows own consecutive segments)
+};
+
+// A CSR resident on the device, with the row-split table for rows whose length
+// is at least `long_min`.  Long rows are cut into segments of `seg_len` entries.
+struct DevCsr {
+    uint32_t* rp = nullptr;      // n+1
+    int32_t* col = nullptr;      // m
+    Segment* seg = nullptr;      // nseg
+    int32_t* long_rows = nullptr;  // nlong row ids
+    int32_t* long_first = nullptr; // nlong+1: first segment of each long row
+    int64_t nseg = 0;
+    int64_t nlong = 0;
+    uint32_t long_min = 0;
+    int group = 8;               // threads per short row
+};
+
+struct Graph {
+    int device = 0;
+    int sm_count = 0;
+    int64_t n = 0, m = 0;
+    DevCsr in;    // rows = nodes, entries = in-neighbours (walks, reverse sweep)
+    DevCsr out;   // rows = nodes, entries = out-neighbours (forward sweep)
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    // options
+    double kappa = 0.0;
+    int alloc_mode = 0;
+    int exclude_source = 1;
+    double pair_budget = 1e15;
+    int timing = 0;
+    // workspace
+    Status* status = nullptr;     // device
+    Status* status_host = nullptr; // pinned host copy
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* partial = nullptr;    // long-row partial sums (max nseg of in/out)
+    unsigned long long* scan_part = nullptr;  // scan partials
+    double* norm_part = nullptr;
+    int64_t scan_blocks = 0;
+    void* topk_ws = nullptr;
+    // timing events
+    cudaEvent_t ev[8] = {};
+    // last stats
+    int32_t last_L = 0;
+    int32_t last_launches = 0;
+    double last_R_b = 0, last_kappa = 0, last_norm2 = 0;
+    unsigned long long last_sum_R = 0, last_steps = 0;
+    float last_ms[6] = {};
+};
+
+// sweep.cu
+cudaError_t launch_forward(const Graph& g, int64_t u, double c, int32_t L, double* hist, double* xa, double* xb);
+cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double c, const double* dhat, double* s_out,
+                           double* sa, double* sb);
+
+// sample.cu
+int64_t allocate_blocks(int64_t n);
+cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, double R_b, int mode, double* pi_out,
+                            uint64_t* R_out, uint64_t* off);
+cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
+                          uint64_t* pair_steps);
+cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
+uint32_t walk_threshold(double c);
+
+// topk.cu
+constexpr int kTopkMax = 4096;
+size_t topk_workspace_bytes(int64_t n);
+cudaError_t launch_topk(const Graph& g, const double* scores, int64_t exclude, int32_t k, int32_t* ids_out,
+                        double* vals_out, void* ws);
+
+}  // namespace esim

@@ -1,0 +1,304 @@
+// Sample allocation, walk-pair sampler and diagonal estimate.
+//
+//   allocation (Lemma 4, "Sampling according to pi(k)^2"; Algorithm 1 for the
+//   basic form): pi(k) = sum_l pi^l(k); R(k) = ceil(R_b * pi(k)^2) or
+//   ceil(R_b * pi(k)); off = exclusive prefix sum of R (uint64).
+//
+//   sampler (Algorithm 2, walk semantics of Eq. scwwalk): R(k) pairs of
+//   independent sqrt(c)-walks from each node k; nonmeet(k) counts the pairs that
+//   never visit the same node at the same step.  Pair r of node k draws its
+//   randomness from Philox-4x32-10 with counter (r_lo, r_hi, k, t) at step t, so
+//   the result is independent of how pairs are spread over threads.
+//
+//   D^(k) = nonmeet(k) / R(k) (Algorithm 2).
+#include "common.cuh"
+#include "internal.h"
+#include "philox.cuh"
+
+#include <math.h>
+
+namespace esim {
+
+constexpr int kAllocItems = 8;
+constexpr int64_t kAllocTile = (int64_t)kBlock * kAllocItems;
+constexpr int kScanThreads = 1024;
+constexpr uint32_t kWalkMaxSteps = 65536;
+
+int64_t allocate_blocks(int64_t n) { return (n + kAllocTile - 1) / kAllocTile; }
+
+uint32_t walk_threshold(double c) {
+    double v = floor(sqrt(c) * 4294967296.0);
+    if (v >= 4294967295.0) return 0xFFFFFFFFu;
+    if (v <= 0.0) return 0u;
+    return (uint32_t)v;
+}
+
+// Block-wide exclusive scan of one uint64 per thread; *total gets the block sum.
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* smem,
+                                                                   unsigned long long* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = lane < nw ? smem[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        smem[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long warp_off = wid ? smem[wid - 1] : 0ull;
+    *total = smem[nw - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+// pi(k), R(k) per node; per-tile sums of R (exact and in double) and of pi^2.
+__global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const double* __restrict__ hist, int32_t L,
+                                                              double R_b, int mode, double* __restrict__ pi_out,
+                                                              uint64_t* __restrict__ R_out,
+                                                              unsigned long long* __restrict__ part_R,
+                                                              double* __restrict__ part_norm,
+                                                              double* __restrict__ part_Rd, Status* __restrict__ st) {
+    __shared__ unsigned long long red_u[kBlock / 32];
+    __shared__ double red_d[kBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * kAllocTile;
+    unsigned long long sum_r = 0;
+    double norm = 0.0, sum_rd = 0.0;
+    bool overflow = false;
+#pragma unroll 1
+    for (int i = 0; i < kAllocItems; ++i) {
+        const int64_t k = base + (int64_t)i * kBlock + threadIdx.x;
+        if (k >= n) break;
+        double p = 0.0;
+        for (int32_t l = 0; l <= L; ++l) p += hist[(size_t)l * (size_t)n + (size_t)k];
+        if (pi_out) pi_out[k] = p;
+        const double v = mode == 0 ? R_b * (p * p) : R_b * p;
+        unsigned long long r = 0;
+        if (v >= 9.2e18 || v != v) {
+            overflow = true;
+        } else {
+            r = (unsigned long long)ceil(v);
+        }
+        R_out[k] = r;
+        sum_r += r;
+        sum_rd += (double)r;
+        norm += p * p;
+    }
+    if (overflow) atomicOr(&st->err, kErrBudget);
+    sum_r = block_sum(sum_r, red_u);
+    norm = block_sum(norm, red_d);
+    sum_rd = block_sum(sum_rd, red_d);
+    if (threadIdx.x == 0) {
+        part_R[blockIdx.x] = sum_r;
+        part_norm[blockIdx.x] = norm;
+        part_Rd[blockIdx.x] = sum_rd;
+    }
+}
+
+// One block: exclusive scan of the tile sums (in place), totals into the status
+// block and off[n]; the budget check.
+__global__ void __launch_bounds__(kScanThreads) alloc_partials_kernel(int64_t nblocks, unsigned long long* part_R,
+                                                                      const double* __restrict__ part_norm,
+                                                                      const double* __restrict__ part_Rd,
+                                                                      double budget, uint64_t* __restrict__ off_n,
+                                                                      Status* __restrict__ st) {
+    __shared__ unsigned long long su[32];
+    __shared__ double sd[32];
+    const int64_t per = (nblocks + kScanThreads - 1) / kScanThreads;
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    const int64_t b1 = b0 + per < nblocks ? b0 + per : nblocks;
+    unsigned long long local = 0;
+    double nrm = 0.0, rd = 0.0;
+    for (int64_t b = b0; b < b1; ++b) {
+        local += part_R[b];
+        nrm += part_norm[b];
+        rd += part_Rd[b];
+    }
+    unsigned long long total;
+    unsigned long long run = block_exclusive_scan(local, su, &total);
+    for (int64_t b = b0; b < b1; ++b) {
+        const unsigned long long v = part_R[b];
+        part_R[b] = run;
+        run += v;
+    }
+    nrm = block_sum(nrm, sd);
+    rd = block_sum(rd, sd);
+    if (threadIdx.x == 0) {
+        *off_n = total;
+        st->sum_R = total;
+        st->pi_norm2 = nrm;
+        if (rd > budget || rd >= 1.8e19) atomicOr(&st->err, kErrBudget);
+    }
+}
+
+// off[k] = tile offset + exclusive prefix of R within the tile.
+__global__ void __launch_bounds__(kBlock) alloc_scan_kernel(int64_t n, const uint64_t* __restrict__ R,
+                                                            const unsigned long long* __restrict__ tile_off,
+                                                            uint64_t* __restrict__ off) {
+    __shared__ unsigned long long su[32];
+    const int64_t base = (int64_t)blockIdx.x * kAllocTile + (int64_t)threadIdx.x * kAllocItems;
+    unsigned long long v[kAllocItems];
+    unsigned long long local = 0;
+#pragma unroll
+    for (int i = 0; i < kAllocItems; ++i) {
+        const int64_t k = base + i;
+        v[i] = k < n ? R[k] : 0ull;
+        local += v[i];
+    }
+    unsigned long long total;
+    unsigned long long run = tile_off[blockIdx.x] + block_exclusive_scan(local, su, &total);
+#pragma unroll
+    for (int i = 0; i < kAllocItems; ++i) {
+        const int64_t k = base + i;
+        if (k < n) off[k] = run;
+        run += v[i];
+    }
+}
+
+cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, double R_b, int mode, double* pi_out,
+                            uint64_t* R_out, uint64_t* off) {
+    const int64_t nb = allocate_blocks(g.n);
+    unsigned long long* part_R = g.scan_part;
+    double* part_norm = g.norm_part;
+    double* part_Rd = g.norm_part + nb;
+    alloc_reduce_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, hist, L, R_b, mode, pi_out, R_out, part_R,
+                                                               part_norm, part_Rd, g.status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    alloc_partials_kernel<<<1, kScanThreads, 0, g.stream>>>(nb, part_R, part_norm, part_Rd, g.pair_budget,
+                                                            off + g.n, g.status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    alloc_scan_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, R_out, part_R, off);
+    return cudaGetLastError();
+}
+
+// Persistent walk-pair sampler.  Thread t takes a contiguous run of global pair
+// indices (about total / #threads of them) and walks them one step per loop
+// iteration, so a lane whose pair ended starts its next pair at once.  Counts
+// are kept in a register while the node does not change and flushed with one
+// atomic add per (thread, node).
+__global__ void __launch_bounds__(kBlock) sample_pairs_kernel(int64_t n, const uint32_t* __restrict__ rp,
+                                                              const int32_t* __restrict__ col,
+                                                              const uint64_t* __restrict__ off, uint32_t T,
+                                                              uint32_t key0, uint32_t key1, double budget,
+                                                              unsigned long long* __restrict__ nonmeet,
+                                                              unsigned long long* __restrict__ steps_out,
+                                                              Status* __restrict__ st) {
+    __shared__ unsigned long long red[kBlock / 32];
+    const unsigned long long total = off[n];
+    if ((double)total > budget || (st->err & kErrBudget)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->err, kErrBudget);
+        return;
+    }
+    const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long per = total / nthreads, rem = total % nthreads;
+    unsigned long long g = tid * per + (tid < rem ? tid : rem);
+    const unsigned long long end = g + per + (tid < rem ? 1ull : 0ull);
+    unsigned long long steps = 0;
+    if (g < end) {
+        // node of pair g: off[k] <= g < off[k+1]
+        int64_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= g) lo = mid; else hi = mid;
+        }
+        uint32_t k = (uint32_t)lo;
+        unsigned long long kend = off[k + 1];
+        unsigned long long r = g - off[k];
+        uint32_t xa = k, xb = k, t = 0;
+        unsigned long long cnt = 0;
+        for (;;) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), k, t), key0, key1);
+            ++steps;
+            bool ended = true, met = false;
+            if (w.x < T && w.z < T) {
+                const uint32_t ba = __ldg(rp + xa), da = __ldg(rp + xa + 1) - ba;
+                const uint32_t bb = __ldg(rp + xb), db = __ldg(rp + xb + 1) - bb;
+                if (da != 0u && db != 0u) {
+                    const uint32_t na = (uint32_t)__ldg(col + ba + __umulhi(w.y, da));
+                    const uint32_t nb = (uint32_t)__ldg(col + bb + __umulhi(w.w, db));
+                    if (na == nb) {
+                        met = true;
+                    } else if (t + 1u < kWalkMaxSteps) {
+                        xa = na;
+                        xb = nb;
+                        ++t;
+                        ended = false;
+                    }
+                }
+            }
+            if (ended) {
+                cnt += met ? 0ull : 1ull;
+                ++g;
+                ++r;
+                t = 0;
+                if (g == end) break;
+                if (g == kend) {
+                    if (cnt) atomicAdd(nonmeet + k, cnt);
+                    cnt = 0;
+                    while (off[k + 1] <= g) ++k;
+                    kend = off[k + 1];
+                    r = 0;
+                }
+                xa = k;
+                xb = k;
+            }
+        }
+        if (cnt) atomicAdd(nonmeet + k, cnt);
+    }
+    steps = block_sum(steps, red);
+    if (threadIdx.x == 0 && steps) atomicAdd(steps_out, steps);
+}
+
+__global__ void dhat_kernel(int64_t n, const uint64_t* __restrict__ nonmeet, const uint64_t* __restrict__ off,
+                            double* __restrict__ dhat) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t R = off[k + 1] - off[k];
+        dhat[k] = R ? (double)nonmeet[k] / (double)R : 0.0;
+    }
+}
+
+static int g_sample_blocks_per_sm = 0;
+
+cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
+                          uint64_t* pair_steps) {
+    cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)g.n, g.stream);
+    if (e != cudaSuccess) return e;
+    unsigned long long* steps = pair_steps ? (unsigned long long*)pair_steps : &g.status->pair_steps;
+    if (pair_steps) {
+        e = cudaMemsetAsync(pair_steps, 0, sizeof(uint64_t), g.stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (g_sample_blocks_per_sm == 0) {
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sample_pairs_kernel, kBlock, 0);
+        if (e != cudaSuccess) return e;
+        g_sample_blocks_per_sm = b > 0 ? b : 1;
+    }
+    const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
+    sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, g.in.rp, g.in.col, off, walk_threshold(c),
+                                                         (uint32_t)seed, (uint32_t)(seed >> 32), g.pair_budget,
+                                                         (unsigned long long*)nonmeet, steps, g.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat) {
+    int64_t b = (g.n + kBlock - 1) / kBlock;
+    if (b > (int64_t)g.sm_count * 8) b = (int64_t)g.sm_count * 8;
+    dhat_kernel<<<(unsigned)(b < 1 ? 1 : b), kBlock, 0, g.stream>>>(g.n, nonmeet, off, dhat);
+    return cudaGetLastError();
+}
+
+}  // namespace esim

@@ -1,0 +1,95 @@
+"""The C ABI library loads and exports every entry point of include/exactsim.h.
+
+Runs without a GPU: only host-side entry points (parameters, validation) are
+called.  Calls that need a device are made in the ``gpu`` tests.
+"""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import linearization as lin
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2004_03493_gb300 import buildlib as build_mod
+    build_mod.build()
+    from paper_2004_03493_gb300 import _native
+    return _native
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "exactsim.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(esim_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(native):
+    names = _declared_functions()
+    assert len(names) >= 20
+    h = ctypes.CDLL(native.LIB_PATH)
+    for name in names:
+        assert hasattr(h, name), name
+        assert name in native.SIGNATURES, name
+    assert set(native.SIGNATURES) == set(names)
+
+
+def test_version(native):
+    assert "sm_103a" in native.esim_version()
+
+
+@pytest.mark.parametrize("c,eps", [(0.6, 1e-4), (0.6, 1e-5), (0.6, 1e-6), (0.6, 1e-7), (0.8, 1e-3), (0.25, 0.5)])
+def test_levels_and_sample_base_match_oracle(native, c, eps):
+    assert native.esim_levels(c, eps) == lin.levels(c, eps)
+    for n in (2, 2000, 33554432):
+        assert native.esim_sample_base(n, c, eps, 0.0) == lin.sample_base(n, c, eps)
+        assert native.esim_sample_base(n, c, eps, 3.5) == lin.sample_base(n, c, eps, 3.5)
+
+
+def test_walk_threshold_matches_oracle(native):
+    for c in (0.6, 0.8, 0.25, 1e-9, 0.999999):
+        assert native.esim_walk_threshold(c) == lin.pair_threshold(c)
+
+
+def test_parameter_validation(native):
+    assert native.esim_levels(0.0, 1e-3) == -1
+    assert native.esim_levels(0.6, 1.0) == -1
+    assert native.esim_sample_base(0, 0.6, 1e-3, 0.0) == -1.0
+
+
+@pytest.mark.parametrize("case", ["rowptr0", "decreasing", "col_range", "negative_col", "n_zero"])
+def test_load_graph_rejects_bad_csr(native, case):
+    n, rp, col = synth.erdos_renyi(50, 200, seed=1)
+    rp = rp.copy()
+    col = col.copy()
+    if case == "rowptr0":
+        rp[0] = 1
+    elif case == "decreasing":
+        rp[10] = rp[11] + 1
+    elif case == "col_range":
+        col[5] = n
+    elif case == "negative_col":
+        col[5] = -1
+    elif case == "n_zero":
+        with pytest.raises(native.EsimError) as e:
+            native.esim_load_graph(0, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32))
+        assert e.value.status == -1
+        return
+    with pytest.raises(native.EsimError) as e:
+        native.esim_load_graph(n, rp, col)
+    assert e.value.status == -1  # ESIM_EINVAL, raised before any device work
+
+
+def test_null_handle_is_rejected(native):
+    out = np.empty(4)
+    with pytest.raises(native.EsimError) as e:
+        native.esim_query(None, 0, 0.6, 1e-3, 0, out)
+    assert e.value.status == -1
