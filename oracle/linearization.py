@@ -14,7 +14,8 @@ Notation follows Sec. 3.1: a = 1 - sqrt(c); P is the reverse transition matrix
                          from the exponential of the Bernstein inequality)
 * ``allocate``        -- R(k) = ceil(R_b pi(k)^2) (the pi^2 scheme of Lemma 4 with R
                          scaled by ||pi||^2, as in the proof of Lemma 4), or
-                         R(k) = ceil(R_b pi(k)) (Algorithm 1, "basic" allocation)
+                         R(k) = ceil(R_b pi(k)) (Algorithm 1, "basic" allocation);
+                         at least 1 wherever pi(k) > 0
 * ``dhat``            -- D^(k) = nonmeet(k) / R(k)                  (Algorithm 2)
 * ``reverse``         -- s^0 = D^ pi^L / a; s^l = sqrt(c) P^T s^{l-1} + D^ pi^{L-l} / a
                          (Algorithm 1, reverse loop; Eq. sL)
@@ -78,10 +79,12 @@ def ppr(H: np.ndarray) -> np.ndarray:
 
 
 def allocate(pi: np.ndarray, R_b: float, mode: str = "pi2") -> np.ndarray:
-    """Per-node pair counts R(k) (uint64).
+    """Per-node pair counts R(k) (uint64); every node with pi(k) > 0 gets at least one.
 
-    pi2:   R(k) = ceil(R_b * (pi(k) * pi(k)))
-    basic: R(k) = ceil(R_b * pi(k))
+    pi2:   R(k) = max(1, ceil(R_b * (pi(k) * pi(k))))   for pi(k) > 0
+    basic: R(k) = max(1, ceil(R_b * pi(k)))             for pi(k) > 0
+    R(k) = 0 where pi(k) = 0.  The ceiling of a positive number is already >= 1;
+    the floor of one only matters when R_b * pi(k)^2 underflows or R_b = 0 (n = 1).
     """
     pi = np.asarray(pi, dtype=np.float64)
     if mode == "pi2":
@@ -90,7 +93,9 @@ def allocate(pi: np.ndarray, R_b: float, mode: str = "pi2") -> np.ndarray:
         v = R_b * pi
     else:
         raise ValueError(mode)
-    return np.ceil(v).astype(np.uint64)
+    R = np.ceil(v).astype(np.uint64)
+    R[(pi > 0) & (R == 0)] = 1
+    return R
 
 
 def dhat(nonmeet: np.ndarray, R: np.ndarray) -> np.ndarray:

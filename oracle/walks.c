@@ -27,9 +27,17 @@
  *   T        = floor(sqrt(c) * 2^32)
  *   walk A moves iff w0 < T and din(xA) > 0; walk B moves iff w2 < T and din(xB) > 0
  *   if either does not move, the pair ends without meeting
- *   otherwise xA <- I(xA)[(w1 * din(xA)) >> 32], xB <- I(xB)[(w3 * din(xB)) >> 32]
+ *   otherwise xA <- I(xA)[pick(w1, din(xA), A)], xB <- I(xB)[pick(w3, din(xB), B)]
  *   if xA == xB the pair ends as a meeting; else t <- t + 1
  *   a pair that reaches t = 65536 steps ends without meeting (probability c^65536)
+ *
+ * pick(x, d, W) is an exactly uniform index in [0, d): Lemire's multiply-shift with
+ * rejection (D. Lemire, "Fast Random Integer Generation in an Interval", ACM TOMS
+ * 2019): with p = x * d (64 bits), accept p >> 32 unless low32(p) < (2^32 mod d);
+ * a rejected word is replaced by the next word of walk W's side stream, the words
+ * z0..z3 of Philox(counter (r_lo, r_hi, k, 2^31 | W 2^30 | j 2^16 | t)) for
+ * j = 0, 1, ..., W = 0 for walk A and 1 for walk B.  After 2^14 side blocks the
+ * last index is kept (probability below 2^-65536).
  */
 #include <math.h>
 #include <stdint.h>
@@ -83,12 +91,44 @@ uint32_t oracle_walk_threshold(double c) {
     return (uint32_t)v;
 }
 
-/* One walk pair; returns 1 if the walks never meet.  *steps counts Philox calls. */
+/* Exactly uniform index in [0, d) (Lemire's method, side stream on rejection). */
+static uint32_t pick(uint32_t x, uint32_t d, uint32_t rlo, uint32_t rhi, uint32_t k, uint32_t tag,
+                     uint32_t k0, uint32_t k1) {
+    uint64_t m = (uint64_t)x * (uint64_t)d;
+    uint32_t l = (uint32_t)m;
+    if (l < d) {
+        const uint32_t thr = (uint32_t)(0u - d) % d;
+        uint32_t j = 0, z[4];
+        int used = 4;
+        while (l < thr) {
+            if (used == 4) {
+                if (j == (1u << 14)) break;
+                uint32_t ctr[4] = {rlo, rhi, k, tag | (j << 16)};
+                philox4x32_10(ctr, k0, k1, z);
+                ++j;
+                used = 0;
+            }
+            x = z[used++];
+            m = (uint64_t)x * (uint64_t)d;
+            l = (uint32_t)m;
+        }
+    }
+    return (uint32_t)(m >> 32);
+}
+
+/* pick() for `count` words x[i] with one d (test hook for the rejection path). */
+void oracle_pick_many(int64_t count, const uint32_t* x, uint32_t d, uint64_t seed, uint32_t* out) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int64_t i = 0; i < count; ++i) out[i] = pick(x[i], d, (uint32_t)i, 0u, 0u, 0x80000000u, k0, k1);
+}
+
+/* One walk pair; returns 1 if the walks never meet.  *steps counts main-stream Philox calls. */
 static int walk_pair(const int64_t* rp, const int32_t* col, uint32_t k, uint64_t r,
                      uint32_t T, uint32_t k0, uint32_t k1, uint64_t* steps) {
     uint32_t xa = k, xb = k;
+    const uint32_t rlo = (uint32_t)r, rhi = (uint32_t)(r >> 32);
     for (uint32_t t = 0; t < WALK_T_MAX; ++t) {
-        uint32_t ctr[4] = {(uint32_t)r, (uint32_t)(r >> 32), k, t};
+        uint32_t ctr[4] = {rlo, rhi, k, t};
         uint32_t w[4];
         philox4x32_10(ctr, k0, k1, w);
         *steps += 1;
@@ -97,8 +137,10 @@ static int walk_pair(const int64_t* rp, const int32_t* col, uint32_t k, uint64_t
         int move_a = (w[0] < T) && (da > 0);
         int move_b = (w[2] < T) && (db > 0);
         if (!(move_a && move_b)) return 1;
-        uint32_t na = (uint32_t)col[rp[xa] + (int64_t)(((uint64_t)w[1] * da) >> 32)];
-        uint32_t nb = (uint32_t)col[rp[xb] + (int64_t)(((uint64_t)w[3] * db) >> 32)];
+        uint32_t ia = pick(w[1], (uint32_t)da, rlo, rhi, k, 0x80000000u | t, k0, k1);
+        uint32_t ib = pick(w[3], (uint32_t)db, rlo, rhi, k, 0xC0000000u | t, k0, k1);
+        uint32_t na = (uint32_t)col[rp[xa] + (int64_t)ia];
+        uint32_t nb = (uint32_t)col[rp[xb] + (int64_t)ib];
         if (na == nb) return 0;
         xa = na;
         xb = nb;

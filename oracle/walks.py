@@ -54,6 +54,9 @@ def _load():
             lib.oracle_walk_threshold.restype = ctypes.c_uint32
             lib.oracle_walk_threshold.argtypes = [ctypes.c_double]
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_pick_many.restype = None
+            lib.oracle_pick_many.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                             ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -63,6 +66,14 @@ def philox(counters: np.ndarray, seed: int) -> np.ndarray:
     ctr = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
     out = np.zeros_like(ctr)
     _load().oracle_philox_many(ctr.shape[0], ctr.ctypes.data, ctypes.c_uint64(seed), out.ctypes.data)
+    return out
+
+
+def pick(words: np.ndarray, d: int, seed: int = 0) -> np.ndarray:
+    """Uniform indices in [0, d) from 32-bit words (rejections redraw from the side stream)."""
+    x = np.ascontiguousarray(words, dtype=np.uint32)
+    out = np.zeros_like(x)
+    _load().oracle_pick_many(x.size, x.ctypes.data, d, ctypes.c_uint64(seed), out.ctypes.data)
     return out
 
 

@@ -10,16 +10,33 @@
 
 namespace esim {
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
-#pragma unroll
+// The ten round keys of one seed, computed once on the host and passed as a
+// kernel parameter, so each round reads its key from the constant bank instead
+// of holding twenty key registers per thread.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int i = 0; i < 10; ++i) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, x.x);
-        const uint32_t lo0 = 0xD2511F53u * x.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x.z);
-        const uint32_t lo1 = 0xCD9E8D57u * x.z;
-        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        K.k0[i] = k0;
+        K.k1[i] = k1;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const PhiloxKeys& K) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * x.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * x.z;
+        x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ K.k0[i], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ K.k1[i],
+                       (uint32_t)p0);
     }
     return x;
 }

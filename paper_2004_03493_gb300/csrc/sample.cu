@@ -2,13 +2,17 @@
 //
 //   allocation (Lemma 4, "Sampling according to pi(k)^2"; Algorithm 1 for the
 //   basic form): pi(k) = sum_l pi^l(k); R(k) = ceil(R_b * pi(k)^2) or
-//   ceil(R_b * pi(k)); off = exclusive prefix sum of R (uint64).
+//   ceil(R_b * pi(k)), at least 1 where pi(k) > 0; off = exclusive prefix sum
+//   of R (uint64).
 //
 //   sampler (Algorithm 2, walk semantics of Eq. scwwalk): R(k) pairs of
 //   independent sqrt(c)-walks from each node k; nonmeet(k) counts the pairs that
 //   never visit the same node at the same step.  Pair r of node k draws its
 //   randomness from Philox-4x32-10 with counter (r_lo, r_hi, k, t) at step t, so
-//   the result is independent of how pairs are spread over threads.
+//   the result is independent of how pairs are spread over threads.  In-neighbour
+//   choices are exactly uniform (Lemire's multiply-shift with rejection, ACM TOMS
+//   2019; rejected words are replaced from a side stream with counter
+//   (r_lo, r_hi, k, 2^31 | W 2^30 | j 2^16 | t), W = 0 for walk A, 1 for walk B).
 //
 //   D^(k) = nonmeet(k) / R(k) (Algorithm 2).
 #include "common.cuh"
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const d
             overflow = true;
         } else {
             r = (unsigned long long)ceil(v);
+            if (r == 0ull && p > 0.0) r = 1ull;  // every reached node gets a pair
         }
         R_out[k] = r;
         sum_r += r;
@@ -183,15 +188,46 @@ cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, doubl
     return cudaGetLastError();
 }
 
+// Exactly uniform index in [0, d) from word x (Lemire); rejections (probability
+// below d / 2^32) redraw from the walk's side stream.
+__device__ __forceinline__ uint32_t pick_redraw(uint32_t d, unsigned long long m, uint32_t rlo, uint32_t rhi, uint32_t k,
+                                             uint32_t tag, const PhiloxKeys& K) {
+    const uint32_t thr = (0u - d) % d;
+    uint32_t l = (uint32_t)m;
+    uint32_t j = 0;
+    int used = 4;
+    uint4 z = make_uint4(0, 0, 0, 0);
+    while (l < thr) {
+        if (used == 4) {
+            if (j == (1u << 14)) break;
+            z = philox4x32_10(make_uint4(rlo, rhi, k, tag | (j << 16)), K);
+            ++j;
+            used = 0;
+        }
+        const uint32_t x = used == 0 ? z.x : (used == 1 ? z.y : (used == 2 ? z.z : z.w));
+        ++used;
+        m = (unsigned long long)x * d;
+        l = (uint32_t)m;
+    }
+    return (uint32_t)(m >> 32);
+}
+
+__device__ __forceinline__ uint32_t pick(uint32_t x, uint32_t d, uint32_t rlo, uint32_t rhi, uint32_t k, uint32_t tag,
+                                         const PhiloxKeys& K) {
+    const unsigned long long m = (unsigned long long)x * d;
+    if (__builtin_expect((uint32_t)m < d, 0)) return pick_redraw(d, m, rlo, rhi, k, tag, K);
+    return (uint32_t)(m >> 32);
+}
+
 // Persistent walk-pair sampler.  Thread t takes a contiguous run of global pair
-// indices (about total / #threads of them) and walks them one step per loop
-// iteration, so a lane whose pair ended starts its next pair at once.  Counts
-// are kept in a register while the node does not change and flushed with one
-// atomic add per (thread, node).
-__global__ void __launch_bounds__(kBlock) sample_pairs_kernel(int64_t n, const uint32_t* __restrict__ rp,
+// indices (about total / #threads of them) and advances its current pair by one
+// step per loop iteration, so a lane whose pair ended starts its next pair at
+// once and lanes stay busy.  Counts are kept in a register while the node does
+// not change and flushed with one atomic add per (thread, node).
+__global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, const uint32_t* __restrict__ rp,
                                                               const int32_t* __restrict__ col,
                                                               const uint64_t* __restrict__ off, uint32_t T,
-                                                              uint32_t key0, uint32_t key1, double budget,
+                                                              const __grid_constant__ PhiloxKeys K, double budget,
                                                               unsigned long long* __restrict__ nonmeet,
                                                               unsigned long long* __restrict__ steps_out,
                                                               Status* __restrict__ st) {
@@ -204,57 +240,59 @@ __global__ void __launch_bounds__(kBlock) sample_pairs_kernel(int64_t n, const u
     const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long per = total / nthreads, rem = total % nthreads;
-    unsigned long long g = tid * per + (tid < rem ? tid : rem);
-    const unsigned long long end = g + per + (tid < rem ? 1ull : 0ull);
+    const unsigned long long g0 = tid * per + (tid < rem ? tid : rem);
+    unsigned long long left = per + (tid < rem ? 1ull : 0ull);  // pairs still to run
     unsigned long long steps = 0;
-    if (g < end) {
-        // node of pair g: off[k] <= g < off[k+1]
+    if (left) {
+        // node of pair g0: off[k] <= g0 < off[k+1]
         int64_t lo = 0, hi = n;
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
-            if (off[mid] <= g) lo = mid; else hi = mid;
+            if (__ldg(off + mid) <= g0) lo = mid; else hi = mid;
         }
         uint32_t k = (uint32_t)lo;
-        unsigned long long kend = off[k + 1];
-        unsigned long long r = g - off[k];
+        unsigned long long r = g0 - __ldg(off + k);             // pair index within node k
+        unsigned long long rk = __ldg(off + k + 1) - __ldg(off + k);  // R(k)
         uint32_t xa = k, xb = k, t = 0;
         unsigned long long cnt = 0;
         for (;;) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), k, t), key0, key1);
+            const uint32_t rlo = (uint32_t)r, rhi = (uint32_t)(r >> 32);
+            const uint4 w = philox4x32_10(make_uint4(rlo, rhi, k, t), K);
             ++steps;
-            bool ended = true, met = false;
-            if (w.x < T && w.z < T) {
+            bool cont = (w.x < T) & (w.z < T);
+            uint32_t na = 0, nb = 0;
+            if (cont) {
                 const uint32_t ba = __ldg(rp + xa), da = __ldg(rp + xa + 1) - ba;
                 const uint32_t bb = __ldg(rp + xb), db = __ldg(rp + xb + 1) - bb;
-                if (da != 0u && db != 0u) {
-                    const uint32_t na = (uint32_t)__ldg(col + ba + __umulhi(w.y, da));
-                    const uint32_t nb = (uint32_t)__ldg(col + bb + __umulhi(w.w, db));
-                    if (na == nb) {
-                        met = true;
-                    } else if (t + 1u < kWalkMaxSteps) {
-                        xa = na;
-                        xb = nb;
-                        ++t;
-                        ended = false;
-                    }
+                cont = (da != 0u) & (db != 0u);
+                if (cont) {
+                    na = (uint32_t)__ldg(col + ba + pick(w.y, da, rlo, rhi, k, 0x80000000u | t, K));
+                    nb = (uint32_t)__ldg(col + bb + pick(w.w, db, rlo, rhi, k, 0xC0000000u | t, K));
                 }
             }
-            if (ended) {
-                cnt += met ? 0ull : 1ull;
-                ++g;
-                ++r;
-                t = 0;
-                if (g == end) break;
-                if (g == kend) {
-                    if (cnt) atomicAdd(nonmeet + k, cnt);
-                    cnt = 0;
-                    while (off[k + 1] <= g) ++k;
-                    kend = off[k + 1];
-                    r = 0;
-                }
-                xa = k;
-                xb = k;
+            const bool meet = cont & (na == nb);
+            const bool ended = !cont | meet | (t + 1u >= kWalkMaxSteps);
+            if (!ended) {
+                xa = na;
+                xb = nb;
+                ++t;
+                continue;
             }
+            cnt += meet ? 0ull : 1ull;
+            if (--left == 0) break;
+            t = 0;
+            if (++r == rk) {  // node k is done: flush and move to the next node with pairs
+                if (cnt) atomicAdd(nonmeet + k, cnt);
+                cnt = 0;
+                const unsigned long long g = g0 + (per + (tid < rem ? 1ull : 0ull)) - left;
+                do {
+                    ++k;
+                } while (__ldg(off + k + 1) <= g);
+                r = 0;
+                rk = __ldg(off + k + 1) - __ldg(off + k);
+            }
+            xa = k;
+            xb = k;
         }
         if (cnt) atomicAdd(nonmeet + k, cnt);
     }
@@ -289,7 +327,7 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
     }
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
     sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, g.in.rp, g.in.col, off, walk_threshold(c),
-                                                         (uint32_t)seed, (uint32_t)(seed >> 32), g.pair_budget,
+                                                         philox_keys(seed), g.pair_budget,
                                                          (unsigned long long*)nonmeet, steps, g.status);
     return cudaGetLastError();
 }

@@ -58,6 +58,9 @@ def test_allocate_hand_values():
     assert lin.allocate(pi, 10.0, "basic").tolist() == [5, 3, 0, 1]
     # exact integers stay
     assert lin.allocate(np.array([0.5]), 4.0, "pi2").tolist() == [1]
+    # every reached node gets a pair, even when R_b = 0 (n = 1: ln n = 0) or pi^2 underflows
+    assert lin.allocate(np.array([0.3, 0.0]), 0.0, "pi2").tolist() == [1, 0]
+    assert lin.allocate(np.array([1e-200]), 1e12, "pi2").tolist() == [1]
 
 
 def test_dhat_ratio():

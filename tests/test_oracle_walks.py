@@ -130,3 +130,25 @@ def test_thread_count_independence_and_seed_dependence(oracle_walks):
     d, _ = oracle_walks.walk_pairs(n, rp, col, R, C, seed=43, threads=4)
     assert not np.array_equal(a, d)
     assert np.all(a <= R)
+
+
+def test_pick_is_exactly_uniform_with_rejection(oracle_walks):
+    # d = 3 * 2^30: 2^32 mod d = 2^30, so a quarter of the words are rejected and redrawn
+    d = 3 * 2 ** 30
+    rng = np.random.default_rng(2)
+    x = rng.integers(0, 2 ** 32, size=60000, dtype=np.uint64).astype(np.uint32)
+    got = oracle_walks.pick(x, d, seed=9).astype(np.uint64)
+    assert got.max() < d
+    plain = (x.astype(np.uint64) * d) >> 32
+    low = (x.astype(np.uint64) * d) & 0xFFFFFFFF
+    accepted = low >= 2 ** 30
+    assert np.array_equal(got[accepted], plain[accepted])       # accepted words keep multiply-shift
+    assert 0.23 < 1 - accepted.mean() < 0.27                     # rejection rate 1/4
+    # multiply-shift alone maps x to floor(3x/4): indices i = 0 mod 3 receive two words of
+    # every four, so they would carry probability 1/2 instead of 1/3
+    frac_plain = float(np.mean(plain % 3 == 0))
+    frac_got = float(np.mean(got % 3 == 0))
+    assert abs(frac_plain - 0.5) < 0.01
+    assert abs(frac_got - 1.0 / 3.0) < 0.01
+    # small d: no word is ever rejected
+    assert np.array_equal(oracle_walks.pick(x, 7), ((x.astype(np.uint64) * 7) >> 32).astype(np.uint32))
