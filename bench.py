@@ -42,6 +42,12 @@ WORKLOADS = {
                    source_seed=0, k=50),
 }
 METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6, top-50)"
+# integer instructions of one pair-step at the issue limit: Philox-4x32-10 = 10 rounds x (2 wide
+# multiplies + 2 three-input XORs); step logic = 2 threshold compares, 2 multiply-shift picks,
+# 2 row loads, 2 neighbour loads
+INSTR_PER_PAIR_STEP = 48.0
+# DRAM bytes per sampler launch from the ncu capture named in profiles/ (None once the kernel changes)
+KERNEL_TRAFFIC = {"sample_pairs_kernel": None}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -290,21 +296,33 @@ def main():
     value = queries / (total_ms / 1000.0)
 
     # roofline of the dominant kernel (the walk-pair sampler): pair-steps per second against
-    # the integer-issue limit of the Philox-4x32-10 block
+    # the integer-issue limit of one Philox-4x32-10 block plus the step logic
     steps_total = sum(s["pair_steps"] for s in stats)
     ms_sample = sum(s["ms_sample"] for s in stats)
     ms_phase = {p: sum(s[f"ms_{p}"] for s in stats) for p in ("forward", "allocate", "sample", "reverse", "topk")}
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    instr_per_step = 48.0
-    peak_steps = sm_count * 128 * sm_max * 1e6 / instr_per_step
+    peak_steps = sm_count * 128 * sm_max * 1e6 / INSTR_PER_PAIR_STEP
     achieved = steps_total / (ms_sample / 1000.0) if ms_sample > 0 else 0.0
-    sweep_bytes = 2 * (4 * len(col) + 4 * (n + 1)) + 3 * 8 * n  # per forward+reverse level pair
     L = stats[0]["L"] if stats else 0
+    # algorithmic bytes of one forward plus one reverse level: each reads its
+    # CSR (4 B per entry, 4 B per row pointer) and gathers one 8 B value per entry; the forward
+    # level writes pi^l and x^l (16 B per node), the reverse level reads pi^(L-l) and D^ and
+    # writes s^l (24 B per node)
+    m_edges = len(col)
+    sweep_bytes = 2 * (4 * m_edges + 4 * (n + 1) + 8 * m_edges) + 16 * n + 24 * n
     sweep_gbs = (len(stats) * L * sweep_bytes) / ((ms_phase["forward"] + ms_phase["reverse"]) / 1000.0) / 1e9 \
         if stats else 0.0
     launches = sum(s["launches"] for s in stats)
+    # Lemma 2 with the pi^2 allocation: Var s(v) <= ||pi_v||^2 / (4 a^4 R_b) (using D(1-D) <= 1/4);
+    # ||pi_v||^2 <= 1 bounds every node, ||pi_u||^2 (measured) the source itself
+    a = 1.0 - math.sqrt(c)
+    R_b = stats[0]["R_b"] if stats else 0.0
+    norm_u = statistics.mean(s["pi_norm2"] for s in stats) if stats else 0.0
+    sigma_u = math.sqrt(norm_u / (4 * a ** 4 * R_b)) if R_b > 0 else None
+    sigma_any = math.sqrt(1.0 / (4 * a ** 4 * R_b)) if R_b > 0 else None
+    traffic = KERNEL_TRAFFIC.get("sample_pairs_kernel")
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -317,12 +335,15 @@ def main():
         "gpu_launches": launches,
         "roofline": {"kernel": "sample_pairs_kernel", "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak_steps / 1e9, "unit": "G pair-steps/s", "frac": achieved / peak_steps,
-                     "traffic": None,
-                     "peak_source": f"{sm_count} SMs x 128 lanes x {sm_max:.0f} MHz ({pk_src}) / {instr_per_step:.0f} "
-                                    "instr per pair-step"},
+                     "traffic": traffic,
+                     "peak_source": f"{sm_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz ({pk_src} clock) / "
+                                    f"{INSTR_PER_PAIR_STEP:.0f} integer instructions per pair-step"},
         "phases_ms": {p: v / max(len(stats), 1) for p, v in ms_phase.items()},
         "walk": {"pairs_per_query": sum(s["sum_R"] for s in stats) / max(len(stats), 1),
-                 "pair_steps_per_s": achieved, "L": L},
+                 "pair_steps_per_s": achieved, "L": L, "R_b": R_b},
+        "error_bound": {"sigma_source": sigma_u, "sigma_any_node": sigma_any, "eps": eps,
+                        "note": "Lemma 2 variance bound with the pi^2 allocation at this kappa; "
+                                "kappa = 6/(1-sqrt c)^4 carries Theorem 1's guarantee"},
         "sweep_hbm_gbs": sweep_gbs,
         "wall_s": wall,
     }

@@ -48,6 +48,7 @@ cudaError_t dev_alloc(T** p, size_t count) {
 void free_csr(DevCsr& c) {
     cudaFree(c.rp);
     cudaFree(c.col);
+    cudaFree(c.info);
     cudaFree(c.seg);
     cudaFree(c.long_rows);
     cudaFree(c.long_first);
@@ -65,7 +66,8 @@ int group_for(double avg_degree) {
 constexpr uint32_t kSegLen = 4096;
 
 // Upload a host CSR and build its row-split table.
-esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::vector<int32_t>& col, DevCsr& d) {
+esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::vector<int32_t>& col, DevCsr& d,
+                       bool with_info) {
     const int64_t m = (int64_t)rp[n];
     d.group = group_for(n ? (double)m / (double)n : 1.0);
     d.long_min = std::max<uint32_t>(256u, 32u * (uint32_t)d.group);
@@ -97,6 +99,12 @@ esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::ve
                       "upload long rows");
     ESIM_CUDA_TRY(cudaMemcpy(d.long_first, long_first.data(), sizeof(int32_t) * long_first.size(), cudaMemcpyHostToDevice),
                   "upload long first");
+    if (with_info) {
+        std::vector<uint2> info((size_t)n);
+        for (int64_t r = 0; r < n; ++r) info[r] = make_uint2(rp[r], rp[r + 1] - rp[r]);
+        if (dev_alloc(&d.info, (size_t)n) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(row info)");
+        ESIM_CUDA_TRY(cudaMemcpy(d.info, info.data(), sizeof(uint2) * (size_t)n, cudaMemcpyHostToDevice), "upload row info");
+    }
     return ESIM_OK;
 }
 
@@ -316,8 +324,8 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
         for (int64_t j = 0; j < n; ++j)
             for (int64_t p = in_rowptr[j]; p < in_rowptr[j + 1]; ++p) out_c[cur[in_col[p]]++] = (int32_t)j;
     }
-    esim_status st = upload_csr(n, in_rp, in_c, g.in);
-    if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out);
+    esim_status st = upload_csr(n, in_rp, in_c, g.in, true);
+    if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out, false);
     if (st != ESIM_OK) {
         release(g);
         delete h;

@@ -37,6 +37,7 @@ struct Segment {
 struct DevCsr {
     uint32_t* rp = nullptr;      // n+1
     int32_t* col = nullptr;      // m
+    uint2* info = nullptr;       // n: (rp[i], rp[i+1] - rp[i]), one 8-byte load per row (walks)
     Segment* seg = nullptr;      // nseg
     int32_t* long_rows = nullptr;  // nlong row ids
     int32_t* long_first = nullptr; // nlong+1: first segment of each long row

@@ -212,25 +212,75 @@ __device__ __forceinline__ uint32_t pick_redraw(uint32_t d, unsigned long long m
     return (uint32_t)(m >> 32);
 }
 
-__device__ __forceinline__ uint32_t pick(uint32_t x, uint32_t d, uint32_t rlo, uint32_t rhi, uint32_t k, uint32_t tag,
-                                         const PhiloxKeys& K) {
-    const unsigned long long m = (unsigned long long)x * d;
-    if (__builtin_expect((uint32_t)m < d, 0)) return pick_redraw(d, m, rlo, rhi, k, tag, K);
-    return (uint32_t)(m >> 32);
+// State of one walk pair stream: the thread's current node k, pair r of R(k)
+// (rk), the two walk positions, the step t, and the pairs still to run.
+struct PairState {
+    unsigned long long r, rk, left, cnt, g_end;
+    uint32_t k, xa, xb, t;
+};
+
+// One step of the current pair (branch-free apart from the rare Lemire
+// rejection and the change of node): both walks' rows and chosen in-neighbours
+// are loaded whether or not the walks move (an index into a row without
+// in-edges is clamped to entry 0), and the outcome is applied with selects.
+__device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict__ row,
+                                          const int32_t* __restrict__ col, const uint64_t* __restrict__ off,
+                                          uint32_t T, const PhiloxKeys& K, unsigned long long* __restrict__ nonmeet,
+                                          unsigned long long& steps) {
+    const uint32_t rlo = (uint32_t)S.r, rhi = (uint32_t)(S.r >> 32);
+    const uint4 w = philox4x32_10(make_uint4(rlo, rhi, S.k, S.t), K);
+    const uint2 ra = __ldg(row + S.xa), rb = __ldg(row + S.xb);  // (first in-edge, din)
+    const bool cont = (w.x < T) & (w.z < T) & (ra.y != 0u) & (rb.y != 0u);
+    const unsigned long long ma = (unsigned long long)w.y * ra.y;
+    const unsigned long long mb = (unsigned long long)w.w * rb.y;
+    uint32_t ia = (uint32_t)(ma >> 32), ib = (uint32_t)(mb >> 32);
+    if (__builtin_expect(cont & (((uint32_t)ma < ra.y) | ((uint32_t)mb < rb.y)), 0)) {
+        if ((uint32_t)ma < ra.y) ia = pick_redraw(ra.y, ma, rlo, rhi, S.k, 0x80000000u | S.t, K);
+        if ((uint32_t)mb < rb.y) ib = pick_redraw(rb.y, mb, rlo, rhi, S.k, 0xC0000000u | S.t, K);
+    }
+    const uint32_t na = (uint32_t)__ldg(col + (ra.y ? ra.x + ia : 0u));
+    const uint32_t nb = (uint32_t)__ldg(col + (rb.y ? rb.x + ib : 0u));
+    const bool meet = cont & (na == nb);
+    const bool ended = !cont | meet | (S.t + 1u >= kWalkMaxSteps);
+    S.xa = ended ? S.k : na;
+    S.xb = ended ? S.k : nb;
+    if (!ended) {
+        ++S.t;
+        return;
+    }
+    steps += S.t + 1u;
+    S.cnt += meet ? 0ull : 1ull;
+    S.t = 0;
+    if (--S.left == 0) {
+        if (S.cnt) atomicAdd(nonmeet + S.k, S.cnt);
+        S.cnt = 0;
+        return;
+    }
+    if (++S.r == S.rk) {  // node k is done: flush and move to the next node with pairs
+        if (S.cnt) atomicAdd(nonmeet + S.k, S.cnt);
+        S.cnt = 0;
+        const unsigned long long g = S.g_end - S.left;
+        do {
+            ++S.k;
+        } while (__ldg(off + S.k + 1) <= g);
+        S.r = 0;
+        S.rk = __ldg(off + S.k + 1) - __ldg(off + S.k);
+        S.xa = S.xb = S.k;
+    }
 }
 
 // Persistent walk-pair sampler.  Thread t takes a contiguous run of global pair
 // indices (about total / #threads of them) and advances its current pair by one
 // step per loop iteration, so a lane whose pair ended starts its next pair at
-// once and lanes stay busy.  Counts are kept in a register while the node does
-// not change and flushed with one atomic add per (thread, node).
-__global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, const uint32_t* __restrict__ rp,
-                                                              const int32_t* __restrict__ col,
-                                                              const uint64_t* __restrict__ off, uint32_t T,
-                                                              const __grid_constant__ PhiloxKeys K, double budget,
-                                                              unsigned long long* __restrict__ nonmeet,
-                                                              unsigned long long* __restrict__ steps_out,
-                                                              Status* __restrict__ st) {
+// once and lanes stay busy.  Counts stay in registers while the node does not
+// change and are flushed with one atomic add per (thread, node).
+__global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, const uint2* __restrict__ row,
+                                                                 const int32_t* __restrict__ col,
+                                                                 const uint64_t* __restrict__ off, uint32_t T,
+                                                                 const __grid_constant__ PhiloxKeys K, double budget,
+                                                                 unsigned long long* __restrict__ nonmeet,
+                                                                 unsigned long long* __restrict__ steps_out,
+                                                                 Status* __restrict__ st) {
     __shared__ unsigned long long red[kBlock / 32];
     const unsigned long long total = off[n];
     if ((double)total > budget || (st->err & kErrBudget)) {
@@ -241,60 +291,26 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, cons
     const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long per = total / nthreads, rem = total % nthreads;
     const unsigned long long g0 = tid * per + (tid < rem ? tid : rem);
-    unsigned long long left = per + (tid < rem ? 1ull : 0ull);  // pairs still to run
+    PairState S;
+    S.left = per + (tid < rem ? 1ull : 0ull);
+    S.g_end = g0 + S.left;
+    S.cnt = 0;
+    S.t = 0;
     unsigned long long steps = 0;
-    if (left) {
-        // node of pair g0: off[k] <= g0 < off[k+1]
-        int64_t lo = 0, hi = n;
+    if (S.left) {
+        int64_t lo = 0, hi = n;  // node of pair g0: off[k] <= g0 < off[k+1]
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (__ldg(off + mid) <= g0) lo = mid; else hi = mid;
         }
-        uint32_t k = (uint32_t)lo;
-        unsigned long long r = g0 - __ldg(off + k);             // pair index within node k
-        unsigned long long rk = __ldg(off + k + 1) - __ldg(off + k);  // R(k)
-        uint32_t xa = k, xb = k, t = 0;
-        unsigned long long cnt = 0;
+        S.k = (uint32_t)lo;
+        S.r = g0 - __ldg(off + S.k);
+        S.rk = __ldg(off + S.k + 1) - __ldg(off + S.k);
+        S.xa = S.xb = S.k;
         for (;;) {
-            const uint32_t rlo = (uint32_t)r, rhi = (uint32_t)(r >> 32);
-            const uint4 w = philox4x32_10(make_uint4(rlo, rhi, k, t), K);
-            ++steps;
-            bool cont = (w.x < T) & (w.z < T);
-            uint32_t na = 0, nb = 0;
-            if (cont) {
-                const uint32_t ba = __ldg(rp + xa), da = __ldg(rp + xa + 1) - ba;
-                const uint32_t bb = __ldg(rp + xb), db = __ldg(rp + xb + 1) - bb;
-                cont = (da != 0u) & (db != 0u);
-                if (cont) {
-                    na = (uint32_t)__ldg(col + ba + pick(w.y, da, rlo, rhi, k, 0x80000000u | t, K));
-                    nb = (uint32_t)__ldg(col + bb + pick(w.w, db, rlo, rhi, k, 0xC0000000u | t, K));
-                }
-            }
-            const bool meet = cont & (na == nb);
-            const bool ended = !cont | meet | (t + 1u >= kWalkMaxSteps);
-            if (!ended) {
-                xa = na;
-                xb = nb;
-                ++t;
-                continue;
-            }
-            cnt += meet ? 0ull : 1ull;
-            if (--left == 0) break;
-            t = 0;
-            if (++r == rk) {  // node k is done: flush and move to the next node with pairs
-                if (cnt) atomicAdd(nonmeet + k, cnt);
-                cnt = 0;
-                const unsigned long long g = g0 + (per + (tid < rem ? 1ull : 0ull)) - left;
-                do {
-                    ++k;
-                } while (__ldg(off + k + 1) <= g);
-                r = 0;
-                rk = __ldg(off + k + 1) - __ldg(off + k);
-            }
-            xa = k;
-            xb = k;
+            if (!S.left) break;
+            pair_step(S, row, col, off, T, K, nonmeet, steps);
         }
-        if (cnt) atomicAdd(nonmeet + k, cnt);
     }
     steps = block_sum(steps, red);
     if (threadIdx.x == 0 && steps) atomicAdd(steps_out, steps);
@@ -326,7 +342,7 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
         g_sample_blocks_per_sm = b > 0 ? b : 1;
     }
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
-    sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, g.in.rp, g.in.col, off, walk_threshold(c),
+    sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
                                                          (unsigned long long*)nonmeet, steps, g.status);
     return cudaGetLastError();
