@@ -194,6 +194,26 @@ esim_status esim_reverse(esim_graph* g, const double* hist, int32_t L, double c,
 esim_status esim_select_topk(esim_graph* g, const double* scores, int64_t exclude, int32_t k,
                              int32_t* ids_out, double* vals_out);
 
+/* Top-k selection that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code running
+ * inside a host framework that owns all device memory (a fixed arena, a
+ * memory-capped serving process) and latency-critical threads that must not
+ * take the device synchronisation an allocation or free may cause.
+ * Same result as esim_select_topk: ids_out[k], vals_out[k] (device) receive the k
+ * largest scores[n] (device), ordered (score desc, id asc); exclude = -1 keeps
+ * every node; slots beyond the eligible nodes get id -1 and score 0.  Needs no
+ * graph handle; work is enqueued on `stream` (a cudaStream_t of the current
+ * device, NULL for the legacy default stream) and the call returns without
+ * waiting.  Scratch: a static device array of about 66 KB (the radix-select state
+ * and 4096 candidates), resident on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller.  Limits: 1 <= k <= 4096
+ * (ESIM_ENOTSUP above), 1 <= n < 2^31.  Calls no cudaMalloc or cudaFree. */
+esim_status esim_select_topk_static(const double* scores, int64_t n, int64_t exclude, int32_t k, int32_t* ids_out,
+                                    double* vals_out, void* stream);
+
 /* Wait for the graph's stream; returns the first device-side error recorded
  * since the last esim_sync (ESIM_EBUDGET, ESIM_ETIMEOUT) or ESIM_ECUDA. */
 esim_status esim_sync(esim_graph* g);

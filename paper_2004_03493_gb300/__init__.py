@@ -30,6 +30,7 @@ from ._native import (  # noqa: F401
     esim_sample,
     esim_sample_base,
     esim_select_topk,
+    esim_select_topk_static,
     esim_set_option,
     esim_set_stream,
     esim_sync,

@@ -71,6 +71,7 @@ SIGNATURES = {
     "esim_reverse": (_ST, [_P, _P, _I32, _D, _P, _P]),
     "esim_select_topk": (_ST, [_P, _P, _I64, _I32, _P, _P]),
     "esim_sync": (_ST, [_P]),
+    "esim_select_topk_static": (_ST, [_P, _I64, _I64, _I32, _P, _P, _P]),
 }
 
 
@@ -245,6 +246,14 @@ def esim_reverse(g: int, hist, L: int, c: float, dhat, s_out) -> None:
 def esim_select_topk(g: int, scores, exclude: int, k: int, ids_out, vals_out) -> None:
     _check(lib().esim_select_topk(g, _ptr(scores, "float64", device=True), exclude, k,
                                   _ptr(ids_out, "int32", device=True), _ptr(vals_out, "float64", device=True)))
+
+
+def esim_select_topk_static(scores, n: int, exclude: int, k: int, ids_out, vals_out, stream=None) -> None:
+    """Top-k selection with static scratch (no allocation); see include/exactsim.h."""
+    ptr = getattr(stream, "cuda_stream", stream)
+    _check(lib().esim_select_topk_static(_ptr(scores, "float64", device=True), n, exclude, k,
+                                         _ptr(ids_out, "int32", device=True), _ptr(vals_out, "float64", device=True),
+                                         ptr))
 
 
 def esim_sync(g: int) -> None:

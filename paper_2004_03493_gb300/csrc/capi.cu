@@ -262,6 +262,11 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
 
 }  // namespace
 
+int esim::set_error(int status, const std::string& message) {
+    t_err = message;
+    return status;
+}
+
 extern "C" {
 
 const char* esim_version(void) { return "exactsim-gb300 0.1 (sm_103a)"; }

@@ -95,6 +95,9 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
 uint32_t walk_threshold(double c);
 
+// capi.cu: record a message for esim_last_error() and return `status` (as an esim_status int)
+int set_error(int status, const std::string& message);
+
 // topk.cu
 constexpr int kTopkMax = 4096;
 size_t topk_workspace_bytes(int64_t n);

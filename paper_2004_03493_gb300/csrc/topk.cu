@@ -9,6 +9,10 @@
 // the <= 4096 winners (bitonic, shared memory).
 #include "common.cuh"
 #include "internal.h"
+#include "exactsim.h"
+
+#include <mutex>
+#include <string>
 
 namespace esim {
 
@@ -214,3 +218,99 @@ cudaError_t launch_topk(const Graph& g, const double* scores, int64_t exclude, i
 }
 
 }  // namespace esim
+
+// ---------------------------------------------------------------------------
+// Top-k selection that allocates nothing (esim_select_topk_static).
+//
+// Some callers cannot call cudaMalloc: code that runs inside a host framework
+// which owns every byte of device memory (a fixed arena or a memory-capped
+// serving process), and latency-critical threads that must not pay the device
+// synchronisation cudaMalloc/cudaFree may cause.  For them the selection's
+// scratch (its radix-select state and the candidate list, about 66 KB) lives in
+// the file-scope array below instead of a library or caller allocation.  Every
+// GPU that loads the library holds this array until the process exits.
+//
+// In host code the symbol `g_topk_static_scratch` is only a host-side stand-in:
+// passing it to a kernel would fault or, where the GPU can reach host memory,
+// silently use the wrong memory.  The device address is taken once per device
+// with cudaGetSymbolAddress (the first call on a device does this, with that
+// device current; make that first call before any stream capture) and passed to
+// the kernels.  All calls share the array and it keeps the last call's contents;
+// topk_init_kernel clears the state every call.  Calls whose work overlaps on the
+// GPU (different streams, or several host threads) race on the array.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kStaticTopkStateBytes = ((sizeof(esim::TopkState) + 255) / 256) * 256;
+constexpr size_t kStaticTopkScratchBytes = kStaticTopkStateBytes + sizeof(esim::Cand) * (size_t)esim::kTopkMax;
+
+static __device__ __align__(256) unsigned char g_topk_static_scratch[kStaticTopkScratchBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+int g_static_sms[kStaticMaxDevices] = {};
+
+// Device address of the scratch array and the SM count of the current device.
+cudaError_t static_scratch(int dev, void** ptr, int* sms) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_topk_static_scratch);
+        if (e != cudaSuccess) return e;
+        int s = 0;
+        e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_static_sms[dev] = s;
+        g_static_ptr[dev] = p;
+    }
+    *ptr = g_static_ptr[dev];
+    *sms = g_static_sms[dev];
+    return cudaSuccess;
+}
+
+esim_status static_fail(esim_status status, const std::string& message) {
+    esim::set_error((int)status, message);
+    return status;
+}
+
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) esim_status esim_select_topk_static(
+    const double* scores, int64_t n, int64_t exclude, int32_t k, int32_t* ids_out, double* vals_out, void* stream) {
+    using namespace esim;
+    if (!scores || !ids_out || !vals_out) return static_fail(ESIM_EINVAL, "NULL argument");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return static_fail(ESIM_EINVAL, "need 1 <= n < 2^31");
+    if (k < 1) return static_fail(ESIM_EINVAL, "k must be >= 1");
+    if (k > kTopkMax)
+        return static_fail(ESIM_ENOTSUP, "k above 4096: the static top-k scratch holds at most 4096 candidates");
+    if (exclude < -1 || exclude >= n) return static_fail(ESIM_EINVAL, "exclude out of range");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(ESIM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kStaticMaxDevices) return static_fail(ESIM_ENOTSUP, "device ordinal above 63");
+    void* ws = nullptr;
+    int sms = 0;
+    e = static_scratch(dev, &ws, &sms);
+    if (e != cudaSuccess)
+        return static_fail(ESIM_ECUDA, std::string("static scratch set-up: ") + cudaGetErrorString(e));
+    cudaStream_t st = (cudaStream_t)stream;
+    TopkState* state = (TopkState*)ws;
+    Cand* cand = (Cand*)((char*)ws + kStaticTopkStateBytes);
+    topk_init_kernel<<<1, 256, 0, st>>>(state, (unsigned)k);
+    int64_t blocks = (n + kBlock - 1) / kBlock;
+    if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+    if (blocks < 1) blocks = 1;
+    for (int d = 0; d < 12; ++d) {
+        topk_hist_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, d);
+        topk_select_kernel<<<1, 32, 0, st>>>(state, d);
+    }
+    topk_gather_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, cand, (unsigned)kTopkMax);
+    int P = 1;
+    while (P < k) P <<= 1;
+    topk_sort_kernel<<<1, 1024, (size_t)P * 12, st>>>(state, cand, k, P, ids_out, vals_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return static_fail(ESIM_ECUDA, std::string("static top-k launch: ") + cudaGetErrorString(e));
+    return ESIM_OK;
+}
