@@ -40,6 +40,9 @@ WORKLOADS = {
                    sources=10, source_seed=7, k=50),
     "er2000": dict(kind="erdos_renyi", n=2000, m=20_000, graph_seed=1, c=0.6, eps=1e-4, sources=1,
                    source_seed=0, k=50),
+    # precision form: FP32c against FP64 sweeps on the same sources and the same D^
+    "cl4m": dict(kind="chung_lu", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
+                 sources=4, source_seed=7, k=50),
 }
 METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6, top-50)"
 # integer instructions of one pair-step at the issue limit: Philox-4x32-10 = 10 rounds x (2 wide
@@ -51,6 +54,16 @@ INSTR_PER_PAIR_STEP = 48.0
 # 6.16 MB and 6.47 MB read, 0 B written; the graph stays in L2, so this is its compulsory read)
 KERNEL_TRAFFIC = {"sample_pairs_kernel": 6.31e6}
 L2_FLUSH_BYTES = 512 << 20
+
+
+def sweep_level_bytes(n, m, precision):
+    """Compulsory bytes of one forward plus one reverse level."""
+    csr = 4 * m + 4 * (n + 1)
+    if precision == "fp64":
+        return 2 * csr + (8 + 16) * n + (8 + 24) * n
+    # FP32c: forward reads x (4 B), writes pi, x (8 B); reverse reads s (8 B two-float), pi (4 B),
+    # w (8 B) and writes s (8 B)
+    return 2 * csr + (4 + 8) * n + (8 + 4 + 8 + 8) * n
 
 
 def make_graph(w):
@@ -189,6 +202,81 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args, w):
+    """Sweep throughput and error of the FP32c precision form against FP64, same D^."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+    n, rp, col = make_graph(w)
+    m = len(col)
+    srcs = sources_for(w, rp, 1, 0)
+    c, eps = w["c"], w["eps"]
+    L = esim.esim_levels(c, eps)
+    kappa = args.kappa
+    g = esim.Graph(n, rp, col, kappa=kappa)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream)
+    hist64 = torch.empty((L + 1) * n, dtype=torch.float64, device="cuda")
+    hist32 = torch.empty((L + 1) * n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(n, dtype=torch.float64, device="cuda")
+    R = torch.zeros(n, dtype=torch.uint64, device="cuda")
+    off = torch.zeros(n + 1, dtype=torch.uint64, device="cuda")
+    nm = torch.zeros(n, dtype=torch.uint64, device="cuda")
+    dh = torch.empty(n, dtype=torch.float64, device="cuda")
+    s64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    s32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    R_b = esim.esim_sample_base(n, c, eps, kappa)
+    per_source = []
+    t = {"fp64": [], "fp32c": []}
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for u in srcs:
+        # D^ sampled once (FP64 forward + allocation + walks) and shared by both forms
+        g.forward(u, c, L, hist64)
+        g.allocate(hist64, L, R_b, 0, pi, R, off)
+        g.sample(off, c, 1, nm)
+        g.dhat(nm, off, dh)
+        g.sync()
+        pairs = int(off[n].item())
+        for rep in range(args.warmup + args.steps):
+            a = timed(lambda: (g.forward(u, c, L, hist64), g.reverse(hist64, L, c, dh, s64)))
+            b = timed(lambda: (g.forward_f32(u, c, L, hist32), g.reverse_f32(hist32, L, c, dh, s32)))
+            if rep >= args.warmup:
+                t["fp64"].append(a)
+                t["fp32c"].append(b)
+        g.sync()
+        err = float((s32 - s64).abs().max().item())
+        per_source.append({"u": u, "max_abs_err_fp32c_vs_fp64": err, "pairs_for_dhat": pairs,
+                           "s_u": float(s64[u].item())})
+    out = {}
+    pk, pk_src = peaks()
+    for prec in ("fp64", "fp32c"):
+        ms = statistics.mean(t[prec])
+        gbs = L * sweep_level_bytes(n, m, prec) / (ms / 1000.0) / 1e9
+        out[prec] = {"ms_per_query_sweeps": ms, "sweep_gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"]}
+    line = {"metric": "sweep HBM GB/s, FP32c vs FP64 (same sources, same D^)", "value": out["fp32c"]["sweep_gbs"],
+            "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32+two-float", "data": "synthetic",
+            "config": {"workload": "cl4m", "graph": "chung_lu", "n": n, "m": m, "gamma": w["gamma"], "c": c,
+                       "eps": eps, "L": L, "kappa_for_dhat": kappa, "sources": srcs,
+                       "l2": "inputs larger than L2 (in- and out-CSR 0.56 GB)"},
+            "forms": out, "per_source": per_source,
+            "error_bound_fp32c": 2.0 ** -24 * (2 * c / (1 - c) ** 2 + 2 / (1 - c)),
+            "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_src}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources_per_step": w["sources"],
@@ -216,6 +304,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, w, rank, world)
+        return
+    if args.workload == "cl4m":
+        run_precision(args, w)
         return
 
     import torch
@@ -309,12 +400,12 @@ def main():
     peak_steps = sm_count * 128 * sm_max * 1e6 / INSTR_PER_PAIR_STEP
     achieved = steps_total / (ms_sample / 1000.0) if ms_sample > 0 else 0.0
     L = stats[0]["L"] if stats else 0
-    # algorithmic bytes of one forward plus one reverse level: each reads its
-    # CSR (4 B per entry, 4 B per row pointer) and gathers one 8 B value per entry; the forward
-    # level writes pi^l and x^l (16 B per node), the reverse level reads pi^(L-l) and D^ and
-    # writes s^l (24 B per node)
+    # compulsory bytes of one forward plus one reverse FP64 level: each reads its CSR
+    # (4 B per entry, 4 B per row pointer) and its input vector once (8 B per node); the
+    # forward level writes pi^l and x^l (16 B per node), the reverse level reads pi^(L-l)
+    # and D^ and writes s^l (24 B per node)
     m_edges = len(col)
-    sweep_bytes = 2 * (4 * m_edges + 4 * (n + 1) + 8 * m_edges) + 16 * n + 24 * n
+    sweep_bytes = sweep_level_bytes(n, m_edges, "fp64")
     sweep_gbs = (len(stats) * L * sweep_bytes) / ((ms_phase["forward"] + ms_phase["reverse"]) / 1000.0) / 1e9 \
         if stats else 0.0
     launches = sum(s["launches"] for s in stats)

@@ -129,6 +129,10 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
  *                    query returns ESIM_EBUDGET without running walks
  *   "timing"         1: record per-phase CUDA event times in the stats
+ *   "precision"      0: FP64 sweeps (default);
+ *                    1: FP32c, the precision form -- pi^l and x^l stored in FP32
+ *                    with two-float (compensated) row sums, s^l stored and summed
+ *                    as two-floats, FP64 only for the final s and for D^
  * Errors: ESIM_EINVAL for an unknown key or a bad value. */
 esim_status esim_set_option(esim_graph* g, const char* key, double value);
 esim_status esim_get_option(const esim_graph* g, const char* key, double* value);
@@ -188,6 +192,18 @@ esim_status esim_dhat(esim_graph* g, const uint64_t* nonmeet, const uint64_t* of
  * s_out[n] = s^L. */
 esim_status esim_reverse(esim_graph* g, const double* hist, int32_t L, double c, const double* dhat,
                          double* s_out);
+
+/* Precision-form steps (FP32c, see option "precision").  esim_forward_f32 writes
+ * pi^0 .. pi^L as FP32 into hist[(L+1) * n] (each row sum formed in two-float and
+ * rounded once).  esim_allocate_f32 is esim_allocate over an FP32 history, the
+ * level sums taken in two-float and rounded to FP64 before R(k) is decided.
+ * esim_reverse_f32 runs the reverse accumulation from an FP32 history with
+ * two-float vectors and writes s^L in FP64. */
+esim_status esim_forward_f32(esim_graph* g, int64_t u, double c, int32_t L, float* hist);
+esim_status esim_allocate_f32(esim_graph* g, const float* hist, int32_t L, double R_b, int32_t mode,
+                              double* pi_out, uint64_t* R_out, uint64_t* off);
+esim_status esim_reverse_f32(esim_graph* g, const float* hist, int32_t L, double c, const double* dhat,
+                             double* s_out);
 
 /* Top-k selection over scores[n] (device): ids_out[k], vals_out[k] (device),
  * ordered (score desc, id asc); exclude = -1 keeps every node.  1 <= k <= 4096. */

@@ -16,6 +16,9 @@ from ._native import (  # noqa: F401
     esim_allocate,
     esim_dhat,
     esim_forward,
+    esim_forward_f32,
+    esim_allocate_f32,
+    esim_reverse_f32,
     esim_free_graph,
     esim_get_option,
     esim_last_error,
@@ -110,6 +113,15 @@ class Graph:
 
     def sample(self, off, c, seed, nonmeet, pair_steps=None):
         esim_sample(self.handle, off, c, seed, nonmeet, pair_steps)
+
+    def forward_f32(self, u, c, L, hist):
+        esim_forward_f32(self.handle, u, c, L, hist)
+
+    def allocate_f32(self, hist, L, R_b, mode, pi_out, R_out, off):
+        esim_allocate_f32(self.handle, hist, L, R_b, mode, pi_out, R_out, off)
+
+    def reverse_f32(self, hist, L, c, dhat, s_out):
+        esim_reverse_f32(self.handle, hist, L, c, dhat, s_out)
 
     def dhat(self, nonmeet, off, out):
         esim_dhat(self.handle, nonmeet, off, out)

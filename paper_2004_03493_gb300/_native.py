@@ -72,6 +72,9 @@ SIGNATURES = {
     "esim_select_topk": (_ST, [_P, _P, _I64, _I32, _P, _P]),
     "esim_sync": (_ST, [_P]),
     "esim_select_topk_static": (_ST, [_P, _I64, _I64, _I32, _P, _P, _P]),
+    "esim_forward_f32": (_ST, [_P, _I64, _D, _I32, _P]),
+    "esim_allocate_f32": (_ST, [_P, _P, _I32, _D, _I32, _P, _P, _P]),
+    "esim_reverse_f32": (_ST, [_P, _P, _I32, _D, _P, _P]),
 }
 
 
@@ -231,6 +234,21 @@ def esim_allocate(g: int, hist, L: int, R_b: float, mode: int, pi_out, R_out, of
 def esim_sample(g: int, off, c: float, seed: int, nonmeet, pair_steps=None) -> None:
     _check(lib().esim_sample(g, _ptr(off, "uint64", device=True), c, seed, _ptr(nonmeet, "uint64", device=True),
                              _ptr(pair_steps, "uint64", device=True, allow_none=True)))
+
+
+def esim_forward_f32(g: int, u: int, c: float, L: int, hist) -> None:
+    _check(lib().esim_forward_f32(g, u, c, L, _ptr(hist, "float32", device=True)))
+
+
+def esim_allocate_f32(g: int, hist, L: int, R_b: float, mode: int, pi_out, R_out, off) -> None:
+    _check(lib().esim_allocate_f32(g, _ptr(hist, "float32", device=True), L, R_b, mode,
+                                   _ptr(pi_out, "float64", device=True, allow_none=True),
+                                   _ptr(R_out, "uint64", device=True), _ptr(off, "uint64", device=True)))
+
+
+def esim_reverse_f32(g: int, hist, L: int, c: float, dhat, s_out) -> None:
+    _check(lib().esim_reverse_f32(g, _ptr(hist, "float32", device=True), L, c, _ptr(dhat, "float64", device=True),
+                                  _ptr(s_out, "float64", device=True)))
 
 
 def esim_dhat(g: int, nonmeet, off, dhat) -> None:

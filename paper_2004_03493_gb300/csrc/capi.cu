@@ -113,6 +113,7 @@ void release(Graph& g) {
     if (g.own_stream) cudaStreamSynchronize(g.own_stream);
     free_csr(g.in);
     free_csr(g.out);
+    cudaFree(g.inv_din);
     cudaFree(g.status);
     if (g.status_host) cudaFreeHost(g.status_host);
     cudaFree(g.ws);
@@ -136,26 +137,65 @@ double kappa_of(const Graph& g, double c) {
     return 6.0 / (a * a * a * a);
 }
 
-// Query workspace layout (doubles / uint64, each n long unless noted).
+// Query workspace (one device arena per graph handle, grown on demand).  The
+// FP64 form uses hist/xa/xb; the FP32c form uses hist32/xa32/xb32 and the
+// two-float buffers w/sa2/sb2.  Every buffer starts on a 256-byte boundary.
 struct Ws {
-    double* hist;     // (L+1) n
-    double* xa;       // n (forward x, then reverse ping-pong)
-    double* xb;       // n
-    double* pi;       // n
-    uint64_t* R;      // n
-    uint64_t* off;    // n+1
-    uint64_t* nonmeet;// n
-    double* dhat;     // n
-    double* s;        // n
+    double* hist;      // (L+1) n  FP64 history
+    double* xa;        // n        forward x, then reverse ping-pong (FP64)
+    double* xb;        // n
+    float* hist32;     // (L+1) n  FP32 history
+    float* xa32;       // n
+    float* xb32;       // n
+    float2* w2;        // n        D^/a as two-floats
+    float2* sa2;       // n        reverse ping-pong (two-float)
+    float2* sb2;       // n
+    double* pi;        // n
+    uint64_t* R;       // n
+    uint64_t* off;     // n+1
+    uint64_t* nonmeet; // n
+    double* dhat;      // n
+    double* s;         // n
 };
 
-size_t ws_bytes_for(int64_t n, int32_t L) {
-    const size_t v = (size_t)n * 8;
-    return v * (size_t)(L + 1) + 8 * v + 8 + 8 * 256;
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Lay out the arena at `base` (or only measure it when base is null); returns bytes.
+size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w) {
+    const size_t n = (size_t)n_;
+    size_t o = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + o : nullptr;
+        o += round256(bytes);
+        return p;
+    };
+    Ws t{};
+    if (precision == 0) {
+        t.hist = (double*)take(8 * n * (size_t)(L + 1));
+        t.xa = (double*)take(8 * n);
+        t.xb = (double*)take(8 * n);
+    } else {
+        t.hist32 = (float*)take(4 * n * (size_t)(L + 1));
+        t.xa32 = (float*)take(4 * n);
+        t.xb32 = (float*)take(4 * n);
+        t.w2 = (float2*)take(8 * n);
+        t.sa2 = (float2*)take(8 * n);
+        t.sb2 = (float2*)take(8 * n);
+        t.xa = (double*)t.sa2;  // FP64 scratch for step calls that need one (aliases sa2)
+        t.xb = (double*)t.sb2;
+    }
+    t.pi = (double*)take(8 * n);
+    t.R = (uint64_t*)take(8 * n);
+    t.off = (uint64_t*)take(8 * (n + 1));
+    t.nonmeet = (uint64_t*)take(8 * n);
+    t.dhat = (double*)take(8 * n);
+    t.s = (double*)take(8 * n);
+    if (w) *w = t;
+    return o;
 }
 
-esim_status ensure_ws(Graph& g, int32_t L, Ws& w) {
-    const size_t need = ws_bytes_for(g.n, L);
+esim_status ensure_ws(Graph& g, int32_t L, int precision, Ws& w) {
+    const size_t need = ws_layout(g.n, L, precision, nullptr, nullptr);
     if (need > g.ws_bytes) {
         cudaStreamSynchronize(g.stream);
         cudaFree(g.ws);
@@ -167,18 +207,7 @@ esim_status ensure_ws(Graph& g, int32_t L, Ws& w) {
         }
         g.ws_bytes = need;
     }
-    const size_t n = (size_t)g.n;
-    double* p = (double*)g.ws;
-    w.hist = p;
-    p += n * (size_t)(L + 1);
-    w.xa = p; p += n;
-    w.xb = p; p += n;
-    w.pi = p; p += n;
-    w.R = (uint64_t*)p; p += n;
-    w.off = (uint64_t*)p; p += n + 1;
-    w.nonmeet = (uint64_t*)p; p += n;
-    w.dhat = p; p += n;
-    w.s = p;
+    ws_layout(g.n, L, precision, (char*)g.ws, &w);
     return ESIM_OK;
 }
 
@@ -198,7 +227,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     const double kappa = kappa_of(g, c);
     const double R_b = kappa * log((double)g.n) / (eps * eps);
     Ws w;
-    esim_status st = ensure_ws(g, L, w);
+    esim_status st = ensure_ws(g, L, g.precision, w);
     if (st != ESIM_OK) return st;
     double* s = s_dev ? s_dev : w.s;
     if (g.timing)
@@ -206,14 +235,20 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
             if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
     ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
     if (g.timing) cudaEventRecord(g.ev[0], g.stream);
-    ESIM_CUDA_TRY(launch_forward(g, u, c, L, w.hist, w.xa, w.xb), "forward sweeps");
+    if (g.precision == 0) ESIM_CUDA_TRY(launch_forward(g, u, c, L, w.hist, w.xa, w.xb), "forward sweeps");
+    else ESIM_CUDA_TRY(launch_forward32(g, u, c, L, w.hist32, w.xa32, w.xb32), "forward sweeps (FP32c)");
     if (g.timing) cudaEventRecord(g.ev[1], g.stream);
-    ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
+    if (g.precision == 0)
+        ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
+    else
+        ESIM_CUDA_TRY(launch_allocate32(g, w.hist32, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation (FP32c)");
     if (g.timing) cudaEventRecord(g.ev[2], g.stream);
     ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr), "walk pairs");
     if (g.timing) cudaEventRecord(g.ev[3], g.stream);
     ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
-    ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
+    if (g.precision == 0) ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
+    else
+        ESIM_CUDA_TRY(launch_reverse32(g, w.hist32, L, c, w.dhat, s, w.w2, w.sa2, w.sb2), "reverse sweeps (FP32c)");
     if (g.timing) cudaEventRecord(g.ev[4], g.stream);
     if (k > 0) {
         int32_t* ids = ids_dev;
@@ -329,6 +364,20 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
         for (int64_t j = 0; j < n; ++j)
             for (int64_t p = in_rowptr[j]; p < in_rowptr[j + 1]; ++p) out_c[cur[in_col[p]]++] = (int32_t)j;
     }
+    {
+        std::vector<double> inv((size_t)n);
+        for (int64_t j = 0; j < n; ++j) {
+            const int64_t d = in_rowptr[j + 1] - in_rowptr[j];
+            inv[j] = d ? 1.0 / (double)d : 0.0;
+        }
+        if (dev_alloc(&g.inv_din, (size_t)n) != cudaSuccess ||
+            cudaMemcpy(g.inv_din, inv.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            release(g);
+            delete h;
+            return fail(ESIM_ENOMEM, "device allocation for 1/din");
+        }
+    }
     esim_status st = upload_csr(n, in_rp, in_c, g.in, true);
     if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out, false);
     if (st != ESIM_OK) {
@@ -391,6 +440,9 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "timing") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "timing must be 0 or 1");
         g.timing = (int)value;
+    } else if (k == "precision") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
+        g.precision = (int)value;
     } else {
         return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     }
@@ -407,6 +459,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "exclude_source") *value = g.exclude_source;
     else if (k == "pair_budget") *value = g.pair_budget;
     else if (k == "timing") *value = g.timing;
+    else if (k == "precision") *value = g.precision;
     else return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     return ESIM_OK;
 }
@@ -469,7 +522,7 @@ esim_status esim_forward(esim_graph* h, int64_t u, double c, int32_t L, double* 
     if (!hist) return fail(ESIM_EINVAL, "hist is NULL");
     ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
     Ws w;
-    esim_status st = ensure_ws(g, 0, w);
+    esim_status st = ensure_ws(g, 0, 0, w);
     if (st != ESIM_OK) return st;
     ESIM_CUDA_TRY(launch_forward(g, u, c, L, hist, w.xa, w.xb), "forward sweeps");
     return ESIM_OK;
@@ -516,7 +569,7 @@ esim_status esim_reverse(esim_graph* h, const double* hist, int32_t L, double c,
     if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
     ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
     Ws w;
-    esim_status st = ensure_ws(g, 0, w);
+    esim_status st = ensure_ws(g, 0, 0, w);
     if (st != ESIM_OK) return st;
     ESIM_CUDA_TRY(launch_reverse(g, hist, L, c, dhat, s_out, w.xa, w.xb), "reverse sweeps");
     return ESIM_OK;
@@ -532,6 +585,49 @@ esim_status esim_select_topk(esim_graph* h, const double* scores, int64_t exclud
     if (exclude < -1 || exclude >= g.n) return fail(ESIM_EINVAL, "exclude out of range");
     ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
     ESIM_CUDA_TRY(launch_topk(g, scores, exclude, k, ids_out, vals_out, g.topk_ws), "top-k");
+    return ESIM_OK;
+}
+
+esim_status esim_forward_f32(esim_graph* h, int64_t u, double c, int32_t L, float* hist) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (u < 0 || u >= g.n) return fail(ESIM_EINVAL, "source node out of range");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (!hist) return fail(ESIM_EINVAL, "hist is NULL");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    Ws w;
+    esim_status st = ensure_ws(g, 0, 1, w);
+    if (st != ESIM_OK) return st;
+    ESIM_CUDA_TRY(launch_forward32(g, u, c, L, hist, w.xa32, w.xb32), "forward sweeps (FP32c)");
+    return ESIM_OK;
+}
+
+esim_status esim_allocate_f32(esim_graph* h, const float* hist, int32_t L, double R_b, int32_t mode, double* pi_out,
+                              uint64_t* R_out, uint64_t* off) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!hist || !R_out || !off) return fail(ESIM_EINVAL, "NULL argument");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (mode != 0 && mode != 1) return fail(ESIM_EINVAL, "mode must be 0 or 1");
+    if (!(R_b >= 0.0)) return fail(ESIM_EINVAL, "need R_b >= 0");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_allocate32(g, hist, L, R_b, mode, pi_out, R_out, off), "allocation (FP32c)");
+    return ESIM_OK;
+}
+
+esim_status esim_reverse_f32(esim_graph* h, const float* hist, int32_t L, double c, const double* dhat,
+                             double* s_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!hist || !dhat || !s_out) return fail(ESIM_EINVAL, "NULL argument");
+    if (L < 0 || L > 4096) return fail(ESIM_EINVAL, "need 0 <= L <= 4096");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    Ws w;
+    esim_status st = ensure_ws(g, 0, 1, w);
+    if (st != ESIM_OK) return st;
+    ESIM_CUDA_TRY(launch_reverse32(g, hist, L, c, dhat, s_out, w.w2, w.sa2, w.sb2), "reverse sweeps (FP32c)");
     return ESIM_OK;
 }
 

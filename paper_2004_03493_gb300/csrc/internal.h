@@ -53,6 +53,7 @@ struct Graph {
     int64_t n = 0, m = 0;
     DevCsr in;    // rows = nodes, entries = in-neighbours (walks, reverse sweep)
     DevCsr out;   // rows = nodes, entries = out-neighbours (forward sweep)
+    double* inv_din = nullptr;  // n: 1/din(i) (0 where din = 0), for the FP64 sweeps
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     // options
@@ -61,6 +62,7 @@ struct Graph {
     int exclude_source = 1;
     double pair_budget = 1e15;
     int timing = 0;
+    int precision = 0;            // 0: FP64 sweeps; 1: FP32 storage with two-float sums (FP32c)
     // workspace
     Status* status = nullptr;     // device
     Status* status_host = nullptr; // pinned host copy
@@ -85,11 +87,16 @@ struct Graph {
 cudaError_t launch_forward(const Graph& g, int64_t u, double c, int32_t L, double* hist, double* xa, double* xb);
 cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double c, const double* dhat, double* s_out,
                            double* sa, double* sb);
+cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb);
+cudaError_t launch_reverse32(const Graph& g, const float* hist, int32_t L, double c, const double* dhat,
+                             double* s_out, float2* w, float2* sa, float2* sb);
 
 // sample.cu
 int64_t allocate_blocks(int64_t n);
 cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, double R_b, int mode, double* pi_out,
                             uint64_t* R_out, uint64_t* off);
+cudaError_t launch_allocate32(const Graph& g, const float* hist, int32_t L, double R_b, int mode, double* pi_out,
+                              uint64_t* R_out, uint64_t* off);
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
                           uint64_t* pair_steps);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "philox.cuh"
+#include "twofloat.cuh"
 
 #include <math.h>
 
@@ -66,8 +67,23 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
     return warp_off + x - v;
 }
 
+// pi(k) = sum over levels of hist, in level order: FP64 sums for an FP64 history,
+// two-float sums (rounded to FP64) for an FP32 history.
+__device__ __forceinline__ double level_sum(const double* __restrict__ hist, int64_t n, int64_t k, int32_t L) {
+    double p = 0.0;
+    for (int32_t l = 0; l <= L; ++l) p += hist[(size_t)l * (size_t)n + (size_t)k];
+    return p;
+}
+
+__device__ __forceinline__ double level_sum(const float* __restrict__ hist, int64_t n, int64_t k, int32_t L) {
+    f2 p = f2{0.f, 0.f};
+    for (int32_t l = 0; l <= L; ++l) p = f2_add_f(p, hist[(size_t)l * (size_t)n + (size_t)k]);
+    return f2_to_double(p);
+}
+
 // pi(k), R(k) per node; per-tile sums of R (exact and in double) and of pi^2.
-__global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const double* __restrict__ hist, int32_t L,
+template <typename H>
+__global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const H* __restrict__ hist, int32_t L,
                                                               double R_b, int mode, double* __restrict__ pi_out,
                                                               uint64_t* __restrict__ R_out,
                                                               unsigned long long* __restrict__ part_R,
@@ -83,8 +99,7 @@ __global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const d
     for (int i = 0; i < kAllocItems; ++i) {
         const int64_t k = base + (int64_t)i * kBlock + threadIdx.x;
         if (k >= n) break;
-        double p = 0.0;
-        for (int32_t l = 0; l <= L; ++l) p += hist[(size_t)l * (size_t)n + (size_t)k];
+        const double p = level_sum(hist, n, k, L);
         if (pi_out) pi_out[k] = p;
         const double v = mode == 0 ? R_b * (p * p) : R_b * p;
         unsigned long long r = 0;
@@ -170,14 +185,15 @@ __global__ void __launch_bounds__(kBlock) alloc_scan_kernel(int64_t n, const uin
     }
 }
 
-cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, double R_b, int mode, double* pi_out,
-                            uint64_t* R_out, uint64_t* off) {
+template <typename H>
+cudaError_t launch_allocate_t(const Graph& g, const H* hist, int32_t L, double R_b, int mode, double* pi_out,
+                              uint64_t* R_out, uint64_t* off) {
     const int64_t nb = allocate_blocks(g.n);
     unsigned long long* part_R = g.scan_part;
     double* part_norm = g.norm_part;
     double* part_Rd = g.norm_part + nb;
-    alloc_reduce_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, hist, L, R_b, mode, pi_out, R_out, part_R,
-                                                               part_norm, part_Rd, g.status);
+    alloc_reduce_kernel<H><<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, hist, L, R_b, mode, pi_out, R_out, part_R,
+                                                                  part_norm, part_Rd, g.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     alloc_partials_kernel<<<1, kScanThreads, 0, g.stream>>>(nb, part_R, part_norm, part_Rd, g.pair_budget,
@@ -186,6 +202,16 @@ cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, doubl
     if (e != cudaSuccess) return e;
     alloc_scan_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, R_out, part_R, off);
     return cudaGetLastError();
+}
+
+cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, double R_b, int mode, double* pi_out,
+                            uint64_t* R_out, uint64_t* off) {
+    return launch_allocate_t<double>(g, hist, L, R_b, mode, pi_out, R_out, off);
+}
+
+cudaError_t launch_allocate32(const Graph& g, const float* hist, int32_t L, double R_b, int mode, double* pi_out,
+                              uint64_t* R_out, uint64_t* off) {
+    return launch_allocate_t<float>(g, hist, L, R_b, mode, pi_out, R_out, off);
 }
 
 // Exactly uniform index in [0, d) from word x (Lemire); rejections (probability

@@ -10,57 +10,151 @@
 // (P pi)(i) = sum_j P(i,j) pi(j) with P(i,j) = 1/din(j) for i in I(j), so the
 // forward product pulls along out-edges with the 1/din factor folded into the
 // gathered vector x; (P^T s)(j) = (1/din(j)) sum_{i in I(j)} s(i) pulls along
-// in-edges.  Both are atomic-free and deterministic: each row's sum is formed
-// in a fixed order by one thread group (short rows) or by fixed segments plus an
+// in-edges.  Both are atomic-free and deterministic: each row's sum is formed in
+// a fixed order by one thread group (short rows) or by fixed segments plus an
 // in-order combine (long rows).
+//
+// Two arithmetic forms share the kernels through a value/accumulator policy:
+//   FP64  -- values and sums in FP64 (the plain method);
+//   FP32c -- the precision form: pi^l and x^l stored in FP32 with two-float
+//            (compensated) row sums; s^l stored and summed as two-floats; FP64
+//            only for the final s^L and the D^ ratio.  On GB300, whose FP64 issue
+//            rate is a small fraction of FP32, this keeps the sweeps bound by
+//            memory rather than by FP64 arithmetic.
 #include "common.cuh"
 #include "internal.h"
+#include "twofloat.cuh"
 
 namespace esim {
 
-struct ForwardOp {
+// ---------------------------------------------------------------- policies
+
+struct Pol64 {  // FP64 values, FP64 sums
+    using V = double;
+    using A = double;
+    static __device__ __forceinline__ A zero() { return 0.0; }
+    static __device__ __forceinline__ A add(A a, V v) { return a + v; }
+    static __device__ __forceinline__ A combine(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A shfl(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
+};
+
+struct Pol32c {  // FP32 values, two-float sums
+    using V = float;
+    using A = f2;
+    static __device__ __forceinline__ A zero() { return f2{0.f, 0.f}; }
+    static __device__ __forceinline__ A add(A a, V v) { return f2_add_f(a, v); }
+    static __device__ __forceinline__ A combine(A a, A b) { return f2_add(a, b); }
+    static __device__ __forceinline__ A shfl(A a, int o, int w) { return f2_shfl_down(a, o, w); }
+};
+
+struct Pol2f {  // two-float values (float2: hi, lo), two-float sums
+    using V = float2;
+    using A = f2;
+    static __device__ __forceinline__ A zero() { return f2{0.f, 0.f}; }
+    static __device__ __forceinline__ A add(A a, V v) { return f2_add(a, f2{v.x, v.y}); }
+    static __device__ __forceinline__ A combine(A a, A b) { return f2_add(a, b); }
+    static __device__ __forceinline__ A shfl(A a, int o, int w) { return f2_shfl_down(a, o, w); }
+};
+
+template <class Pol>
+__device__ __forceinline__ typename Pol::A block_combine(typename Pol::A v, typename Pol::A* smem) {
+    using A = typename Pol::A;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = Pol::combine(v, Pol::shfl(v, o, 32));
+    if (lane == 0) smem[wid] = v;
+    __syncthreads();
+    A r = Pol::zero();
+    if (wid == 0) {
+        r = lane < nw ? smem[lane] : Pol::zero();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = Pol::combine(r, Pol::shfl(r, o, 32));
+    }
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- row epilogues
+
+struct ForwardOp {  // FP64
     double sc;
-    const uint32_t* __restrict__ in_rp;
+    const double* __restrict__ inv_din;
     double* __restrict__ pi_out;
     double* __restrict__ x_out;
     __device__ __forceinline__ void operator()(int64_t row, double acc) const {
         const double p = sc * acc;
         pi_out[row] = p;
-        const uint32_t d = in_rp[row + 1] - in_rp[row];
-        x_out[row] = d ? p / (double)d : 0.0;
+        x_out[row] = p * inv_din[row];
     }
 };
 
-struct ReverseOp {
+struct ReverseOp {  // FP64
     double sc;
     double a;
-    const uint32_t* __restrict__ rp;  // the in-edge CSR being swept
+    const double* __restrict__ inv_din;
     const double* __restrict__ dhat;
-    const double* __restrict__ h;     // pi^{L-l}
+    const double* __restrict__ h;  // pi^{L-l}
     double* __restrict__ s_out;
     __device__ __forceinline__ void operator()(int64_t row, double acc) const {
-        const uint32_t d = rp[row + 1] - rp[row];
-        const double prop = d ? (sc * acc) / (double)d : 0.0;
-        s_out[row] = prop + dhat[row] * h[row] / a;
+        s_out[row] = (sc * acc) * inv_din[row] + dhat[row] * h[row] / a;
     }
 };
 
+struct ForwardOp32c {  // FP32 storage, two-float sum
+    f2 sc;
+    const uint32_t* __restrict__ in_rp;
+    float* __restrict__ pi_out;
+    float* __restrict__ x_out;
+    __device__ __forceinline__ void operator()(int64_t row, f2 acc) const {
+        const f2 p = f2_mul(acc, sc);
+        const float pf = __fadd_rn(p.hi, p.lo);
+        pi_out[row] = pf;
+        const uint32_t d = in_rp[row + 1] - in_rp[row];
+        x_out[row] = d ? __fdiv_rn(pf, (float)d) : 0.f;
+    }
+};
+
+// Reverse level in two-float: s^l = sqrt(c) (P^T s^{l-1}) + w pi^{L-l}, w = D^/a
+// as a two-float; intermediate levels store float2, the last level FP64.
+template <bool kFinal>
+struct ReverseOp2f {
+    f2 sc;
+    const uint32_t* __restrict__ rp;
+    const float2* __restrict__ w;
+    const float* __restrict__ h;
+    float2* __restrict__ s_out;
+    double* __restrict__ s_final;
+    __device__ __forceinline__ void operator()(int64_t row, f2 acc) const {
+        const uint32_t d = rp[row + 1] - rp[row];
+        f2 prop = f2{0.f, 0.f};
+        if (d) prop = f2_div_f(f2_mul(acc, sc), (float)d);
+        const float2 wv = w[row];
+        const f2 s = f2_add(prop, f2_mul_f(f2{wv.x, wv.y}, h[row]));
+        if (kFinal) s_final[row] = f2_to_double(s);
+        else s_out[row] = make_float2(s.hi, s.lo);
+    }
+};
+
+// ---------------------------------------------------------------- row kernels
+
 // Blocks [0, short_blocks) sweep the short rows, G lanes per row; the remaining
-// blocks each sum one segment of a long row into partial[].
-template <int G, class Op>
+// blocks each combine one segment of a long row into partial[].
+template <class Pol, int G, class Op>
 __global__ void __launch_bounds__(kBlock) rows_kernel(int64_t n, const uint32_t* __restrict__ rp,
                                                       const int32_t* __restrict__ col,
-                                                      const double* __restrict__ x, uint32_t long_min, Op op,
+                                                      const typename Pol::V* __restrict__ x, uint32_t long_min, Op op,
                                                       int64_t nseg, const Segment* __restrict__ seg,
-                                                      double* __restrict__ partial, int short_blocks) {
-    __shared__ double red[kBlock / 32];
+                                                      typename Pol::A* __restrict__ partial, int short_blocks) {
+    using A = typename Pol::A;
+    __shared__ A red[kBlock / 32];
     if ((int)blockIdx.x >= short_blocks) {
         const int64_t nsb = (int64_t)gridDim.x - short_blocks;
         for (int64_t s = (int64_t)blockIdx.x - short_blocks; s < nseg; s += nsb) {
             const Segment sg = seg[s];
-            double acc = 0.0;
-            for (uint32_t p = sg.beg + threadIdx.x; p < sg.end; p += blockDim.x) acc += __ldg(x + __ldg(col + p));
-            acc = block_sum(acc, red);
+            A acc = Pol::zero();
+            for (uint32_t p = sg.beg + threadIdx.x; p < sg.end; p += blockDim.x) acc = Pol::add(acc, x[__ldg(col + p)]);
+            acc = block_combine<Pol>(acc, red);
             if (threadIdx.x == 0) partial[s] = acc;
         }
         return;
@@ -80,42 +174,52 @@ __global__ void __launch_bounds__(kBlock) rows_kernel(int64_t n, const uint32_t*
             mine = (e - b) < long_min;
             if (!mine) e = b;
         }
-        double acc0 = 0.0, acc1 = 0.0;
+        A acc0 = Pol::zero(), acc1 = Pol::zero();
         uint32_t p = b + gl;
         for (; p + G < e; p += 2 * G) {
             const int32_t c0 = __ldg(col + p), c1 = __ldg(col + p + G);
-            acc0 += __ldg(x + c0);
-            acc1 += __ldg(x + c1);
+            acc0 = Pol::add(acc0, x[c0]);
+            acc1 = Pol::add(acc1, x[c1]);
         }
-        if (p < e) acc0 += __ldg(x + __ldg(col + p));
-        double acc = acc0 + acc1;
+        if (p < e) acc0 = Pol::add(acc0, x[__ldg(col + p)]);
+        A acc = Pol::combine(acc0, acc1);
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+        for (int o = G / 2; o > 0; o >>= 1) acc = Pol::combine(acc, Pol::shfl(acc, o, G));
         if (gl == 0 && mine) op(row, acc);
     }
 }
 
 // One warp per long row: combine the row's segment partials in order.
-template <class Op>
+template <class Pol, class Op>
 __global__ void __launch_bounds__(kBlock) long_rows_kernel(int64_t nlong, const int32_t* __restrict__ long_rows,
                                                            const int32_t* __restrict__ long_first,
-                                                           const double* __restrict__ partial, Op op) {
+                                                           const typename Pol::A* __restrict__ partial, Op op) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nlong || lane != 0) return;
-    double acc = 0.0;
-    for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc += partial[s];
+    typename Pol::A acc = Pol::zero();
+    for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc = Pol::combine(acc, partial[s]);
     op(long_rows[w], acc);
 }
 
-__global__ void forward_init_kernel(int64_t n, int64_t u, double a, const uint32_t* __restrict__ in_rp,
+// ---------------------------------------------------------------- level 0
+
+__global__ void forward_init_kernel(int64_t n, int64_t u, double a, const double* __restrict__ inv_din,
                                     double* __restrict__ pi0, double* __restrict__ x0) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double p = 0.0, xv = 0.0;
+        pi0[i] = i == u ? a : 0.0;
+        x0[i] = i == u ? a * inv_din[i] : 0.0;
+    }
+}
+
+__global__ void forward_init32_kernel(int64_t n, int64_t u, float a, const uint32_t* __restrict__ in_rp,
+                                      float* __restrict__ pi0, float* __restrict__ x0) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float p = 0.f, xv = 0.f;
         if (i == u) {
             p = a;
             const uint32_t d = in_rp[i + 1] - in_rp[i];
-            xv = d ? a / (double)d : 0.0;
+            xv = d ? __fdiv_rn(a, (float)d) : 0.f;
         }
         pi0[i] = p;
         x0[i] = xv;
@@ -128,6 +232,21 @@ __global__ void reverse_init_kernel(int64_t n, double a, const double* __restric
         s0[i] = dhat[i] * h[i] / a;
 }
 
+// w = D^ / a as two-floats, and s^0 = w pi^L (float2, or FP64 when L = 0)
+__global__ void reverse_init2f_kernel(int64_t n, double inv_a, const double* __restrict__ dhat,
+                                      const float* __restrict__ h, float2* __restrict__ w, float2* __restrict__ s0,
+                                      double* __restrict__ s_final) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const f2 wv = f2_from_double(dhat[i] * inv_a);
+        w[i] = make_float2(wv.hi, wv.lo);
+        const f2 s = f2_mul_f(wv, h[i]);
+        if (s_final) s_final[i] = f2_to_double(s);
+        else s0[i] = make_float2(s.hi, s.lo);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
 namespace {
 
 int elementwise_blocks(const Graph& g, int64_t n) {
@@ -137,8 +256,10 @@ int elementwise_blocks(const Graph& g, int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
-template <int G, class Op>
-cudaError_t sweep_level_g(const Graph& g, const DevCsr& A, const double* x, const Op& op, double* partial) {
+template <class Pol, int G, class Op>
+cudaError_t sweep_level_g(const Graph& g, const DevCsr& A, const typename Pol::V* x, const Op& op) {
+    using Acc = typename Pol::A;
+    Acc* partial = reinterpret_cast<Acc*>(g.partial);
     int64_t rows_per_block = kBlock / G;
     int64_t sb = (g.n + rows_per_block - 1) / rows_per_block;
     int64_t cap = (int64_t)g.sm_count * 16;
@@ -146,27 +267,33 @@ cudaError_t sweep_level_g(const Graph& g, const DevCsr& A, const double* x, cons
     if (sb < 1) sb = 1;
     int64_t segb = A.nseg;
     if (segb > (int64_t)g.sm_count * 16) segb = (int64_t)g.sm_count * 16;
-    rows_kernel<G, Op><<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, x, A.long_min, op, A.nseg,
-                                                                       A.seg, partial, (int)sb);
+    rows_kernel<Pol, G, Op><<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, x, A.long_min, op, A.nseg,
+                                                                            A.seg, partial, (int)sb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (A.nlong > 0) {
         int64_t blocks = (A.nlong * 32 + kBlock - 1) / kBlock;
-        long_rows_kernel<Op><<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.nlong, A.long_rows, A.long_first, partial, op);
+        long_rows_kernel<Pol, Op><<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.nlong, A.long_rows, A.long_first,
+                                                                             partial, op);
         e = cudaGetLastError();
     }
     return e;
 }
 
-template <class Op>
-cudaError_t sweep_level(const Graph& g, const DevCsr& A, const double* x, const Op& op, double* partial) {
+template <class Pol, class Op>
+cudaError_t sweep_level(const Graph& g, const DevCsr& A, const typename Pol::V* x, const Op& op) {
     switch (A.group) {
-        case 2: return sweep_level_g<2>(g, A, x, op, partial);
-        case 4: return sweep_level_g<4>(g, A, x, op, partial);
-        case 8: return sweep_level_g<8>(g, A, x, op, partial);
-        case 16: return sweep_level_g<16>(g, A, x, op, partial);
-        default: return sweep_level_g<32>(g, A, x, op, partial);
+        case 2: return sweep_level_g<Pol, 2>(g, A, x, op);
+        case 4: return sweep_level_g<Pol, 4>(g, A, x, op);
+        case 8: return sweep_level_g<Pol, 8>(g, A, x, op);
+        case 16: return sweep_level_g<Pol, 16>(g, A, x, op);
+        default: return sweep_level_g<Pol, 32>(g, A, x, op);
     }
+}
+
+f2 host_f2(double v) {
+    const float h = (float)v;
+    return f2{h, (float)(v - (double)h)};
 }
 
 }  // namespace
@@ -174,15 +301,15 @@ cudaError_t sweep_level(const Graph& g, const DevCsr& A, const double* x, const 
 cudaError_t launch_forward(const Graph& g, int64_t u, double c, int32_t L, double* hist, double* xa, double* xb) {
     const double sc = sqrt(c);
     const double a = 1.0 - sc;
-    forward_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, a, g.in.rp, hist, xa);
+    forward_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, a, g.inv_din, hist, xa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double* x[2] = {xa, xb};
     for (int32_t l = 1; l <= L; ++l) {
         const double* xp = x[(l - 1) & 1];
         double* xn = x[l & 1];
-        ForwardOp op{sc, g.in.rp, hist + (size_t)l * (size_t)g.n, xn};
-        e = sweep_level(g, g.out, xp, op, g.partial);
+        ForwardOp op{sc, g.inv_din, hist + (size_t)l * (size_t)g.n, xn};
+        e = sweep_level<Pol64>(g, g.out, xp, op);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -201,8 +328,49 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
     for (int32_t l = 1; l <= L; ++l) {
         const double* sp = buf[(L - l + 1) & 1];
         double* sn = buf[(L - l) & 1];
-        ReverseOp op{sc, a, g.in.rp, dhat, hist + (size_t)(L - l) * g.n, sn};
-        e = sweep_level(g, g.in, sp, op, g.partial);
+        ReverseOp op{sc, a, g.inv_din, dhat, hist + (size_t)(L - l) * g.n, sn};
+        e = sweep_level<Pol64>(g, g.in, sp, op);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb) {
+    const double sc = sqrt(c);
+    const float a = (float)(1.0 - sc);
+    forward_init32_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, a, g.in.rp, hist, xa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    float* x[2] = {xa, xb};
+    const f2 sc2 = host_f2(sc);
+    for (int32_t l = 1; l <= L; ++l) {
+        ForwardOp32c op{sc2, g.in.rp, hist + (size_t)l * (size_t)g.n, x[l & 1]};
+        e = sweep_level<Pol32c>(g, g.out, x[(l - 1) & 1], op);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_reverse32(const Graph& g, const float* hist, int32_t L, double c, const double* dhat,
+                             double* s_out, float2* w, float2* sa, float2* sb) {
+    const double sc = sqrt(c);
+    const double a = 1.0 - sc;
+    float2* buf[2] = {sa, sb};
+    reverse_init2f_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(
+        g.n, 1.0 / a, dhat, hist + (size_t)L * g.n, w, buf[0], L == 0 ? s_out : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const f2 sc2 = host_f2(sc);
+    for (int32_t l = 1; l <= L; ++l) {
+        const float2* sp = buf[(l - 1) & 1];
+        const float* h = hist + (size_t)(L - l) * g.n;
+        if (l < L) {
+            ReverseOp2f<false> op{sc2, g.in.rp, w, h, buf[l & 1], nullptr};
+            e = sweep_level<Pol2f>(g, g.in, sp, op);
+        } else {
+            ReverseOp2f<true> op{sc2, g.in.rp, w, h, nullptr, s_out};
+            e = sweep_level<Pol2f>(g, g.in, sp, op);
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
