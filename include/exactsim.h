@@ -129,6 +129,8 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
  *                    query returns ESIM_EBUDGET without running walks
  *   "timing"         1: record per-phase CUDA event times in the stats
+ *   "batch_tile"     -1: batched sweeps pick their tile by timing (default);
+ *                    0, 1, 2: force 32, 16 or 8 lanes per row (results do not change)
  *   "precision"      0: FP64 sweeps (default);
  *                    1: FP32c, the precision form -- pi^l and x^l stored in FP32
  *                    with two-float (compensated) row sums, s^l stored and summed
@@ -158,6 +160,30 @@ esim_status esim_topk(esim_graph* g, int64_t u, double c, double eps, uint64_t s
 /* As esim_topk with device outputs. */
 esim_status esim_topk_device(esim_graph* g, int64_t u, double c, double eps, uint64_t seed, int32_t k,
                              int32_t* ids_dev, double* scores_dev);
+
+/* Batched queries (B <= 64 sources, each with its own eps, one launch sequence).
+ * The sweeps become sparse-matrix x dense-matrix products over an n x W block
+ * (W = 32 for B <= 32, else 64), in the precision form (FP32 storage, two-float
+ * sums, FP64 output).  Column q runs Algorithm 1 with its own depth
+ * L_q = ceil(log_{1/c}(2/eps[q])) (levels above L_q are zero) and its own
+ * R_b = kappa ln(n)/eps[q]^2.  All columns draw their walk pairs from the one
+ * seed: pair r of node k is the same pair in every column and in a single query
+ * with that seed.  A column's result does not depend on the other columns of the
+ * batch (each column sums a row's entries in the same fixed order whatever the
+ * batch or the tile shape), so a query gives bit-identical results alone (B = 1)
+ * and in any mix.  s_out[B * n] is query-major: s_out[q * n + v].
+ * Errors: ESIM_EINVAL, ESIM_ENOTSUP (B > 64, k > 4096), ESIM_EBUDGET, ESIM_ENOMEM,
+ * ESIM_ECUDA. */
+esim_status esim_query_batch(esim_graph* g, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
+                             double* s_out);
+esim_status esim_query_batch_device(esim_graph* g, int32_t B, const int64_t* u, const double* eps, uint64_t seed,
+                                    double c, double* s_dev);
+/* Batched top-k: ids_out[B * k], scores_out[B * k] (row q holds query q's top-k,
+ * ordered (score desc, id asc), its source left out unless "exclude_source" is 0). */
+esim_status esim_topk_batch(esim_graph* g, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
+                            int32_t k, int32_t* ids_out, double* scores_out);
+esim_status esim_topk_batch_device(esim_graph* g, int32_t B, const int64_t* u, const double* eps, uint64_t seed,
+                                   double c, int32_t k, int32_t* ids_dev, double* scores_dev);
 
 /* Statistics of the last whole query on g. */
 esim_status esim_last_stats(const esim_graph* g, esim_query_stats* out);

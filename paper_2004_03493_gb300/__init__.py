@@ -28,6 +28,10 @@ from ._native import (  # noqa: F401
     esim_num_edges,
     esim_num_nodes,
     esim_query,
+    esim_query_batch,
+    esim_query_batch_device,
+    esim_topk_batch,
+    esim_topk_batch_device,
     esim_query_device,
     esim_reverse,
     esim_sample,
@@ -99,6 +103,28 @@ class Graph:
 
     def topk_device(self, u: int, c: float, eps: float, k: int, seed: int, ids_out, vals_out):
         esim_topk_device(self.handle, u, c, eps, seed, k, ids_out, vals_out)
+        return ids_out, vals_out
+
+    def query_batch(self, u, eps, c: float, seed: int = 0) -> np.ndarray:
+        """Scores of a batch of sources, shape (B, n)."""
+        u = np.asarray(u, dtype=np.int64)
+        out = np.empty((u.size, self.n), dtype=np.float64)
+        esim_query_batch(self.handle, u, eps, seed, c, out)
+        return out
+
+    def query_batch_device(self, u, eps, c: float, seed: int, out):
+        esim_query_batch_device(self.handle, u, eps, seed, c, out)
+        return out
+
+    def topk_batch(self, u, eps, c: float, k: int, seed: int = 0):
+        u = np.asarray(u, dtype=np.int64)
+        ids = np.empty((u.size, k), dtype=np.int32)
+        vals = np.empty((u.size, k), dtype=np.float64)
+        esim_topk_batch(self.handle, u, eps, seed, c, k, ids, vals)
+        return ids, vals
+
+    def topk_batch_device(self, u, eps, c: float, k: int, seed: int, ids_out, vals_out):
+        esim_topk_batch_device(self.handle, u, eps, seed, c, k, ids_out, vals_out)
         return ids_out, vals_out
 
     def stats(self) -> dict:

@@ -75,6 +75,10 @@ SIGNATURES = {
     "esim_forward_f32": (_ST, [_P, _I64, _D, _I32, _P]),
     "esim_allocate_f32": (_ST, [_P, _P, _I32, _D, _I32, _P, _P, _P]),
     "esim_reverse_f32": (_ST, [_P, _P, _I32, _D, _P, _P]),
+    "esim_query_batch": (_ST, [_P, _I32, _P, _P, _U64, _D, _P]),
+    "esim_query_batch_device": (_ST, [_P, _I32, _P, _P, _U64, _D, _P]),
+    "esim_topk_batch": (_ST, [_P, _I32, _P, _P, _U64, _D, _I32, _P, _P]),
+    "esim_topk_batch_device": (_ST, [_P, _I32, _P, _P, _U64, _D, _I32, _P, _P]),
 }
 
 
@@ -210,6 +214,38 @@ def esim_topk(g: int, u: int, c: float, eps: float, seed: int, k: int, ids_out: 
 def esim_topk_device(g: int, u: int, c: float, eps: float, seed: int, k: int, ids_dev, scores_dev) -> None:
     _check(lib().esim_topk_device(g, u, c, eps, seed, k, _ptr(ids_dev, "int32", device=True),
                                   _ptr(scores_dev, "float64", device=True)))
+
+
+def _batch_params(u, eps):
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    if u.shape != eps.shape or u.ndim != 1:
+        raise ValueError("u and eps must be 1-D arrays of the same length")
+    return u, eps
+
+
+def esim_query_batch(g: int, u, eps, seed: int, c: float, s_out: np.ndarray) -> None:
+    u, eps = _batch_params(u, eps)
+    _check(lib().esim_query_batch(g, u.size, u.ctypes.data, eps.ctypes.data, seed, c,
+                                  _ptr(s_out, "float64", device=False)))
+
+
+def esim_query_batch_device(g: int, u, eps, seed: int, c: float, s_dev) -> None:
+    u, eps = _batch_params(u, eps)
+    _check(lib().esim_query_batch_device(g, u.size, u.ctypes.data, eps.ctypes.data, seed, c,
+                                         _ptr(s_dev, "float64", device=True)))
+
+
+def esim_topk_batch(g: int, u, eps, seed: int, c: float, k: int, ids_out: np.ndarray, scores_out: np.ndarray) -> None:
+    u, eps = _batch_params(u, eps)
+    _check(lib().esim_topk_batch(g, u.size, u.ctypes.data, eps.ctypes.data, seed, c, k,
+                                 _ptr(ids_out, "int32", device=False), _ptr(scores_out, "float64", device=False)))
+
+
+def esim_topk_batch_device(g: int, u, eps, seed: int, c: float, k: int, ids_dev, scores_dev) -> None:
+    u, eps = _batch_params(u, eps)
+    _check(lib().esim_topk_batch_device(g, u.size, u.ctypes.data, eps.ctypes.data, seed, c, k,
+                                        _ptr(ids_dev, "int32", device=True), _ptr(scores_dev, "float64", device=True)))
 
 
 def esim_last_stats(g: int) -> dict:

@@ -117,6 +117,7 @@ void release(Graph& g) {
     cudaFree(g.status);
     if (g.status_host) cudaFreeHost(g.status_host);
     cudaFree(g.ws);
+    cudaFree(g.bws);
     cudaFree(g.partial);
     cudaFree(g.scan_part);
     cudaFree(g.norm_part);
@@ -295,6 +296,240 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     return ESIM_OK;
 }
 
+
+constexpr int kBatchMax = 64;
+
+// Batch workspace (its own arena).
+struct BWs {
+    float* hist;      // (Lmax+1) n W
+    float* xa;        // n W
+    float* xb;        // n W
+    float2* w;        // n W
+    float2* sa;       // n W
+    float2* sb;       // n W
+    void* partial;    // nseg_max W two-floats
+    uint64_t* R;      // B n
+    uint64_t* off;    // B n + 1
+    uint64_t* nonmeet;// B n
+    double* dhat;     // B n
+    double* s;        // B n
+    int64_t* u;       // W
+    int32_t* L;       // W
+    double* Rb;       // W
+    unsigned long long* part_R;  // tiles of B n
+    double* part_norm;
+    double* part_Rd;
+    void* topk;       // batched top-k state
+    int32_t* ids;     // B k (host staging)
+    double* vals;     // B k
+};
+
+size_t bws_layout(int64_t n_, int W, int B, int32_t Lmax, int64_t nseg_max, int k, char* base, BWs* out) {
+    const size_t n = (size_t)n_, nw = n * (size_t)W, bn = n * (size_t)B;
+    size_t o = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + o : nullptr;
+        o += round256(bytes);
+        return p;
+    };
+    BWs t{};
+    t.hist = (float*)take(4 * nw * (size_t)(Lmax + 1));
+    t.xa = (float*)take(4 * nw);
+    t.xb = (float*)take(4 * nw);
+    t.w = (float2*)take(8 * nw);
+    t.sa = (float2*)take(8 * nw);
+    t.sb = (float2*)take(8 * nw);
+    t.partial = take(8 * (size_t)std::max<int64_t>(1, nseg_max) * (size_t)W);
+    t.R = (uint64_t*)take(8 * bn);
+    t.off = (uint64_t*)take(8 * (bn + 1));
+    t.nonmeet = (uint64_t*)take(8 * bn);
+    t.dhat = (double*)take(8 * bn);
+    t.s = (double*)take(8 * bn);
+    t.u = (int64_t*)take(8 * W);
+    t.L = (int32_t*)take(4 * W);
+    t.Rb = (double*)take(8 * W);
+    const size_t nb = (size_t)allocate_blocks((int64_t)bn);
+    t.part_R = (unsigned long long*)take(8 * nb);
+    t.part_norm = (double*)take(8 * nb);
+    t.part_Rd = (double*)take(8 * nb);
+    t.topk = take(topk_batch_workspace_bytes(B));
+    t.ids = (int32_t*)take(4 * (size_t)B * (size_t)std::max(k, 1));
+    t.vals = (double*)take(8 * (size_t)B * (size_t)std::max(k, 1));
+    if (out) *out = t;
+    return o;
+}
+
+esim_status ensure_bws(Graph& g, int W, int B, int32_t Lmax, int k, BWs& w) {
+    const int64_t nseg_max = std::max(g.in.nseg, g.out.nseg);
+    const size_t need = bws_layout(g.n, W, B, Lmax, nseg_max, k, nullptr, nullptr);
+    if (need > g.bws_bytes) {
+        cudaStreamSynchronize(g.stream);
+        cudaFree(g.bws);
+        g.bws = nullptr;
+        g.bws_bytes = 0;
+        if (cudaMalloc(&g.bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ESIM_ENOMEM, "cudaMalloc(batch workspace of " + std::to_string(need) + " bytes)");
+        }
+        g.bws_bytes = need;
+    }
+    bws_layout(g.n, W, B, Lmax, nseg_max, k, (char*)g.bws, &w);
+    return ESIM_OK;
+}
+
+// Autotune: time each tile shape on one forward and one reverse level of the live
+// batch (the results are identical for every tile, so the timing runs are harmless).
+esim_status tune_batch_tiles(Graph& g, int W, int B, double c, const BWs& w) {
+    const int wi = W == 32 ? 0 : 1;
+    if (g.batch_tile_force >= 0) {
+        g.batch_tile_fwd[wi] = g.batch_tile_rev[wi] = g.batch_tile_force;
+        return ESIM_OK;
+    }
+    if (g.batch_tile_fwd[wi] >= 0) return ESIM_OK;
+    cudaEvent_t e0, e1;
+    ESIM_CUDA_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+    ESIM_CUDA_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+    const size_t nw = (size_t)g.n * W;
+    float best_f = 1e30f, best_r = 1e30f;
+    for (int t = 0; t < batch_tile_count(); ++t) {
+        for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+            cudaEventRecord(e0, g.stream);
+            ESIM_CUDA_TRY(launch_batch_forward_level(g, W, t, 1, c, w.L, w.xa, w.hist + nw, w.xb, w.partial),
+                          "batch tune forward");
+            cudaEventRecord(e1, g.stream);
+            ESIM_CUDA_TRY(cudaEventSynchronize(e1), "batch tune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1) {
+                g.batch_tune_ms[wi][0][t] = ms;
+                if (ms < best_f) { best_f = ms; g.batch_tile_fwd[wi] = t; }
+            }
+            cudaEventRecord(e0, g.stream);
+            ESIM_CUDA_TRY(launch_batch_reverse_level(g, W, B, t, false, c, w.w, w.hist, w.sa, w.sb, nullptr, w.partial),
+                          "batch tune reverse");
+            cudaEventRecord(e1, g.stream);
+            ESIM_CUDA_TRY(cudaEventSynchronize(e1), "batch tune");
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1) {
+                g.batch_tune_ms[wi][1][t] = ms;
+                if (ms < best_r) { best_r = ms; g.batch_tile_rev[wi] = t; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ESIM_OK;
+}
+
+esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
+                      double* s_dev, double* s_host, int32_t k, int32_t* ids_dev, double* vals_dev, int32_t* ids_host,
+                      double* vals_host) {
+    if (B < 1) return fail(ESIM_EINVAL, "need B >= 1");
+    if (B > kBatchMax) return fail(ESIM_ENOTSUP, "B above 64: split the batch");
+    if (!u || !eps) return fail(ESIM_EINVAL, "NULL u or eps");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
+    int32_t Lq[kBatchMax];
+    double Rb[kBatchMax];
+    int64_t uq[kBatchMax];
+    int32_t Lmax = 0;
+    const double kappa = g.kappa;
+    for (int q = 0; q < kBatchMax; ++q) {
+        Lq[q] = -1;
+        Rb[q] = 0.0;
+        uq[q] = -1;
+    }
+    for (int q = 0; q < B; ++q) {
+        if (u[q] < 0 || u[q] >= g.n) return fail(ESIM_EINVAL, "source node out of range");
+        if (!valid_c_eps(c, eps[q])) return fail(ESIM_EINVAL, "need 0 < eps < 1");
+        Lq[q] = esim_levels(c, eps[q]);
+        Rb[q] = kappa_of(g, c) * log((double)g.n) / (eps[q] * eps[q]);
+        uq[q] = u[q];
+        Lmax = std::max(Lmax, Lq[q]);
+    }
+    (void)kappa;
+    const int W = B <= 32 ? 32 : 64;
+    const int wi = W == 32 ? 0 : 1;
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    BWs w;
+    esim_status st = ensure_bws(g, W, B, Lmax, k, w);
+    if (st != ESIM_OK) return st;
+    const size_t nw = (size_t)g.n * W;
+    const int64_t N = g.n * (int64_t)B;
+    if (g.timing)
+        for (auto& ev : g.ev)
+            if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
+    ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.u, uq, sizeof(int64_t) * W, cudaMemcpyHostToDevice, g.stream), "upload sources");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.L, Lq, sizeof(int32_t) * W, cudaMemcpyHostToDevice, g.stream), "upload depths");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.Rb, Rb, sizeof(double) * W, cudaMemcpyHostToDevice, g.stream), "upload R_b");
+    if (g.timing) cudaEventRecord(g.ev[0], g.stream);
+    ESIM_CUDA_TRY(launch_batch_forward_init(g, W, B, w.u, c, w.hist, w.xa), "batch forward init");
+    if (Lmax >= 1) {
+        esim_status ts = tune_batch_tiles(g, W, B, c, w);
+        if (ts != ESIM_OK) return ts;
+    }
+    const int tf = g.batch_tile_fwd[wi] < 0 ? 0 : g.batch_tile_fwd[wi];
+    const int tr = g.batch_tile_rev[wi] < 0 ? 0 : g.batch_tile_rev[wi];
+    float* x[2] = {w.xa, w.xb};
+    for (int32_t l = 1; l <= Lmax; ++l)
+        ESIM_CUDA_TRY(launch_batch_forward_level(g, W, tf, l, c, w.L, x[(l - 1) & 1], w.hist + (size_t)l * nw,
+                                                 x[l & 1], w.partial),
+                      "batch forward level");
+    if (g.timing) cudaEventRecord(g.ev[1], g.stream);
+    ESIM_CUDA_TRY(launch_batch_alloc(g, W, B, w.hist, Lmax, w.Rb, g.alloc_mode, w.R), "batch allocation");
+    ESIM_CUDA_TRY(launch_scan_R(g, N, w.R, w.off, w.part_R, w.part_norm, w.part_Rd), "batch scan");
+    if (g.timing) cudaEventRecord(g.ev[2], g.stream);
+    ESIM_CUDA_TRY(launch_sample_segments(g, N, w.off, c, seed, w.nonmeet, nullptr), "batch walk pairs");
+    if (g.timing) cudaEventRecord(g.ev[3], g.stream);
+    ESIM_CUDA_TRY(launch_dhat_segments(g, N, w.nonmeet, w.off, w.dhat), "batch dhat");
+    double* s = s_dev ? s_dev : w.s;
+    ESIM_CUDA_TRY(launch_batch_reverse_init(g, W, B, w.dhat, c, w.hist + (size_t)Lmax * nw, w.w, w.sa,
+                                            Lmax == 0 ? s : nullptr),
+                  "batch reverse init");
+    float2* sb[2] = {w.sa, w.sb};
+    for (int32_t l = 1; l <= Lmax; ++l)
+        ESIM_CUDA_TRY(launch_batch_reverse_level(g, W, B, tr, l == Lmax, c, w.w, w.hist + (size_t)(Lmax - l) * nw,
+                                                 sb[(l - 1) & 1], sb[l & 1], s, w.partial),
+                      "batch reverse level");
+    if (g.timing) cudaEventRecord(g.ev[4], g.stream);
+    if (k > 0) {
+        int32_t* ids = ids_dev ? ids_dev : w.ids;
+        double* vals = vals_dev ? vals_dev : w.vals;
+        ESIM_CUDA_TRY(launch_topk_batch(g, B, s, g.exclude_source ? w.u : nullptr, k, ids, vals, w.topk), "batch top-k");
+        if (ids_host) {
+            ESIM_CUDA_TRY(cudaMemcpyAsync(ids_host, ids, sizeof(int32_t) * (size_t)B * k, cudaMemcpyDeviceToHost,
+                                          g.stream), "copy ids");
+            ESIM_CUDA_TRY(cudaMemcpyAsync(vals_host, vals, sizeof(double) * (size_t)B * k, cudaMemcpyDeviceToHost,
+                                          g.stream), "copy scores");
+        }
+    }
+    if (g.timing) cudaEventRecord(g.ev[5], g.stream);
+    if (s_host)
+        ESIM_CUDA_TRY(cudaMemcpyAsync(s_host, s, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, g.stream),
+                      "copy scores");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(g.status_host, g.status, sizeof(Status), cudaMemcpyDeviceToHost, g.stream),
+                  "copy status");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "batch query");
+    const Status hs = *g.status_host;
+    g.last_L = Lmax;
+    g.last_launches = 1 + Lmax * (1 + (g.out.nlong > 0 ? 1 : 0)) + 1 + 3 + 1 + 1 + 1 +
+                      Lmax * (1 + (g.in.nlong > 0 ? 1 : 0)) + (k > 0 ? 27 : 0);
+    g.last_R_b = Rb[0];
+    g.last_kappa = kappa_of(g, c);
+    g.last_norm2 = 0.0;
+    g.last_sum_R = hs.sum_R;
+    g.last_steps = hs.pair_steps;
+    for (float& x : g.last_ms) x = 0.f;
+    if (g.timing) {
+        for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
+        cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
+    }
+    if (hs.err & kErrBudget)
+        return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
+    return ESIM_OK;
+}
+
 }  // namespace
 
 int esim::set_error(int status, const std::string& message) {
@@ -440,6 +675,11 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "timing") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "timing must be 0 or 1");
         g.timing = (int)value;
+    } else if (k == "batch_tile") {
+        if (value != -1.0 && value != 0.0 && value != 1.0 && value != 2.0)
+            return fail(ESIM_EINVAL, "batch_tile must be -1 (autotune), 0, 1 or 2");
+        g.batch_tile_force = (int)value;
+        g.batch_tile_fwd[0] = g.batch_tile_fwd[1] = g.batch_tile_rev[0] = g.batch_tile_rev[1] = -1;
     } else if (k == "precision") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
         g.precision = (int)value;
@@ -460,6 +700,11 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "pair_budget") *value = g.pair_budget;
     else if (k == "timing") *value = g.timing;
     else if (k == "precision") *value = g.precision;
+    else if (k == "batch_tile") *value = g.batch_tile_force;
+    else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[0];
+    else if (k == "batch_tile_fwd64") *value = g.batch_tile_fwd[1];
+    else if (k == "batch_tile_rev32") *value = g.batch_tile_rev[0];
+    else if (k == "batch_tile_rev64") *value = g.batch_tile_rev[1];
     else return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     return ESIM_OK;
 }
@@ -629,6 +874,36 @@ esim_status esim_reverse_f32(esim_graph* h, const float* hist, int32_t L, double
     if (st != ESIM_OK) return st;
     ESIM_CUDA_TRY(launch_reverse32(g, hist, L, c, dhat, s_out, w.w2, w.sa2, w.sb2), "reverse sweeps (FP32c)");
     return ESIM_OK;
+}
+
+esim_status esim_query_batch(esim_graph* h, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
+                             double* s_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!s_out) return fail(ESIM_EINVAL, "s_out is NULL");
+    return run_batch(h->g, B, u, eps, seed, c, nullptr, s_out, 0, nullptr, nullptr, nullptr, nullptr);
+}
+
+esim_status esim_query_batch_device(esim_graph* h, int32_t B, const int64_t* u, const double* eps, uint64_t seed,
+                                    double c, double* s_dev) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (!s_dev) return fail(ESIM_EINVAL, "s_dev is NULL");
+    return run_batch(h->g, B, u, eps, seed, c, s_dev, nullptr, 0, nullptr, nullptr, nullptr, nullptr);
+}
+
+esim_status esim_topk_batch(esim_graph* h, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
+                            int32_t k, int32_t* ids_out, double* scores_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
+    if (!ids_out || !scores_out) return fail(ESIM_EINVAL, "NULL output");
+    return run_batch(h->g, B, u, eps, seed, c, nullptr, nullptr, k, nullptr, nullptr, ids_out, scores_out);
+}
+
+esim_status esim_topk_batch_device(esim_graph* h, int32_t B, const int64_t* u, const double* eps, uint64_t seed,
+                                   double c, int32_t k, int32_t* ids_dev, double* scores_dev) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
+    if (!ids_dev || !scores_dev) return fail(ESIM_EINVAL, "NULL output");
+    return run_batch(h->g, B, u, eps, seed, c, nullptr, nullptr, k, ids_dev, scores_dev, nullptr, nullptr);
 }
 
 esim_status esim_sync(esim_graph* h) {

@@ -63,6 +63,13 @@ struct Graph {
     double pair_budget = 1e15;
     int timing = 0;
     int precision = 0;            // 0: FP64 sweeps; 1: FP32 storage with two-float sums (FP32c)
+    // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
+    void* bws = nullptr;
+    size_t bws_bytes = 0;
+    int batch_tile_fwd[2] = {-1, -1};
+    int batch_tile_rev[2] = {-1, -1};
+    int batch_tile_force = -1;    // option "batch_tile": -1 autotune, else 0..2
+    float batch_tune_ms[2][2][3] = {};
     // workspace
     Status* status = nullptr;     // device
     Status* status_host = nullptr; // pinned host copy
@@ -100,15 +107,39 @@ cudaError_t launch_allocate32(const Graph& g, const float* hist, int32_t L, doub
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
                           uint64_t* pair_steps);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
+// batches: nseg = B * n segments, segment q*n + k = node k of column q
+cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
+                                   uint64_t* nonmeet, uint64_t* pair_steps);
+cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
+                                 double* dhat);
+cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
+                          double* part_norm, double* part_Rd);
 uint32_t walk_threshold(double c);
 
 // capi.cu: record a message for esim_last_error() and return `status` (as an esim_status int)
 int set_error(int status, const std::string& message);
+
+// batch.cu
+int batch_tile_count();
+int batch_tile_lpr(int tile);
+cudaError_t launch_batch_forward_init(const Graph& g, int W, int B, const int64_t* u, double c, float* hist0, float* x0);
+cudaError_t launch_batch_forward_level(const Graph& g, int W, int tile, int level, double c, const int32_t* Lq,
+                                       const float* x_prev, float* hist_l, float* x_next, void* partial);
+cudaError_t launch_batch_alloc(const Graph& g, int W, int B, const float* hist, int32_t Lmax, const double* Rb,
+                               int mode, uint64_t* R);
+cudaError_t launch_batch_reverse_init(const Graph& g, int W, int B, const double* dhat, double c, const float* hL,
+                                      float2* w, float2* s0, double* s_out_if_final);
+cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, bool final_level, double c,
+                                       const float2* w, const float* h, const float2* s_prev, float2* s_next,
+                                       double* s_out, void* partial);
 
 // topk.cu
 constexpr int kTopkMax = 4096;
 size_t topk_workspace_bytes(int64_t n);
 cudaError_t launch_topk(const Graph& g, const double* scores, int64_t exclude, int32_t k, int32_t* ids_out,
                         double* vals_out, void* ws);
+size_t topk_batch_workspace_bytes(int32_t B);
+cudaError_t launch_topk_batch(const Graph& g, int32_t B, const double* scores, const int64_t* exclude, int32_t k,
+                              int32_t* ids_out, double* vals_out, void* ws);
 
 }  // namespace esim

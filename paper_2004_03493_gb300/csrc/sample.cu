@@ -240,8 +240,10 @@ __device__ __forceinline__ uint32_t pick_redraw(uint32_t d, unsigned long long m
 
 // State of one walk pair stream: the thread's current node k, pair r of R(k)
 // (rk), the two walk positions, the step t, and the pairs still to run.
+// A segment is the run of pairs of one (column, node): in a single query segment k
+// is node k; in a batch of B columns segment q*n + k is node k of column q.
 struct PairState {
-    unsigned long long r, rk, left, cnt, g_end;
+    unsigned long long r, rk, left, cnt, g_end, seg;
     uint32_t k, xa, xb, t;
 };
 
@@ -252,7 +254,7 @@ struct PairState {
 __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict__ row,
                                           const int32_t* __restrict__ col, const uint64_t* __restrict__ off,
                                           uint32_t T, const PhiloxKeys& K, unsigned long long* __restrict__ nonmeet,
-                                          unsigned long long& steps) {
+                                          unsigned long long& steps, unsigned long long n_nodes) {
     const uint32_t rlo = (uint32_t)S.r, rhi = (uint32_t)(S.r >> 32);
     const uint4 w = philox4x32_10(make_uint4(rlo, rhi, S.k, S.t), K);
     const uint2 ra = __ldg(row + S.xa), rb = __ldg(row + S.xb);  // (first in-edge, din)
@@ -278,19 +280,20 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
     S.cnt += meet ? 0ull : 1ull;
     S.t = 0;
     if (--S.left == 0) {
-        if (S.cnt) atomicAdd(nonmeet + S.k, S.cnt);
+        if (S.cnt) atomicAdd(nonmeet + S.seg, S.cnt);
         S.cnt = 0;
         return;
     }
-    if (++S.r == S.rk) {  // node k is done: flush and move to the next node with pairs
-        if (S.cnt) atomicAdd(nonmeet + S.k, S.cnt);
+    if (++S.r == S.rk) {  // segment done: flush and move to the next segment with pairs
+        if (S.cnt) atomicAdd(nonmeet + S.seg, S.cnt);
         S.cnt = 0;
         const unsigned long long g = S.g_end - S.left;
         do {
-            ++S.k;
-        } while (__ldg(off + S.k + 1) <= g);
+            ++S.seg;
+        } while (__ldg(off + S.seg + 1) <= g);
         S.r = 0;
-        S.rk = __ldg(off + S.k + 1) - __ldg(off + S.k);
+        S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
+        S.k = (uint32_t)(S.seg < n_nodes ? S.seg : S.seg % n_nodes);
         S.xa = S.xb = S.k;
     }
 }
@@ -300,7 +303,7 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
 // step per loop iteration, so a lane whose pair ended starts its next pair at
 // once and lanes stay busy.  Counts stay in registers while the node does not
 // change and are flushed with one atomic add per (thread, node).
-__global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, const uint2* __restrict__ row,
+__global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int64_t nseg, const uint2* __restrict__ row,
                                                                  const int32_t* __restrict__ col,
                                                                  const uint64_t* __restrict__ off, uint32_t T,
                                                                  const __grid_constant__ PhiloxKeys K, double budget,
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, cons
                                                                  unsigned long long* __restrict__ steps_out,
                                                                  Status* __restrict__ st) {
     __shared__ unsigned long long red[kBlock / 32];
-    const unsigned long long total = off[n];
+    const unsigned long long total = off[nseg];
     if ((double)total > budget || (st->err & kErrBudget)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->err, kErrBudget);
         return;
@@ -324,18 +327,19 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, cons
     S.t = 0;
     unsigned long long steps = 0;
     if (S.left) {
-        int64_t lo = 0, hi = n;  // node of pair g0: off[k] <= g0 < off[k+1]
+        int64_t lo = 0, hi = nseg;  // segment of pair g0: off[seg] <= g0 < off[seg+1]
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (__ldg(off + mid) <= g0) lo = mid; else hi = mid;
         }
-        S.k = (uint32_t)lo;
-        S.r = g0 - __ldg(off + S.k);
-        S.rk = __ldg(off + S.k + 1) - __ldg(off + S.k);
+        S.seg = (unsigned long long)lo;
+        S.k = (uint32_t)(lo < n ? lo : lo % n);
+        S.r = g0 - __ldg(off + S.seg);
+        S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
         S.xa = S.xb = S.k;
         for (;;) {
             if (!S.left) break;
-            pair_step(S, row, col, off, T, K, nonmeet, steps);
+            pair_step(S, row, col, off, T, K, nonmeet, steps, (unsigned long long)n);
         }
     }
     steps = block_sum(steps, red);
@@ -354,7 +358,12 @@ static int g_sample_blocks_per_sm = 0;
 
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
                           uint64_t* pair_steps) {
-    cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)g.n, g.stream);
+    return launch_sample_segments(g, g.n, off, c, seed, nonmeet, pair_steps);
+}
+
+cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
+                                   uint64_t* nonmeet, uint64_t* pair_steps) {
+    cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)nseg, g.stream);
     if (e != cudaSuccess) return e;
     unsigned long long* steps = pair_steps ? (unsigned long long*)pair_steps : &g.status->pair_steps;
     if (pair_steps) {
@@ -368,16 +377,61 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
         g_sample_blocks_per_sm = b > 0 ? b : 1;
     }
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
-    sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, g.in.info, g.in.col, off, walk_threshold(c),
+    sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, nseg, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
                                                          (unsigned long long*)nonmeet, steps, g.status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat) {
-    int64_t b = (g.n + kBlock - 1) / kBlock;
+    return launch_dhat_segments(g, g.n, nonmeet, off, dhat);
+}
+
+cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
+                                 double* dhat) {
+    int64_t b = (nseg + kBlock - 1) / kBlock;
     if (b > (int64_t)g.sm_count * 8) b = (int64_t)g.sm_count * 8;
-    dhat_kernel<<<(unsigned)(b < 1 ? 1 : b), kBlock, 0, g.stream>>>(g.n, nonmeet, off, dhat);
+    dhat_kernel<<<(unsigned)(b < 1 ? 1 : b), kBlock, 0, g.stream>>>(nseg, nonmeet, off, dhat);
+    return cudaGetLastError();
+}
+
+// Scan of a ready R array of N segments (batches): tile sums, tile offsets, off[].
+__global__ void __launch_bounds__(kBlock) tile_sums_kernel(int64_t N, const uint64_t* __restrict__ R,
+                                                           unsigned long long* __restrict__ part_R,
+                                                           double* __restrict__ part_Rd) {
+    __shared__ unsigned long long red_u[kBlock / 32];
+    __shared__ double red_d[kBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * kAllocTile;
+    unsigned long long su = 0;
+    double sd = 0.0;
+    for (int i = 0; i < kAllocItems; ++i) {
+        const int64_t k = base + (int64_t)i * kBlock + threadIdx.x;
+        if (k < N) {
+            su += R[k];
+            sd += (double)R[k];
+        }
+    }
+    su = block_sum(su, red_u);
+    sd = block_sum(sd, red_d);
+    if (threadIdx.x == 0) {
+        part_R[blockIdx.x] = su;
+        part_Rd[blockIdx.x] = sd;
+    }
+}
+
+cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
+                          double* part_norm, double* part_Rd) {
+    const int64_t nb = allocate_blocks(N);
+    cudaError_t e = cudaMemsetAsync(part_norm, 0, sizeof(double) * (size_t)nb, g.stream);
+    if (e != cudaSuccess) return e;
+    tile_sums_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(N, R, part_R, part_Rd);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    alloc_partials_kernel<<<1, kScanThreads, 0, g.stream>>>(nb, part_R, part_norm, part_Rd, g.pair_budget, off + N,
+                                                            g.status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    alloc_scan_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(N, R, part_R, off);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,10 @@ __device__ __forceinline__ int cmp_prefix(unsigned long long hi, unsigned lo, co
     return a < b ? -1 : (a > b ? 1 : 0);
 }
 
+// Every kernel below handles one column per blockIdx.y (select/sort: blockIdx.x);
+// a single selection is the one-column case.
 __global__ void topk_init_kernel(TopkState* st, unsigned k) {
+    st += blockIdx.x;
     const int t = threadIdx.x;
     if (t == 0) {
         st->pre_hi = 0;
@@ -77,8 +80,12 @@ __global__ void topk_init_kernel(TopkState* st, unsigned k) {
 }
 
 __global__ void __launch_bounds__(kBlock) topk_hist_kernel(int64_t n, const double* __restrict__ scores,
-                                                           int64_t exclude, TopkState* __restrict__ st, int d) {
+                                                           int64_t exclude, TopkState* __restrict__ st, int d,
+                                                           int64_t col_stride, const int64_t* __restrict__ excl) {
     __shared__ unsigned int h[256];
+    scores += (int64_t)blockIdx.y * col_stride;
+    st += blockIdx.y;
+    if (excl) exclude = excl[blockIdx.y];
     if (st->done) return;
     for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
     __syncthreads();
@@ -104,6 +111,7 @@ __global__ void __launch_bounds__(kBlock) topk_hist_kernel(int64_t n, const doub
 }
 
 __global__ void topk_select_kernel(TopkState* st, int d) {
+    st += blockIdx.x;
     if (threadIdx.x != 0 || st->done) return;
     unsigned total = 0;
     for (int b = 0; b < 256; ++b) total += st->hist[b];
@@ -132,7 +140,12 @@ __global__ void topk_select_kernel(TopkState* st, int d) {
 
 __global__ void __launch_bounds__(kBlock) topk_gather_kernel(int64_t n, const double* __restrict__ scores,
                                                              int64_t exclude, TopkState* __restrict__ st,
-                                                             Cand* __restrict__ cand, unsigned cap) {
+                                                             Cand* __restrict__ cand, unsigned cap, int64_t col_stride,
+                                                             const int64_t* __restrict__ excl) {
+    scores += (int64_t)blockIdx.y * col_stride;
+    st += blockIdx.y;
+    cand += (size_t)blockIdx.y * cap;
+    if (excl) exclude = excl[blockIdx.y];
     const TopkState s = *st;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (i == exclude) continue;
@@ -148,8 +161,13 @@ __global__ void __launch_bounds__(kBlock) topk_gather_kernel(int64_t n, const do
 // two >= k) keys live in dynamic shared memory: P * 12 bytes <= 48 KB.
 __global__ void __launch_bounds__(1024) topk_sort_kernel(const TopkState* __restrict__ st,
                                                          const Cand* __restrict__ cand, int k, int P,
-                                                         int32_t* __restrict__ ids_out, double* __restrict__ vals_out) {
+                                                         int32_t* __restrict__ ids_out, double* __restrict__ vals_out,
+                                                         unsigned cap) {
     extern __shared__ unsigned long long sm_hi[];
+    st += blockIdx.x;
+    cand += (size_t)blockIdx.x * cap;
+    ids_out += (size_t)blockIdx.x * k;
+    vals_out += (size_t)blockIdx.x * k;
     unsigned* sm_lo = (unsigned*)(sm_hi + P);
     unsigned cnt = st->count;
     if (cnt > (unsigned)k) cnt = (unsigned)k;  // cannot happen for unique keys; guards the buffer
@@ -205,15 +223,48 @@ cudaError_t launch_topk(const Graph& g, const double* scores, int64_t exclude, i
     if (blocks > (int64_t)g.sm_count * 4) blocks = (int64_t)g.sm_count * 4;
     if (blocks < 1) blocks = 1;
     for (int d = 0; d < 12; ++d) {
-        topk_hist_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(g.n, scores, exclude, st, d);
+        topk_hist_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(g.n, scores, exclude, st, d, 0, nullptr);
         topk_select_kernel<<<1, 32, 0, g.stream>>>(st, d);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    topk_gather_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(g.n, scores, exclude, st, cand, (unsigned)kTopkMax);
+    topk_gather_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(g.n, scores, exclude, st, cand, (unsigned)kTopkMax, 0,
+                                                                  nullptr);
     int P = 1;
     while (P < k) P <<= 1;
-    topk_sort_kernel<<<1, 1024, (size_t)P * 12, g.stream>>>(st, cand, k, P, ids_out, vals_out);
+    topk_sort_kernel<<<1, 1024, (size_t)P * 12, g.stream>>>(st, cand, k, P, ids_out, vals_out, (unsigned)kTopkMax);
+    return cudaGetLastError();
+}
+
+size_t topk_batch_workspace_bytes(int32_t B) {
+    return ((sizeof(TopkState) * (size_t)B + 255) / 256) * 256 + sizeof(Cand) * (size_t)kTopkMax * (size_t)B;
+}
+
+// B independent selections: column q of scores starts at scores + q * n; exclude[q]
+// (device, may be NULL for none) is left out of column q.
+cudaError_t launch_topk_batch(const Graph& g, int32_t B, const double* scores, const int64_t* exclude, int32_t k,
+                              int32_t* ids_out, double* vals_out, void* ws) {
+    TopkState* st = (TopkState*)ws;
+    Cand* cand = (Cand*)((char*)ws + ((sizeof(TopkState) * (size_t)B + 255) / 256) * 256);
+    topk_init_kernel<<<(unsigned)B, 256, 0, g.stream>>>(st, (unsigned)k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (g.n + kBlock - 1) / kBlock;
+    int64_t cap = ((int64_t)g.sm_count * 4 + B - 1) / B;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    const dim3 grid((unsigned)blocks, (unsigned)B);
+    for (int d = 0; d < 12; ++d) {
+        topk_hist_kernel<<<grid, kBlock, 0, g.stream>>>(g.n, scores, -1, st, d, g.n, exclude);
+        topk_select_kernel<<<(unsigned)B, 32, 0, g.stream>>>(st, d);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    topk_gather_kernel<<<grid, kBlock, 0, g.stream>>>(g.n, scores, -1, st, cand, (unsigned)kTopkMax, g.n, exclude);
+    int P = 1;
+    while (P < k) P <<= 1;
+    topk_sort_kernel<<<(unsigned)B, 1024, (size_t)P * 12, g.stream>>>(st, cand, k, P, ids_out, vals_out,
+                                                                     (unsigned)kTopkMax);
     return cudaGetLastError();
 }
 
@@ -303,13 +354,14 @@ extern "C" __attribute__((visibility("default"))) esim_status esim_select_topk_s
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
     if (blocks < 1) blocks = 1;
     for (int d = 0; d < 12; ++d) {
-        topk_hist_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, d);
+        topk_hist_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, d, 0, nullptr);
         topk_select_kernel<<<1, 32, 0, st>>>(state, d);
     }
-    topk_gather_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, cand, (unsigned)kTopkMax);
+    topk_gather_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(n, scores, exclude, state, cand, (unsigned)kTopkMax, 0,
+                                                              nullptr);
     int P = 1;
     while (P < k) P <<= 1;
-    topk_sort_kernel<<<1, 1024, (size_t)P * 12, st>>>(state, cand, k, P, ids_out, vals_out);
+    topk_sort_kernel<<<1, 1024, (size_t)P * 12, st>>>(state, cand, k, P, ids_out, vals_out, (unsigned)kTopkMax);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(ESIM_ECUDA, std::string("static top-k launch: ") + cudaGetErrorString(e));
     return ESIM_OK;
