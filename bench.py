@@ -40,6 +40,9 @@ WORKLOADS = {
                    sources=10, source_seed=7, k=50),
     "er2000": dict(kind="erdos_renyi", n=2000, m=20_000, graph_seed=1, c=0.6, eps=1e-4, sources=1,
                    source_seed=0, k=50),
+    # batched form: 64 sources per launch, eps log-uniform in [1e-7, 1e-4]
+    "rmat20": dict(kind="rmat", scale=20, n=1 << 20, m=30_000_000, graph_seed=1, c=0.6, eps_lo=1e-7, eps_hi=1e-4,
+                   eps=1e-4, sources=64, source_seed=7, k=100),
     # precision form: FP32c against FP64 sweeps on the same sources and the same D^
     "cl4m": dict(kind="chung_lu", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
                  sources=4, source_seed=7, k=50),
@@ -68,6 +71,8 @@ def sweep_level_bytes(n, m, precision):
 
 def make_graph(w):
     import synth
+    if w["kind"] == "rmat":
+        return synth.rmat(w["scale"], w["m"], seed=w["graph_seed"])
     if w["kind"] == "chung_lu":
         return synth.chung_lu(w["n"], w["m"], gamma=w["gamma"], seed=w["graph_seed"])
     return synth.erdos_renyi(w["n"], w["m"], seed=w["graph_seed"])
@@ -277,6 +282,80 @@ def run_precision(args, w):
     g.close()
 
 
+def run_batched(args, w):
+    """Batched FP32c queries (64 per launch) against plain FP64 single queries, same sources, eps, seed, kappa."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+    n, rp, col = make_graph(w)
+    rng = np.random.default_rng(w["source_seed"] + 1)
+    srcs = sources_for(w, rp, 1, 0)
+    eps = np.exp(rng.uniform(np.log(w["eps_lo"]), np.log(w["eps_hi"]), size=len(srcs)))
+    c, k = w["c"], w["k"]
+    gb = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
+    gs = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
+    stream = torch.cuda.current_stream()
+    gb.set_stream(stream)
+    gs.set_stream(stream)
+    B = len(srcs)
+    ids = torch.empty(B * k, dtype=torch.int32, device="cuda")
+    vals = torch.empty(B * k, dtype=torch.float64, device="cuda")
+    ids1 = torch.empty(k, dtype=torch.int32, device="cuda")
+    vals1 = torch.empty(k, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def batch():
+        gb.topk_batch_device(srcs, eps, c, k, 1, ids, vals)
+
+    def singles():
+        for q in range(B):
+            gs.topk_device(srcs[q], c, float(eps[q]), k, 1, ids1, vals1)
+
+    tb, ts, bstats = [], [], []
+    for i in range(args.warmup + args.steps):
+        a = timed(batch)
+        st = gb.stats()
+        b = timed(singles)
+        if i >= args.warmup:
+            tb.append(a)
+            ts.append(b)
+            bstats.append(st)
+    # accuracy of the batched form against the plain FP64 single queries on the same walks
+    sb = gb.query_batch(srcs[:8], eps[:8], c, seed=1)
+    diffs = [float(np.max(np.abs(sb[q] - gs.query(srcs[q], c, float(eps[q]), 1)))) for q in range(8)]
+    qb = B / (statistics.mean(tb) / 1000.0)
+    qs = B / (statistics.mean(ts) / 1000.0)
+    line = {"metric": "top-k queries/s, batched FP32c (64 per launch) vs plain FP64 single queries", "value": qb,
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32+two-float", "data": "synthetic",
+            "config": {"workload": "rmat20", "graph": "rmat", "n": n, "m": len(col), "abcd": [0.57, 0.19, 0.19, 0.05],
+                       "c": c, "eps": "log-uniform [1e-7, 1e-4]", "sources_per_launch": B, "top_k": k,
+                       "kappa": args.kappa, "l2": "flushed (512 MB write) before each timed step",
+                       "batch_tile_fwd": gb.get_option("batch_tile_fwd64"),
+                       "batch_tile_rev": gb.get_option("batch_tile_rev64")},
+            "batched_fp32c_qps": qb, "single_fp64_qps": qs, "speedup": qb / qs,
+            "batched_phases_ms": {p: statistics.mean(s_[f"ms_{p}"] for s_ in bstats)
+                                  for p in ("forward", "allocate", "sample", "reverse", "topk")},
+            "max_abs_diff_batched_vs_single_first8": max(diffs),
+            "note": "both forms draw the same walk pairs (one seed); the difference is FP32c rounding plus "
+                    "the sampling noise of R(k) decided from FP32 pi"}
+    print(json.dumps(line), flush=True)
+    gb.close()
+    gs.close()
+
+
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources_per_step": w["sources"],
@@ -307,6 +386,9 @@ def main():
         return
     if args.workload == "cl4m":
         run_precision(args, w)
+        return
+    if args.workload == "rmat20":
+        run_batched(args, w)
         return
 
     import torch
