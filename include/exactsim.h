@@ -185,6 +185,57 @@ esim_status esim_topk_batch(esim_graph* g, int32_t B, const int64_t* u, const do
 esim_status esim_topk_batch_device(esim_graph* g, int32_t B, const int64_t* u, const double* eps, uint64_t seed,
                                    double c, int32_t k, int32_t* ids_dev, double* scores_dev);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop over one resident graph with continuous batching.  Requests
+ * (u, eps) enter a queue; a scheduler thread forms waves of up to max_batch
+ * requests and runs each wave as a batched query (esim_topk_batch) on its own
+ * CUDA stream and workspace.  Up to max_waves waves are in flight, admitted while
+ * their workspaces fit mem_budget_bytes; when a wave completes its slots and
+ * memory go to the next queued requests, so requests that arrive while others
+ * run start as soon as a slot set frees, and the waves' kernels overlap on the
+ * device.  A request's result is bit-identical to the same request served alone.
+ * While a server runs it owns the graph: make no other call on that graph handle.
+ * Every wait is bounded; no device-side wait exists. */
+typedef struct esim_server esim_server;
+
+typedef struct {
+    double c;                /* decay factor, 0 < c < 1 */
+    double kappa;            /* sample constant to set on the graph; 0 keeps the graph's option */
+    uint64_t seed;           /* walk stream shared by all requests */
+    int32_t k;               /* top-k of every request, 1..4096 */
+    int32_t max_batch;       /* requests per wave, 1..64 */
+    int32_t max_waves;       /* waves in flight, 1..8 (one CUDA stream each) */
+    int32_t reserved;
+    double mem_budget_bytes; /* device memory for wave workspaces; <= 0: 80 % of the free memory */
+} esim_server_config;
+
+typedef struct {
+    uint64_t completed;      /* requests answered */
+    uint64_t failed;         /* requests that ended with an error (or were cancelled) */
+    uint64_t waves;          /* waves launched */
+    double mean_batch;       /* requests per wave */
+    double p50_ms;           /* latency from submit to completion, over completed requests */
+    double p99_ms;
+    double max_ms;
+    int32_t max_running;     /* most requests on the GPU at once */
+    int32_t queued;          /* requests waiting now */
+} esim_server_stats;
+
+esim_status esim_server_create(esim_graph* g, const esim_server_config* cfg, esim_server** out);
+/* Queue a top-k query of source u with error eps; *id_out identifies it. */
+esim_status esim_server_submit(esim_server* s, int64_t u, double eps, uint64_t* id_out);
+/* *state: 0 queued, 1 running, 2 done, 3 failed. */
+esim_status esim_server_poll(esim_server* s, uint64_t id, int32_t* state);
+/* Wait up to timeout_ms for request id; on success copies its k ids and scores
+ * (either may be NULL) and its latency, and forgets the request.  ESIM_ETIMEOUT
+ * if it is not finished in time (it stays known); the request's own error if it
+ * failed. */
+esim_status esim_server_wait(esim_server* s, uint64_t id, int32_t timeout_ms, int32_t* ids_out, double* scores_out,
+                             double* latency_ms);
+esim_status esim_server_get_stats(esim_server* s, esim_server_stats* out);
+/* Cancel queued requests, let running waves finish, release everything. */
+void esim_server_destroy(esim_server* s);
+
 /* Statistics of the last whole query on g. */
 esim_status esim_last_stats(const esim_graph* g, esim_query_stats* out);
 

@@ -40,6 +40,12 @@ from ._native import (  # noqa: F401
     esim_select_topk_static,
     esim_set_option,
     esim_set_stream,
+    esim_server_create,
+    esim_server_destroy,
+    esim_server_get_stats,
+    esim_server_poll,
+    esim_server_submit,
+    esim_server_wait,
     esim_sync,
     esim_topk,
     esim_topk_device,
@@ -160,6 +166,48 @@ class Graph:
 
     def sync(self):
         esim_sync(self.handle)
+
+
+class Server:
+    """Continuous-batching request loop over a loaded Graph (top-k queries)."""
+
+    def __init__(self, graph: Graph, c: float, k: int, seed: int = 0, kappa: float = 0.0, max_batch: int = 64,
+                 max_waves: int = 2, mem_budget_bytes: float = 0.0):
+        self.graph = graph
+        self.k = int(k)
+        self.handle = esim_server_create(graph.handle, c, k, seed, kappa, max_batch, max_waves, mem_budget_bytes)
+
+    def submit(self, u: int, eps: float) -> int:
+        return esim_server_submit(self.handle, int(u), float(eps))
+
+    def poll(self, rid: int) -> int:
+        return esim_server_poll(self.handle, rid)
+
+    def wait(self, rid: int, timeout_ms: int = 60000):
+        ids = np.empty(self.k, dtype=np.int32)
+        vals = np.empty(self.k, dtype=np.float64)
+        lat = esim_server_wait(self.handle, rid, timeout_ms, ids, vals)
+        return ids, vals, lat
+
+    def stats(self) -> dict:
+        return esim_server_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            esim_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build(force: bool = False) -> str:

@@ -38,6 +38,21 @@ class QueryStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ }
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("kappa", ctypes.c_double), ("seed", ctypes.c_uint64), ("k", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_waves", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("waves", ctypes.c_uint64),
+                ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("max_running", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -79,6 +94,12 @@ SIGNATURES = {
     "esim_query_batch_device": (_ST, [_P, _I32, _P, _P, _U64, _D, _P]),
     "esim_topk_batch": (_ST, [_P, _I32, _P, _P, _U64, _D, _I32, _P, _P]),
     "esim_topk_batch_device": (_ST, [_P, _I32, _P, _P, _U64, _D, _I32, _P, _P]),
+    "esim_server_create": (_ST, [_P, ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    "esim_server_submit": (_ST, [_P, _I64, _D, ctypes.POINTER(_U64)]),
+    "esim_server_poll": (_ST, [_P, _U64, ctypes.POINTER(_I32)]),
+    "esim_server_wait": (_ST, [_P, _U64, _I32, _P, _P, ctypes.POINTER(_D)]),
+    "esim_server_get_stats": (_ST, [_P, ctypes.POINTER(ServerStats)]),
+    "esim_server_destroy": (None, [_P]),
 }
 
 
@@ -246,6 +267,43 @@ def esim_topk_batch_device(g: int, u, eps, seed: int, c: float, k: int, ids_dev,
     u, eps = _batch_params(u, eps)
     _check(lib().esim_topk_batch_device(g, u.size, u.ctypes.data, eps.ctypes.data, seed, c, k,
                                         _ptr(ids_dev, "int32", device=True), _ptr(scores_dev, "float64", device=True)))
+
+
+def esim_server_create(g: int, c: float, k: int, seed: int = 0, kappa: float = 0.0, max_batch: int = 64,
+                       max_waves: int = 2, mem_budget_bytes: float = 0.0) -> int:
+    cfg = ServerConfig(c, kappa, seed, k, max_batch, max_waves, 0, mem_budget_bytes)
+    out = _P()
+    _check(lib().esim_server_create(g, ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def esim_server_submit(s: int, u: int, eps: float) -> int:
+    rid = _U64()
+    _check(lib().esim_server_submit(s, u, eps, ctypes.byref(rid)))
+    return rid.value
+
+
+def esim_server_poll(s: int, rid: int) -> int:
+    st = _I32()
+    _check(lib().esim_server_poll(s, rid, ctypes.byref(st)))
+    return st.value
+
+
+def esim_server_wait(s: int, rid: int, timeout_ms: int, ids_out: np.ndarray, scores_out: np.ndarray) -> float:
+    lat = _D()
+    _check(lib().esim_server_wait(s, rid, timeout_ms, _ptr(ids_out, "int32", device=False),
+                                  _ptr(scores_out, "float64", device=False), ctypes.byref(lat)))
+    return lat.value
+
+
+def esim_server_get_stats(s: int) -> dict:
+    st = ServerStats()
+    _check(lib().esim_server_get_stats(s, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def esim_server_destroy(s: int) -> None:
+    lib().esim_server_destroy(s)
 
 
 def esim_last_stats(g: int) -> dict:

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libexactsim.so")
 
-SOURCES = ["capi.cu", "sweep.cu", "sample.cu", "topk.cu", "batch.cu"]
+SOURCES = ["capi.cu", "sweep.cu", "sample.cu", "topk.cu", "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
         flags = [f for f in FLAGS]
-        if src == "capi.cu":
+        if src in ("capi.cu", "server.cu"):
             i = flags.index("-fvisibility=hidden")
             del flags[i - 1:i + 1]
         cmd = [cc, *ARCH, *flags, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]

@@ -301,25 +301,28 @@ cudaError_t batch_level(const Graph& g, const DevCsr& A, const V* X, const Op& o
 
 }  // namespace
 
-// Tile shapes: lanes per row for W = 32 (CPL = 32/LPR) and W = 64 (CPL = 64/LPR).
+// Tile shapes: lanes per row (the rest of the columns go to each lane): for W >= 32
+// the tiles are 32, 16 and 8 lanes per row; for W = 16 they are 16, 8 and 4.
 int batch_tile_count() { return 3; }
 int batch_tile_lpr(int tile) { return tile == 0 ? 32 : (tile == 1 ? 16 : 8); }
 
 template <int W>
 cudaError_t batch_level_dispatch_fwd(const Graph& g, int tile, const float* X, const BFwdOp& op, f2* partial) {
+    constexpr int L0 = W >= 32 ? 32 : 16;
     switch (tile) {
-        case 0: return batch_level<float, 32, W / 32>(g, g.out, X, op, partial);
-        case 1: return batch_level<float, 16, W / 16>(g, g.out, X, op, partial);
-        default: return batch_level<float, 8, W / 8>(g, g.out, X, op, partial);
+        case 0: return batch_level<float, L0, W / L0>(g, g.out, X, op, partial);
+        case 1: return batch_level<float, L0 / 2, W / (L0 / 2)>(g, g.out, X, op, partial);
+        default: return batch_level<float, L0 / 4, W / (L0 / 4)>(g, g.out, X, op, partial);
     }
 }
 
 template <int W, bool kFinal>
 cudaError_t batch_level_dispatch_rev(const Graph& g, int tile, const float2* S, const BRevOp<kFinal>& op, f2* partial) {
+    constexpr int L0 = W >= 32 ? 32 : 16;
     switch (tile) {
-        case 0: return batch_level<float2, 32, W / 32>(g, g.in, S, op, partial);
-        case 1: return batch_level<float2, 16, W / 16>(g, g.in, S, op, partial);
-        default: return batch_level<float2, 8, W / 8>(g, g.in, S, op, partial);
+        case 0: return batch_level<float2, L0, W / L0>(g, g.in, S, op, partial);
+        case 1: return batch_level<float2, L0 / 2, W / (L0 / 2)>(g, g.in, S, op, partial);
+        default: return batch_level<float2, L0 / 4, W / (L0 / 4)>(g, g.in, S, op, partial);
     }
 }
 
@@ -328,6 +331,7 @@ cudaError_t launch_batch_forward_level(const Graph& g, int W, int tile, int leve
     const double sc = sqrt(c);
     const f2 sc2 = f2{(float)sc, (float)(sc - (double)(float)sc)};
     BFwdOp op{sc2, level, Lq, g.in.rp, hist_l, x_next, W};
+    if (W == 16) return batch_level_dispatch_fwd<16>(g, tile, x_prev, op, (f2*)partial);
     if (W == 32) return batch_level_dispatch_fwd<32>(g, tile, x_prev, op, (f2*)partial);
     return batch_level_dispatch_fwd<64>(g, tile, x_prev, op, (f2*)partial);
 }
@@ -339,10 +343,12 @@ cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, b
     const f2 sc2 = f2{(float)sc, (float)(sc - (double)(float)sc)};
     if (final_level) {
         BRevOp<true> op{sc2, g.in.rp, w, h, nullptr, s_out, W, B, g.n};
+        if (W == 16) return batch_level_dispatch_rev<16, true>(g, tile, s_prev, op, (f2*)partial);
         if (W == 32) return batch_level_dispatch_rev<32, true>(g, tile, s_prev, op, (f2*)partial);
         return batch_level_dispatch_rev<64, true>(g, tile, s_prev, op, (f2*)partial);
     }
     BRevOp<false> op{sc2, g.in.rp, w, h, s_next, nullptr, W, B, g.n};
+    if (W == 16) return batch_level_dispatch_rev<16, false>(g, tile, s_prev, op, (f2*)partial);
     if (W == 32) return batch_level_dispatch_rev<32, false>(g, tile, s_prev, op, (f2*)partial);
     return batch_level_dispatch_rev<64, false>(g, tile, s_prev, op, (f2*)partial);
 }

@@ -297,7 +297,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
 }
 
 
-constexpr int kBatchMax = 64;
+// ---------------------------------------------------------------- batches
 
 // Batch workspace (its own arena).
 struct BWs {
@@ -320,7 +320,7 @@ struct BWs {
     double* part_norm;
     double* part_Rd;
     void* topk;       // batched top-k state
-    int32_t* ids;     // B k (host staging)
+    int32_t* ids;     // B k (staging)
     double* vals;     // B k
 };
 
@@ -359,28 +359,10 @@ size_t bws_layout(int64_t n_, int W, int B, int32_t Lmax, int64_t nseg_max, int 
     return o;
 }
 
-esim_status ensure_bws(Graph& g, int W, int B, int32_t Lmax, int k, BWs& w) {
-    const int64_t nseg_max = std::max(g.in.nseg, g.out.nseg);
-    const size_t need = bws_layout(g.n, W, B, Lmax, nseg_max, k, nullptr, nullptr);
-    if (need > g.bws_bytes) {
-        cudaStreamSynchronize(g.stream);
-        cudaFree(g.bws);
-        g.bws = nullptr;
-        g.bws_bytes = 0;
-        if (cudaMalloc(&g.bws, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ESIM_ENOMEM, "cudaMalloc(batch workspace of " + std::to_string(need) + " bytes)");
-        }
-        g.bws_bytes = need;
-    }
-    bws_layout(g.n, W, B, Lmax, nseg_max, k, (char*)g.bws, &w);
-    return ESIM_OK;
-}
-
 // Autotune: time each tile shape on one forward and one reverse level of the live
 // batch (the results are identical for every tile, so the timing runs are harmless).
-esim_status tune_batch_tiles(Graph& g, int W, int B, double c, const BWs& w) {
-    const int wi = W == 32 ? 0 : 1;
+esim_status tune_batch_tiles(Graph& g, const Graph& view, int W, int B, double c, const BWs& w) {
+    const int wi = batch_wi(W);
     if (g.batch_tile_force >= 0) {
         g.batch_tile_fwd[wi] = g.batch_tile_rev[wi] = g.batch_tile_force;
         return ESIM_OK;
@@ -393,10 +375,10 @@ esim_status tune_batch_tiles(Graph& g, int W, int B, double c, const BWs& w) {
     float best_f = 1e30f, best_r = 1e30f;
     for (int t = 0; t < batch_tile_count(); ++t) {
         for (int rep = 0; rep < 2; ++rep) {  // first run warms up
-            cudaEventRecord(e0, g.stream);
-            ESIM_CUDA_TRY(launch_batch_forward_level(g, W, t, 1, c, w.L, w.xa, w.hist + nw, w.xb, w.partial),
+            cudaEventRecord(e0, view.stream);
+            ESIM_CUDA_TRY(launch_batch_forward_level(view, W, t, 1, c, w.L, w.xa, w.hist + nw, w.xb, w.partial),
                           "batch tune forward");
-            cudaEventRecord(e1, g.stream);
+            cudaEventRecord(e1, view.stream);
             ESIM_CUDA_TRY(cudaEventSynchronize(e1), "batch tune");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -404,10 +386,11 @@ esim_status tune_batch_tiles(Graph& g, int W, int B, double c, const BWs& w) {
                 g.batch_tune_ms[wi][0][t] = ms;
                 if (ms < best_f) { best_f = ms; g.batch_tile_fwd[wi] = t; }
             }
-            cudaEventRecord(e0, g.stream);
-            ESIM_CUDA_TRY(launch_batch_reverse_level(g, W, B, t, false, c, w.w, w.hist, w.sa, w.sb, nullptr, w.partial),
+            cudaEventRecord(e0, view.stream);
+            ESIM_CUDA_TRY(launch_batch_reverse_level(view, W, B, t, false, c, w.w, w.hist, w.sa, w.sb, nullptr,
+                                                     w.partial),
                           "batch tune reverse");
-            cudaEventRecord(e1, g.stream);
+            cudaEventRecord(e1, view.stream);
             ESIM_CUDA_TRY(cudaEventSynchronize(e1), "batch tune");
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 1) {
@@ -424,98 +407,34 @@ esim_status tune_batch_tiles(Graph& g, int W, int B, double c, const BWs& w) {
 esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, uint64_t seed, double c,
                       double* s_dev, double* s_host, int32_t k, int32_t* ids_dev, double* vals_dev, int32_t* ids_host,
                       double* vals_host) {
-    if (B < 1) return fail(ESIM_EINVAL, "need B >= 1");
-    if (B > kBatchMax) return fail(ESIM_ENOTSUP, "B above 64: split the batch");
-    if (!u || !eps) return fail(ESIM_EINVAL, "NULL u or eps");
-    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
-    if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
-    int32_t Lq[kBatchMax];
-    double Rb[kBatchMax];
-    int64_t uq[kBatchMax];
-    int32_t Lmax = 0;
-    const double kappa = g.kappa;
-    for (int q = 0; q < kBatchMax; ++q) {
-        Lq[q] = -1;
-        Rb[q] = 0.0;
-        uq[q] = -1;
-    }
-    for (int q = 0; q < B; ++q) {
-        if (u[q] < 0 || u[q] >= g.n) return fail(ESIM_EINVAL, "source node out of range");
-        if (!valid_c_eps(c, eps[q])) return fail(ESIM_EINVAL, "need 0 < eps < 1");
-        Lq[q] = esim_levels(c, eps[q]);
-        Rb[q] = kappa_of(g, c) * log((double)g.n) / (eps[q] * eps[q]);
-        uq[q] = u[q];
-        Lmax = std::max(Lmax, Lq[q]);
-    }
-    (void)kappa;
-    const int W = B <= 32 ? 32 : 64;
-    const int wi = W == 32 ? 0 : 1;
-    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
-    BWs w;
-    esim_status st = ensure_bws(g, W, B, Lmax, k, w);
+    BatchPlan plan;
+    esim_status st = (esim_status)batch_plan(g, B, u, eps, c, k, &plan);
     if (st != ESIM_OK) return st;
-    const size_t nw = (size_t)g.n * W;
-    const int64_t N = g.n * (int64_t)B;
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    const size_t need = batch_ws_bytes(g, plan);
+    if (need > g.bws_bytes) {
+        cudaStreamSynchronize(g.stream);
+        cudaFree(g.bws);
+        g.bws = nullptr;
+        g.bws_bytes = 0;
+        if (cudaMalloc(&g.bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ESIM_ENOMEM, "cudaMalloc(batch workspace of " + std::to_string(need) + " bytes)");
+        }
+        g.bws_bytes = need;
+    }
     if (g.timing)
         for (auto& ev : g.ev)
             if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
-    ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.u, uq, sizeof(int64_t) * W, cudaMemcpyHostToDevice, g.stream), "upload sources");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.L, Lq, sizeof(int32_t) * W, cudaMemcpyHostToDevice, g.stream), "upload depths");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.Rb, Rb, sizeof(double) * W, cudaMemcpyHostToDevice, g.stream), "upload R_b");
-    if (g.timing) cudaEventRecord(g.ev[0], g.stream);
-    ESIM_CUDA_TRY(launch_batch_forward_init(g, W, B, w.u, c, w.hist, w.xa), "batch forward init");
-    if (Lmax >= 1) {
-        esim_status ts = tune_batch_tiles(g, W, B, c, w);
-        if (ts != ESIM_OK) return ts;
-    }
-    const int tf = g.batch_tile_fwd[wi] < 0 ? 0 : g.batch_tile_fwd[wi];
-    const int tr = g.batch_tile_rev[wi] < 0 ? 0 : g.batch_tile_rev[wi];
-    float* x[2] = {w.xa, w.xb};
-    for (int32_t l = 1; l <= Lmax; ++l)
-        ESIM_CUDA_TRY(launch_batch_forward_level(g, W, tf, l, c, w.L, x[(l - 1) & 1], w.hist + (size_t)l * nw,
-                                                 x[l & 1], w.partial),
-                      "batch forward level");
-    if (g.timing) cudaEventRecord(g.ev[1], g.stream);
-    ESIM_CUDA_TRY(launch_batch_alloc(g, W, B, w.hist, Lmax, w.Rb, g.alloc_mode, w.R), "batch allocation");
-    ESIM_CUDA_TRY(launch_scan_R(g, N, w.R, w.off, w.part_R, w.part_norm, w.part_Rd), "batch scan");
-    if (g.timing) cudaEventRecord(g.ev[2], g.stream);
-    ESIM_CUDA_TRY(launch_sample_segments(g, N, w.off, c, seed, w.nonmeet, nullptr), "batch walk pairs");
-    if (g.timing) cudaEventRecord(g.ev[3], g.stream);
-    ESIM_CUDA_TRY(launch_dhat_segments(g, N, w.nonmeet, w.off, w.dhat), "batch dhat");
-    double* s = s_dev ? s_dev : w.s;
-    ESIM_CUDA_TRY(launch_batch_reverse_init(g, W, B, w.dhat, c, w.hist + (size_t)Lmax * nw, w.w, w.sa,
-                                            Lmax == 0 ? s : nullptr),
-                  "batch reverse init");
-    float2* sb[2] = {w.sa, w.sb};
-    for (int32_t l = 1; l <= Lmax; ++l)
-        ESIM_CUDA_TRY(launch_batch_reverse_level(g, W, B, tr, l == Lmax, c, w.w, w.hist + (size_t)(Lmax - l) * nw,
-                                                 sb[(l - 1) & 1], sb[l & 1], s, w.partial),
-                      "batch reverse level");
-    if (g.timing) cudaEventRecord(g.ev[4], g.stream);
-    if (k > 0) {
-        int32_t* ids = ids_dev ? ids_dev : w.ids;
-        double* vals = vals_dev ? vals_dev : w.vals;
-        ESIM_CUDA_TRY(launch_topk_batch(g, B, s, g.exclude_source ? w.u : nullptr, k, ids, vals, w.topk), "batch top-k");
-        if (ids_host) {
-            ESIM_CUDA_TRY(cudaMemcpyAsync(ids_host, ids, sizeof(int32_t) * (size_t)B * k, cudaMemcpyDeviceToHost,
-                                          g.stream), "copy ids");
-            ESIM_CUDA_TRY(cudaMemcpyAsync(vals_host, vals, sizeof(double) * (size_t)B * k, cudaMemcpyDeviceToHost,
-                                          g.stream), "copy scores");
-        }
-    }
-    if (g.timing) cudaEventRecord(g.ev[5], g.stream);
-    if (s_host)
-        ESIM_CUDA_TRY(cudaMemcpyAsync(s_host, s, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, g.stream),
-                      "copy scores");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(g.status_host, g.status, sizeof(Status), cudaMemcpyDeviceToHost, g.stream),
-                  "copy status");
+    st = (esim_status)batch_enqueue(g, g, plan, g.bws, seed, c, s_dev, s_host, ids_dev, vals_dev, ids_host, vals_host,
+                                   true);
+    if (st != ESIM_OK) return st;
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "batch query");
     const Status hs = *g.status_host;
-    g.last_L = Lmax;
-    g.last_launches = 1 + Lmax * (1 + (g.out.nlong > 0 ? 1 : 0)) + 1 + 3 + 1 + 1 + 1 +
-                      Lmax * (1 + (g.in.nlong > 0 ? 1 : 0)) + (k > 0 ? 27 : 0);
-    g.last_R_b = Rb[0];
+    g.last_L = plan.Lmax;
+    g.last_launches = 1 + plan.Lmax * (1 + (g.out.nlong > 0 ? 1 : 0)) + 1 + 3 + 1 + 1 + 1 +
+                      plan.Lmax * (1 + (g.in.nlong > 0 ? 1 : 0)) + (k > 0 ? 27 : 0);
+    g.last_R_b = plan.Rb[0];
     g.last_kappa = kappa_of(g, c);
     g.last_norm2 = 0.0;
     g.last_sum_R = hs.sum_R;
@@ -536,6 +455,117 @@ int esim::set_error(int status, const std::string& message) {
     t_err = message;
     return status;
 }
+
+namespace esim {
+
+Graph* graph_of(::esim_graph* h) { return &h->g; }
+
+int batch_width(int B) { return B <= 16 ? 16 : (B <= 32 ? 32 : 64); }
+int batch_wi(int W) { return W == 16 ? 0 : (W == 32 ? 1 : 2); }
+
+int batch_plan(const Graph& g, int32_t B, const int64_t* u, const double* eps, double c, int32_t k, BatchPlan* plan) {
+    if (B < 1) return fail(ESIM_EINVAL, "need B >= 1");
+    if (B > kBatchMax) return fail(ESIM_ENOTSUP, "B above 64: split the batch");
+    if (!u || !eps) return fail(ESIM_EINVAL, "NULL u or eps");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
+    BatchPlan p{};
+    p.B = B;
+    p.W = batch_width(B);
+    p.k = k;
+    p.Lmax = 0;
+    for (int q = 0; q < kBatchMax; ++q) {
+        p.Lq[q] = -1;
+        p.Rb[q] = 0.0;
+        p.u[q] = -1;
+    }
+    for (int q = 0; q < B; ++q) {
+        if (u[q] < 0 || u[q] >= g.n) return fail(ESIM_EINVAL, "source node out of range");
+        if (!valid_c_eps(c, eps[q])) return fail(ESIM_EINVAL, "need 0 < eps < 1");
+        p.Lq[q] = esim_levels(c, eps[q]);
+        p.Rb[q] = kappa_of(g, c) * log((double)g.n) / (eps[q] * eps[q]);
+        p.u[q] = u[q];
+        p.Lmax = std::max(p.Lmax, p.Lq[q]);
+    }
+    *plan = p;
+    return ESIM_OK;
+}
+
+size_t batch_ws_bytes(const Graph& g, const BatchPlan& p) {
+    return bws_layout(g.n, p.W, p.B, p.Lmax, std::max(g.in.nseg, g.out.nseg), p.k, nullptr, nullptr);
+}
+
+// Enqueue the whole batch on view.stream using the arena `ws`; results go to the
+// given device or host buffers (host copies are asynchronous).  The status block
+// view.status is reset first and copied to view.status_host last.
+int batch_enqueue(Graph& tuner, const Graph& view, const BatchPlan& p, void* ws, uint64_t seed, double c,
+                  double* s_dev, double* s_host, int32_t* ids_dev, double* vals_dev, int32_t* ids_host,
+                  double* vals_host, bool allow_tune) {
+    BWs w;
+    bws_layout(view.n, p.W, p.B, p.Lmax, std::max(view.in.nseg, view.out.nseg), p.k, (char*)ws, &w);
+    const int W = p.W, B = p.B, k = p.k;
+    const int32_t Lmax = p.Lmax;
+    const size_t nw = (size_t)view.n * W;
+    const int64_t N = view.n * (int64_t)B;
+    const cudaStream_t stream = view.stream;
+    const bool timing = view.timing && view.ev[0];
+    ESIM_CUDA_TRY(cudaMemsetAsync(view.status, 0, sizeof(Status), stream), "reset status");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.u, p.u, sizeof(int64_t) * W, cudaMemcpyHostToDevice, stream), "upload sources");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.L, p.Lq, sizeof(int32_t) * W, cudaMemcpyHostToDevice, stream), "upload depths");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.Rb, p.Rb, sizeof(double) * W, cudaMemcpyHostToDevice, stream), "upload R_b");
+    if (timing) cudaEventRecord(view.ev[0], stream);
+    ESIM_CUDA_TRY(launch_batch_forward_init(view, W, B, w.u, c, w.hist, w.xa), "batch forward init");
+    const int wi = batch_wi(W);
+    if (Lmax >= 1 && allow_tune) {
+        esim_status ts = (esim_status)tune_batch_tiles(tuner, view, W, B, c, w);
+        if (ts != ESIM_OK) return ts;
+    }
+    const int tf = tuner.batch_tile_fwd[wi] < 0 ? 0 : tuner.batch_tile_fwd[wi];
+    const int tr = tuner.batch_tile_rev[wi] < 0 ? 0 : tuner.batch_tile_rev[wi];
+    float* x[2] = {w.xa, w.xb};
+    for (int32_t l = 1; l <= Lmax; ++l)
+        ESIM_CUDA_TRY(launch_batch_forward_level(view, W, tf, l, c, w.L, x[(l - 1) & 1], w.hist + (size_t)l * nw,
+                                                 x[l & 1], w.partial),
+                      "batch forward level");
+    if (timing) cudaEventRecord(view.ev[1], stream);
+    ESIM_CUDA_TRY(launch_batch_alloc(view, W, B, w.hist, Lmax, w.Rb, view.alloc_mode, w.R), "batch allocation");
+    ESIM_CUDA_TRY(launch_scan_R(view, N, w.R, w.off, w.part_R, w.part_norm, w.part_Rd), "batch scan");
+    if (timing) cudaEventRecord(view.ev[2], stream);
+    ESIM_CUDA_TRY(launch_sample_segments(view, N, w.off, c, seed, w.nonmeet, nullptr), "batch walk pairs");
+    if (timing) cudaEventRecord(view.ev[3], stream);
+    ESIM_CUDA_TRY(launch_dhat_segments(view, N, w.nonmeet, w.off, w.dhat), "batch dhat");
+    double* s = s_dev ? s_dev : w.s;
+    ESIM_CUDA_TRY(launch_batch_reverse_init(view, W, B, w.dhat, c, w.hist + (size_t)Lmax * nw, w.w, w.sa,
+                                            Lmax == 0 ? s : nullptr),
+                  "batch reverse init");
+    float2* sb[2] = {w.sa, w.sb};
+    for (int32_t l = 1; l <= Lmax; ++l)
+        ESIM_CUDA_TRY(launch_batch_reverse_level(view, W, B, tr, l == Lmax, c, w.w, w.hist + (size_t)(Lmax - l) * nw,
+                                                 sb[(l - 1) & 1], sb[l & 1], s, w.partial),
+                      "batch reverse level");
+    if (timing) cudaEventRecord(view.ev[4], stream);
+    if (k > 0) {
+        int32_t* ids = ids_dev ? ids_dev : w.ids;
+        double* vals = vals_dev ? vals_dev : w.vals;
+        ESIM_CUDA_TRY(launch_topk_batch(view, B, s, view.exclude_source ? w.u : nullptr, k, ids, vals, w.topk),
+                      "batch top-k");
+        if (ids_host) {
+            ESIM_CUDA_TRY(cudaMemcpyAsync(ids_host, ids, sizeof(int32_t) * (size_t)B * k, cudaMemcpyDeviceToHost,
+                                          stream), "copy ids");
+            ESIM_CUDA_TRY(cudaMemcpyAsync(vals_host, vals, sizeof(double) * (size_t)B * k, cudaMemcpyDeviceToHost,
+                                          stream), "copy scores");
+        }
+    }
+    if (timing) cudaEventRecord(view.ev[5], stream);
+    if (s_host)
+        ESIM_CUDA_TRY(cudaMemcpyAsync(s_host, s, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, stream),
+                      "copy scores");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(view.status_host, view.status, sizeof(Status), cudaMemcpyDeviceToHost, stream),
+                  "copy status");
+    return ESIM_OK;
+}
+
+}  // namespace esim
 
 extern "C" {
 
@@ -679,7 +709,7 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
         if (value != -1.0 && value != 0.0 && value != 1.0 && value != 2.0)
             return fail(ESIM_EINVAL, "batch_tile must be -1 (autotune), 0, 1 or 2");
         g.batch_tile_force = (int)value;
-        g.batch_tile_fwd[0] = g.batch_tile_fwd[1] = g.batch_tile_rev[0] = g.batch_tile_rev[1] = -1;
+        for (int i = 0; i < 3; ++i) g.batch_tile_fwd[i] = g.batch_tile_rev[i] = -1;
     } else if (k == "precision") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
         g.precision = (int)value;
@@ -701,10 +731,12 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "timing") *value = g.timing;
     else if (k == "precision") *value = g.precision;
     else if (k == "batch_tile") *value = g.batch_tile_force;
-    else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[0];
-    else if (k == "batch_tile_fwd64") *value = g.batch_tile_fwd[1];
-    else if (k == "batch_tile_rev32") *value = g.batch_tile_rev[0];
-    else if (k == "batch_tile_rev64") *value = g.batch_tile_rev[1];
+    else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];
+    else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[1];
+    else if (k == "batch_tile_fwd64") *value = g.batch_tile_fwd[2];
+    else if (k == "batch_tile_rev16") *value = g.batch_tile_rev[0];
+    else if (k == "batch_tile_rev32") *value = g.batch_tile_rev[1];
+    else if (k == "batch_tile_rev64") *value = g.batch_tile_rev[2];
     else return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     return ESIM_OK;
 }

@@ -7,6 +7,8 @@
 
 #include <string>
 
+struct esim_graph;
+
 namespace esim {
 
 // Device-side error bits, accumulated in Status::err.
@@ -66,10 +68,10 @@ struct Graph {
     // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
     void* bws = nullptr;
     size_t bws_bytes = 0;
-    int batch_tile_fwd[2] = {-1, -1};
-    int batch_tile_rev[2] = {-1, -1};
+    int batch_tile_fwd[3] = {-1, -1, -1};  // per width W = 16, 32, 64
+    int batch_tile_rev[3] = {-1, -1, -1};
     int batch_tile_force = -1;    // option "batch_tile": -1 autotune, else 0..2
-    float batch_tune_ms[2][2][3] = {};
+    float batch_tune_ms[3][2][3] = {};
     // workspace
     Status* status = nullptr;     // device
     Status* status_host = nullptr; // pinned host copy
@@ -135,6 +137,25 @@ cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, b
 
 // topk.cu
 constexpr int kTopkMax = 4096;
+
+// capi.cu: batch planning and enqueueing (shared by the batch calls and the server)
+constexpr int kBatchMax = 64;
+struct BatchPlan {
+    int W, B, k;
+    int32_t Lmax;
+    int32_t Lq[kBatchMax];
+    double Rb[kBatchMax];
+    int64_t u[kBatchMax];
+};
+int batch_width(int B);
+int batch_wi(int W);
+int batch_plan(const Graph& g, int32_t B, const int64_t* u, const double* eps, double c, int32_t k, BatchPlan* plan);
+size_t batch_ws_bytes(const Graph& g, const BatchPlan& p);
+// the Graph behind a public handle
+Graph* graph_of(struct ::esim_graph* h);
+int batch_enqueue(Graph& tuner, const Graph& view, const BatchPlan& p, void* ws, uint64_t seed, double c,
+                  double* s_dev, double* s_host, int32_t* ids_dev, double* vals_dev, int32_t* ids_host,
+                  double* vals_host, bool allow_tune);
 size_t topk_workspace_bytes(int64_t n);
 cudaError_t launch_topk(const Graph& g, const double* scores, int64_t exclude, int32_t k, int32_t* ids_out,
                         double* vals_out, void* ws);
