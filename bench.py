@@ -43,6 +43,9 @@ WORKLOADS = {
     # batched form: 64 sources per launch, eps log-uniform in [1e-7, 1e-4]
     "rmat20": dict(kind="rmat", scale=20, n=1 << 20, m=30_000_000, graph_seed=1, c=0.6, eps_lo=1e-7, eps_hi=1e-4,
                    eps=1e-4, sources=64, source_seed=7, k=100),
+    # serving form: Poisson arrivals of top-100 queries, eps from {1e-5, 1e-6, 1e-7}
+    "rmat25": dict(kind="rmat_torch", scale=25, n=1 << 25, m=500_000_000, graph_seed=1, c=0.6,
+                   eps_set=(1e-5, 1e-6, 1e-7), eps=1e-6, sources=4096, source_seed=7, k=100),
     # precision form: FP32c against FP64 sweeps on the same sources and the same D^
     "cl4m": dict(kind="chung_lu", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
                  sources=4, source_seed=7, k=50),
@@ -73,6 +76,8 @@ def make_graph(w):
     import synth
     if w["kind"] == "rmat":
         return synth.rmat(w["scale"], w["m"], seed=w["graph_seed"])
+    if w["kind"] == "rmat_torch":
+        return synth.rmat_torch(w["scale"], w["m"], seed=w["graph_seed"], device="cuda")
     if w["kind"] == "chung_lu":
         return synth.chung_lu(w["n"], w["m"], gamma=w["gamma"], seed=w["graph_seed"])
     return synth.erdos_renyi(w["n"], w["m"], seed=w["graph_seed"])
@@ -356,6 +361,84 @@ def run_batched(args, w):
     gs.close()
 
 
+def run_serving(args, w):
+    """Continuous-batching server under Poisson arrivals: p50/p99 latency and queries/s per rate."""
+    import threading
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+    t_gen = time.perf_counter()
+    n, rp, col = make_graph(w)
+    torch.cuda.empty_cache()
+    t_gen = time.perf_counter() - t_gen
+    t_load = time.perf_counter()
+    g = esim.Graph(n, rp, col)
+    t_load = time.perf_counter() - t_load
+    m = len(col)
+    srcs = synth_sources(rp, w["sources"], w["source_seed"])
+    del rp, col
+    c, k = w["c"], w["k"]
+    rng = np.random.default_rng(11)
+    srv = esim.Server(g, c, k=k, seed=1, kappa=args.kappa, max_batch=args.max_batch, max_waves=args.max_waves)
+    # warm-up: one wave per width the run will use (tunes the batched tiles)
+    for u in srcs[:args.max_batch]:
+        srv.submit(int(u), 1e-5)
+    ids = np.empty(k, dtype=np.int32)
+    vals = np.empty(k, dtype=np.float64)
+    results = []
+    rates = [float(x) for x in args.rates.split(",")]
+    per_rate = []
+    while True:
+        st0 = srv.stats()
+        if st0["completed"] + st0["failed"] >= args.max_batch:
+            break
+        time.sleep(0.05)
+    base = srv.stats()
+    si = args.max_batch
+    for lam in rates:
+        rids = []
+        t0 = time.perf_counter()
+        nxt = t0
+        while nxt - t0 < args.duration:
+            now = time.perf_counter()
+            if nxt > now:
+                time.sleep(nxt - now)
+            u = int(srcs[si % len(srcs)])
+            si += 1
+            e = float(rng.choice(w["eps_set"]))
+            rids.append(srv.submit(u, e))
+            nxt += rng.exponential(1.0 / lam)
+        lat = []
+        for r in rids:
+            lat.append(srv.wait(r, 600000)[2])
+        t_end = time.perf_counter()
+        st = srv.stats()
+        lat = np.array(lat)
+        per_rate.append({"rate_qps": lam, "submitted": len(rids), "queries_per_s": len(rids) / (t_end - t0),
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "max_ms": float(lat.max()), "waves": st["waves"] - base["waves"],
+                         "mean_batch": st["mean_batch"], "max_running": st["max_running"]})
+        base = st
+    srv.close()
+    best = max(per_rate, key=lambda r: r["queries_per_s"])
+    line = {"metric": "served top-100 queries/s with p50/p99 latency (Poisson arrivals)", "value": best["queries_per_s"],
+            "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+two-float", "data": "synthetic",
+            "config": {"workload": "rmat25", "graph": "rmat (torch generator)", "n": n, "m": m,
+                       "abcd": [0.57, 0.19, 0.19, 0.05], "c": c, "eps": list(w["eps_set"]), "top_k": k,
+                       "kappa": args.kappa, "max_batch": args.max_batch, "max_waves": args.max_waves,
+                       "duration_s_per_rate": args.duration},
+            "rates": per_rate, "graph_gen_s": t_gen, "graph_load_s": t_load}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def synth_sources(rp, count, seed):
+    import synth
+    return synth.random_sources(rp, count, seed=seed)
+
+
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources_per_step": w["sources"],
@@ -374,6 +457,10 @@ def main():
                     help="sample constant: R_b = kappa ln(n) / eps^2 (<= 0: the paper's 6/(1-sqrt c)^4)")
     ap.add_argument("--ref-pairs", type=float, default=2e8, help="walk pairs per CPU reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
+    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--max-batch", type=int, default=8, help="serving: requests per wave")
+    ap.add_argument("--max-waves", type=int, default=2, help="serving: waves in flight")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
 
@@ -389,6 +476,9 @@ def main():
         return
     if args.workload == "rmat20":
         run_batched(args, w)
+        return
+    if args.workload == "rmat25":
+        run_serving(args, w)
         return
 
     import torch

@@ -9,6 +9,7 @@ from .graphs import (  # noqa: F401
     erdos_renyi,
     chung_lu,
     rmat,
+    rmat_torch,
     random_sources,
     uniform_diagonal,
     out_star,

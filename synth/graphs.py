@@ -12,7 +12,9 @@ Generators:
   out-weights w = (1-U)^(-1/(gamma-1)), endpoints drawn proportionally to the
   weights, self-loops dropped, duplicates removed, redrawn to exactly m edges.
 * ``rmat``         -- recursive-matrix graph with quadrant probabilities
-  (a, b, c, d), duplicates and loops removed, seeded random vertex permutation.
+  (a, b, c, d), duplicates and loops removed, seeded random vertex permutation;
+  ``rmat_torch`` draws the same kind of graph with torch on a GPU for the
+  largest sizes.
 
 Small named graphs (stars, cycle, complete digraph, ...) serve the closed-form
 checks.  Nothing here computes any part of SimRank.
@@ -130,6 +132,61 @@ def rmat(scale: int, m: int, a=0.57, b=0.19, c=0.19, d=0.05, seed: int = 1):
 
     s, t = _fill_distinct(n, m, draw, rng)
     return edges_to_in_csr(n, s, t)
+
+
+def rmat_torch(scale: int, m: int, a=0.57, b=0.19, c=0.19, d=0.05, seed: int = 1, device: str = "cuda"):
+    """R-MAT graph generated with torch on `device` (for the largest configurations).
+
+    Same recipe as ``rmat`` (quadrant probabilities, loops and duplicates removed,
+    seeded vertex permutation, exactly m distinct edges) with torch's generator:
+    it is deterministic for a given seed, device type and torch version, but it
+    draws a different graph than the NumPy ``rmat``.  Surplus edges are drawn,
+    deduplicated, and m of them are kept by a seeded permutation.
+    """
+    import torch
+    n = 1 << scale
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    perm = torch.randperm(n, generator=gen, device=device)
+    t0, t1, t2 = a, a + b, a + b + c
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    draw = int(m * 1.3) + 4096
+    for _ in range(20):
+        chunk = 1 << 26
+        parts = []
+        left = draw
+        while left > 0:
+            k = min(chunk, left)
+            left -= k
+            src = torch.zeros(k, dtype=torch.int64, device=device)
+            dst = torch.zeros(k, dtype=torch.int64, device=device)
+            for _lvl in range(scale):
+                r = torch.rand(k, generator=gen, device=device)
+                q = (r >= t0).long() + (r >= t1).long() + (r >= t2).long()
+                src = (src << 1) | (q >> 1)
+                dst = (dst << 1) | (q & 1)
+            keep = src != dst
+            parts.append(perm[src[keep]] * n + perm[dst[keep]])
+            del src, dst, keep
+        keys = torch.unique(torch.cat([keys] + parts))
+        del parts
+        if keys.numel() >= m:
+            break
+        draw = int((m - keys.numel()) * 2) + 4096
+    if keys.numel() < m:
+        raise RuntimeError("could not reach the requested number of distinct edges")
+    pick = torch.randperm(keys.numel(), generator=gen, device=device)[:m]
+    keys = keys[pick]
+    src = keys // n
+    dst = keys % n
+    del keys, pick
+    order = torch.argsort(dst * n + src)
+    src = src[order]
+    dst = dst[order]
+    counts = torch.bincount(dst, minlength=n)
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(counts, 0)
+    return n, rowptr.cpu().numpy(), src.to(torch.int32).cpu().numpy()
 
 
 def random_sources(in_rowptr: np.ndarray, count: int, seed: int = 7) -> np.ndarray:
