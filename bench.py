@@ -91,6 +91,21 @@ def sources_for(w, rp, world, rank):
     return [int(x) for x in allsrc[rank * w["sources"]:(rank + 1) * w["sources"]]]
 
 
+def reduce_max(values, device):
+    """Element-wise maximum of `values` over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units processed by all ranks divided by the slowest rank's time (weak scaling)."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -439,6 +454,46 @@ def synth_sources(rp, count, seed):
     return synth.random_sources(rp, count, seed=seed)
 
 
+def run_exceed(args, w):
+    """Theorem 1 check: max_v |s(v) - S(u, v)| over many seeds on the small ER workload.
+
+    The Power Method (CPU oracle) gives S; each seed is one GPU query with the
+    stated kappa (the paper's 6/(1-sqrt c)^4 by default).  Reports the exceed rate
+    (fraction of seeds with max error > eps) and the error distribution.
+    """
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+    from oracle import power
+    n, rp, col = make_graph(w)
+    c, eps = w["c"], w["eps"]
+    S = power.power_method(n, rp, col, c)
+    g = esim.Graph(n, rp, col, kappa=args.kappa, precision=args.precision)
+    us = [0] + [int(x) for x in synth_sources(rp, 4, 3)]
+    errs = []
+    t0 = time.perf_counter()
+    for seed in range(args.seeds):
+        u = us[seed % len(us)]
+        s = g.query(u, c, eps, seed)
+        errs.append(float(np.max(np.abs(s - S[:, u]))))
+    wall = time.perf_counter() - t0
+    st = g.stats()
+    errs = np.array(errs)
+    line = {"metric": "exceed rate of max_v |s(v) - S(u,v)| > eps over seeds (Theorem 1)", "value": float(np.mean(errs > eps)),
+            "unit": "fraction", "n_gpus": 1, "higher_is_better": False, "dtype": "f64" if args.precision == 0 else "fp32c",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graph": w["kind"], "n": n, "m": len(col), "c": c, "eps": eps,
+                       "kappa": args.kappa if args.kappa > 0 else "6/(1-sqrt c)^4", "seeds": args.seeds,
+                       "sources": us, "oracle": "Power Method (FP64 CPU)"},
+            "max_err": {"max": float(errs.max()), "p50": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
+                        "mean": float(errs.mean())},
+            "pairs_per_query": st["sum_R"], "queries_per_s": args.seeds / wall}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources_per_step": w["sources"],
@@ -457,6 +512,9 @@ def main():
                     help="sample constant: R_b = kappa ln(n) / eps^2 (<= 0: the paper's 6/(1-sqrt c)^4)")
     ap.add_argument("--ref-pairs", type=float, default=2e8, help="walk pairs per CPU reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--exceed", action="store_true", help="Theorem 1 exceed rate over --seeds seeds (small workloads)")
+    ap.add_argument("--seeds", type=int, default=100)
+    ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
     ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-batch", type=int, default=8, help="serving: requests per wave")
@@ -479,6 +537,9 @@ def main():
         return
     if args.workload == "rmat25":
         run_serving(args, w)
+        return
+    if args.exceed:
+        run_exceed(args, w)
         return
 
     import torch
@@ -554,12 +615,9 @@ def main():
             esim.esim_topk(g.handle, u, c, eps, 1000 * (args.warmup + i) + q, k, host_ids, host_vals)
     e2e_s = time.perf_counter() - t0
 
-    t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = reduce_max([total_ms, e2e_s], dev)
     queries = args.steps * len(srcs) * world
-    value = queries / (total_ms / 1000.0)
+    value = whole_job_rate(args.steps * len(srcs), world, total_ms)
 
     # roofline of the dominant kernel (the walk-pair sampler): pair-steps per second against
     # the integer-issue limit of one Philox-4x32-10 block plus the step logic
