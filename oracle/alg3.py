@@ -1,0 +1,129 @@
+"""Algorithm 3 ("Improved method for estimating D(k,k)") in the oracle, FP64.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+* ``first_meeting_lemma5`` -- Z_l(k) = sum_q Z_l(k, q) for l = 1..depth by the
+  recursion of Lemma 5:
+      Z_l(k, q) = c^l (P^T)^l(k, q)^2
+                  - sum_{l'=1}^{l-1} sum_{q'} c^{l'} (P^T)^{l'}(q', q)^2 Z_{l-l'}(k, q'),
+  where (P^T)^l(k, .) is the distribution of a non-stop walk (uniform in-neighbour
+  moves) from k after l steps.  Each (P^T)^j(q', .) is propagated separately, so
+  the code follows the lemma term by term.
+* ``first_meeting_bruteforce`` -- the same quantity from the definition: the exact
+  (rational) distribution of two non-stop walks from k over pairs of nodes, step by
+  step, removing the pairs that have met; Z_l = c^l * (mass that first meets at
+  step l).  An independent formulation that pins the lemma's recursion.
+* ``exploitation_plan`` -- the depth-limited exploitation the library uses: the
+  heaviest nodes (by pi(k), at most ``max_nodes``, with R(k) >= ``min_pairs`` and
+  din(k) >= 2) get depth 3 if din(k) <= 64 else 2 (capped by ``max_depth``); their
+  sample count becomes max(1, ceil(R_b pi(k)^2 c^(2 depth))).  Nodes with din <= 1
+  take the exact values of Algorithm 3 (D = 1 at din = 0, 1 - c at din = 1) and no
+  samples.
+* ``dhat_alg3`` -- D^(k) = 1 - sum_{l <= depth} Z_l(k) - c^depth * tailmeet(k) / R(k)
+  for exploited nodes (Algorithm 3), nonmeet / R for the others.
+
+Pinned by: the rational brute force (Z to 1e-14), the identity
+sum_l Z_l(k) = 1 - D(k) against the Power Method's exact D (the truncated sum stays
+below it and the tail estimator closes the gap), and z-tests of the tail walks.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from .power import transition_matrix, in_degrees
+
+
+def walk_distribution(P, k: int, steps: int) -> np.ndarray:
+    """(P^T)^l(k, .) for l = 0..steps: non-stop walk from k along in-edges (rows l)."""
+    n = P.shape[0]
+    H = np.zeros((steps + 1, n))
+    H[0, k] = 1.0
+    for ell in range(1, steps + 1):
+        H[ell] = P @ H[ell - 1]
+    return H
+
+
+def first_meeting_lemma5(n: int, in_rowptr, in_col, k: int, c: float, depth: int) -> list[float]:
+    P = transition_matrix(n, in_rowptr, in_col)
+    hk = walk_distribution(P, k, depth)
+    cache: dict[int, np.ndarray] = {}
+
+    def h_from(q: int, j: int) -> np.ndarray:
+        if q not in cache:
+            cache[q] = walk_distribution(P, q, depth)
+        return cache[q][j]
+
+    Z = [None]  # Z[l] is the vector Z_l(k, .)
+    for ell in range(1, depth + 1):
+        z = c ** ell * hk[ell] ** 2
+        for lp in range(1, ell):
+            # sum_{q'} c^{l'} (P^T)^{l'}(q', .)^2 Z_{l-l'}(k, q')
+            zz = Z[ell - lp]
+            for qp in np.nonzero(zz)[0]:
+                z = z - c ** lp * h_from(int(qp), lp) ** 2 * zz[qp]
+        Z.append(z)
+    return [float(Z[ell].sum()) for ell in range(1, depth + 1)]
+
+
+def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, depth: int) -> list[Fraction]:
+    """Exact Z_1..Z_depth from the pair distribution of two non-stop walks (tiny graphs)."""
+    c = Fraction(c)
+    rp = [int(x) for x in in_rowptr]
+    col = [int(x) for x in in_col]
+    I = [col[rp[j]:rp[j + 1]] for j in range(n)]
+    dist = {(k, k): Fraction(1)}  # step 0 is not a meeting
+    out = []
+    for ell in range(1, depth + 1):
+        nxt: dict[tuple[int, int], Fraction] = {}
+        for (a, b), w in dist.items():
+            if not I[a] or not I[b]:
+                continue
+            wa = Fraction(1, len(I[a]))
+            wb = Fraction(1, len(I[b]))
+            for x in I[a]:
+                for y in I[b]:
+                    nxt[(x, y)] = nxt.get((x, y), Fraction(0)) + w * wa * wb
+        met = sum((w for (x, y), w in nxt.items() if x == y), Fraction(0))
+        out.append(c ** ell * met)
+        dist = {p: w for p, w in nxt.items() if p[0] != p[1]}
+    return out
+
+
+def exploitation_plan(n: int, in_rowptr, pi: np.ndarray, R_b: float, c: float, max_depth: int = 3,
+                      min_pairs: float = 1e6, max_nodes: int = 64):
+    """(depth uint8[n], R uint64[n]) of the depth-limited Algorithm 3."""
+    din = in_degrees(in_rowptr)
+    pi = np.asarray(pi, dtype=np.float64)
+    R = np.ceil(R_b * (pi * pi)).astype(np.uint64)
+    R[(pi > 0) & (R == 0)] = 1
+    depth = np.zeros(n, dtype=np.uint8)
+    R[din <= 1] = 0  # exact D for din 0 and 1
+    order = np.lexsort((np.arange(n), -pi))[:max_nodes]
+    for kk in order:
+        kk = int(kk)
+        if pi[kk] <= 0 or din[kk] < 2 or R[kk] < min_pairs or max_depth < 1:
+            continue
+        d = min(max_depth, 3 if din[kk] <= 64 else 2)
+        depth[kk] = d
+        v = R_b * (pi[kk] * pi[kk]) * c ** (2 * d)
+        R[kk] = max(1, int(math.ceil(v)))
+    return depth, R
+
+
+def dhat_alg3(counts: np.ndarray, R: np.ndarray, depth: np.ndarray, zsum: np.ndarray, din: np.ndarray,
+              c: float) -> np.ndarray:
+    """D^ of Algorithm 3 (exploited nodes), Algorithm 2 (others), exact values at din <= 1."""
+    counts = np.asarray(counts, dtype=np.uint64)
+    R = np.asarray(R, dtype=np.uint64)
+    D = np.zeros(R.size)
+    nz = R > 0
+    D[nz] = counts[nz].astype(np.float64) / R[nz].astype(np.float64)
+    ex = depth > 0
+    D[ex] = 1.0 - zsum[ex] - (c ** depth[ex].astype(np.float64)) * (
+        counts[ex].astype(np.float64) / R[ex].astype(np.float64))
+    D[din == 0] = 1.0
+    D[din == 1] = 1.0 - c
+    return D

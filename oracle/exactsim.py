@@ -14,6 +14,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import alg3 as a3
 from . import linearization as lin
 from . import walks
 
@@ -29,16 +30,31 @@ class QueryResult:
     L: int
     R_b: float
     pair_steps: int
+    depth: np.ndarray | None = None
+    zsum: np.ndarray | None = None
 
 
 def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
-          kappa: float | None = None, mode: str = "pi2", threads: int = 0) -> QueryResult:
+          kappa: float | None = None, mode: str = "pi2", threads: int = 0, alg3: bool = False,
+          alg3_max_depth: int = 3, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64) -> QueryResult:
     L = lin.levels(c, eps)
     H = lin.hop_vectors(n, in_rowptr, in_col, u, c, L)
     pi = lin.ppr(H)
     R_b = lin.sample_base(n, c, eps, kappa)
-    R = lin.allocate(pi, R_b, mode)
-    nonmeet, steps = walks.walk_pairs(n, in_rowptr, in_col, R, c, seed, threads)
-    D = lin.dhat(nonmeet, R)
+    if not alg3:
+        R = lin.allocate(pi, R_b, mode)
+        nonmeet, steps = walks.walk_pairs(n, in_rowptr, in_col, R, c, seed, threads)
+        D = lin.dhat(nonmeet, R)
+        s = lin.reverse(n, in_rowptr, in_col, H, D, c)
+        return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
+    # Algorithm 3 for the heaviest nodes (pi^2 allocation)
+    depth, R = a3.exploitation_plan(n, in_rowptr, pi, R_b, c, alg3_max_depth, alg3_min_pairs, alg3_max_nodes)
+    zsum = np.zeros(n)
+    for k in np.nonzero(depth)[0]:
+        zsum[k] = sum(a3.first_meeting_lemma5(n, in_rowptr, in_col, int(k), c, int(depth[k])))
+    counts, steps = walks.walk_pairs_depth(n, in_rowptr, in_col, R, depth, c, seed, threads)
+    din = np.diff(np.asarray(in_rowptr, dtype=np.int64))
+    D = a3.dhat_alg3(counts, R, depth, zsum, din, c)
     s = lin.reverse(n, in_rowptr, in_col, H, D, c)
-    return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
+    return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=counts, D=D, L=L, R_b=R_b, pair_steps=steps,
+                       depth=depth, zsum=zsum)

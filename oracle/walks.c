@@ -122,9 +122,13 @@ void oracle_pick_many(int64_t count, const uint32_t* x, uint32_t d, uint64_t see
     for (int64_t i = 0; i < count; ++i) out[i] = pick(x[i], d, (uint32_t)i, 0u, 0u, 0x80000000u, k0, k1);
 }
 
-/* One walk pair; returns 1 if the walks never meet.  *steps counts main-stream Philox calls. */
+/* One walk pair.  Depth 0 (Algorithm 2): returns 1 if the walks never meet.
+ * Depth d > 0 (Algorithm 3's special pair): the first d steps move without the
+ * continuation draw (non-stop walks); returns 1 if the walks first meet at a step
+ * after d, 0 otherwise (a meeting within the first d steps is already counted in
+ * the exact first-meeting probabilities).  *steps counts main-stream Philox calls. */
 static int walk_pair(const int64_t* rp, const int32_t* col, uint32_t k, uint64_t r,
-                     uint32_t T, uint32_t k0, uint32_t k1, uint64_t* steps) {
+                     uint32_t T, uint32_t k0, uint32_t k1, uint32_t depth, uint64_t* steps) {
     uint32_t xa = k, xb = k;
     const uint32_t rlo = (uint32_t)r, rhi = (uint32_t)(r >> 32);
     for (uint32_t t = 0; t < WALK_T_MAX; ++t) {
@@ -134,18 +138,19 @@ static int walk_pair(const int64_t* rp, const int32_t* col, uint32_t k, uint64_t
         *steps += 1;
         uint64_t da = (uint64_t)(rp[xa + 1] - rp[xa]);
         uint64_t db = (uint64_t)(rp[xb + 1] - rp[xb]);
-        int move_a = (w[0] < T) && (da > 0);
-        int move_b = (w[2] < T) && (db > 0);
-        if (!(move_a && move_b)) return 1;
+        int forced = t < depth;
+        int move_a = (forced || w[0] < T) && (da > 0);
+        int move_b = (forced || w[2] < T) && (db > 0);
+        if (!(move_a && move_b)) return depth ? 0 : 1;
         uint32_t ia = pick(w[1], (uint32_t)da, rlo, rhi, k, 0x80000000u | t, k0, k1);
         uint32_t ib = pick(w[3], (uint32_t)db, rlo, rhi, k, 0xC0000000u | t, k0, k1);
         uint32_t na = (uint32_t)col[rp[xa] + (int64_t)ia];
         uint32_t nb = (uint32_t)col[rp[xb] + (int64_t)ib];
-        if (na == nb) return 0;
+        if (na == nb) return depth ? (t >= depth ? 1 : 0) : 0;
         xa = na;
         xb = nb;
     }
-    return 1;
+    return depth ? 0 : 1;
 }
 
 /*
@@ -153,9 +158,24 @@ static int walk_pair(const int64_t* rp, const int32_t* col, uint32_t k, uint64_t
  * Returns the total number of Philox calls (pair-steps), or -1 on bad input.
  * nthreads <= 0 uses the OpenMP default.
  */
+int64_t oracle_walk_pairs_depth(int64_t n, const int64_t* in_rowptr, const int32_t* in_col,
+                                const uint64_t* R, const uint8_t* depth, double c, uint64_t seed,
+                                uint64_t* nonmeet, int nthreads);
+
 int64_t oracle_walk_pairs(int64_t n, const int64_t* in_rowptr, const int32_t* in_col,
                           const uint64_t* R, double c, uint64_t seed, uint64_t* nonmeet,
                           int nthreads) {
+    return oracle_walk_pairs_depth(n, in_rowptr, in_col, R, NULL, c, seed, nonmeet, nthreads);
+}
+
+/*
+ * As oracle_walk_pairs, with depth[k] (may be NULL) selecting Algorithm 3's special
+ * pairs for node k: counts[k] is then the number of pairs that first meet after
+ * step depth[k].
+ */
+int64_t oracle_walk_pairs_depth(int64_t n, const int64_t* in_rowptr, const int32_t* in_col,
+                                const uint64_t* R, const uint8_t* depth, double c, uint64_t seed,
+                                uint64_t* nonmeet, int nthreads) {
     if (n <= 0 || n > 0xFFFFFFFFll) return -1;
     uint32_t T = oracle_walk_threshold(c);
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -187,8 +207,9 @@ int64_t oracle_walk_pairs(int64_t n, const int64_t* in_rowptr, const int32_t* in
             while (off[k + 1] <= g) ++k;
             uint64_t kend = off[k + 1] < end ? off[k + 1] : end;
             local = 0;
+            const uint32_t d = depth ? depth[k] : 0u;
             for (; g < kend; ++g)
-                local += (uint64_t)walk_pair(in_rowptr, in_col, (uint32_t)k, g - off[k], T, k0, k1, &steps);
+                local += (uint64_t)walk_pair(in_rowptr, in_col, (uint32_t)k, g - off[k], T, k0, k1, d, &steps);
 #ifdef _OPENMP
 #pragma omp atomic
 #endif

@@ -54,6 +54,10 @@ def _load():
             lib.oracle_walk_threshold.restype = ctypes.c_uint32
             lib.oracle_walk_threshold.argtypes = [ctypes.c_double]
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_walk_pairs_depth.restype = ctypes.c_int64
+            lib.oracle_walk_pairs_depth.argtypes = [
+                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
             lib.oracle_pick_many.restype = None
             lib.oracle_pick_many.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                              ctypes.c_void_p]
@@ -98,3 +102,19 @@ def walk_pairs(n: int, in_rowptr, in_col, R, c: float, seed: int, threads: int =
     if steps < 0:
         raise ValueError("oracle_walk_pairs rejected its input")
     return nonmeet, int(steps)
+
+
+def walk_pairs_depth(n: int, in_rowptr, in_col, R, depth, c: float, seed: int, threads: int = 0):
+    """(counts uint64[n], pair_steps): nonmeet for depth 0, tail meets (Algorithm 3) for depth > 0."""
+    rp = np.ascontiguousarray(in_rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(in_col, dtype=np.int32)
+    R = np.ascontiguousarray(R, dtype=np.uint64)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    if rp.size != n + 1 or R.size != n or d.size != n:
+        raise ValueError("shape mismatch")
+    counts = np.zeros(n, dtype=np.uint64)
+    steps = _load().oracle_walk_pairs_depth(n, rp.ctypes.data, col.ctypes.data, R.ctypes.data, d.ctypes.data,
+                                            float(c), ctypes.c_uint64(seed), counts.ctypes.data, int(threads))
+    if steps < 0:
+        raise ValueError("oracle_walk_pairs_depth rejected its input")
+    return counts, int(steps)

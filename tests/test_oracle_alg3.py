@@ -1,0 +1,105 @@
+"""Pins of the oracle's Algorithm 3 (local deterministic exploitation).
+
+* Lemma 5's recursion against exact rational first-meeting probabilities of two
+  non-stop walks (brute force over pairs of nodes).
+* The truncated sum of Z_l(k) stays below 1 - D(k) of the Power Method, and the
+  special tail walks estimate the remainder without bias (z-test).
+* The exploitation plan's rules, and the whole Algorithm 3 query within eps of
+  the Power Method.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import alg3 as a3
+from oracle import exactsim, power
+
+C = 0.6
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_lemma5_matches_bruteforce(seed):
+    n = 7 if seed % 2 else 8
+    g = synth.random_small(n, p=0.45, seed=seed)
+    nn, rp, col = g
+    din = np.diff(rp)
+    for k in range(n):
+        if din[k] == 0:
+            continue
+        z = a3.first_meeting_lemma5(nn, rp, col, k, C, 4)
+        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), 4)]
+        assert np.max(np.abs(np.array(z) - np.array(zb))) < 1e-14, (k, z, zb)
+
+
+def test_truncated_meeting_mass_is_below_one_minus_D():
+    g = synth.chung_lu(80, 600, gamma=2.1, seed=5)
+    n, rp, col = g
+    S = power.power_method(n, rp, col, C)
+    D = power.exact_diagonal(n, rp, col, C, S)
+    din = np.diff(rp)
+    for k in np.nonzero(din >= 2)[0][:12]:
+        z = a3.first_meeting_lemma5(n, rp, col, int(k), C, 3)
+        assert all(x >= -1e-15 for x in z)
+        assert sum(z) <= 1 - D[k] + 1e-12
+        # one step: Z_1 = c * sum_a (1/din)^2 = c / din for a simple graph
+        assert z[0] == pytest.approx(C / din[k], rel=1e-12)
+
+
+def test_tail_walks_estimate_the_remainder(oracle_walks):
+    g = synth.chung_lu(60, 500, gamma=2.1, seed=6)
+    n, rp, col = g
+    S = power.power_method(n, rp, col, C)
+    D = power.exact_diagonal(n, rp, col, C, S)
+    din = np.diff(rp)
+    ks = [int(k) for k in np.nonzero(din >= 2)[0][:6]]
+    R = np.zeros(n, dtype=np.uint64)
+    depth = np.zeros(n, dtype=np.uint8)
+    zsum = np.zeros(n)
+    for i, k in enumerate(ks):
+        d = 1 + i % 3
+        depth[k] = d
+        R[k] = 300_000
+        zsum[k] = sum(a3.first_meeting_lemma5(n, rp, col, k, C, d))
+    counts, _ = oracle_walks.walk_pairs_depth(n, rp, col, R, depth, C, seed=3)
+    Dh = a3.dhat_alg3(counts, R, depth, zsum, din, C)
+    for k in ks:
+        d = int(depth[k])
+        p = (1 - D[k] - zsum[k]) / C ** d  # probability of a tail meeting
+        sd = C ** d * np.sqrt(max(p * (1 - p), 1e-300) / 300_000)
+        assert abs(Dh[k] - D[k]) < 5 * sd + 1e-12, (k, d, Dh[k], D[k])
+    # depth 0 everywhere is Algorithm 2
+    c0, _ = oracle_walks.walk_pairs_depth(n, rp, col, R, np.zeros(n, dtype=np.uint8), C, seed=3)
+    c1, _ = oracle_walks.walk_pairs(n, rp, col, R, C, seed=3)
+    assert np.array_equal(c0, c1)
+
+
+def test_exploitation_plan_rules():
+    n, rp, col = synth.chung_lu(400, 4000, gamma=2.1, seed=7)
+    din = np.diff(rp)
+    pi = np.random.default_rng(1).random(n) * 0.1
+    pi[din == 0] = 0.05
+    R_b = 1e10
+    depth, R = a3.exploitation_plan(n, rp, pi, R_b, C, max_depth=3, min_pairs=1e6, max_nodes=10)
+    assert np.all(R[din <= 1] == 0)
+    assert np.count_nonzero(depth) <= 10
+    top = np.lexsort((np.arange(n), -pi))[:10]
+    for k in np.nonzero(depth)[0]:
+        assert k in top and din[k] >= 2
+        d = int(depth[k])
+        assert d == (3 if din[k] <= 64 else 2)
+        assert R[k] == max(1, int(np.ceil(R_b * pi[k] ** 2 * C ** (2 * d))))
+    other = (depth == 0) & (din >= 2)
+    assert np.array_equal(R[other], np.maximum(1, np.ceil(R_b * pi[other] ** 2)).astype(np.uint64))
+
+
+def test_alg3_query_within_eps_of_power_method(oracle_walks):
+    g = synth.erdos_renyi(300, 2400, seed=4)
+    n, rp, col = g
+    S = power.power_method(n, rp, col, C)
+    eps = 2e-3
+    for u, seed in ((0, 1), (57, 2)):
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=16.0, alg3=True, alg3_min_pairs=1e3)
+        assert np.count_nonzero(q.depth) > 0
+        assert np.max(np.abs(q.s - S[:, u])) <= eps
