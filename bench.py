@@ -169,8 +169,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0):
+def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0, alg3=False):
     """Time one bounded sample of the CPU oracle query; return (seconds per full query, info)."""
+    from oracle import alg3 as a3
     from oracle import linearization as lin
     from oracle import walks
     c, eps = w["c"], w["eps"]
@@ -179,14 +180,23 @@ def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0):
     H = lin.hop_vectors(n, rp, col, u, c, L)
     pi = lin.ppr(H)
     R_b = lin.sample_base(n, c, eps, kappa)
-    R = lin.allocate(pi, R_b, "pi2")
+    depth = None
+    if alg3:
+        depth, R = a3.exploitation_plan(n, rp, pi, R_b, c)
+        for k in np.nonzero(depth)[0]:
+            sum(a3.first_meeting_lemma5(n, rp, col, int(k), c, int(depth[k])))
+    else:
+        R = lin.allocate(pi, R_b, "pi2")
     t_sweep_fwd = time.perf_counter() - t0
     total = int(R.sum())
     # bounded sample of the walk pairs: the same per-node proportions, scaled down
     scale = min(1.0, pair_cap / max(total, 1))
     R_s = np.floor(R.astype(np.float64) * scale).astype(np.uint64)
     t1 = time.perf_counter()
-    nonmeet, steps = walks.walk_pairs(n, rp, col, R_s, c, 1, threads)
+    if alg3:
+        nonmeet, steps = walks.walk_pairs_depth(n, rp, col, R_s, depth, c, 1, threads)
+    else:
+        nonmeet, steps = walks.walk_pairs(n, rp, col, R_s, c, 1, threads)
     t_walk = time.perf_counter() - t1
     D = lin.dhat(nonmeet, R_s)
     t2 = time.perf_counter()
@@ -212,7 +222,7 @@ def run_reference(args, w, rank, world):
     info = None
     for i in range(args.warmup + args.steps):
         u = srcs[i % len(srcs)]
-        t, info = cpu_reference_sample(w, n, rp, col, u, args.kappa, args.ref_pairs)
+        t, info = cpu_reference_sample(w, n, rp, col, u, args.kappa, args.ref_pairs, alg3=bool(args.alg3))
         if i >= args.warmup:
             per_query.append(t)
     q_per_s = 1.0 / statistics.mean(per_query)
@@ -501,6 +511,8 @@ def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources": w["sources"], "queries_per_step": 1,
             "top_k": w["k"], "kappa": args.kappa, "alloc": "pi^2 (Lemma 4)",
+            "dhat": ("Algorithm 3 (exact Z_1..Z_d for the 64 heaviest nodes, d <= 3, then tail walk pairs)"
+                     if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
             "l2": "flushed (512 MB write) before each timed step", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -518,6 +530,7 @@ def main():
     ap.add_argument("--exceed", action="store_true", help="Theorem 1 exceed rate over --seeds seeds (small workloads)")
     ap.add_argument("--seeds", type=int, default=100)
     ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
+    ap.add_argument("--alg3", type=int, default=0, help="1: Algorithm 3 D^ estimator for the heaviest nodes")
     ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-batch", type=int, default=8, help="serving: requests per wave")
@@ -566,7 +579,7 @@ def main():
     n, rp, col = make_graph(w)
     srcs = sources_for(w, rp, world, rank)
     c, eps, k = w["c"], w["eps"], w["k"]
-    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
+    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3)
     stream = torch.cuda.current_stream()
     g.set_stream(stream)
     ids = torch.empty(k, dtype=torch.int32, device=dev)
@@ -677,7 +690,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import walks
         walks.build()
-        t, info = cpu_reference_sample(w, n, rp, col, srcs[0], args.kappa, args.ref_pairs)
+        t, info = cpu_reference_sample(w, n, rp, col, srcs[0], args.kappa, args.ref_pairs, alg3=bool(args.alg3))
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": "queries/s", "cores": walks.max_threads(), "kind": "oracle",
                                 "sample": f"one query (u={srcs[0]}): sweeps in full, {info['pairs_sampled']:.3g} of "
                                           f"{info['pairs_total']:.3g} walk pairs, walk time scaled"}

@@ -81,6 +81,8 @@ typedef struct {
     float ms_reverse;
     float ms_topk;
     float ms_total;
+    int32_t alg3_nodes;   /* nodes exploited by Algorithm 3 in the last query */
+    int32_t reserved2;
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */
@@ -129,6 +131,18 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
  *                    query returns ESIM_EBUDGET without running walks
  *   "timing"         1: record per-phase CUDA event times in the stats
+ *   "alg3"           1: Algorithm 3 (local deterministic exploitation) for the
+ *                    heaviest nodes, depth-limited (see esim_alg3_first_meeting);
+ *                    nodes with din <= 1 take the exact D (1 at din 0, 1-c at din 1)
+ *                    and no walk pairs.  An exploited node k of depth d gets the
+ *                    exact Z_1..Z_d (Lemma 5) and max(1, ceil(R_b pi(k)^2 c^(2d)))
+ *                    special pairs that move for d steps without the continuation
+ *                    draw; D^(k) = 1 - sum Z - c^d (pairs meeting after step d)/R.
+ *                    Needs a graph without repeated in-edges (else ESIM_ENOTSUP).
+ *   "alg3_max_nodes" heaviest nodes (by pi) considered, 1..4096 (default 64)
+ *   "alg3_min_pairs" smallest Algorithm 2 pair count worth exploiting (default 1e6)
+ *   "alg3_max_depth" 1..3 (default 3); depth 3 also needs din(k) <= "alg3_d3_max_din"
+ *                    (default 64) and m <= "alg3_d3_max_edges" (default 5e7), else 2
  *   "batch_tile"     -1: batched sweeps pick their tile by timing (default);
  *                    0, 1, 2: force 32, 16 or 8 lanes per row (results do not change)
  *   "precision"      0: FP64 sweeps (default);
@@ -281,6 +295,20 @@ esim_status esim_allocate_f32(esim_graph* g, const float* hist, int32_t L, doubl
                               double* pi_out, uint64_t* R_out, uint64_t* off);
 esim_status esim_reverse_f32(esim_graph* g, const float* hist, int32_t L, double c, const double* dhat,
                              double* s_out);
+
+/* Algorithm 3 steps.  esim_alg3_first_meeting writes Z_1..Z_depth of node k
+ * (1 <= depth <= 3) into z_out (host): Z_l(k) = c^l * the probability that two
+ * non-stop walks from k first meet at step l (Lemma 5, summed over the meeting
+ * node); synchronous.  esim_sample_depth is esim_sample with depth[n] (device,
+ * uint8, may be NULL): for a node of depth d > 0 its pairs move without the
+ * continuation draw for d steps and counts[k] is the number that first meet after
+ * step d.  esim_dhat_alg3 gives D^ = counts/R for depth 0, 1 - zsum - c^d counts/R
+ * for depth d > 0, and 1 (din 0) or 1-c (din 1) exactly. */
+esim_status esim_alg3_first_meeting(esim_graph* g, int64_t k, int32_t depth, double c, double* z_out);
+esim_status esim_sample_depth(esim_graph* g, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
+                              uint64_t* counts, uint64_t* pair_steps);
+esim_status esim_dhat_alg3(esim_graph* g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,
+                           const double* zsum, double c, double* dhat);
 
 /* Top-k selection over scores[n] (device): ids_out[k], vals_out[k] (device),
  * ordered (score desc, id asc); exclude = -1 keeps every node.  1 <= k <= 4096. */

@@ -15,7 +15,8 @@ Test infrastructure only (see ``oracle/__init__.py``).
   step l).  An independent formulation that pins the lemma's recursion.
 * ``exploitation_plan`` -- the depth-limited exploitation the library uses: the
   heaviest nodes (by pi(k), at most ``max_nodes``, with R(k) >= ``min_pairs`` and
-  din(k) >= 2) get depth 3 if din(k) <= 64 else 2 (capped by ``max_depth``); their
+  din(k) >= 2) get depth 3 if din(k) <= 64 and m <= 5e7, else 2 (capped by
+  ``max_depth``); their
   sample count becomes max(1, ceil(R_b pi(k)^2 c^(2 depth))).  Nodes with din <= 1
   take the exact values of Algorithm 3 (D = 1 at din = 0, 1 - c at din = 1) and no
   samples.
@@ -93,9 +94,11 @@ def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, dep
 
 
 def exploitation_plan(n: int, in_rowptr, pi: np.ndarray, R_b: float, c: float, max_depth: int = 3,
-                      min_pairs: float = 1e6, max_nodes: int = 64):
+                      min_pairs: float = 1e6, max_nodes: int = 64, d3_max_din: int = 64,
+                      d3_max_edges: float = 5e7):
     """(depth uint8[n], R uint64[n]) of the depth-limited Algorithm 3."""
     din = in_degrees(in_rowptr)
+    m = int(np.asarray(in_rowptr)[-1])
     pi = np.asarray(pi, dtype=np.float64)
     R = np.ceil(R_b * (pi * pi)).astype(np.uint64)
     R[(pi > 0) & (R == 0)] = 1
@@ -106,7 +109,7 @@ def exploitation_plan(n: int, in_rowptr, pi: np.ndarray, R_b: float, c: float, m
         kk = int(kk)
         if pi[kk] <= 0 or din[kk] < 2 or R[kk] < min_pairs or max_depth < 1:
             continue
-        d = min(max_depth, 3 if din[kk] <= 64 else 2)
+        d = min(max_depth, 3 if (din[kk] <= d3_max_din and m <= d3_max_edges) else 2)
         depth[kk] = d
         v = R_b * (pi[kk] * pi[kk]) * c ** (2 * d)
         R[kk] = max(1, int(math.ceil(v)))

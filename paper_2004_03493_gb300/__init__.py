@@ -14,6 +14,9 @@ from . import _native
 from ._native import (  # noqa: F401
     EsimError,
     esim_allocate,
+    esim_alg3_first_meeting,
+    esim_sample_depth,
+    esim_dhat_alg3,
     esim_dhat,
     esim_forward,
     esim_forward_f32,
@@ -154,6 +157,15 @@ class Graph:
 
     def reverse_f32(self, hist, L, c, dhat, s_out):
         esim_reverse_f32(self.handle, hist, L, c, dhat, s_out)
+
+    def alg3_first_meeting(self, k, depth, c):
+        return esim_alg3_first_meeting(self.handle, k, depth, c)
+
+    def sample_depth(self, off, depth, c, seed, counts, pair_steps=None):
+        esim_sample_depth(self.handle, off, depth, c, seed, counts, pair_steps)
+
+    def dhat_alg3(self, counts, off, depth, zsum, c, out):
+        esim_dhat_alg3(self.handle, counts, off, depth, zsum, c, out)
 
     def dhat(self, nonmeet, off, out):
         esim_dhat(self.handle, nonmeet, off, out)

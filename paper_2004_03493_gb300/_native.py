@@ -32,10 +32,10 @@ class QueryStats(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("pi_norm2", ctypes.c_double), ("sum_R", ctypes.c_uint64),
                 ("pair_steps", ctypes.c_uint64), ("ms_forward", ctypes.c_float), ("ms_allocate", ctypes.c_float),
                 ("ms_sample", ctypes.c_float), ("ms_reverse", ctypes.c_float), ("ms_topk", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("alg3_nodes", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ }
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved2"}
 
 
 class ServerConfig(ctypes.Structure):
@@ -100,6 +100,9 @@ SIGNATURES = {
     "esim_server_wait": (_ST, [_P, _U64, _I32, _P, _P, ctypes.POINTER(_D)]),
     "esim_server_get_stats": (_ST, [_P, ctypes.POINTER(ServerStats)]),
     "esim_server_destroy": (None, [_P]),
+    "esim_alg3_first_meeting": (_ST, [_P, _I64, _I32, _D, _P]),
+    "esim_sample_depth": (_ST, [_P, _P, _P, _D, _U64, _P, _P]),
+    "esim_dhat_alg3": (_ST, [_P, _P, _P, _P, _P, _D, _P]),
 }
 
 
@@ -343,6 +346,24 @@ def esim_allocate_f32(g: int, hist, L: int, R_b: float, mode: int, pi_out, R_out
 def esim_reverse_f32(g: int, hist, L: int, c: float, dhat, s_out) -> None:
     _check(lib().esim_reverse_f32(g, _ptr(hist, "float32", device=True), L, c, _ptr(dhat, "float64", device=True),
                                   _ptr(s_out, "float64", device=True)))
+
+
+def esim_alg3_first_meeting(g: int, k: int, depth: int, c: float) -> np.ndarray:
+    z = np.zeros(depth, dtype=np.float64)
+    _check(lib().esim_alg3_first_meeting(g, k, depth, c, z.ctypes.data))
+    return z
+
+
+def esim_sample_depth(g: int, off, depth, c: float, seed: int, counts, pair_steps=None) -> None:
+    _check(lib().esim_sample_depth(g, _ptr(off, "uint64", device=True), _ptr(depth, "uint8", device=True, allow_none=True),
+                                   c, seed, _ptr(counts, "uint64", device=True),
+                                   _ptr(pair_steps, "uint64", device=True, allow_none=True)))
+
+
+def esim_dhat_alg3(g: int, counts, off, depth, zsum, c: float, dhat) -> None:
+    _check(lib().esim_dhat_alg3(g, _ptr(counts, "uint64", device=True), _ptr(off, "uint64", device=True),
+                                _ptr(depth, "uint8", device=True), _ptr(zsum, "float64", device=True), c,
+                                _ptr(dhat, "float64", device=True)))
 
 
 def esim_dhat(g: int, nonmeet, off, dhat) -> None:

@@ -5,6 +5,7 @@
 #include "internal.h"
 
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -118,6 +119,7 @@ void release(Graph& g) {
     if (g.status_host) cudaFreeHost(g.status_host);
     cudaFree(g.ws);
     cudaFree(g.bws);
+    cudaFree(g.a3ws);
     cudaFree(g.partial);
     cudaFree(g.scan_part);
     cudaFree(g.norm_part);
@@ -157,6 +159,8 @@ struct Ws {
     uint64_t* nonmeet; // n
     double* dhat;      // n
     double* s;         // n
+    uint8_t* depth;    // n  Algorithm 3 depth per node (0: Algorithm 2)
+    double* zsum;      // n  Algorithm 3: sum of the exact Z_l(k)
 };
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
@@ -191,6 +195,8 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w) {
     t.nonmeet = (uint64_t*)take(8 * n);
     t.dhat = (double*)take(8 * n);
     t.s = (double*)take(8 * n);
+    t.depth = (uint8_t*)take(n);
+    t.zsum = (double*)take(8 * n);
     if (w) *w = t;
     return o;
 }
@@ -214,6 +220,74 @@ esim_status ensure_ws(Graph& g, int32_t L, int precision, Ws& w) {
 
 esim_status check_graph(const esim_graph* h) {
     if (!h) return fail(ESIM_EINVAL, "graph handle is NULL");
+    return ESIM_OK;
+}
+
+// Algorithm 3 for the heaviest nodes (by pi): exact Z_1..Z_d (Lemma 5) on the GPU,
+// depth d = 3 if din(k) <= alg3_d3_max_din and m <= alg3_d3_max_edges, else 2 (both
+// capped by alg3_max_depth); the node's pair count becomes
+// max(1, ceil(R_b pi(k)^2 c^(2d))) (pi(k) for the basic allocation), the tail
+// estimator's variance and range being c^(2d) and c^d of Algorithm 2's.  Nodes with
+// din <= 1 already got no pairs from the allocation.  Then the offsets are rescanned.
+esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches) {
+    if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
+    if (!g.a3ws) {
+        const size_t need = alg3_workspace_bytes(g.n);
+        if (cudaMalloc(&g.a3ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 workspace)");
+        }
+        g.a3ws_bytes = need;
+    }
+    ESIM_CUDA_TRY(cudaMemsetAsync(w.depth, 0, (size_t)g.n, g.stream), "reset depth");
+    ESIM_CUDA_TRY(cudaMemsetAsync(w.zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
+    const int K = (int)std::min<int64_t>(g.alg3_max_nodes, g.n);
+    char* stage = (char*)g.topk_ws + topk_stage_offset(g.n);
+    double* vals_d = (double*)stage;
+    int32_t* ids_d = (int32_t*)(stage + sizeof(double) * kTopkMax);
+    ESIM_CUDA_TRY(launch_topk(g, w.pi, -1, K, ids_d, vals_d, g.topk_ws), "Algorithm 3 node selection");
+    *launches += 27;
+    std::vector<int32_t> ids((size_t)K);
+    std::vector<double> pis((size_t)K);
+    ESIM_CUDA_TRY(cudaMemcpyAsync(ids.data(), ids_d, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, g.stream), "copy ids");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(pis.data(), vals_d, sizeof(double) * K, cudaMemcpyDeviceToHost, g.stream), "copy pi");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 node selection");
+    const std::vector<uint32_t>& din = *g.din_host;
+    int used = 0;
+    for (int i = 0; i < K; ++i) {
+        const int32_t kk = ids[i];
+        const double p = pis[i];
+        if (kk < 0 || !(p > 0.0)) break;
+        if (din[kk] < 2) continue;
+        const double v = g.alloc_mode == 0 ? R_b * (p * p) : R_b * p;
+        double r0 = ceil(v);
+        if (r0 < 1.0) r0 = 1.0;
+        if (r0 < g.alg3_min_pairs) continue;
+        int d = (din[kk] <= (uint32_t)g.alg3_d3_max_din && (double)g.m <= g.alg3_d3_max_edges) ? 3 : 2;
+        d = std::min(d, g.alg3_max_depth);
+        if (d < 1) continue;
+        double z[3] = {0.0, 0.0, 0.0};
+        ESIM_CUDA_TRY(alg3_first_meeting(g, kk, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
+        const double zs = z[0] + z[1] + z[2];
+        double r = ceil(v * pow(c, (double)(2 * d)));
+        if (r < 1.0) r = 1.0;
+        if (r >= 1.8e19) r = 1.8e19;  // the rescan's budget check reports it
+        const uint64_t R1 = (uint64_t)r;
+        const uint8_t dd = (uint8_t)d;
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.R + kk, &R1, sizeof(uint64_t), cudaMemcpyHostToDevice, g.stream), "set R");
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.depth + kk, &dd, 1, cudaMemcpyHostToDevice, g.stream), "set depth");
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum + kk, &zs, sizeof(double), cudaMemcpyHostToDevice, g.stream), "set zsum");
+        ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // host values above are locals
+        ++used;
+    }
+    g.last_alg3_nodes = used;
+    // The budget applies to the pairs actually drawn: drop the verdict on the
+    // Algorithm 2 counts (no other error can be raised before the walks) and let
+    // the rescan judge the new ones.
+    ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
+    const int64_t nb = allocate_blocks(g.n);
+    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R, w.off, g.scan_part, nullptr, g.norm_part + nb), "Algorithm 3 rescan");
+    *launches += 3;
     return ESIM_OK;
 }
 
@@ -243,10 +317,17 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
         ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
     else
         ESIM_CUDA_TRY(launch_allocate32(g, w.hist32, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation (FP32c)");
+    int extra_launches = 0;
+    g.last_alg3_nodes = 0;
+    if (g.alg3) {
+        esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches);
+        if (a3 != ESIM_OK) return a3;
+    }
     if (g.timing) cudaEventRecord(g.ev[2], g.stream);
-    ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr), "walk pairs");
+    ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr), "walk pairs");
     if (g.timing) cudaEventRecord(g.ev[3], g.stream);
-    ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
+    if (g.alg3) ESIM_CUDA_TRY(launch_dhat_alg3(g, w.nonmeet, w.off, w.depth, w.zsum, c, w.dhat), "dhat (Algorithm 3)");
+    else ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
     if (g.precision == 0) ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
     else
         ESIM_CUDA_TRY(launch_reverse32(g, w.hist32, L, c, w.dhat, s, w.w2, w.sa2, w.sb2), "reverse sweeps (FP32c)");
@@ -279,7 +360,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     // kernels launched: forward init + per level (rows [+ long rows]), 3 allocation
     // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
     g.last_launches = (1 + L * (1 + (g.out.nlong > 0 ? 1 : 0))) + 3 + 1 + 1 +
-                      (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0);
+                      (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0) + extra_launches;
     g.last_R_b = R_b;
     g.last_kappa = kappa;
     g.last_norm2 = hs.pi_norm2;
@@ -630,6 +711,21 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
             for (int64_t p = in_rowptr[j]; p < in_rowptr[j + 1]; ++p) out_c[cur[in_col[p]]++] = (int32_t)j;
     }
     {
+        // repeated in-edges (Algorithm 3 needs a simple graph) and the host in-degrees
+        std::vector<int64_t> mark((size_t)n, -1);
+        auto din = std::make_shared<std::vector<uint32_t>>((size_t)n);
+        for (int64_t j = 0; j < n && !g.has_duplicates; ++j)
+            for (int64_t p = in_rowptr[j]; p < in_rowptr[j + 1]; ++p) {
+                if (mark[in_col[p]] == j) {
+                    g.has_duplicates = true;
+                    break;
+                }
+                mark[in_col[p]] = j;
+            }
+        for (int64_t j = 0; j < n; ++j) (*din)[j] = (uint32_t)(in_rowptr[j + 1] - in_rowptr[j]);
+        g.din_host = din;
+    }
+    {
         std::vector<double> inv((size_t)n);
         for (int64_t j = 0; j < n; ++j) {
             const int64_t d = in_rowptr[j + 1] - in_rowptr[j];
@@ -713,6 +809,26 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "precision") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
         g.precision = (int)value;
+    } else if (k == "alg3") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "alg3 must be 0 or 1");
+        if (value == 1.0 && g.has_duplicates)
+            return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
+        g.alg3 = (int)value;
+    } else if (k == "alg3_max_depth") {
+        if (value != 1.0 && value != 2.0 && value != 3.0) return fail(ESIM_EINVAL, "alg3_max_depth must be 1, 2 or 3");
+        g.alg3_max_depth = (int)value;
+    } else if (k == "alg3_min_pairs") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_min_pairs must be >= 0");
+        g.alg3_min_pairs = value;
+    } else if (k == "alg3_max_nodes") {
+        if (!(value >= 1.0 && value <= 4096.0)) return fail(ESIM_EINVAL, "alg3_max_nodes must be in [1, 4096]");
+        g.alg3_max_nodes = (int)value;
+    } else if (k == "alg3_d3_max_din") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_d3_max_din must be >= 0");
+        g.alg3_d3_max_din = (int)value;
+    } else if (k == "alg3_d3_max_edges") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_d3_max_edges must be >= 0");
+        g.alg3_d3_max_edges = value;
     } else {
         return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     }
@@ -730,6 +846,12 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "pair_budget") *value = g.pair_budget;
     else if (k == "timing") *value = g.timing;
     else if (k == "precision") *value = g.precision;
+    else if (k == "alg3") *value = g.alg3;
+    else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
+    else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
+    else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
+    else if (k == "alg3_d3_max_din") *value = g.alg3_d3_max_din;
+    else if (k == "alg3_d3_max_edges") *value = g.alg3_d3_max_edges;
     else if (k == "batch_tile") *value = g.batch_tile_force;
     else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];
     else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[1];
@@ -787,6 +909,7 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->ms_reverse = g.last_ms[3];
     out->ms_topk = g.last_ms[4];
     out->ms_total = g.last_ms[5];
+    out->alg3_nodes = g.last_alg3_nodes;
     return ESIM_OK;
 }
 
@@ -936,6 +1059,48 @@ esim_status esim_topk_batch_device(esim_graph* h, int32_t B, const int64_t* u, c
     if (k < 1) return fail(ESIM_EINVAL, "k must be >= 1");
     if (!ids_dev || !scores_dev) return fail(ESIM_EINVAL, "NULL output");
     return run_batch(h->g, B, u, eps, seed, c, nullptr, nullptr, k, ids_dev, scores_dev, nullptr, nullptr);
+}
+
+esim_status esim_alg3_first_meeting(esim_graph* h, int64_t k, int32_t depth, double c, double* z_out) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (k < 0 || k >= g.n) return fail(ESIM_EINVAL, "node out of range");
+    if (depth < 1 || depth > 3) return fail(ESIM_EINVAL, "need 1 <= depth <= 3");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (!z_out) return fail(ESIM_EINVAL, "z_out is NULL");
+    if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    if (!g.a3ws) {
+        if (cudaMalloc(&g.a3ws, alg3_workspace_bytes(g.n)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 workspace)");
+        }
+        g.a3ws_bytes = alg3_workspace_bytes(g.n);
+    }
+    ESIM_CUDA_TRY(alg3_first_meeting(g, k, depth, c, g.a3ws, z_out, nullptr), "Algorithm 3 first meetings");
+    return ESIM_OK;
+}
+
+esim_status esim_sample_depth(esim_graph* h, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
+                              uint64_t* counts, uint64_t* pair_steps) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!off || !counts) return fail(ESIM_EINVAL, "NULL argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_sample(g, off, c, seed, counts, pair_steps, depth), "walk pairs");
+    return ESIM_OK;
+}
+
+esim_status esim_dhat_alg3(esim_graph* h, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,
+                           const double* zsum, double c, double* dhat) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!counts || !off || !depth || !zsum || !dhat) return fail(ESIM_EINVAL, "NULL argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    ESIM_CUDA_TRY(launch_dhat_alg3(g, counts, off, depth, zsum, c, dhat), "dhat (Algorithm 3)");
+    return ESIM_OK;
 }
 
 esim_status esim_sync(esim_graph* h) {

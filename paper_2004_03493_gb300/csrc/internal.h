@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <memory>
+#include <vector>
 
 struct esim_graph;
 
@@ -65,6 +67,18 @@ struct Graph {
     double pair_budget = 1e15;
     int timing = 0;
     int precision = 0;            // 0: FP64 sweeps; 1: FP32 storage with two-float sums (FP32c)
+    // Algorithm 3 (local deterministic exploitation)
+    int alg3 = 0;
+    int alg3_max_depth = 3;
+    double alg3_min_pairs = 1e6;
+    int alg3_max_nodes = 64;
+    int alg3_d3_max_din = 64;
+    double alg3_d3_max_edges = 5e7;
+    bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
+    std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
+    void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
+    size_t a3ws_bytes = 0;
+    int32_t last_alg3_nodes = 0;
     // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
     void* bws = nullptr;
     size_t bws_bytes = 0;
@@ -97,6 +111,8 @@ cudaError_t launch_forward(const Graph& g, int64_t u, double c, int32_t L, doubl
 cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double c, const double* dhat, double* s_out,
                            double* sa, double* sb);
 cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb);
+cudaError_t launch_walk_distributions(const Graph& g, int64_t u, int steps, double* H, double* xa, double* xb);
+cudaError_t launch_pull_sum(const Graph& g, const double* x, double* out);
 cudaError_t launch_reverse32(const Graph& g, const float* hist, int32_t L, double c, const double* dhat,
                              double* s_out, float2* w, float2* sa, float2* sb);
 
@@ -107,11 +123,11 @@ cudaError_t launch_allocate(const Graph& g, const double* hist, int32_t L, doubl
 cudaError_t launch_allocate32(const Graph& g, const float* hist, int32_t L, double R_b, int mode, double* pi_out,
                               uint64_t* R_out, uint64_t* off);
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
-                          uint64_t* pair_steps);
+                          uint64_t* pair_steps, const uint8_t* depth = nullptr);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
-                                   uint64_t* nonmeet, uint64_t* pair_steps);
+                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr);
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
                                  double* dhat);
 cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
@@ -134,6 +150,14 @@ cudaError_t launch_batch_reverse_init(const Graph& g, int W, int B, const double
 cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, bool final_level, double c,
                                        const float2* w, const float* h, const float2* s_prev, float2* s_next,
                                        double* s_out, void* partial);
+
+// alg3.cu
+size_t alg3_workspace_bytes(int64_t n);
+// Z_1..Z_depth of node k (Lemma 5) into z_out (host); synchronises g.stream.
+cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, void* ws, double* z_out,
+                               int* launches);
+cudaError_t launch_dhat_alg3(const Graph& g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,
+                             const double* zsum, double c, double* dhat);
 
 // topk.cu
 constexpr int kTopkMax = 4096;

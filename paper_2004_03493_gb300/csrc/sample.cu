@@ -84,7 +84,8 @@ __device__ __forceinline__ double level_sum(const float* __restrict__ hist, int6
 // pi(k), R(k) per node; per-tile sums of R (exact and in double) and of pi^2.
 template <typename H>
 __global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const H* __restrict__ hist, int32_t L,
-                                                              double R_b, int mode, double* __restrict__ pi_out,
+                                                              double R_b, int mode, const uint32_t* __restrict__ exact_din,
+                                                              double* __restrict__ pi_out,
                                                               uint64_t* __restrict__ R_out,
                                                               unsigned long long* __restrict__ part_R,
                                                               double* __restrict__ part_norm,
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(kBlock) alloc_reduce_kernel(int64_t n, const H
         } else {
             r = (unsigned long long)ceil(v);
             if (r == 0ull && p > 0.0) r = 1ull;  // every reached node gets a pair
+            // Algorithm 3: D is exact for din <= 1, so those nodes need no pairs
+            if (exact_din && exact_din[k + 1] - exact_din[k] <= 1u) r = 0ull;
         }
         R_out[k] = r;
         sum_r += r;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kScanThreads) alloc_partials_kernel(int64_t nb
     double nrm = 0.0, rd = 0.0;
     for (int64_t b = b0; b < b1; ++b) {
         local += part_R[b];
-        nrm += part_norm[b];
+        if (part_norm) nrm += part_norm[b];
         rd += part_Rd[b];
     }
     unsigned long long total;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kScanThreads) alloc_partials_kernel(int64_t nb
     if (threadIdx.x == 0) {
         *off_n = total;
         st->sum_R = total;
-        st->pi_norm2 = nrm;
+        if (part_norm) st->pi_norm2 = nrm;
         if (rd > budget || rd >= 1.8e19) atomicOr(&st->err, kErrBudget);
     }
 }
@@ -192,7 +195,8 @@ cudaError_t launch_allocate_t(const Graph& g, const H* hist, int32_t L, double R
     unsigned long long* part_R = g.scan_part;
     double* part_norm = g.norm_part;
     double* part_Rd = g.norm_part + nb;
-    alloc_reduce_kernel<H><<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, hist, L, R_b, mode, pi_out, R_out, part_R,
+    alloc_reduce_kernel<H><<<(unsigned)nb, kBlock, 0, g.stream>>>(g.n, hist, L, R_b, mode,
+                                                                  g.alg3 ? g.in.rp : nullptr, pi_out, R_out, part_R,
                                                                   part_norm, part_Rd, g.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -244,7 +248,7 @@ __device__ __forceinline__ uint32_t pick_redraw(uint32_t d, unsigned long long m
 // is node k; in a batch of B columns segment q*n + k is node k of column q.
 struct PairState {
     unsigned long long r, rk, left, cnt, g_end, seg;
-    uint32_t k, xa, xb, t;
+    uint32_t k, xa, xb, t, d;  // d: Algorithm 3 depth of node k (0: Algorithm 2)
 };
 
 // One step of the current pair (branch-free apart from the rare Lemire
@@ -254,11 +258,14 @@ struct PairState {
 __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict__ row,
                                           const int32_t* __restrict__ col, const uint64_t* __restrict__ off,
                                           uint32_t T, const PhiloxKeys& K, unsigned long long* __restrict__ nonmeet,
-                                          unsigned long long& steps, unsigned long long n_nodes) {
+                                          unsigned long long& steps, unsigned long long n_nodes,
+                                          const uint8_t* __restrict__ depth) {
     const uint32_t rlo = (uint32_t)S.r, rhi = (uint32_t)(S.r >> 32);
     const uint4 w = philox4x32_10(make_uint4(rlo, rhi, S.k, S.t), K);
     const uint2 ra = __ldg(row + S.xa), rb = __ldg(row + S.xb);  // (first in-edge, din)
-    const bool cont = (w.x < T) & (w.z < T) & (ra.y != 0u) & (rb.y != 0u);
+    // Algorithm 3's special pairs move without the continuation draw for their first d steps
+    const bool forced = S.t < S.d;
+    const bool cont = (forced | ((w.x < T) & (w.z < T))) & (ra.y != 0u) & (rb.y != 0u);
     const unsigned long long ma = (unsigned long long)w.y * ra.y;
     const unsigned long long mb = (unsigned long long)w.w * rb.y;
     uint32_t ia = (uint32_t)(ma >> 32), ib = (uint32_t)(mb >> 32);
@@ -277,7 +284,9 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
         return;
     }
     steps += S.t + 1u;
-    S.cnt += meet ? 0ull : 1ull;
+    // Algorithm 2 counts pairs that never meet; Algorithm 3 counts pairs that first
+    // meet after their d forced steps
+    S.cnt += S.d ? ((meet & (S.t >= S.d)) ? 1ull : 0ull) : (meet ? 0ull : 1ull);
     S.t = 0;
     if (--S.left == 0) {
         if (S.cnt) atomicAdd(nonmeet + S.seg, S.cnt);
@@ -294,6 +303,7 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
         S.r = 0;
         S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
         S.k = (uint32_t)(S.seg < n_nodes ? S.seg : S.seg % n_nodes);
+        S.d = depth ? depth[S.k] : 0u;
         S.xa = S.xb = S.k;
     }
 }
@@ -309,7 +319,8 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
                                                                  const __grid_constant__ PhiloxKeys K, double budget,
                                                                  unsigned long long* __restrict__ nonmeet,
                                                                  unsigned long long* __restrict__ steps_out,
-                                                                 Status* __restrict__ st) {
+                                                                 Status* __restrict__ st,
+                                                                 const uint8_t* __restrict__ depth) {
     __shared__ unsigned long long red[kBlock / 32];
     const unsigned long long total = off[nseg];
     if ((double)total > budget || (st->err & kErrBudget)) {
@@ -334,12 +345,13 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
         }
         S.seg = (unsigned long long)lo;
         S.k = (uint32_t)(lo < n ? lo : lo % n);
+        S.d = depth ? depth[S.k] : 0u;
         S.r = g0 - __ldg(off + S.seg);
         S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
         S.xa = S.xb = S.k;
         for (;;) {
             if (!S.left) break;
-            pair_step(S, row, col, off, T, K, nonmeet, steps, (unsigned long long)n);
+            pair_step(S, row, col, off, T, K, nonmeet, steps, (unsigned long long)n, depth);
         }
     }
     steps = block_sum(steps, red);
@@ -357,12 +369,12 @@ __global__ void dhat_kernel(int64_t n, const uint64_t* __restrict__ nonmeet, con
 static int g_sample_blocks_per_sm = 0;
 
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
-                          uint64_t* pair_steps) {
-    return launch_sample_segments(g, g.n, off, c, seed, nonmeet, pair_steps);
+                          uint64_t* pair_steps, const uint8_t* depth) {
+    return launch_sample_segments(g, g.n, off, c, seed, nonmeet, pair_steps, depth);
 }
 
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
-                                   uint64_t* nonmeet, uint64_t* pair_steps) {
+                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth) {
     cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)nseg, g.stream);
     if (e != cudaSuccess) return e;
     unsigned long long* steps = pair_steps ? (unsigned long long*)pair_steps : &g.status->pair_steps;
@@ -379,7 +391,7 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
     sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, nseg, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
-                                                         (unsigned long long*)nonmeet, steps, g.status);
+                                                         (unsigned long long*)nonmeet, steps, g.status, depth);
     return cudaGetLastError();
 }
 
@@ -422,12 +434,11 @@ __global__ void __launch_bounds__(kBlock) tile_sums_kernel(int64_t N, const uint
 cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
                           double* part_norm, double* part_Rd) {
     const int64_t nb = allocate_blocks(N);
-    cudaError_t e = cudaMemsetAsync(part_norm, 0, sizeof(double) * (size_t)nb, g.stream);
-    if (e != cudaSuccess) return e;
+    (void)part_norm;  // the scan of a ready R leaves the recorded ||pi||^2 as it is
     tile_sums_kernel<<<(unsigned)nb, kBlock, 0, g.stream>>>(N, R, part_R, part_Rd);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    alloc_partials_kernel<<<1, kScanThreads, 0, g.stream>>>(nb, part_R, part_norm, part_Rd, g.pair_budget, off + N,
+    alloc_partials_kernel<<<1, kScanThreads, 0, g.stream>>>(nb, part_R, nullptr, part_Rd, g.pair_budget, off + N,
                                                             g.status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -335,6 +335,31 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
     return cudaSuccess;
 }
 
+// Algorithm 3 helpers: h_l = (P^T)^l(u, .), the distribution of a non-stop walk from
+// u (no decay, no stop), for l = 0..steps, into H[(steps+1) * n] (FP64).
+cudaError_t launch_walk_distributions(const Graph& g, int64_t u, int steps, double* H, double* xa, double* xb) {
+    forward_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, 1.0, g.inv_din, H, xa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double* x[2] = {xa, xb};
+    for (int l = 1; l <= steps; ++l) {
+        ForwardOp op{1.0, g.inv_din, H + (size_t)l * (size_t)g.n, x[l & 1]};
+        e = sweep_level<Pol64>(g, g.out, x[(l - 1) & 1], op);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+struct PlainOp {
+    double* __restrict__ out;
+    __device__ __forceinline__ void operator()(int64_t row, double acc) const { out[row] = acc; }
+};
+
+// out(i) = sum_{j in Out(i)} x(j): the pull product over out-edges without weights.
+cudaError_t launch_pull_sum(const Graph& g, const double* x, double* out) {
+    return sweep_level<Pol64>(g, g.out, x, PlainOp{out});
+}
+
 cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb) {
     const double sc = sqrt(c);
     const float a = (float)(1.0 - sc);

@@ -103,3 +103,21 @@ def test_alg3_query_within_eps_of_power_method(oracle_walks):
         q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=16.0, alg3=True, alg3_min_pairs=1e3)
         assert np.count_nonzero(q.depth) > 0
         assert np.max(np.abs(q.s - S[:, u])) <= eps
+
+
+def test_exploitation_plan_depth_caps():
+    n, rp, col = synth.chung_lu(400, 4000, gamma=2.1, seed=8)
+    din = np.diff(rp)
+    pi = np.random.default_rng(2).random(n) * 0.1
+    R_b = 1e10
+    # a graph above the edge limit gets depth 2 everywhere; max_depth caps both rules
+    d_big, _ = a3.exploitation_plan(n, rp, pi, R_b, C, max_nodes=20, d3_max_edges=100)
+    assert set(np.unique(d_big[d_big > 0])) == {2}
+    d1, R1 = a3.exploitation_plan(n, rp, pi, R_b, C, max_depth=1, max_nodes=20)
+    ex = np.nonzero(d1)[0]
+    assert len(ex) > 0 and np.all(d1[ex] == 1)
+    assert np.array_equal(R1[ex], np.maximum(1, np.ceil(R_b * pi[ex] ** 2 * C ** 2)).astype(np.uint64))
+    # the din threshold moves nodes between depth 3 and 2
+    d_t, _ = a3.exploitation_plan(n, rp, pi, R_b, C, max_nodes=40, d3_max_din=3)
+    for k in np.nonzero(d_t)[0]:
+        assert d_t[k] == (3 if din[k] <= 3 else 2)
