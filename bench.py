@@ -5,11 +5,12 @@ Workload (default "cl100k"): directed Chung-Lu power-law graph, n = 100,000,
 m = 1,000,000, in/out Pareto weights with exponent 2.1 (graph seed 1);
 c = 0.6, eps = 1e-6, ten seeded sources (uniform over nodes with din >= 1) run
 one at a time, top-50 each.  One step = one top-k query (the sources cycle),
-every step of the hot path (forward sweeps, allocation, walk pairs, reverse
-sweeps, top-k) on the GPU, with kappa = 4 by default: on the small ER workload
-kappa = 4 gave no error above eps in 100 seeds (the paper's 6/(1-sqrt c)^4 is
-infeasible at eps = 1e-6).  The graph is synthetic; the paper's datasets are not
-available.
+every step of the hot path (forward sweeps, allocation, Algorithm 3's exact
+first-meeting terms for the heaviest nodes, walk pairs, reverse sweeps, top-k) on
+the GPU, with kappa = 4 by default: on the small ER workload kappa = 4 gave no
+error above eps in 100 seeds (the paper's 6/(1-sqrt c)^4 is infeasible at
+eps = 1e-6).  --alg3 0 runs Algorithm 2 alone.  The graph is synthetic; the
+paper's datasets are not available.
 
 Timing: W warm-up steps, then K timed steps; the graph (8 MB) fits in L2, so
 L2 is flushed (a 512 MB write) before every timed step, outside the CUDA-event
@@ -483,7 +484,7 @@ def run_exceed(args, w):
     n, rp, col = make_graph(w)
     c, eps = w["c"], w["eps"]
     S = power.power_method(n, rp, col, c)
-    g = esim.Graph(n, rp, col, kappa=args.kappa, precision=args.precision)
+    g = esim.Graph(n, rp, col, kappa=args.kappa, precision=args.precision, alg3=args.alg3)
     us = [0] + [int(x) for x in synth_sources(rp, 4, 3)]
     errs = []
     t0 = time.perf_counter()
@@ -499,7 +500,8 @@ def run_exceed(args, w):
             "data": "synthetic",
             "config": {"workload": args.workload, "graph": w["kind"], "n": n, "m": len(col), "c": c, "eps": eps,
                        "kappa": args.kappa if args.kappa > 0 else "6/(1-sqrt c)^4", "seeds": args.seeds,
-                       "sources": us, "oracle": "Power Method (FP64 CPU)"},
+                       "sources": us, "oracle": "Power Method (FP64 CPU)",
+                       "dhat": "Algorithm 3" if args.alg3 else "Algorithm 2", "alg3_nodes_last": st["alg3_nodes"]},
             "max_err": {"max": float(errs.max()), "p50": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
                         "mean": float(errs.mean())},
             "pairs_per_query": st["sum_R"], "queries_per_s": args.seeds / wall}
@@ -530,7 +532,8 @@ def main():
     ap.add_argument("--exceed", action="store_true", help="Theorem 1 exceed rate over --seeds seeds (small workloads)")
     ap.add_argument("--seeds", type=int, default=100)
     ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
-    ap.add_argument("--alg3", type=int, default=0, help="1: Algorithm 3 D^ estimator for the heaviest nodes")
+    ap.add_argument("--alg3", type=int, default=1,
+                    help="1 (default): Algorithm 3 D^ estimator for the heaviest nodes; 0: Algorithm 2 only")
     ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-batch", type=int, default=8, help="serving: requests per wave")
