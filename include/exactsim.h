@@ -83,6 +83,8 @@ typedef struct {
     float ms_total;
     int32_t alg3_nodes;   /* nodes exploited by Algorithm 3 in the last query */
     int32_t reserved2;
+    uint64_t hist_entries;    /* stored history entries: (L+1) n dense, kept entries sparse */
+    uint64_t workspace_bytes; /* device bytes of the last query's workspace layout */
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */
@@ -131,6 +133,14 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
  *                    query returns ESIM_EBUDGET without running walks
  *   "timing"         1: record per-phase CUDA event times in the stats
+ *   "sparse_hist"    1: sparse linearization (Section 3.2; FP64 only): the query runs
+ *                    at eps/2 (L and R_b) and keeps only the history entries
+ *                    pi^l(k) > (1-sqrt c)^2 eps/2 -- fewer than 1/that many, whatever n --
+ *                    which adds at most eps/2 to the error; pi for the allocation is
+ *                    still the dense sum.  0: dense history (default)
+ *   "diag"           0: D^ estimated by walk pairs (default); 1: ParSim's approximation
+ *                    D = (1-c) I (Section 2, related work), no allocation and no walk pairs -- the
+ *                    baseline of the paper's comparison of diagonal corrections
  *   "alg3"           1: Algorithm 3 (local deterministic exploitation) for the
  *                    heaviest nodes, depth-limited (see esim_alg3_first_meeting);
  *                    nodes with din <= 1 take the exact D (1 at din 0, 1-c at din 1)

@@ -36,17 +36,30 @@ class QueryResult:
 
 def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
           kappa: float | None = None, mode: str = "pi2", threads: int = 0, alg3: bool = False,
-          alg3_max_depth: int = 3, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64) -> QueryResult:
+          alg3_max_depth: int = 3, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64,
+          sparse: bool = False, diag: str = "estimated") -> QueryResult:
+    """One single-source query.  ``sparse``: sparse Linearization (Sec. 3.2) -- the
+    query runs at eps/2 and the reverse loop reads the history with entries at or
+    below (1 - sqrt(c))^2 eps/2 dropped (pi for the allocation is the full sum).
+    ``diag="parsim"``: D = (1 - c) I with no walks, ParSim's approximation (Sec. 2)."""
+    if sparse:
+        eps = 0.5 * eps
     L = lin.levels(c, eps)
     H = lin.hop_vectors(n, in_rowptr, in_col, u, c, L)
     pi = lin.ppr(H)
     R_b = lin.sample_base(n, c, eps, kappa)
+    Hr = lin.sparsify(H, lin.sparse_threshold(c, eps)) if sparse else H
+    if diag == "parsim":
+        D = np.full(n, 1.0 - c)
+        s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
+        z = np.zeros(n, dtype=np.uint64)
+        return QueryResult(s=s, H=Hr, pi=pi, R=z, nonmeet=z, D=D, L=L, R_b=R_b, pair_steps=0)
     if not alg3:
         R = lin.allocate(pi, R_b, mode)
         nonmeet, steps = walks.walk_pairs(n, in_rowptr, in_col, R, c, seed, threads)
         D = lin.dhat(nonmeet, R)
-        s = lin.reverse(n, in_rowptr, in_col, H, D, c)
-        return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
+        s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
+        return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
     # Algorithm 3 for the heaviest nodes (pi^2 allocation)
     depth, R = a3.exploitation_plan(n, in_rowptr, pi, R_b, c, alg3_max_depth, alg3_min_pairs, alg3_max_nodes)
     zsum = np.zeros(n)
@@ -55,6 +68,6 @@ def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0
     counts, steps = walks.walk_pairs_depth(n, in_rowptr, in_col, R, depth, c, seed, threads)
     din = np.diff(np.asarray(in_rowptr, dtype=np.int64))
     D = a3.dhat_alg3(counts, R, depth, zsum, din, c)
-    s = lin.reverse(n, in_rowptr, in_col, H, D, c)
-    return QueryResult(s=s, H=H, pi=pi, R=R, nonmeet=counts, D=D, L=L, R_b=R_b, pair_steps=steps,
+    s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
+    return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=counts, D=D, L=L, R_b=R_b, pair_steps=steps,
                        depth=depth, zsum=zsum)

@@ -24,6 +24,9 @@ Notation follows Sec. 3.1: a = 1 - sqrt(c); P is the reverse transition matrix
                          evaluation of the same sum used to pin ``reverse``
 * ``topk``            -- k nodes with the largest scores (Sec. 1), order (score desc,
                          id asc), source excluded unless asked
+* ``sparse_threshold``/``sparsify`` -- sparse Linearization (Sec. 3.2): the stored
+                         pi^l keep only entries above (1 - sqrt(c))^2 eps; the sparse-
+                         linearization lemma bounds the extra error by eps
 
 Floating-point decisions that pick integers (L, R(k)) are made with the exact
 operation order the library documents, so both sides take them in FP64.
@@ -148,3 +151,14 @@ __all__ = [
     "levels", "kappa_paper", "sample_base", "hop_vectors", "ppr", "allocate", "dhat",
     "reverse", "bilinear", "topk", "pair_threshold", "in_degrees",
 ]
+
+
+def sparse_threshold(c: float, eps: float) -> float:
+    """theta = (1 - sqrt(c))^2 eps: history entries at or below it are dropped (Sec. 3.2)."""
+    a = 1.0 - math.sqrt(c)
+    return a * a * eps
+
+
+def sparsify(H: np.ndarray, theta: float) -> np.ndarray:
+    """The stored history of sparse Linearization: pi^l(k) if pi^l(k) > theta, else 0."""
+    return np.where(H > theta, H, 0.0)

@@ -161,12 +161,25 @@ struct Ws {
     double* s;         // n
     uint8_t* depth;    // n  Algorithm 3 depth per node (0: Algorithm 2)
     double* zsum;      // n  Algorithm 3: sum of the exact Z_l(k)
+    // sparse linearization (FP64): rolling pi^l, the running pi, the kept entries
+    double* lev;       // n
+    double* pirun;     // n
+    SparseHist sh;     // cap entries, L+2 level ends
 };
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Lay out the arena at `base` (or only measure it when base is null); returns bytes.
-size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w) {
+// Capacity of the sparse history: fewer than 1/theta entries exceed theta, because
+// the pi^l(k) over all levels and nodes sum to at most 1 (pigeonhole, Section 3.2);
+// never more than the dense (L+1) n.
+uint64_t sparse_capacity(int64_t n, int32_t L, double theta) {
+    const double bound = floor(1.000001 / theta) + 1.0;
+    const double dense = (double)(L + 1) * (double)n;
+    return (uint64_t)(bound < dense ? bound : dense);
+}
+
+size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64_t sparse_cap = 0) {
     const size_t n = (size_t)n_;
     size_t o = 0;
     auto take = [&](size_t bytes) -> char* {
@@ -175,7 +188,16 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w) {
         return p;
     };
     Ws t{};
-    if (precision == 0) {
+    if (precision == 0 && sparse_cap > 0) {
+        t.lev = (double*)take(8 * n);
+        t.pirun = (double*)take(8 * n);
+        t.xa = (double*)take(8 * n);
+        t.xb = (double*)take(8 * n);
+        t.sh.idx = (int32_t*)take(4 * (size_t)sparse_cap);
+        t.sh.val = (double*)take(8 * (size_t)sparse_cap);
+        t.sh.lvl = (uint64_t*)take(8 * (size_t)(L + 2));
+        t.sh.cap = sparse_cap;
+    } else if (precision == 0) {
         t.hist = (double*)take(8 * n * (size_t)(L + 1));
         t.xa = (double*)take(8 * n);
         t.xb = (double*)take(8 * n);
@@ -201,8 +223,9 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w) {
     return o;
 }
 
-esim_status ensure_ws(Graph& g, int32_t L, int precision, Ws& w) {
-    const size_t need = ws_layout(g.n, L, precision, nullptr, nullptr);
+esim_status ensure_ws(Graph& g, int32_t L, int precision, Ws& w, uint64_t sparse_cap = 0) {
+    const size_t need = ws_layout(g.n, L, precision, nullptr, nullptr, sparse_cap);
+    g.last_ws_bytes = need;
     if (need > g.ws_bytes) {
         cudaStreamSynchronize(g.stream);
         cudaFree(g.ws);
@@ -214,7 +237,7 @@ esim_status ensure_ws(Graph& g, int32_t L, int precision, Ws& w) {
         }
         g.ws_bytes = need;
     }
-    ws_layout(g.n, L, precision, (char*)g.ws, &w);
+    ws_layout(g.n, L, precision, (char*)g.ws, &w, sparse_cap);
     return ESIM_OK;
 }
 
@@ -298,11 +321,18 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     if (!valid_c_eps(c, eps)) return fail(ESIM_EINVAL, "need 0 < c < 1 and 0 < eps < 1");
     if (k > kTopkMax) return fail(ESIM_ENOTSUP, "k above 4096");
     ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
-    const int32_t L = esim_levels(c, eps);
+    // sparse linearization (Section 3.2): the query runs at eps/2 and drops the
+    // history entries pi^l(k) <= (1 - sqrt c)^2 eps/2, which adds at most eps/2
+    const bool sparse = g.sparse_hist && g.precision == 0;
+    const double eps_q = sparse ? 0.5 * eps : eps;
+    const int32_t L = esim_levels(c, eps_q);
     const double kappa = kappa_of(g, c);
-    const double R_b = kappa * log((double)g.n) / (eps * eps);
+    const double R_b = kappa * log((double)g.n) / (eps_q * eps_q);
+    const double a_c = 1.0 - sqrt(c);
+    const double theta = a_c * a_c * eps_q;
+    const uint64_t cap = sparse ? sparse_capacity(g.n, L, theta) : 0;
     Ws w;
-    esim_status st = ensure_ws(g, L, g.precision, w);
+    esim_status st = ensure_ws(g, L, g.precision, w, cap);
     if (st != ESIM_OK) return st;
     double* s = s_dev ? s_dev : w.s;
     if (g.timing)
@@ -310,25 +340,44 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
             if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
     ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
     if (g.timing) cudaEventRecord(g.ev[0], g.stream);
-    if (g.precision == 0) ESIM_CUDA_TRY(launch_forward(g, u, c, L, w.hist, w.xa, w.xb), "forward sweeps");
+    if (sparse)
+        ESIM_CUDA_TRY(launch_forward_sparse(g, u, c, L, theta, w.sh, w.lev, w.pirun, w.xa, w.xb),
+                      "forward sweeps (sparse history)");
+    else if (g.precision == 0) ESIM_CUDA_TRY(launch_forward(g, u, c, L, w.hist, w.xa, w.xb), "forward sweeps");
     else ESIM_CUDA_TRY(launch_forward32(g, u, c, L, w.hist32, w.xa32, w.xb32), "forward sweeps (FP32c)");
     if (g.timing) cudaEventRecord(g.ev[1], g.stream);
-    if (g.precision == 0)
-        ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
-    else
-        ESIM_CUDA_TRY(launch_allocate32(g, w.hist32, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation (FP32c)");
+    // kernels of the allocation, sampling and D^ phases (the default counts 3 + 1 + 1)
     int extra_launches = 0;
     g.last_alg3_nodes = 0;
-    if (g.alg3) {
-        esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches);
-        if (a3 != ESIM_OK) return a3;
+    if (g.diag_mode == 1) {
+        // ParSim's approximation D = (1-c) I: no allocation and no walk pairs
+        if (g.timing) cudaEventRecord(g.ev[2], g.stream);
+        if (g.timing) cudaEventRecord(g.ev[3], g.stream);
+        ESIM_CUDA_TRY(launch_fill(g, g.n, 1.0 - c, w.dhat), "dhat (ParSim)");
+        extra_launches -= 4;
+    } else {
+        if (sparse)  // pi was summed level by level during the forward sweeps
+            ESIM_CUDA_TRY(launch_allocate(g, w.pirun, 0, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
+        else if (g.precision == 0)
+            ESIM_CUDA_TRY(launch_allocate(g, w.hist, L, R_b, g.alloc_mode, w.pi, w.R, w.off), "allocation");
+        else
+            ESIM_CUDA_TRY(launch_allocate32(g, w.hist32, L, R_b, g.alloc_mode, w.pi, w.R, w.off),
+                          "allocation (FP32c)");
+        if (g.alg3) {
+            esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches);
+            if (a3 != ESIM_OK) return a3;
+        }
+        if (g.timing) cudaEventRecord(g.ev[2], g.stream);
+        ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr), "walk pairs");
+        if (g.timing) cudaEventRecord(g.ev[3], g.stream);
+        if (g.alg3)
+            ESIM_CUDA_TRY(launch_dhat_alg3(g, w.nonmeet, w.off, w.depth, w.zsum, c, w.dhat), "dhat (Algorithm 3)");
+        else ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
     }
-    if (g.timing) cudaEventRecord(g.ev[2], g.stream);
-    ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr), "walk pairs");
-    if (g.timing) cudaEventRecord(g.ev[3], g.stream);
-    if (g.alg3) ESIM_CUDA_TRY(launch_dhat_alg3(g, w.nonmeet, w.off, w.depth, w.zsum, c, w.dhat), "dhat (Algorithm 3)");
-    else ESIM_CUDA_TRY(launch_dhat(g, w.nonmeet, w.off, w.dhat), "dhat");
-    if (g.precision == 0) ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
+    if (sparse)
+        ESIM_CUDA_TRY(launch_reverse_sparse(g, w.sh, L, c, w.dhat, s, w.xa), "reverse sweeps (sparse history)");
+    else if (g.precision == 0)
+        ESIM_CUDA_TRY(launch_reverse(g, w.hist, L, c, w.dhat, s, w.xa, w.xb), "reverse sweeps");
     else
         ESIM_CUDA_TRY(launch_reverse32(g, w.hist32, L, c, w.dhat, s, w.w2, w.sa2, w.sb2), "reverse sweeps (FP32c)");
     if (g.timing) cudaEventRecord(g.ev[4], g.stream);
@@ -361,6 +410,8 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
     g.last_launches = (1 + L * (1 + (g.out.nlong > 0 ? 1 : 0))) + 3 + 1 + 1 +
                       (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0) + extra_launches;
+    if (sparse) g.last_launches += 2 * (L + 1);  // a compaction and a scatter per level
+    g.last_hist_entries = sparse ? std::min<uint64_t>(hs.hist_count, cap) : (uint64_t)(L + 1) * (uint64_t)g.n;
     g.last_R_b = R_b;
     g.last_kappa = kappa;
     g.last_norm2 = hs.pi_norm2;
@@ -374,6 +425,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     if (hs.err & kErrBudget)
         return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
     if (hs.err & kErrTimeout) return fail(ESIM_ETIMEOUT, "device wait timed out");
+    if (hs.err & kErrCapacity) return fail(ESIM_ENOMEM, "sparse history above its capacity");
     return ESIM_OK;
 }
 
@@ -808,7 +860,15 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
         for (int i = 0; i < 3; ++i) g.batch_tile_fwd[i] = g.batch_tile_rev[i] = -1;
     } else if (k == "precision") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
+        if (value == 1.0 && g.sparse_hist) return fail(ESIM_ENOTSUP, "sparse_hist needs precision 0 (FP64)");
         g.precision = (int)value;
+    } else if (k == "sparse_hist") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "sparse_hist must be 0 or 1");
+        if (value == 1.0 && g.precision != 0) return fail(ESIM_ENOTSUP, "sparse_hist needs precision 0 (FP64)");
+        g.sparse_hist = (int)value;
+    } else if (k == "diag") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "diag must be 0 (estimated) or 1 (ParSim (1-c) I)");
+        g.diag_mode = (int)value;
     } else if (k == "alg3") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "alg3 must be 0 or 1");
         if (value == 1.0 && g.has_duplicates)
@@ -846,6 +906,8 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "pair_budget") *value = g.pair_budget;
     else if (k == "timing") *value = g.timing;
     else if (k == "precision") *value = g.precision;
+    else if (k == "diag") *value = g.diag_mode;
+    else if (k == "sparse_hist") *value = g.sparse_hist;
     else if (k == "alg3") *value = g.alg3;
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
@@ -910,6 +972,8 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->ms_topk = g.last_ms[4];
     out->ms_total = g.last_ms[5];
     out->alg3_nodes = g.last_alg3_nodes;
+    out->hist_entries = g.last_hist_entries;
+    out->workspace_bytes = g.last_ws_bytes;
     return ESIM_OK;
 }
 

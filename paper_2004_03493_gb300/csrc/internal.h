@@ -17,6 +17,7 @@ namespace esim {
 enum : int {
     kErrBudget = 1,   // sum of R(k) above the pair budget, or R(k) overflow
     kErrTimeout = 2,  // a bounded wait ran out
+    kErrCapacity = 4, // the sparse history outgrew its (pigeonhole) capacity
 };
 
 // Per-query device status block (one per graph handle).
@@ -25,7 +26,17 @@ struct Status {
     unsigned long long pair_steps;
     double pi_norm2;
     int err;
-    int pad;
+    unsigned int ticket;             // last-block ticket of the sparse-history compaction
+    unsigned long long hist_count;   // sparse history entries so far
+};
+
+// Sparse history of one query (sparse linearization): entries [lvl[l], lvl[l+1]) are
+// the kept (node, pi^l(node)) of level l.
+struct SparseHist {
+    int32_t* idx;
+    double* val;
+    uint64_t* lvl;   // L + 2
+    uint64_t cap;
 };
 
 // One segment of a long CSR row: entries [beg, end) of row `row`.
@@ -67,8 +78,10 @@ struct Graph {
     double pair_budget = 1e15;
     int timing = 0;
     int precision = 0;            // 0: FP64 sweeps; 1: FP32 storage with two-float sums (FP32c)
+    int sparse_hist = 0;          // 1: sparse linearization (FP64 only; the query runs at eps/2)
     // Algorithm 3 (local deterministic exploitation)
     int alg3 = 0;
+    int diag_mode = 0;  // 0: D^ from walk pairs (Algorithm 2 / 3); 1: ParSim's D = (1-c) I
     int alg3_max_depth = 3;
     double alg3_min_pairs = 1e6;
     int alg3_max_nodes = 64;
@@ -79,6 +92,8 @@ struct Graph {
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
     size_t a3ws_bytes = 0;
     int32_t last_alg3_nodes = 0;
+    uint64_t last_hist_entries = 0;
+    uint64_t last_ws_bytes = 0;
     // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
     void* bws = nullptr;
     size_t bws_bytes = 0;
@@ -115,6 +130,10 @@ cudaError_t launch_walk_distributions(const Graph& g, int64_t u, int steps, doub
 cudaError_t launch_pull_sum(const Graph& g, const double* x, double* out);
 cudaError_t launch_reverse32(const Graph& g, const float* hist, int32_t L, double c, const double* dhat,
                              double* s_out, float2* w, float2* sa, float2* sb);
+cudaError_t launch_forward_sparse(const Graph& g, int64_t u, double c, int32_t L, double theta, const SparseHist& h,
+                                  double* lev, double* pi_run, double* xa, double* xb);
+cudaError_t launch_reverse_sparse(const Graph& g, const SparseHist& h, int32_t L, double c, const double* dhat,
+                                  double* s_out, double* sa);
 
 // sample.cu
 int64_t allocate_blocks(int64_t n);
@@ -125,6 +144,7 @@ cudaError_t launch_allocate32(const Graph& g, const float* hist, int32_t L, doub
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
                           uint64_t* pair_steps, const uint8_t* depth = nullptr);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
+cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
                                    uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr);

@@ -366,6 +366,11 @@ __global__ void dhat_kernel(int64_t n, const uint64_t* __restrict__ nonmeet, con
     }
 }
 
+__global__ void fill_kernel(int64_t n, double value, double* __restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = value;
+}
+
 static int g_sample_blocks_per_sm = 0;
 
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
@@ -397,6 +402,13 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
 
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat) {
     return launch_dhat_segments(g, g.n, nonmeet, off, dhat);
+}
+
+cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    if (b > (int64_t)g.sm_count * 8) b = (int64_t)g.sm_count * 8;
+    fill_kernel<<<(unsigned)(b < 1 ? 1 : b), kBlock, 0, g.stream>>>(n, value, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,

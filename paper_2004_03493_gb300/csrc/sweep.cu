@@ -101,6 +101,13 @@ struct ReverseOp {  // FP64
     }
 };
 
+struct ReverseSparseOp {  // FP64; the D^ pi^{L-l} / a term is scattered from the sparse history
+    double sc;
+    const double* __restrict__ inv_din;
+    double* __restrict__ s_out;
+    __device__ __forceinline__ void operator()(int64_t row, double acc) const { s_out[row] = (sc * acc) * inv_din[row]; }
+};
+
 struct ForwardOp32c {  // FP32 storage, two-float sum
     f2 sc;
     const uint32_t* __restrict__ in_rp;
@@ -249,6 +256,69 @@ __global__ void reverse_init2f_kernel(int64_t n, double inv_a, const double* __r
 
 namespace {
 
+// Sparse linearization (Section 3.2): after forward level l, pi_run += pi^l (level
+// order, as the dense sum) and the entries pi^l(k) > theta are appended to the
+// sparse history as (k, pi^l(k)).  Warps take their slots with one atomic each; the
+// order of entries within a level therefore varies, but each node appears at most
+// once per level, so the reverse scatter gives the same values whatever the order.
+// The last block to finish records the level's end (a ticket, no waiting).
+__global__ void __launch_bounds__(kBlock) compact_level_kernel(int64_t n, const double* __restrict__ lev,
+                                                               double* __restrict__ pi_run, int first, double theta,
+                                                               SparseHist h, int level, Status* __restrict__ st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {  // uniform per block
+        const int64_t i = base + threadIdx.x;
+        double v = 0.0;
+        bool keep = false;
+        if (i < n) {
+            v = lev[i];
+            pi_run[i] = first ? v : pi_run[i] + v;
+            keep = v > theta;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (mask) {
+            unsigned long long pos0 = 0ull;
+            if (lane == 0) pos0 = atomicAdd(&st->hist_count, (unsigned long long)__popc(mask));
+            pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+            if (keep) {
+                const unsigned long long pos = pos0 + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+                if (pos < h.cap) {
+                    h.idx[pos] = (int32_t)i;
+                    h.val[pos] = v;
+                } else {
+                    atomicOr(&st->err, kErrCapacity);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&st->ticket, 1u);
+        if (t == gridDim.x - 1) {
+            unsigned long long end = atomicAdd(&st->hist_count, 0ull);
+            if (end > h.cap) end = h.cap;
+            h.lvl[level + 1] = end;
+            st->ticket = 0u;
+        }
+    }
+}
+
+// s(k) += D^(k) pi^level(k) / a over the sparse entries of one level (unique nodes).
+__global__ void __launch_bounds__(kBlock) scatter_level_kernel(const uint64_t* __restrict__ lvl, int level,
+                                                               const int32_t* __restrict__ idx,
+                                                               const double* __restrict__ val,
+                                                               const double* __restrict__ dhat, double a,
+                                                               double* __restrict__ s) {
+    const uint64_t beg = lvl[level], end = lvl[level + 1];
+    for (uint64_t p = beg + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t k = idx[p];
+        s[k] = s[k] + dhat[k] * val[p] / a;
+    }
+}
+
 int elementwise_blocks(const Graph& g, int64_t n) {
     int64_t b = (n + kBlock - 1) / kBlock;
     int64_t cap = (int64_t)g.sm_count * 8;
@@ -331,6 +401,51 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
         ReverseOp op{sc, a, g.inv_din, dhat, hist + (size_t)(L - l) * g.n, sn};
         e = sweep_level<Pol64>(g, g.in, sp, op);
         if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Forward sweeps with the sparse history: dense rolling vectors (lev = pi^l, x^l),
+// pi = sum_l pi^l accumulated in level order, and only pi^l(k) > theta kept.
+cudaError_t launch_forward_sparse(const Graph& g, int64_t u, double c, int32_t L, double theta, const SparseHist& h,
+                                  double* lev, double* pi_run, double* xa, double* xb) {
+    const double sc = sqrt(c);
+    const double a = 1.0 - sc;
+    cudaError_t e = cudaMemsetAsync(h.lvl, 0, sizeof(uint64_t) * (size_t)(L + 2), g.stream);
+    if (e != cudaSuccess) return e;
+    const int eb = elementwise_blocks(g, g.n);
+    forward_init_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, u, a, g.inv_din, lev, xa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    compact_level_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, lev, pi_run, 1, theta, h, 0, g.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    double* x[2] = {xa, xb};
+    for (int32_t l = 1; l <= L; ++l) {
+        ForwardOp op{sc, g.inv_din, lev, x[l & 1]};
+        if ((e = sweep_level<Pol64>(g, g.out, x[(l - 1) & 1], op)) != cudaSuccess) return e;
+        compact_level_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, lev, pi_run, 0, theta, h, l, g.status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Reverse sweeps with the sparse history: s^l = sqrt(c) P^T s^{l-1}, then the kept
+// entries of pi^{L-l} add D^ pi^{L-l} / a.
+cudaError_t launch_reverse_sparse(const Graph& g, const SparseHist& h, int32_t L, double c, const double* dhat,
+                                  double* s_out, double* sa) {
+    const double sc = sqrt(c);
+    const double a = 1.0 - sc;
+    double* buf[2] = {s_out, sa};
+    const unsigned sb = (unsigned)g.sm_count * 4;
+    cudaError_t e = launch_fill(g, g.n, 0.0, buf[L & 1]);
+    if (e != cudaSuccess) return e;
+    scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L, h.idx, h.val, dhat, a, buf[L & 1]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int32_t l = 1; l <= L; ++l) {
+        double* sn = buf[(L - l) & 1];
+        ReverseSparseOp op{sc, g.inv_din, sn};
+        if ((e = sweep_level<Pol64>(g, g.in, buf[(L - l + 1) & 1], op)) != cudaSuccess) return e;
+        scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L - l, h.idx, h.val, dhat, a, sn);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
