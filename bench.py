@@ -509,6 +509,79 @@ def run_exceed(args, w):
     g.close()
 
 
+ABLATION_VARIANTS = (
+    # name, options: the paper's basic ExactSim, each optimization added in turn, and ParSim
+    ("basic", dict(alloc=1, alg3=0, sparse_hist=0)),
+    ("pi2", dict(alloc=0, alg3=0, sparse_hist=0)),
+    ("pi2+alg3", dict(alloc=0, alg3=1, sparse_hist=0)),
+    ("optimized", dict(alloc=0, alg3=1, sparse_hist=1)),
+    ("parsim", dict(diag=1)),
+)
+
+
+def run_ablation(args, w):
+    """The paper's ablation (Sec. 4): basic vs optimized ExactSim, plus ParSim's D.
+
+    Time/error part: the small ER graph (the Power Method gives S), eps in
+    {1e-2, 1e-3, 1e-4}, five sources, one seeded query each per variant; per
+    variant and eps the median device ms per query, the max error over all
+    nodes and over v != u, and the walk pairs per query.  Memory part: the
+    Chung-Lu n=4e6 graph, one query per eps in {1e-5, 1e-6, 1e-7}: the device
+    workspace of the dense history against the sparse one (the walk count does
+    not change the workspace, so these queries run at kappa = 1e-6).
+    """
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_03493_gb300 as esim
+    from oracle import power
+    n, rp, col = make_graph(WORKLOADS["er2000"])
+    c = 0.6
+    S = power.power_method(n, rp, col, c)
+    us = [0] + [int(x) for x in synth_sources(rp, 4, 3)]
+    rows = []
+    for name, opts in ABLATION_VARIANTS:
+        g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, **opts)
+        for eps in (1e-2, 1e-3, 1e-4):
+            g.query(us[0], c, eps, 99)  # warm-up
+            ms, err, err_off, pairs = [], 0.0, 0.0, []
+            for i, u in enumerate(us):
+                s = g.query(u, c, eps, i)
+                st = g.stats()
+                ms.append(st["ms_total"])
+                pairs.append(st["sum_R"])
+                d = np.abs(s - S[:, u])
+                err = max(err, float(d.max()))
+                d[u] = 0.0
+                err_off = max(err_off, float(d.max()))
+            rows.append({"variant": name, "eps": eps, "ms_per_query": float(np.median(ms)), "max_err": err,
+                         "max_err_off_source": err_off, "pairs_per_query": float(np.mean(pairs)),
+                         "within_eps": err <= eps})
+        g.close()
+    wl = WORKLOADS["cl4m"]
+    n4, rp4, col4 = make_graph(wl)
+    u4 = sources_for(wl, rp4, 1, 0)[0]
+    mem = []
+    for sparse in (0, 1):
+        g = esim.Graph(n4, rp4, col4, kappa=1e-6, sparse_hist=sparse, alg3=0)
+        for eps in (1e-5, 1e-6, 1e-7):
+            g.query(u4, c, eps, 0)
+            st = g.stats()
+            mem.append({"sparse_hist": sparse, "eps": eps, "L": st["L"], "hist_entries": st["hist_entries"],
+                        "workspace_bytes": st["workspace_bytes"]})
+        g.close()
+    graph_bytes = 2 * (4 * len(col4) + 4 * (n4 + 1))
+    line = {"metric": "ablation: basic vs optimized ExactSim (time, max error) and history memory",
+            "unit": "rows", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"time_error_graph": "erdos_renyi n=2000 m=20000", "c": c, "kappa": args.kappa,
+                       "sources": us, "oracle": "Power Method (FP64 CPU)",
+                       "memory_graph": f"chung_lu n={n4} m={len(col4)} gamma=2.2", "memory_source": u4,
+                       "graph_csr_bytes": graph_bytes},
+            "time_error": rows, "memory": mem}
+    print(json.dumps(line), flush=True)
+
+
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources": w["sources"], "queries_per_step": 1,
@@ -532,6 +605,8 @@ def main():
     ap.add_argument("--exceed", action="store_true", help="Theorem 1 exceed rate over --seeds seeds (small workloads)")
     ap.add_argument("--seeds", type=int, default=100)
     ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
+    ap.add_argument("--ablation", action="store_true",
+                    help="basic vs optimized ExactSim and ParSim: time/error on the small ER graph, memory on cl4m")
     ap.add_argument("--alg3", type=int, default=1,
                     help="1 (default): Algorithm 3 D^ estimator for the heaviest nodes; 0: Algorithm 2 only")
     ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
@@ -559,6 +634,9 @@ def main():
         return
     if args.exceed:
         run_exceed(args, w)
+        return
+    if args.ablation:
+        run_ablation(args, w)
         return
 
     import torch

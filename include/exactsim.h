@@ -137,7 +137,8 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *                    at eps/2 (L and R_b) and keeps only the history entries
  *                    pi^l(k) > (1-sqrt c)^2 eps/2 -- fewer than 1/that many, whatever n --
  *                    which adds at most eps/2 to the error; pi for the allocation is
- *                    still the dense sum.  0: dense history (default)
+ *                    still the dense sum.  A counting pass of the forward sweeps sizes
+ *                    the workspace to the kept entries.  0: dense history (default)
  *   "diag"           0: D^ estimated by walk pairs (default); 1: ParSim's approximation
  *                    D = (1-c) I (Section 2, related work), no allocation and no walk pairs -- the
  *                    baseline of the paper's comparison of diagonal corrections

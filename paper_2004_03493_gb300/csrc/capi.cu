@@ -188,15 +188,11 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
         return p;
     };
     Ws t{};
-    if (precision == 0 && sparse_cap > 0) {
+    if (precision == 0 && sparse_cap > 0) {  // the entries themselves go last (see below)
         t.lev = (double*)take(8 * n);
         t.pirun = (double*)take(8 * n);
         t.xa = (double*)take(8 * n);
         t.xb = (double*)take(8 * n);
-        t.sh.idx = (int32_t*)take(4 * (size_t)sparse_cap);
-        t.sh.val = (double*)take(8 * (size_t)sparse_cap);
-        t.sh.lvl = (uint64_t*)take(8 * (size_t)(L + 2));
-        t.sh.cap = sparse_cap;
     } else if (precision == 0) {
         t.hist = (double*)take(8 * n * (size_t)(L + 1));
         t.xa = (double*)take(8 * n);
@@ -219,6 +215,13 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
     t.s = (double*)take(8 * n);
     t.depth = (uint8_t*)take(n);
     t.zsum = (double*)take(8 * n);
+    if (precision == 0 && sparse_cap > 0) {
+        // last, so that the layout for a smaller capacity is a prefix of this one
+        t.sh.lvl = (uint64_t*)take(8 * (size_t)(L + 2));
+        t.sh.idx = (int32_t*)take(4 * (size_t)sparse_cap);
+        t.sh.val = (double*)take(8 * (size_t)sparse_cap);
+        t.sh.cap = sparse_cap;
+    }
     if (w) *w = t;
     return o;
 }
@@ -330,8 +333,25 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     const double R_b = kappa * log((double)g.n) / (eps_q * eps_q);
     const double a_c = 1.0 - sqrt(c);
     const double theta = a_c * a_c * eps_q;
-    const uint64_t cap = sparse ? sparse_capacity(g.n, L, theta) : 0;
     Ws w;
+    uint64_t cap = 0;
+    int count_launches = 0;
+    if (sparse) {
+        // counting pass: the forward sweeps once without storing, then a workspace
+        // sized to the kept entries (never above the pigeonhole bound)
+        esim_status st0 = ensure_ws(g, L, 0, w, 1);
+        if (st0 != ESIM_OK) return st0;
+        ESIM_CUDA_TRY(cudaMemsetAsync(g.status, 0, sizeof(Status), g.stream), "reset status");
+        const SparseHist none{nullptr, nullptr, nullptr, 0};
+        ESIM_CUDA_TRY(launch_forward_sparse(g, u, c, L, theta, none, w.lev, w.pirun, w.xa, w.xb),
+                      "forward sweeps (counting pass)");
+        ESIM_CUDA_TRY(cudaMemcpyAsync(g.status_host, g.status, sizeof(Status), cudaMemcpyDeviceToHost, g.stream),
+                      "copy status");
+        ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "forward sweeps (counting pass)");
+        const uint64_t kept = g.status_host->hist_count;
+        cap = std::max<uint64_t>(1, std::min<uint64_t>(kept, sparse_capacity(g.n, L, theta)));
+        count_launches = 2 + L * (2 + (g.out.nlong > 0 ? 1 : 0));
+    }
     esim_status st = ensure_ws(g, L, g.precision, w, cap);
     if (st != ESIM_OK) return st;
     double* s = s_dev ? s_dev : w.s;
@@ -410,7 +430,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
     g.last_launches = (1 + L * (1 + (g.out.nlong > 0 ? 1 : 0))) + 3 + 1 + 1 +
                       (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0) + extra_launches;
-    if (sparse) g.last_launches += 2 * (L + 1);  // a compaction and a scatter per level
+    if (sparse) g.last_launches += 2 * (L + 1) + count_launches;  // compactions, scatters, counting pass
     g.last_hist_entries = sparse ? std::min<uint64_t>(hs.hist_count, cap) : (uint64_t)(L + 1) * (uint64_t)g.n;
     g.last_R_b = R_b;
     g.last_kappa = kappa;

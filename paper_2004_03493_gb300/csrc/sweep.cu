@@ -286,9 +286,9 @@ __global__ void __launch_bounds__(kBlock) compact_level_kernel(int64_t n, const 
                 if (pos < h.cap) {
                     h.idx[pos] = (int32_t)i;
                     h.val[pos] = v;
-                } else {
+                } else if (h.cap) {
                     atomicOr(&st->err, kErrCapacity);
-                }
+                }  // cap = 0: counting pass
             }
         }
     }
@@ -297,9 +297,8 @@ __global__ void __launch_bounds__(kBlock) compact_level_kernel(int64_t n, const 
         __threadfence();
         const unsigned t = atomicAdd(&st->ticket, 1u);
         if (t == gridDim.x - 1) {
-            unsigned long long end = atomicAdd(&st->hist_count, 0ull);
-            if (end > h.cap) end = h.cap;
-            h.lvl[level + 1] = end;
+            const unsigned long long end = atomicAdd(&st->hist_count, 0ull);
+            if (h.lvl) h.lvl[level + 1] = end < h.cap ? end : h.cap;
             st->ticket = 0u;
         }
     }
@@ -406,13 +405,15 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
 }
 
 // Forward sweeps with the sparse history: dense rolling vectors (lev = pi^l, x^l),
-// pi = sum_l pi^l accumulated in level order, and only pi^l(k) > theta kept.
+// pi = sum_l pi^l accumulated in level order, and only pi^l(k) > theta kept.  With
+// h.cap = 0 and h.lvl = NULL the entries are only counted (into Status::hist_count).
 cudaError_t launch_forward_sparse(const Graph& g, int64_t u, double c, int32_t L, double theta, const SparseHist& h,
                                   double* lev, double* pi_run, double* xa, double* xb) {
     const double sc = sqrt(c);
     const double a = 1.0 - sc;
-    cudaError_t e = cudaMemsetAsync(h.lvl, 0, sizeof(uint64_t) * (size_t)(L + 2), g.stream);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (h.lvl && (e = cudaMemsetAsync(h.lvl, 0, sizeof(uint64_t) * (size_t)(L + 2), g.stream)) != cudaSuccess)
+        return e;
     const int eb = elementwise_blocks(g, g.n);
     forward_init_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, u, a, g.inv_din, lev, xa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
