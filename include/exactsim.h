@@ -143,17 +143,18 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *                    D = (1-c) I (Section 2, related work), no allocation and no walk pairs -- the
  *                    baseline of the paper's comparison of diagonal corrections
  *   "alg3"           1: Algorithm 3 (local deterministic exploitation) for the
- *                    heaviest nodes, depth-limited (see esim_alg3_first_meeting);
- *                    nodes with din <= 1 take the exact D (1 at din 0, 1-c at din 1)
- *                    and no walk pairs.  An exploited node k of depth d gets the
- *                    exact Z_1..Z_d (Lemma 5) and max(1, ceil(R_b pi(k)^2 c^(2d)))
- *                    special pairs that move for d steps without the continuation
- *                    draw; D^(k) = 1 - sum Z - c^d (pairs meeting after step d)/R.
+ *                    heaviest nodes; nodes with din <= 1 take the exact D (1 at din 0,
+ *                    1-c at din 1) and no walk pairs.  An exploited node k of depth d
+ *                    gets the exact Z_1..Z_d (Lemma 5) and max(1, ceil(R_b pi(k)^2
+ *                    c^(2d))) special pairs that move for d steps without the
+ *                    continuation draw; D^(k) = 1 - sum Z - c^d (pairs meeting after step
+ *                    d)/R.  The depth minimises an estimate of the GPU work (walks plus
+ *                    the sweeps of Lemma 5, which grow with the supports of
+ *                    (P^T)^i(k, .)); depth 0 leaves the node to Algorithm 2.
  *                    Needs a graph without repeated in-edges (else ESIM_ENOTSUP).
  *   "alg3_max_nodes" heaviest nodes (by pi) considered, 1..4096 (default 64)
- *   "alg3_min_pairs" smallest Algorithm 2 pair count worth exploiting (default 1e6)
- *   "alg3_max_depth" 1..3 (default 3); depth 3 also needs din(k) <= "alg3_d3_max_din"
- *                    (default 64) and m <= "alg3_d3_max_edges" (default 5e7), else 2
+ *   "alg3_min_pairs" smallest Algorithm 2 pair count worth considering (default 1e6)
+ *   "alg3_max_depth" deepest exploitation, 1..16 (default 8)
  *   "batch_tile"     -1: batched sweeps pick their tile by timing (default);
  *                    0, 1, 2: force 32, 16 or 8 lanes per row (results do not change)
  *   "precision"      0: FP64 sweeps (default);
@@ -308,7 +309,7 @@ esim_status esim_reverse_f32(esim_graph* g, const float* hist, int32_t L, double
                              double* s_out);
 
 /* Algorithm 3 steps.  esim_alg3_first_meeting writes Z_1..Z_depth of node k
- * (1 <= depth <= 3) into z_out (host): Z_l(k) = c^l * the probability that two
+ * (1 <= depth <= 16) into z_out (host): Z_l(k) = c^l * the probability that two
  * non-stop walks from k first meet at step l (Lemma 5, summed over the meeting
  * node); synchronous.  esim_sample_depth is esim_sample with depth[n] (device,
  * uint8, may be NULL): for a node of depth d > 0 its pairs move without the

@@ -13,13 +13,13 @@ Test infrastructure only (see ``oracle/__init__.py``).
   (rational) distribution of two non-stop walks from k over pairs of nodes, step by
   step, removing the pairs that have met; Z_l = c^l * (mass that first meets at
   step l).  An independent formulation that pins the lemma's recursion.
-* ``exploitation_plan`` -- the depth-limited exploitation the library uses: the
-  heaviest nodes (by pi(k), at most ``max_nodes``, with R(k) >= ``min_pairs`` and
-  din(k) >= 2) get depth 3 if din(k) <= 64 and m <= 5e7, else 2 (capped by
-  ``max_depth``); their
-  sample count becomes max(1, ceil(R_b pi(k)^2 c^(2 depth))).  Nodes with din <= 1
-  take the exact values of Algorithm 3 (D = 1 at din = 0, 1 - c at din = 1) and no
-  samples.
+* ``exploitation_plan`` -- the exploitation the library uses: the heaviest nodes (by
+  pi(k), at most ``max_nodes``, with R(k) >= ``min_pairs`` and din(k) >= 2) take the
+  depth that minimises ``exploit_cost`` (the paper stops its adaptive exploration
+  when the explored edges reach the walk work; the cost here weighs the library's
+  dense sweeps against its walks); their sample count becomes
+  max(1, ceil(R_b pi(k)^2 c^(2 depth))).  Nodes with din <= 1 take the exact values of
+  Algorithm 3 (D = 1 at din = 0, 1 - c at din = 1) and no samples.
 * ``dhat_alg3`` -- D^(k) = 1 - sum_{l <= depth} Z_l(k) - c^depth * tailmeet(k) / R(k)
   for exploited nodes (Algorithm 3), nonmeet / R for the others.
 
@@ -93,12 +93,54 @@ def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, dep
     return out
 
 
-def exploitation_plan(n: int, in_rowptr, pi: np.ndarray, R_b: float, c: float, max_depth: int = 3,
-                      min_pairs: float = 1e6, max_nodes: int = 64, d3_max_din: int = 64,
-                      d3_max_edges: float = 5e7):
-    """(depth uint8[n], R uint64[n]) of the depth-limited Algorithm 3."""
+def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int) -> float:
+    """Estimated GPU work (in sampler pair-steps) of exploiting a node to depth d.
+
+    d = 0 is Algorithm 2 alone.  Walks: R_d (d + 1/(1-c)) with R_d = max(1, ceil(v c^(2d))),
+    v = R_b pi(k)^2.  Lemma 5 at depth d: 2d-1 single sweeps of m+n entries (weight 4
+    each entry), sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps (weight 0.5 per entry
+    and column), and 2^20 per kernel launch (3 per sweep; 3 per probe step and 2 per
+    block of 32 probes).  The same arithmetic, in the same order, as the library's plan,
+    so that both sides pick the same depth.
+    """
+    r = math.ceil(v) if d == 0 else math.ceil(v * c ** (2 * d))
+    r = max(1.0, float(r))
+    cost = r * (d + 1.0 / (1.0 - c))
+    if d > 0:
+        edges = float(m + n)
+        probe = 0
+        launches = 3 * (2 * d - 1)
+        for i in range(1, d - 1):
+            probe += int(supp[i]) * (d - i)
+            launches += (int(supp[i]) + 31) // 32 * (3 * (d - i) + 2)
+        cost += 4.0 * edges * float(2 * d - 1)
+        cost += 0.5 * edges * float(probe)
+        cost += 1048576.0 * float(launches)
+    return cost
+
+
+def supports(P, k: int, levels: int) -> list[int]:
+    """|supp h_i| for i = 0..levels, h_i the non-stop walk distribution from k."""
+    H = walk_distribution(P, k, levels)
+    return [int(np.count_nonzero(H[i])) for i in range(levels + 1)]
+
+
+def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 8,
+                      min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None):
+    """(depth uint8[n], R uint64[n]) of Algorithm 3 with the cost-minimising depth.
+
+    Candidates: the max_nodes largest pi(k) (ties to the lower id) with pi(k) > 0,
+    din(k) >= 2 and an Algorithm 2 count max(1, ceil(R_b pi(k)^2)) >= min_pairs.  Each
+    takes the depth d in 0..max_depth of least ``exploit_cost`` (the first on ties);
+    d > 0 gives R(k) = max(1, ceil(R_b pi(k)^2 c^(2d))).  Nodes with din <= 1 take the
+    exact D and no samples.  ``stats["min_gap"]`` (if given) receives the smallest
+    relative gap between a chosen cost and another depth's cost: the margin of the
+    floating-point depth decisions.
+    """
+    min_gap = math.inf
     din = in_degrees(in_rowptr)
     m = int(np.asarray(in_rowptr)[-1])
+    P = transition_matrix(n, in_rowptr, in_col)
     pi = np.asarray(pi, dtype=np.float64)
     R = np.ceil(R_b * (pi * pi)).astype(np.uint64)
     R[(pi > 0) & (R == 0)] = 1
@@ -107,12 +149,28 @@ def exploitation_plan(n: int, in_rowptr, pi: np.ndarray, R_b: float, c: float, m
     order = np.lexsort((np.arange(n), -pi))[:max_nodes]
     for kk in order:
         kk = int(kk)
-        if pi[kk] <= 0 or din[kk] < 2 or R[kk] < min_pairs or max_depth < 1:
+        if not pi[kk] > 0:
+            break
+        if din[kk] < 2:
             continue
-        d = min(max_depth, 3 if (din[kk] <= d3_max_din and m <= d3_max_edges) else 2)
+        v = R_b * (pi[kk] * pi[kk])
+        if max(1.0, float(math.ceil(v))) < min_pairs:
+            continue
+        supp = supports(P, kk, max(0, max_depth - 2))
+        costs = [exploit_cost(dd, v, c, supp, n, m) for dd in range(max_depth + 1)]
+        d, best = 0, costs[0]
+        for dd in range(1, max_depth + 1):
+            if costs[dd] < best:
+                d, best = dd, costs[dd]
+        for dd, cost in enumerate(costs):
+            if dd != d:
+                min_gap = min(min_gap, abs(cost - best) / best)
+        if d == 0:
+            continue
         depth[kk] = d
-        v = R_b * (pi[kk] * pi[kk]) * c ** (2 * d)
-        R[kk] = max(1, int(math.ceil(v)))
+        R[kk] = max(1, int(math.ceil(v * c ** (2 * d))))
+    if stats is not None:
+        stats["min_gap"] = min_gap
     return depth, R
 
 

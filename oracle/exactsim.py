@@ -32,11 +32,12 @@ class QueryResult:
     pair_steps: int
     depth: np.ndarray | None = None
     zsum: np.ndarray | None = None
+    plan_gap: float = float("inf")  # margin of Algorithm 3's depth decisions (relative cost gap)
 
 
 def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
           kappa: float | None = None, mode: str = "pi2", threads: int = 0, alg3: bool = False,
-          alg3_max_depth: int = 3, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64,
+          alg3_max_depth: int = 8, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64,
           sparse: bool = False, diag: str = "estimated") -> QueryResult:
     """One single-source query.  ``sparse``: sparse Linearization (Sec. 3.2) -- the
     query runs at eps/2 and the reverse loop reads the history with entries at or
@@ -61,7 +62,9 @@ def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0
         s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
         return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
     # Algorithm 3 for the heaviest nodes (pi^2 allocation)
-    depth, R = a3.exploitation_plan(n, in_rowptr, pi, R_b, c, alg3_max_depth, alg3_min_pairs, alg3_max_nodes)
+    plan = {}
+    depth, R = a3.exploitation_plan(n, in_rowptr, in_col, pi, R_b, c, alg3_max_depth, alg3_min_pairs,
+                                    alg3_max_nodes, stats=plan)
     zsum = np.zeros(n)
     for k in np.nonzero(depth)[0]:
         zsum[k] = sum(a3.first_meeting_lemma5(n, in_rowptr, in_col, int(k), c, int(depth[k])))
@@ -70,4 +73,4 @@ def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0
     D = a3.dhat_alg3(counts, R, depth, zsum, din, c)
     s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
     return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=counts, D=D, L=L, R_b=R_b, pair_steps=steps,
-                       depth=depth, zsum=zsum)
+                       depth=depth, zsum=zsum, plan_gap=plan["min_gap"])

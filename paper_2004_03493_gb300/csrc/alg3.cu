@@ -1,23 +1,25 @@
-// Algorithm 3 ("Improved method for estimating D(k,k)"), depth-limited: exact
-// first-meeting probabilities Z_1..Z_d of node k (d <= 3) from Lemma 5, and the
-// diagonal estimate that combines them with the tail walk pairs.
+// Algorithm 3 ("Improved method for estimating D(k,k)"): exact first-meeting
+// probabilities Z_1..Z_d of node k by Lemma 5, for any depth d <= kAlg3MaxDepth,
+// and the diagonal estimate that combines them with the tail walk pairs.
 //
-// With h_l = (P^T)^l(k, .) the distribution of a non-stop walk from k after l steps
-// (dense FP64, by the pull sweep with no decay), C_j(q) = sum_x (P^T)^j(q, x)^2 the
-// chance that two non-stop walks from q coincide at step j, and P~ the transition
-// matrix with squared entries, Lemma 5 summed over q gives
-//   Z_1 = c   * |h_1|^2
-//   Z_2 = c^2 * (|h_2|^2 - <h_1^2, C_1>)
-//   Z_3 = c^3 * (|h_3|^2 - <h_2^2 - P~ h_1^2, C_1> - sum_{q in I(k)} h_1(q)^2 C_2(q))
-// On a graph without repeated in-edges C_1(q) = 1/din(q), h_1(q) = 1/din(k) on I(k),
-// and (P~ v)(i) = sum_{j : i in I(j)} v(j) / din(j)^2.  C_2(q) of each in-neighbour q
-// of k comes from two more sweeps from q.  Every sum uses fixed-order block
-// partials, so the values are deterministic.
+// Notation: h_l = (P^T)^l(k, .), the distribution of a non-stop walk from k after l
+// steps (dense FP64, by pull sweeps over the out-edge CSR with no decay); Zv_l the
+// vector Z_l(k, .) of Lemma 5; P~ the transition matrix with squared entries.
+// Lemma 5 reads, for each target level j,
+//   Zv_j = c^j h_j^2 - c P~ Zv_{j-1} - sum_{l'=2}^{j-1} c^{l'} sum_{q'} Zv_{j-l'}(q') ((P^T)^{l'}(q', .))^2
+// (the l' = 1 term is one squared-weight sweep, because (P^T)(q', q)^2 = 1/din(q')^2
+// for q in I(q')).  The l' >= 2 terms need the walk distributions of every q' in
+// the support of h_{j-l'}: the "probes".  Probes run 32 at a time as an n x 32 FP64
+// block through a multi-column pull product whose epilogue subtracts
+// c^{l'} Zv_i(q') h^{q'}_{l'}(q)^2 from Zv_{i+l'}(q), column after column in the
+// order of q' (ascending ids), so the result does not depend on the batching.
+// Z_j = sum_q Zv_j(q) by fixed-order block partials.  Everything is deterministic.
 #include "common.cuh"
 #include "internal.h"
 
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 namespace esim {
@@ -25,17 +27,16 @@ namespace esim {
 namespace {
 
 constexpr int kDotBlocks = 1024;
+constexpr int kProbeW = 32;  // probe columns per block (one warp lane each)
 
-// partial[block] of sum_i a(i)^2 * w(i) (w = NULL: sum a(i)^2); kind 1: sum_i a(i) * w(i)
-__global__ void __launch_bounds__(kBlock) wsum_kernel(int64_t n, const double* __restrict__ a,
-                                                      const double* __restrict__ w, int kind,
+// partial[block] of sum_i a(i)^2 (kind 0) or sum_i a(i) (kind 2)
+__global__ void __launch_bounds__(kBlock) wsum_kernel(int64_t n, const double* __restrict__ a, int kind,
                                                       double* __restrict__ partial) {
     __shared__ double red[kBlock / 32];
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = a[i];
-        if (kind == 1) acc += v * w[i];
-        else acc += w ? v * v * w[i] : v * v;
+        acc += kind == 2 ? v : v * v;
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
@@ -50,13 +51,151 @@ __global__ void sum_partials_kernel(int count, const double* __restrict__ partia
     if (threadIdx.x == 0) *out = acc;
 }
 
-// x(j) = (v(j) / din(j))^2: the input of the squared-transition sweep
+// count[0] += |{i : h(i) != 0}| (integer atomics: order-free, so exact)
+__global__ void __launch_bounds__(kBlock) support_kernel(int64_t n, const double* __restrict__ h,
+                                                         unsigned long long* __restrict__ count) {
+    __shared__ unsigned long long red[kBlock / 32];
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += h[i] != 0.0 ? 1ull : 0ull;
+    c = block_sum(c, red);
+    if (threadIdx.x == 0 && c) atomicAdd(count, c);
+}
+
+// flag(i) = h(i) != 0, as the uint64 counts of the offset scan
+__global__ void flag_kernel(int64_t n, const double* __restrict__ h, uint64_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = h[i] != 0.0 ? 1ull : 0ull;
+}
+
+// ids[off(i)] = i for the flagged i: the support in ascending order
+__global__ void scatter_ids_kernel(int64_t n, const uint64_t* __restrict__ flag, const uint64_t* __restrict__ off,
+                                   int32_t* __restrict__ ids) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) ids[off[i]] = (int32_t)i;
+}
+
+// x = v / din^2: the input of the squared-transition sweep P~ v
 __global__ void sq_scale_kernel(int64_t n, const double* __restrict__ v, const double* __restrict__ inv_din,
                                 double* __restrict__ x) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double t = v[i] * inv_din[i];
-        x[i] = t * t;
+        const double w = inv_din[i];
+        x[i] = v[i] * (w * w);
     }
+}
+
+// Zv_j = c^j h_j^2 - c T + Zv_j, where Zv_j already holds the (negative) probe terms
+// and T = P~ Zv_{j-1} (T = NULL at j = 1)
+__global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double* __restrict__ h,
+                                   const double* __restrict__ T, double* __restrict__ zv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double hv = h[i];
+        double z = cj * (hv * hv);
+        if (T) z -= c * T[i];
+        zv[i] = z + zv[i];
+    }
+}
+
+// Probe block start: x_0 = e_{q'} / din(q') in column col (row-major n x 32, zeroed before)
+__global__ void probe_init_kernel(const int32_t* __restrict__ ids, int count, const double* __restrict__ inv_din,
+                                  double* __restrict__ X) {
+    const int col = threadIdx.x;
+    if (col < count) {
+        const int32_t q = ids[col];
+        X[(size_t)q * kProbeW + col] = inv_din[q];
+    }
+}
+
+// coef(col) = c^{l'} Zv_i(q'_col); 0 for unused columns
+__global__ void probe_coef_kernel(const int32_t* __restrict__ ids, int count, const double* __restrict__ zv_src,
+                                  double cl, double* __restrict__ coef) {
+    const int col = threadIdx.x;
+    if (col < kProbeW) coef[col] = col < count ? cl * zv_src[ids[col]] : 0.0;
+}
+
+struct ProbeEpi {
+    const double* inv_din;
+    double* x_next;      // n x 32: h / din for the next step
+    const double* coef;  // 32 (NULL: no accumulation at this step)
+    double* zacc;        // n: Zv of the target level
+};
+
+// Row `row` of h^{q'}_{l'} is `h` in lane = column.  All 32 lanes of the warp call it.
+__device__ __forceinline__ void probe_epilogue(int64_t row, double h, int lane, const ProbeEpi& e) {
+    e.x_next[(size_t)row * kProbeW + lane] = h * e.inv_din[row];
+    if (e.coef) {
+        const double t = e.coef[lane] * (h * h);
+        double acc = e.zacc[row];
+#pragma unroll
+        for (int l = 0; l < kProbeW; ++l) acc -= __shfl_sync(0xffffffffu, t, l);
+        if (lane == 0) e.zacc[row] = acc;
+    }
+}
+
+// One probe step: h(i, col) = sum_{j in Out(i)} X(j, col), a pull over the out-edge
+// CSR for 32 columns at once.  Short rows: one warp per row, lane = column, entries
+// added in order.  Long rows: one warp per 4096-entry segment writes partials that
+// probe_long_rows_kernel adds in segment order.
+__global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uint32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const double* __restrict__ X, uint32_t long_min,
+                                                            int64_t nseg, const Segment* __restrict__ seg,
+                                                            double* __restrict__ partial, int short_blocks,
+                                                            ProbeEpi epi) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int64_t wib = threadIdx.x >> 5;
+    if ((int)blockIdx.x >= short_blocks) {
+        const int64_t nsw = ((int64_t)gridDim.x - short_blocks) * wpb;
+        for (int64_t s = ((int64_t)blockIdx.x - short_blocks) * wpb + wib; s < nseg; s += nsw) {
+            const Segment sg = seg[s];
+            double acc = 0.0;
+            uint32_t p = sg.beg;
+            for (; p + 4 <= sg.end; p += 4) {
+                const int32_t j0 = __ldg(col + p), j1 = __ldg(col + p + 1), j2 = __ldg(col + p + 2),
+                              j3 = __ldg(col + p + 3);
+                const double v0 = X[(size_t)j0 * kProbeW + lane], v1 = X[(size_t)j1 * kProbeW + lane],
+                             v2 = X[(size_t)j2 * kProbeW + lane], v3 = X[(size_t)j3 * kProbeW + lane];
+                acc += v0;
+                acc += v1;
+                acc += v2;
+                acc += v3;
+            }
+            for (; p < sg.end; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
+            partial[(size_t)s * kProbeW + lane] = acc;
+        }
+        return;
+    }
+    const int64_t nw = (int64_t)short_blocks * wpb;
+    for (int64_t row = (int64_t)blockIdx.x * wpb + wib; row < n; row += nw) {
+        const uint32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
+        if (e - b >= long_min) continue;  // warp-uniform: a long row
+        double acc = 0.0;
+        uint32_t p = b;
+        for (; p + 4 <= e; p += 4) {
+            const int32_t j0 = __ldg(col + p), j1 = __ldg(col + p + 1), j2 = __ldg(col + p + 2),
+                          j3 = __ldg(col + p + 3);
+            const double v0 = X[(size_t)j0 * kProbeW + lane], v1 = X[(size_t)j1 * kProbeW + lane],
+                         v2 = X[(size_t)j2 * kProbeW + lane], v3 = X[(size_t)j3 * kProbeW + lane];
+            acc += v0;
+            acc += v1;
+            acc += v2;
+            acc += v3;
+        }
+        for (; p < e; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
+        probe_epilogue(row, acc, lane, epi);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(int64_t nlong, const int32_t* __restrict__ long_rows,
+                                                                 const int32_t* __restrict__ long_first,
+                                                                 const double* __restrict__ partial, ProbeEpi epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nlong) return;  // warp-uniform
+    double acc = 0.0;
+    for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc += partial[(size_t)s * kProbeW + lane];
+    probe_epilogue(long_rows[w], acc, lane, epi);
 }
 
 // D^ of Algorithm 3 for exploited nodes (depth > 0), of Algorithm 2 for the others,
@@ -88,93 +227,185 @@ int eblocks(const Graph& g, int64_t n) {
 }
 
 struct A3Ws {
-    double* H;        // 4 n: h_0 .. h_3 from k
-    double* Hq;       // 3 n: h_0 .. h_2 from an in-neighbour of k
+    double* H;        // (D+1) n: h_0 .. h_D from k
+    double* Zv;       // (D+1) n: Zv_1 .. Zv_D at rows 1..D (row 0 unused)
+    double* T;        // n: P~ Zv_{j-1}
+    double* x;        // n: sweep input
     double* xa;       // n
     double* xb;       // n
-    double* t;        // n: P~ h_1^2
-    double* x;        // n: sweep input
-    double* partial;  // kDotBlocks
-    double* sums;     // 16
+    uint64_t* flag;   // n
+    uint64_t* off;    // n + 1
+    int32_t* ids;     // n
+    double* Xa;       // 32 n probe block
+    double* Xb;       // 32 n
+    double* partial;  // max(kDotBlocks, 32 nseg)
+    double* coef;     // 32
+    double* sums;     // 64
+    unsigned long long* counts;  // 64
 };
 
-A3Ws a3_layout(int64_t n_, void* base) {
+size_t a3_layout(int64_t n_, int64_t nseg, void* base, A3Ws* out) {
     const size_t n = (size_t)n_;
-    double* p = (double*)base;
-    A3Ws w;
-    w.H = p; p += 4 * n;
-    w.Hq = p; p += 3 * n;
-    w.xa = p; p += n;
-    w.xb = p; p += n;
-    w.t = p; p += n;
-    w.x = p; p += n;
-    w.partial = p; p += kDotBlocks;
-    w.sums = p;
-    return w;
+    const size_t D = (size_t)kAlg3MaxDepth;
+    size_t o = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? (char*)base + o : nullptr;
+        o += (bytes + 255) / 256 * 256;
+        return p;
+    };
+    A3Ws w{};
+    w.H = (double*)take(8 * (D + 1) * n);
+    w.Zv = (double*)take(8 * (D + 1) * n);
+    w.T = (double*)take(8 * n);
+    w.x = (double*)take(8 * n);
+    w.xa = (double*)take(8 * n);
+    w.xb = (double*)take(8 * n);
+    w.flag = (uint64_t*)take(8 * n);
+    w.off = (uint64_t*)take(8 * (n + 1));
+    w.ids = (int32_t*)take(4 * n);
+    w.Xa = (double*)take(8 * kProbeW * n);
+    w.Xb = (double*)take(8 * kProbeW * n);
+    const size_t np = std::max<size_t>(kDotBlocks, (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
+    w.partial = (double*)take(8 * np);
+    w.coef = (double*)take(8 * kProbeW);
+    w.sums = (double*)take(8 * 64);
+    w.counts = (unsigned long long*)take(8 * 64);
+    if (out) *out = w;
+    return o;
 }
 
-cudaError_t wsum(const Graph& g, const double* a, const double* w, int kind, const A3Ws& ws, double* out_dev) {
-    wsum_kernel<<<kDotBlocks, kBlock, 0, g.stream>>>(g.n, a, w, kind, ws.partial);
+cudaError_t dsum(const Graph& g, const double* a, int kind, const A3Ws& ws, double* out_dev, int* count) {
+    wsum_kernel<<<kDotBlocks, kBlock, 0, g.stream>>>(g.n, a, kind, ws.partial);
     sum_partials_kernel<<<1, 1024, 0, g.stream>>>(kDotBlocks, ws.partial, out_dev);
+    *count += 2;
     return cudaGetLastError();
+}
+
+// One probe step for the block: X_prev -> h (epilogue: X_next, accumulation).
+cudaError_t probe_step(const Graph& g, const double* X_prev, const ProbeEpi& epi, double* partial, int* count) {
+    const DevCsr& A = g.out;
+    const int wpb = kBlock / 32;
+    int64_t sb = (g.n + wpb - 1) / wpb;
+    if (sb > (int64_t)g.sm_count * 16) sb = (int64_t)g.sm_count * 16;
+    if (sb < 1) sb = 1;
+    int64_t segb = (A.nseg + wpb - 1) / wpb;
+    if (segb > (int64_t)g.sm_count * 8) segb = (int64_t)g.sm_count * 8;
+    probe_rows_kernel<<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, X_prev, A.long_min, A.nseg,
+                                                                       A.seg, partial, (int)sb, epi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++*count;
+    if (A.nlong > 0) {
+        const int64_t blocks = (A.nlong * 32 + kBlock - 1) / kBlock;
+        probe_long_rows_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.nlong, A.long_rows, A.long_first, partial,
+                                                                          epi);
+        e = cudaGetLastError();
+        ++*count;
+    }
+    return e;
 }
 
 }  // namespace
 
-size_t alg3_workspace_bytes(int64_t n) { return sizeof(double) * ((size_t)n * 11 + kDotBlocks + 16); }
+size_t alg3_workspace_bytes(const Graph& g) { return a3_layout(g.n, g.out.nseg, nullptr, nullptr); }
+
+cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* wsp, uint64_t* supp_out, int* launches) {
+    A3Ws ws;
+    a3_layout(g.n, g.out.nseg, wsp, &ws);
+    const size_t n = (size_t)g.n;
+    int count = 0;
+    cudaError_t e = cudaMemsetAsync(ws.counts, 0, sizeof(unsigned long long) * 64, g.stream);
+    if (e != cudaSuccess) return e;
+    if (levels > 0) {
+        if ((e = launch_walk_distributions(g, k, levels, ws.H, ws.xa, ws.xb)) != cudaSuccess) return e;
+        count += 1 + levels * (1 + (g.out.nlong > 0 ? 1 : 0));
+        for (int i = 1; i <= levels; ++i) {
+            support_kernel<<<eblocks(g, g.n), kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)i * n, ws.counts + i);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++count;
+        }
+    }
+    unsigned long long host[64] = {};
+    if ((e = cudaMemcpyAsync(host, ws.counts, sizeof(host), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
+    supp_out[0] = 1;
+    for (int i = 1; i <= levels; ++i) supp_out[i] = host[i];
+    if (launches) *launches += count;
+    return cudaSuccess;
+}
 
 cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, void* wsp, double* z_out, int* launches) {
-    const A3Ws ws = a3_layout(g.n, wsp);
-    const int per_sweep = 1 + (g.out.nlong > 0 ? 1 : 0);
-    int count = 1 + depth * per_sweep + 2;
+    A3Ws ws;
+    a3_layout(g.n, g.out.nseg, wsp, &ws);
     const size_t n = (size_t)g.n;
+    const int per_sweep = 1 + (g.out.nlong > 0 ? 1 : 0);
+    const int eb = eblocks(g, g.n);
+    int count = 0;
     cudaError_t e = launch_walk_distributions(g, k, depth, ws.H, ws.xa, ws.xb);
     if (e != cudaSuccess) return e;
-    // sums: [0] |h_1|^2  [1] |h_2|^2  [2] <h_1^2, C_1>  [3] |h_3|^2  [4] <h_2^2, C_1>  [5] <P~ h_1^2, C_1>
-    if ((e = wsum(g, ws.H + n, nullptr, 0, ws, ws.sums + 0)) != cudaSuccess) return e;
-    if (depth >= 2) {
-        if ((e = wsum(g, ws.H + 2 * n, nullptr, 0, ws, ws.sums + 1)) != cudaSuccess) return e;
-        if ((e = wsum(g, ws.H + n, g.inv_din, 0, ws, ws.sums + 2)) != cudaSuccess) return e;
-        count += 4;
-    }
-    if (depth >= 3) {
-        if ((e = wsum(g, ws.H + 3 * n, nullptr, 0, ws, ws.sums + 3)) != cudaSuccess) return e;
-        if ((e = wsum(g, ws.H + 2 * n, g.inv_din, 0, ws, ws.sums + 4)) != cudaSuccess) return e;
-        sq_scale_kernel<<<eblocks(g, g.n), kBlock, 0, g.stream>>>(g.n, ws.H + n, g.inv_din, ws.x);
+    count += 1 + depth * per_sweep;
+    if ((e = cudaMemsetAsync(ws.Zv, 0, sizeof(double) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess) return e;
+    double cj = 1.0;
+    std::vector<double> cpow((size_t)depth + 1, 1.0);
+    for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
+    for (int j = 1; j <= depth; ++j) {
+        cj = cpow[(size_t)j];
+        double* zv = ws.Zv + (size_t)j * n;
+        const double* T = nullptr;
+        if (j >= 2) {  // T = P~ Zv_{j-1}
+            sq_scale_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.Zv + (size_t)(j - 1) * n, g.inv_din, ws.x);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_pull_sum(g, ws.x, ws.T)) != cudaSuccess) return e;
+            count += 1 + per_sweep;
+            T = ws.T;
+        }
+        zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cj, c, ws.H + (size_t)j * n, T, zv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_pull_sum(g, ws.x, ws.t)) != cudaSuccess) return e;
-        if ((e = wsum(g, ws.t, g.inv_din, 1, ws, ws.sums + 5)) != cudaSuccess) return e;
-        count += 7 + per_sweep;
-    }
-    double sums[8] = {};
-    if ((e = cudaMemcpyAsync(sums, ws.sums, sizeof(double) * 6, cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
-        return e;
-    if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-    z_out[0] = c * sums[0];
-    if (depth >= 2) z_out[1] = c * c * (sums[1] - sums[2]);
-    if (depth >= 3) {
-        uint32_t rp2[2];
-        if ((e = cudaMemcpy(rp2, g.in.rp + k, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
-        const uint32_t beg = rp2[0], end = rp2[1];
-        std::vector<int32_t> nbrs(end - beg);
-        if (end > beg &&
-            (e = cudaMemcpy(nbrs.data(), g.in.col + beg, sizeof(int32_t) * (end - beg), cudaMemcpyDeviceToHost)) !=
+        ++count;
+        if ((e = dsum(g, zv, 2, ws, ws.sums + j, &count)) != cudaSuccess) return e;
+        // probes from the support of h_j feed the levels j+2 .. depth
+        if (j <= depth - 2) {
+            flag_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)j * n, ws.flag);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_scan_R(g, g.n, ws.flag, ws.off, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n))) !=
                 cudaSuccess)
-            return e;
-        const double dk = (double)(end - beg);
-        double e3 = 0.0;
-        for (int32_t q : nbrs) {
-            if ((e = launch_walk_distributions(g, q, 2, ws.Hq, ws.xa, ws.xb)) != cudaSuccess) return e;
-            if ((e = wsum(g, ws.Hq + 2 * n, nullptr, 0, ws, ws.sums + 8)) != cudaSuccess) return e;
-            double c2 = 0.0;
-            if ((e = cudaMemcpyAsync(&c2, ws.sums + 8, sizeof(double), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
+                return e;
+            scatter_ids_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.flag, ws.off, ws.ids);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            count += 5;
+            uint64_t nsup = 0;
+            if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) !=
+                cudaSuccess)
                 return e;
             if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-            e3 += c2 / (dk * dk);
-            count += 1 + 2 * per_sweep + 2;
+            const int steps = depth - j;
+            for (uint64_t b0 = 0; b0 < nsup; b0 += kProbeW) {
+                const int cnt = (int)std::min<uint64_t>(kProbeW, nsup - b0);
+                const int32_t* ids = ws.ids + b0;
+                if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(double) * kProbeW * n, g.stream)) != cudaSuccess) return e;
+                probe_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.inv_din, ws.Xa);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                ++count;
+                double* X[2] = {ws.Xa, ws.Xb};
+                for (int lp = 1; lp <= steps; ++lp) {
+                    ProbeEpi epi{g.inv_din, X[lp & 1], nullptr, ws.Zv + (size_t)(j + lp) * n};
+                    if (lp >= 2) {
+                        probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)lp], ws.coef);
+                        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                        ++count;
+                        epi.coef = ws.coef;
+                    }
+                    if ((e = probe_step(g, X[(lp - 1) & 1], epi, ws.partial, &count)) != cudaSuccess) return e;
+                }
+            }
         }
-        z_out[2] = c * c * c * (sums[3] - (sums[4] - sums[5]) - e3);
     }
+    double sums[64] = {};
+    if ((e = cudaMemcpyAsync(sums, ws.sums, sizeof(double) * (size_t)(depth + 1), cudaMemcpyDeviceToHost, g.stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
+    for (int j = 1; j <= depth; ++j) z_out[j - 1] = sums[j];
     if (launches) *launches += count;
     return cudaSuccess;
 }

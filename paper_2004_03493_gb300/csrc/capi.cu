@@ -249,22 +249,63 @@ esim_status check_graph(const esim_graph* h) {
     return ESIM_OK;
 }
 
-// Algorithm 3 for the heaviest nodes (by pi): exact Z_1..Z_d (Lemma 5) on the GPU,
-// depth d = 3 if din(k) <= alg3_d3_max_din and m <= alg3_d3_max_edges, else 2 (both
-// capped by alg3_max_depth); the node's pair count becomes
-// max(1, ceil(R_b pi(k)^2 c^(2d))) (pi(k) for the basic allocation), the tail
-// estimator's variance and range being c^(2d) and c^d of Algorithm 2's.  Nodes with
+esim_status ensure_a3ws(Graph& g) {
+    const size_t need = alg3_workspace_bytes(g);
+    if (g.a3ws && g.a3ws_bytes >= need) return ESIM_OK;
+    cudaStreamSynchronize(g.stream);
+    cudaFree(g.a3ws);
+    g.a3ws = nullptr;
+    g.a3ws_bytes = 0;
+    if (cudaMalloc(&g.a3ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 workspace of " + std::to_string(need) + " bytes)");
+    }
+    g.a3ws_bytes = need;
+    return ESIM_OK;
+}
+
+// Algorithm 3's depth choice.  The paper grows l(k) until the explored edges reach
+// 2 R(k) / sqrt(c), the walk work they replace.  Here the exploitation is done with
+// dense sweeps, so the depth d of node k minimises an estimate of the GPU work, in
+// pair-steps of the sampler:
+//   walks      R_d (d + 1/(1-c)),  R_d = max(1, ceil(v c^(2d)))  (v = R_b pi(k)^2)
+//   Lemma 5    2d-1 single-vector sweeps of m+n entries (h_1..h_d and the P~ sweeps),
+//              sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps, and the launches;
+// d = 0 is Algorithm 2 alone.  The weights were measured on the bench graph: a pair-step,
+// about 4 of them per entry of a single sweep, 0.5 per entry and column of a 32-column
+// probe sweep, and 2^20 per launch.
+constexpr double kA3SweepEdge = 4.0;
+constexpr double kA3ProbeEdge = 0.5;
+constexpr double kA3Launch = 1048576.0;
+
+double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m) {
+    double r = d == 0 ? ceil(v) : ceil(v * pow(c, (double)(2 * d)));
+    if (r < 1.0) r = 1.0;
+    double cost = r * ((double)d + 1.0 / (1.0 - c));
+    if (d > 0) {
+        const double edges = (double)(m + n);
+        uint64_t probe = 0, launches = 3 * (uint64_t)(2 * d - 1);
+        for (int i = 1; i <= d - 2; ++i) {
+            probe += supp[i] * (uint64_t)(d - i);
+            launches += (supp[i] + 31) / 32 * (uint64_t)(3 * (d - i) + 2);
+        }
+        cost += kA3SweepEdge * edges * (double)(2 * d - 1);
+        cost += kA3ProbeEdge * edges * (double)probe;
+        cost += kA3Launch * (double)launches;
+    }
+    return cost;
+}
+
+// Algorithm 3 for the heaviest nodes (by pi, at most alg3_max_nodes, with din >= 2
+// and an Algorithm 2 count of at least alg3_min_pairs): the depth by alg3_cost (at
+// most alg3_max_depth), exact Z_1..Z_d (Lemma 5) on the GPU, and the pair count
+// max(1, ceil(R_b pi(k)^2 c^(2d))) (pi(k) for the basic allocation): the tail
+// estimator's variance and range are c^(2d) and c^d of Algorithm 2's.  Nodes with
 // din <= 1 already got no pairs from the allocation.  Then the offsets are rescanned.
 esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches) {
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
-    if (!g.a3ws) {
-        const size_t need = alg3_workspace_bytes(g.n);
-        if (cudaMalloc(&g.a3ws, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 workspace)");
-        }
-        g.a3ws_bytes = need;
-    }
+    esim_status a3 = ensure_a3ws(g);
+    if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(cudaMemsetAsync(w.depth, 0, (size_t)g.n, g.stream), "reset depth");
     ESIM_CUDA_TRY(cudaMemsetAsync(w.zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
     const int K = (int)std::min<int64_t>(g.alg3_max_nodes, g.n);
@@ -289,12 +330,23 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         double r0 = ceil(v);
         if (r0 < 1.0) r0 = 1.0;
         if (r0 < g.alg3_min_pairs) continue;
-        int d = (din[kk] <= (uint32_t)g.alg3_d3_max_din && (double)g.m <= g.alg3_d3_max_edges) ? 3 : 2;
-        d = std::min(d, g.alg3_max_depth);
+        uint64_t supp[kAlg3MaxDepth + 1] = {};
+        const int levels = std::max(0, g.alg3_max_depth - 2);
+        ESIM_CUDA_TRY(alg3_supports(g, kk, levels, g.a3ws, supp, launches), "Algorithm 3 supports");
+        int d = 0;
+        double best = alg3_cost(0, v, c, supp, g.n, g.m);
+        for (int dd = 1; dd <= g.alg3_max_depth; ++dd) {
+            const double cost = alg3_cost(dd, v, c, supp, g.n, g.m);
+            if (cost < best) {
+                best = cost;
+                d = dd;
+            }
+        }
         if (d < 1) continue;
-        double z[3] = {0.0, 0.0, 0.0};
+        double z[kAlg3MaxDepth] = {};
         ESIM_CUDA_TRY(alg3_first_meeting(g, kk, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
-        const double zs = z[0] + z[1] + z[2];
+        double zs = 0.0;
+        for (int j = 0; j < d; ++j) zs += z[j];
         double r = ceil(v * pow(c, (double)(2 * d)));
         if (r < 1.0) r = 1.0;
         if (r >= 1.8e19) r = 1.8e19;  // the rescan's budget check reports it
@@ -895,7 +947,8 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
             return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
         g.alg3 = (int)value;
     } else if (k == "alg3_max_depth") {
-        if (value != 1.0 && value != 2.0 && value != 3.0) return fail(ESIM_EINVAL, "alg3_max_depth must be 1, 2 or 3");
+        if (!(value >= 1.0 && value <= (double)kAlg3MaxDepth) || value != floor(value))
+            return fail(ESIM_EINVAL, "alg3_max_depth must be an integer in [1, 16]");
         g.alg3_max_depth = (int)value;
     } else if (k == "alg3_min_pairs") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_min_pairs must be >= 0");
@@ -903,12 +956,6 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_max_nodes") {
         if (!(value >= 1.0 && value <= 4096.0)) return fail(ESIM_EINVAL, "alg3_max_nodes must be in [1, 4096]");
         g.alg3_max_nodes = (int)value;
-    } else if (k == "alg3_d3_max_din") {
-        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_d3_max_din must be >= 0");
-        g.alg3_d3_max_din = (int)value;
-    } else if (k == "alg3_d3_max_edges") {
-        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_d3_max_edges must be >= 0");
-        g.alg3_d3_max_edges = value;
     } else {
         return fail(ESIM_EINVAL, "unknown option '" + k + "'");
     }
@@ -932,8 +979,6 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
-    else if (k == "alg3_d3_max_din") *value = g.alg3_d3_max_din;
-    else if (k == "alg3_d3_max_edges") *value = g.alg3_d3_max_edges;
     else if (k == "batch_tile") *value = g.batch_tile_force;
     else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];
     else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[1];
@@ -1149,18 +1194,13 @@ esim_status esim_alg3_first_meeting(esim_graph* h, int64_t k, int32_t depth, dou
     if (check_graph(h)) return ESIM_EINVAL;
     Graph& g = h->g;
     if (k < 0 || k >= g.n) return fail(ESIM_EINVAL, "node out of range");
-    if (depth < 1 || depth > 3) return fail(ESIM_EINVAL, "need 1 <= depth <= 3");
+    if (depth < 1 || depth > kAlg3MaxDepth) return fail(ESIM_EINVAL, "need 1 <= depth <= 16");
     if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
     if (!z_out) return fail(ESIM_EINVAL, "z_out is NULL");
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
     ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
-    if (!g.a3ws) {
-        if (cudaMalloc(&g.a3ws, alg3_workspace_bytes(g.n)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 workspace)");
-        }
-        g.a3ws_bytes = alg3_workspace_bytes(g.n);
-    }
+    esim_status a3 = ensure_a3ws(g);
+    if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(alg3_first_meeting(g, k, depth, c, g.a3ws, z_out, nullptr), "Algorithm 3 first meetings");
     return ESIM_OK;
 }

@@ -82,11 +82,9 @@ struct Graph {
     // Algorithm 3 (local deterministic exploitation)
     int alg3 = 0;
     int diag_mode = 0;  // 0: D^ from walk pairs (Algorithm 2 / 3); 1: ParSim's D = (1-c) I
-    int alg3_max_depth = 3;
+    int alg3_max_depth = 8;
     double alg3_min_pairs = 1e6;
     int alg3_max_nodes = 64;
-    int alg3_d3_max_din = 64;
-    double alg3_d3_max_edges = 5e7;
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
@@ -172,8 +170,12 @@ cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, b
                                        double* s_out, void* partial);
 
 // alg3.cu
-size_t alg3_workspace_bytes(int64_t n);
-// Z_1..Z_depth of node k (Lemma 5) into z_out (host); synchronises g.stream.
+constexpr int kAlg3MaxDepth = 16;
+size_t alg3_workspace_bytes(const Graph& g);
+// supp_out[i] = number of nodes with (P^T)^i(k, .) != 0, i = 0..levels (levels <= kAlg3MaxDepth);
+// synchronises g.stream.
+cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* ws, uint64_t* supp_out, int* launches);
+// Z_1..Z_depth of node k (Lemma 5) into z_out (host), depth <= kAlg3MaxDepth; synchronises g.stream.
 cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, void* ws, double* z_out,
                                int* launches);
 cudaError_t launch_dhat_alg3(const Graph& g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,

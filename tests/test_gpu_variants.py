@@ -34,6 +34,8 @@ def esim():
 def _clean(q, graph, u, c, eps_q):
     """No integer decision of this query sits within rounding of its boundary."""
     n, rp, col = graph
+    if q.plan_gap <= 1e-9:
+        return False
     v = q.R_b * (q.pi * q.pi)
     vs = [v] if q.depth is None else [v, v * c ** (2.0 * q.depth.astype(np.float64))]
     for vv in vs:

@@ -28,8 +28,8 @@ def test_lemma5_matches_bruteforce(seed):
     for k in range(n):
         if din[k] == 0:
             continue
-        z = a3.first_meeting_lemma5(nn, rp, col, k, C, 4)
-        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), 4)]
+        z = a3.first_meeting_lemma5(nn, rp, col, k, C, 6)
+        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), 6)]
         assert np.max(np.abs(np.array(z) - np.array(zb))) < 1e-14, (k, z, zb)
 
 
@@ -58,7 +58,7 @@ def test_tail_walks_estimate_the_remainder(oracle_walks):
     depth = np.zeros(n, dtype=np.uint8)
     zsum = np.zeros(n)
     for i, k in enumerate(ks):
-        d = 1 + i % 3
+        d = 1 + i  # depths 1..6
         depth[k] = d
         R[k] = 300_000
         zsum[k] = sum(a3.first_meeting_lemma5(n, rp, col, k, C, d))
@@ -80,18 +80,43 @@ def test_exploitation_plan_rules():
     din = np.diff(rp)
     pi = np.random.default_rng(1).random(n) * 0.1
     pi[din == 0] = 0.05
-    R_b = 1e10
-    depth, R = a3.exploitation_plan(n, rp, pi, R_b, C, max_depth=3, min_pairs=1e6, max_nodes=10)
+    R_b = 1e12
+    depth, R = a3.exploitation_plan(n, rp, col, pi, R_b, C, max_depth=6, min_pairs=1e6, max_nodes=10)
     assert np.all(R[din <= 1] == 0)
-    assert np.count_nonzero(depth) <= 10
+    assert 0 < np.count_nonzero(depth) <= 10
     top = np.lexsort((np.arange(n), -pi))[:10]
     for k in np.nonzero(depth)[0]:
         assert k in top and din[k] >= 2
         d = int(depth[k])
-        assert d == (3 if din[k] <= 64 else 2)
+        assert 1 <= d <= 6
         assert R[k] == max(1, int(np.ceil(R_b * pi[k] ** 2 * C ** (2 * d))))
     other = (depth == 0) & (din >= 2)
     assert np.array_equal(R[other], np.maximum(1, np.ceil(R_b * pi[other] ** 2)).astype(np.uint64))
+    # min_pairs above every count: nothing is exploited
+    d0, _ = a3.exploitation_plan(n, rp, col, pi, R_b, C, min_pairs=1e30)
+    assert np.count_nonzero(d0) == 0
+
+
+def test_exploit_cost_limits():
+    n, rp, col = synth.chung_lu(400, 4000, gamma=2.1, seed=8)
+    m = int(rp[-1])
+    P = a3.transition_matrix(n, rp, col)
+    k = int(np.argmax(np.diff(rp)))
+    supp = a3.supports(P, k, 6)
+    assert supp[0] == 1 and supp[1] == np.diff(rp)[k]
+    # Algorithm 2 alone costs its pairs times the mean walk length bound 1/(1-c)
+    assert a3.exploit_cost(0, 1234.2, C, supp, n, m) == 1235 * (1 / (1 - C))
+    # deeper exploitation never costs less deterministic work
+    fixed = [a3.exploit_cost(d, 0.0, C, supp, n, m) for d in range(1, 9)]
+    assert all(b > a for a, b in zip(fixed, fixed[1:]))
+    # with overwhelming walk work the deepest depth wins, with little walk work none
+    depth_hi, _ = a3.exploitation_plan(n, rp, col, np.eye(1, n, k)[0], 1e18, C, max_depth=8, min_pairs=1)
+    assert depth_hi[k] == 8
+    depth_lo, _ = a3.exploitation_plan(n, rp, col, np.eye(1, n, k)[0], 1e3, C, max_depth=8, min_pairs=1)
+    assert depth_lo[k] == 0
+    # max_depth caps the choice
+    depth_1, R1 = a3.exploitation_plan(n, rp, col, np.eye(1, n, k)[0], 1e18, C, max_depth=1, min_pairs=1)
+    assert depth_1[k] == 1 and R1[k] == int(np.ceil(1e18 * C ** 2))
 
 
 def test_alg3_query_within_eps_of_power_method(oracle_walks):
@@ -100,24 +125,6 @@ def test_alg3_query_within_eps_of_power_method(oracle_walks):
     S = power.power_method(n, rp, col, C)
     eps = 2e-3
     for u, seed in ((0, 1), (57, 2)):
-        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=16.0, alg3=True, alg3_min_pairs=1e3)
-        assert np.count_nonzero(q.depth) > 0
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=2000.0, alg3=True, alg3_min_pairs=1e3)
+        assert np.count_nonzero(q.depth) > 0 and q.depth.max() >= 3
         assert np.max(np.abs(q.s - S[:, u])) <= eps
-
-
-def test_exploitation_plan_depth_caps():
-    n, rp, col = synth.chung_lu(400, 4000, gamma=2.1, seed=8)
-    din = np.diff(rp)
-    pi = np.random.default_rng(2).random(n) * 0.1
-    R_b = 1e10
-    # a graph above the edge limit gets depth 2 everywhere; max_depth caps both rules
-    d_big, _ = a3.exploitation_plan(n, rp, pi, R_b, C, max_nodes=20, d3_max_edges=100)
-    assert set(np.unique(d_big[d_big > 0])) == {2}
-    d1, R1 = a3.exploitation_plan(n, rp, pi, R_b, C, max_depth=1, max_nodes=20)
-    ex = np.nonzero(d1)[0]
-    assert len(ex) > 0 and np.all(d1[ex] == 1)
-    assert np.array_equal(R1[ex], np.maximum(1, np.ceil(R_b * pi[ex] ** 2 * C ** 2)).astype(np.uint64))
-    # the din threshold moves nodes between depth 3 and 2
-    d_t, _ = a3.exploitation_plan(n, rp, pi, R_b, C, max_nodes=40, d3_max_din=3)
-    for k in np.nonzero(d_t)[0]:
-        assert d_t[k] == (3 if din[k] <= 3 else 2)
