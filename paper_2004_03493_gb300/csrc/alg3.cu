@@ -132,58 +132,65 @@ __device__ __forceinline__ void probe_epilogue(int64_t row, double h, int lane, 
     }
 }
 
+// Sum of X(col[p], lane) over entries [b, e) in entry order, eight gathers in flight.
+__device__ __forceinline__ double probe_range(const int32_t* __restrict__ col, const double* __restrict__ X,
+                                              uint32_t b, uint32_t e, int lane) {
+    double acc = 0.0;
+    uint32_t p = b;
+    for (; p + 8 <= e; p += 8) {
+        int32_t j[8];
+        double v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) j[t] = __ldg(col + p + t);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = X[(size_t)j[t] * kProbeW + lane];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc += v[t];
+    }
+    for (; p < e; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
+    return acc;
+}
+
 // One probe step: h(i, col) = sum_{j in Out(i)} X(j, col), a pull over the out-edge
 // CSR for 32 columns at once.  Short rows: one warp per row, lane = column, entries
-// added in order.  Long rows: one warp per 4096-entry segment writes partials that
-// probe_long_rows_kernel adds in segment order.
+// added in order.  Long rows: one block per 4096-entry segment, each warp adding a
+// contiguous eighth of it, the eight warp sums added in warp order into the
+// segment's partial; probe_long_rows_kernel adds the partials in segment order.
 __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uint32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const double* __restrict__ X, uint32_t long_min,
                                                             int64_t nseg, const Segment* __restrict__ seg,
                                                             double* __restrict__ partial, int short_blocks,
                                                             ProbeEpi epi) {
+    constexpr int kWarps = kBlock / 32;
     const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const int64_t wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5;
     if ((int)blockIdx.x >= short_blocks) {
-        const int64_t nsw = ((int64_t)gridDim.x - short_blocks) * wpb;
-        for (int64_t s = ((int64_t)blockIdx.x - short_blocks) * wpb + wib; s < nseg; s += nsw) {
+        __shared__ double red[kWarps][kProbeW];
+        const int64_t nsb = (int64_t)gridDim.x - short_blocks;
+        for (int64_t s = (int64_t)blockIdx.x - short_blocks; s < nseg; s += nsb) {  // uniform per block
             const Segment sg = seg[s];
-            double acc = 0.0;
-            uint32_t p = sg.beg;
-            for (; p + 4 <= sg.end; p += 4) {
-                const int32_t j0 = __ldg(col + p), j1 = __ldg(col + p + 1), j2 = __ldg(col + p + 2),
-                              j3 = __ldg(col + p + 3);
-                const double v0 = X[(size_t)j0 * kProbeW + lane], v1 = X[(size_t)j1 * kProbeW + lane],
-                             v2 = X[(size_t)j2 * kProbeW + lane], v3 = X[(size_t)j3 * kProbeW + lane];
-                acc += v0;
-                acc += v1;
-                acc += v2;
-                acc += v3;
+            const uint32_t per = (sg.end - sg.beg + kWarps - 1) / kWarps;
+            uint32_t b = sg.beg + (uint32_t)wib * per;
+            if (b > sg.end) b = sg.end;
+            const uint32_t e = b + per < sg.end ? b + per : sg.end;
+            red[wib][lane] = probe_range(col, X, b, e, lane);
+            __syncthreads();
+            if (wib == 0) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) t += red[w][lane];
+                partial[(size_t)s * kProbeW + lane] = t;
             }
-            for (; p < sg.end; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
-            partial[(size_t)s * kProbeW + lane] = acc;
+            __syncthreads();
         }
         return;
     }
-    const int64_t nw = (int64_t)short_blocks * wpb;
-    for (int64_t row = (int64_t)blockIdx.x * wpb + wib; row < n; row += nw) {
+    const int64_t nw = (int64_t)short_blocks * kWarps;
+    for (int64_t row = (int64_t)blockIdx.x * kWarps + wib; row < n; row += nw) {
         const uint32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
         if (e - b >= long_min) continue;  // warp-uniform: a long row
-        double acc = 0.0;
-        uint32_t p = b;
-        for (; p + 4 <= e; p += 4) {
-            const int32_t j0 = __ldg(col + p), j1 = __ldg(col + p + 1), j2 = __ldg(col + p + 2),
-                          j3 = __ldg(col + p + 3);
-            const double v0 = X[(size_t)j0 * kProbeW + lane], v1 = X[(size_t)j1 * kProbeW + lane],
-                         v2 = X[(size_t)j2 * kProbeW + lane], v3 = X[(size_t)j3 * kProbeW + lane];
-            acc += v0;
-            acc += v1;
-            acc += v2;
-            acc += v3;
-        }
-        for (; p < e; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
-        probe_epilogue(row, acc, lane, epi);
+        probe_epilogue(row, probe_range(col, X, b, e, lane), lane, epi);
     }
 }
 
@@ -288,7 +295,7 @@ cudaError_t probe_step(const Graph& g, const double* X_prev, const ProbeEpi& epi
     int64_t sb = (g.n + wpb - 1) / wpb;
     if (sb > (int64_t)g.sm_count * 16) sb = (int64_t)g.sm_count * 16;
     if (sb < 1) sb = 1;
-    int64_t segb = (A.nseg + wpb - 1) / wpb;
+    int64_t segb = A.nseg;  // one block per segment
     if (segb > (int64_t)g.sm_count * 8) segb = (int64_t)g.sm_count * 8;
     probe_rows_kernel<<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, X_prev, A.long_min, A.nseg,
                                                                        A.seg, partial, (int)sb, epi);
