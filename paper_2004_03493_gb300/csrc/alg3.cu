@@ -11,9 +11,9 @@
 // for q in I(q')).  The l' >= 2 terms need the walk distributions of every q' in
 // the support of h_{j-l'}: the "probes".  Probes run 32 at a time as an n x 32 FP64
 // block through a multi-column pull product whose epilogue subtracts
-// c^{l'} Zv_i(q') h^{q'}_{l'}(q)^2 from Zv_{i+l'}(q), column after column in the
-// order of q' (ascending ids), so the result does not depend on the batching.
-// Z_j = sum_q Zv_j(q) by fixed-order block partials.  Everything is deterministic.
+// sum_col c^{l'} Zv_i(q'_col) h^{q'_col}_{l'}(q)^2 from Zv_{i+l'}(q) (a fixed lane tree;
+// blocks of 32 consecutive q' of the ascending support, in order).  Z_j = sum_q Zv_j(q)
+// by fixed-order block partials.  Everything is deterministic.
 #include "common.cuh"
 #include "internal.h"
 
@@ -120,19 +120,26 @@ struct ProbeEpi {
     double* zacc;        // n: Zv of the target level
 };
 
+// FP64 issue on GB300 is a small fraction of FP32, so the probe kernels skip FP64
+// work wherever a whole warp would only add or scale zeros; the tests for zero look
+// at the bit pattern (the values are non-negative, never -0), an integer operation.
+__device__ __forceinline__ bool nonzero(double v) { return __double_as_longlong(v) != 0ll; }
+
 // Row `row` of h^{q'}_{l'} is `h` in lane = column.  All 32 lanes of the warp call it.
+// The row's term sum_col coef(col) h(col)^2 is a fixed butterfly over the lanes.
 __device__ __forceinline__ void probe_epilogue(int64_t row, double h, int lane, const ProbeEpi& e) {
-    e.x_next[(size_t)row * kProbeW + lane] = h * e.inv_din[row];
-    if (e.coef) {
-        const double t = e.coef[lane] * (h * h);
-        double acc = e.zacc[row];
+    const bool any = __any_sync(0xffffffffu, nonzero(h));
+    e.x_next[(size_t)row * kProbeW + lane] = any ? h * e.inv_din[row] : 0.0;
+    if (e.coef && any) {
+        double t = e.coef[lane] * (h * h);
 #pragma unroll
-        for (int l = 0; l < kProbeW; ++l) acc -= __shfl_sync(0xffffffffu, t, l);
-        if (lane == 0) e.zacc[row] = acc;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) e.zacc[row] = e.zacc[row] - t;
     }
 }
 
-// Sum of X(col[p], lane) over entries [b, e) in entry order, eight gathers in flight.
+// Sum of X(col[p], lane) over entries [b, e) in entry order, eight gathers in flight;
+// an entry whose gathered row is zero in every column adds nothing and is skipped.
 __device__ __forceinline__ double probe_range(const int32_t* __restrict__ col, const double* __restrict__ X,
                                               uint32_t b, uint32_t e, int lane) {
     double acc = 0.0;
@@ -145,9 +152,13 @@ __device__ __forceinline__ double probe_range(const int32_t* __restrict__ col, c
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = X[(size_t)j[t] * kProbeW + lane];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc += v[t];
+        for (int t = 0; t < 8; ++t)
+            if (__any_sync(0xffffffffu, nonzero(v[t]))) acc += v[t];
     }
-    for (; p < e; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
+    for (; p < e; ++p) {
+        const double v = X[(size_t)__ldg(col + p) * kProbeW + lane];
+        if (__any_sync(0xffffffffu, nonzero(v))) acc += v;
+    }
     return acc;
 }
 
