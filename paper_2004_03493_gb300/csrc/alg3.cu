@@ -96,13 +96,31 @@ __global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double*
     }
 }
 
+// ---------------------------------------------------------------- probes
+//
+// A probe value is a probability in [0, 1]; probes carry it in unsigned 64-bit fixed
+// point with 63 fraction bits (kOne = 2^63).  FP64 issue on GB300 is a small fraction
+// of its integer rate, and the probe sweeps add one value per edge and column, so the
+// sums run on the integer pipe: exact additions (no overflow: a row sum of x = h/din
+// over out-neighbours never exceeds the total mass 1), truncating divisions by din
+// and truncating squares.  The truncations cost at most 2^-63 each, far below the
+// FP64 rounding of the rest of the computation.
+constexpr unsigned long long kOne = 1ull << 63;
+constexpr double kInvOne = 1.0 / 9223372036854775808.0;  // 2^-63
+
+// floor(H^2 / 2^63) for H <= 2^63
+__device__ __forceinline__ unsigned long long fx_sq(unsigned long long H) {
+    return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
+}
+
 // Probe block start: x_0 = e_{q'} / din(q') in column col (row-major n x 32, zeroed before)
-__global__ void probe_init_kernel(const int32_t* __restrict__ ids, int count, const double* __restrict__ inv_din,
-                                  double* __restrict__ X) {
+__global__ void probe_init_kernel(const int32_t* __restrict__ ids, int count, const uint32_t* __restrict__ in_rp,
+                                  unsigned long long* __restrict__ X) {
     const int col = threadIdx.x;
     if (col < count) {
         const int32_t q = ids[col];
-        X[(size_t)q * kProbeW + col] = inv_din[q];
+        const uint32_t d = in_rp[q + 1] - in_rp[q];
+        X[(size_t)q * kProbeW + col] = d ? kOne / d : 0ull;
     }
 }
 
@@ -113,71 +131,97 @@ __global__ void probe_coef_kernel(const int32_t* __restrict__ ids, int count, co
     if (col < kProbeW) coef[col] = col < count ? cl * zv_src[ids[col]] : 0.0;
 }
 
+// zlast += sum_col coef(col) * colsum(col) (columns in order); colsum reset for the next block
+__global__ void probe_norm_finish_kernel(const double* __restrict__ coef, unsigned long long* __restrict__ colsum,
+                                         double* __restrict__ zlast) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int col = 0; col < kProbeW; ++col) t += coef[col] * ((double)colsum[col] * kInvOne);
+        *zlast += t;
+    }
+    __syncthreads();
+    if (threadIdx.x < kProbeW) colsum[threadIdx.x] = 0ull;
+}
+
 struct ProbeEpi {
-    const double* inv_din;
-    double* x_next;      // n x 32: h / din for the next step
-    const double* coef;  // 32 (NULL: no accumulation at this step)
-    double* zacc;        // n: Zv of the target level
+    const uint32_t* in_rp;
+    unsigned long long* x_next;  // n x 32: h / din for the next step
+    int mode;                    // 0: none; 1: subtract sum_col coef h^2 from zacc(row); 2: column sums of h^2
+    const double* coef;          // 32 (mode 1)
+    double* zacc;                // n: Zv of the target level (mode 1)
+    unsigned long long* colsum;  // 32 (mode 2)
 };
 
-// FP64 issue on GB300 is a small fraction of FP32, so the probe kernels skip FP64
-// work wherever a whole warp would only add or scale zeros; the tests for zero look
-// at the bit pattern (the values are non-negative, never -0), an integer operation.
-__device__ __forceinline__ bool nonzero(double v) { return __double_as_longlong(v) != 0ll; }
-
-// Row `row` of h^{q'}_{l'} is `h` in lane = column.  All 32 lanes of the warp call it.
-// The row's term sum_col coef(col) h(col)^2 is a fixed butterfly over the lanes.
-__device__ __forceinline__ void probe_epilogue(int64_t row, double h, int lane, const ProbeEpi& e) {
-    const bool any = __any_sync(0xffffffffu, nonzero(h));
-    e.x_next[(size_t)row * kProbeW + lane] = any ? h * e.inv_din[row] : 0.0;
-    if (e.coef && any) {
+// Row `row` of h^{q'}_{l'} is H (fixed point) in lane = column.  All 32 lanes of the
+// warp call it.  Returns this lane's h^2 (fixed point) for mode 2, else 0.  The FP64
+// row term of mode 1 is a fixed butterfly over the lanes, skipped when the row is zero.
+__device__ __forceinline__ unsigned long long probe_epilogue(int64_t row, unsigned long long H, int lane,
+                                                             const ProbeEpi& e) {
+    const uint32_t d = __ldg(e.in_rp + row + 1) - __ldg(e.in_rp + row);
+    e.x_next[(size_t)row * kProbeW + lane] = (d && H) ? H / d : 0ull;
+    if (e.mode == 2) return fx_sq(H);
+    if (e.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
+        const double h = (double)H * kInvOne;
         double t = e.coef[lane] * (h * h);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) e.zacc[row] = e.zacc[row] - t;
     }
+    return 0ull;
 }
 
-// Sum of X(col[p], lane) over entries [b, e) in entry order, eight gathers in flight;
-// an entry whose gathered row is zero in every column adds nothing and is skipped.
-__device__ __forceinline__ double probe_range(const int32_t* __restrict__ col, const double* __restrict__ X,
-                                              uint32_t b, uint32_t e, int lane) {
-    double acc = 0.0;
+// Sum of X(col[p], lane) over entries [b, e), eight gathers in flight (integer adds).
+__device__ __forceinline__ unsigned long long probe_range(const int32_t* __restrict__ col,
+                                                          const unsigned long long* __restrict__ X, uint32_t b,
+                                                          uint32_t e, int lane) {
+    unsigned long long acc = 0ull;
     uint32_t p = b;
     for (; p + 8 <= e; p += 8) {
         int32_t j[8];
-        double v[8];
+        unsigned long long v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) j[t] = __ldg(col + p + t);
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = X[(size_t)j[t] * kProbeW + lane];
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
-            if (__any_sync(0xffffffffu, nonzero(v[t]))) acc += v[t];
+        for (int t = 0; t < 8; ++t) acc += v[t];
     }
-    for (; p < e; ++p) {
-        const double v = X[(size_t)__ldg(col + p) * kProbeW + lane];
-        if (__any_sync(0xffffffffu, nonzero(v))) acc += v;
-    }
+    for (; p < e; ++p) acc += X[(size_t)__ldg(col + p) * kProbeW + lane];
     return acc;
 }
 
+// Column sums of mode 2: lane sums of the block's warps, then one integer atomic per
+// column (integer addition is order-free, so the result is exact and deterministic).
+__device__ __forceinline__ void probe_flush_colsum(unsigned long long v, const ProbeEpi& e) {
+    constexpr int kWarps = kBlock / 32;
+    __shared__ unsigned long long red[kWarps][kProbeW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    red[wib][lane] = v;
+    __syncthreads();
+    if (wib == 0) {
+        unsigned long long t = 0ull;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += red[w][lane];
+        if (t) atomicAdd(e.colsum + lane, t);
+    }
+}
+
 // One probe step: h(i, col) = sum_{j in Out(i)} X(j, col), a pull over the out-edge
-// CSR for 32 columns at once.  Short rows: one warp per row, lane = column, entries
-// added in order.  Long rows: one block per 4096-entry segment, each warp adding a
-// contiguous eighth of it, the eight warp sums added in warp order into the
-// segment's partial; probe_long_rows_kernel adds the partials in segment order.
+// CSR for 32 columns at once.  Short rows: one warp per row, lane = column.  Long
+// rows: one block per 4096-entry segment, each warp adding a contiguous eighth of it
+// into the segment's partial; probe_long_rows_kernel adds a row's partials.
 __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uint32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
-                                                            const double* __restrict__ X, uint32_t long_min,
-                                                            int64_t nseg, const Segment* __restrict__ seg,
-                                                            double* __restrict__ partial, int short_blocks,
+                                                            const unsigned long long* __restrict__ X,
+                                                            uint32_t long_min, int64_t nseg,
+                                                            const Segment* __restrict__ seg,
+                                                            unsigned long long* __restrict__ partial, int short_blocks,
                                                             ProbeEpi epi) {
     constexpr int kWarps = kBlock / 32;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     if ((int)blockIdx.x >= short_blocks) {
-        __shared__ double red[kWarps][kProbeW];
+        __shared__ unsigned long long red[kWarps][kProbeW];
         const int64_t nsb = (int64_t)gridDim.x - short_blocks;
         for (int64_t s = (int64_t)blockIdx.x - short_blocks; s < nseg; s += nsb) {  // uniform per block
             const Segment sg = seg[s];
@@ -188,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uin
             red[wib][lane] = probe_range(col, X, b, e, lane);
             __syncthreads();
             if (wib == 0) {
-                double t = 0.0;
+                unsigned long long t = 0ull;
 #pragma unroll
                 for (int w = 0; w < kWarps; ++w) t += red[w][lane];
                 partial[(size_t)s * kProbeW + lane] = t;
@@ -197,23 +241,29 @@ __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uin
         }
         return;
     }
+    unsigned long long nacc = 0ull;
     const int64_t nw = (int64_t)short_blocks * kWarps;
     for (int64_t row = (int64_t)blockIdx.x * kWarps + wib; row < n; row += nw) {
         const uint32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
         if (e - b >= long_min) continue;  // warp-uniform: a long row
-        probe_epilogue(row, probe_range(col, X, b, e, lane), lane, epi);
+        nacc += probe_epilogue(row, probe_range(col, X, b, e, lane), lane, epi);
     }
+    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
 }
 
 __global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(int64_t nlong, const int32_t* __restrict__ long_rows,
                                                                  const int32_t* __restrict__ long_first,
-                                                                 const double* __restrict__ partial, ProbeEpi epi) {
+                                                                 const unsigned long long* __restrict__ partial,
+                                                                 ProbeEpi epi) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= nlong) return;  // warp-uniform
-    double acc = 0.0;
-    for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc += partial[(size_t)s * kProbeW + lane];
-    probe_epilogue(long_rows[w], acc, lane, epi);
+    unsigned long long nacc = 0ull;
+    if (w < nlong) {  // warp-uniform
+        unsigned long long acc = 0ull;
+        for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc += partial[(size_t)s * kProbeW + lane];
+        nacc = probe_epilogue(long_rows[w], acc, lane, epi);
+    }
+    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
 }
 
 // D^ of Algorithm 3 for exploited nodes (depth > 0), of Algorithm 2 for the others,
@@ -254,11 +304,13 @@ struct A3Ws {
     uint64_t* flag;   // n
     uint64_t* off;    // n + 1
     int32_t* ids;     // n
-    double* Xa;       // 32 n probe block
-    double* Xb;       // 32 n
-    double* partial;  // max(kDotBlocks, 32 nseg)
-    double* coef;     // 32
-    double* sums;     // 64
+    unsigned long long* Xa;      // 32 n probe block (fixed point)
+    unsigned long long* Xb;      // 32 n
+    double* partial;             // kDotBlocks (dot products)
+    unsigned long long* ppart;   // 32 nseg (probe segment partials)
+    double* coef;                // 32
+    unsigned long long* colsum;  // 32
+    double* sums;                // 64: [j] = sum_q Zv_j(q); [63] = the last level's probe terms
     unsigned long long* counts;  // 64
 };
 
@@ -281,11 +333,12 @@ size_t a3_layout(int64_t n_, int64_t nseg, void* base, A3Ws* out) {
     w.flag = (uint64_t*)take(8 * n);
     w.off = (uint64_t*)take(8 * (n + 1));
     w.ids = (int32_t*)take(4 * n);
-    w.Xa = (double*)take(8 * kProbeW * n);
-    w.Xb = (double*)take(8 * kProbeW * n);
-    const size_t np = std::max<size_t>(kDotBlocks, (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
-    w.partial = (double*)take(8 * np);
+    w.Xa = (unsigned long long*)take(8 * kProbeW * n);
+    w.Xb = (unsigned long long*)take(8 * kProbeW * n);
+    w.partial = (double*)take(8 * kDotBlocks);
+    w.ppart = (unsigned long long*)take(8 * (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
     w.coef = (double*)take(8 * kProbeW);
+    w.colsum = (unsigned long long*)take(8 * kProbeW);
     w.sums = (double*)take(8 * 64);
     w.counts = (unsigned long long*)take(8 * 64);
     if (out) *out = w;
@@ -300,7 +353,8 @@ cudaError_t dsum(const Graph& g, const double* a, int kind, const A3Ws& ws, doub
 }
 
 // One probe step for the block: X_prev -> h (epilogue: X_next, accumulation).
-cudaError_t probe_step(const Graph& g, const double* X_prev, const ProbeEpi& epi, double* partial, int* count) {
+cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const ProbeEpi& epi,
+                       unsigned long long* partial, int* count) {
     const DevCsr& A = g.out;
     const int wpb = kBlock / 32;
     int64_t sb = (g.n + wpb - 1) / wpb;
@@ -363,11 +417,11 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     if (e != cudaSuccess) return e;
     count += 1 + depth * per_sweep;
     if ((e = cudaMemsetAsync(ws.Zv, 0, sizeof(double) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess) return e;
-    double cj = 1.0;
+    if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.colsum, 0, sizeof(unsigned long long) * kProbeW, g.stream)) != cudaSuccess) return e;
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
     for (int j = 1; j <= depth; ++j) {
-        cj = cpow[(size_t)j];
         double* zv = ws.Zv + (size_t)j * n;
         const double* T = nullptr;
         if (j >= 2) {  // T = P~ Zv_{j-1}
@@ -377,11 +431,12 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             count += 1 + per_sweep;
             T = ws.T;
         }
-        zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cj, c, ws.H + (size_t)j * n, T, zv);
+        zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cpow[(size_t)j], c, ws.H + (size_t)j * n, T, zv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++count;
         if ((e = dsum(g, zv, 2, ws, ws.sums + j, &count)) != cudaSuccess) return e;
-        // probes from the support of h_j feed the levels j+2 .. depth
+        // probes from the support of h_j feed the levels j+2 .. depth: the vector Zv of
+        // a level below depth, only the sum for the last level
         if (j <= depth - 2) {
             flag_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)j * n, ws.flag);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -400,30 +455,37 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             for (uint64_t b0 = 0; b0 < nsup; b0 += kProbeW) {
                 const int cnt = (int)std::min<uint64_t>(kProbeW, nsup - b0);
                 const int32_t* ids = ws.ids + b0;
-                if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(double) * kProbeW * n, g.stream)) != cudaSuccess) return e;
-                probe_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.inv_din, ws.Xa);
+                if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess)
+                    return e;
+                probe_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.in.rp, ws.Xa);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 ++count;
-                double* X[2] = {ws.Xa, ws.Xb};
+                unsigned long long* X[2] = {ws.Xa, ws.Xb};
                 for (int lp = 1; lp <= steps; ++lp) {
-                    ProbeEpi epi{g.inv_din, X[lp & 1], nullptr, ws.Zv + (size_t)(j + lp) * n};
-                    if (lp >= 2) {
+                    ProbeEpi epi{g.in.rp, X[lp & 1], 0, nullptr, ws.Zv + (size_t)(j + lp) * n, ws.colsum};
+                    if (lp == steps) {
+                        epi.mode = 2;
+                    } else if (lp >= 2) {
                         probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)lp], ws.coef);
                         if ((e = cudaGetLastError()) != cudaSuccess) return e;
                         ++count;
+                        epi.mode = 1;
                         epi.coef = ws.coef;
                     }
-                    if ((e = probe_step(g, X[(lp - 1) & 1], epi, ws.partial, &count)) != cudaSuccess) return e;
+                    if ((e = probe_step(g, X[(lp - 1) & 1], epi, ws.ppart, &count)) != cudaSuccess) return e;
                 }
+                probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)steps], ws.coef);
+                probe_norm_finish_kernel<<<1, kProbeW, 0, g.stream>>>(ws.coef, ws.colsum, ws.sums + 63);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                count += 2;
             }
         }
     }
     double sums[64] = {};
-    if ((e = cudaMemcpyAsync(sums, ws.sums, sizeof(double) * (size_t)(depth + 1), cudaMemcpyDeviceToHost, g.stream)) !=
-        cudaSuccess)
-        return e;
+    if ((e = cudaMemcpyAsync(sums, ws.sums, sizeof(sums), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
     for (int j = 1; j <= depth; ++j) z_out[j - 1] = sums[j];
+    z_out[depth - 1] -= sums[63];  // the last level's probe terms, kept as column sums
     if (launches) *launches += count;
     return cudaSuccess;
 }
