@@ -59,9 +59,10 @@ METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6,
 # multiplies + 2 three-input XORs); step logic = 2 threshold compares, 2 multiply-shift picks,
 # 2 row loads, 2 neighbour loads
 INSTR_PER_PAIR_STEP = 48.0
-# DRAM bytes per sampler launch from the ncu capture named in profiles/ (None once the kernel changes;
-# the last figure, 6.31 MB per launch, predates the Algorithm 3 depth argument)
-KERNEL_TRAFFIC = {"sample_pairs_kernel": None}
+# DRAM bytes per sampler launch from the ncu capture named in profiles/ (None once the kernel changes):
+# dram__bytes_read.sum + dram__bytes_write.sum of the bench query's sampler launch, 6.63 MB read and
+# 0 B written; the graph stays in L2, so this is its compulsory read
+KERNEL_TRAFFIC = {"sample_pairs_kernel": 6.63e6}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -606,7 +607,7 @@ def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources": w["sources"], "queries_per_step": 1,
             "top_k": w["k"], "kappa": args.kappa, "alloc": "pi^2 (Lemma 4)",
-            "dhat": ("Algorithm 3 (exact Z_1..Z_d for the 64 heaviest nodes, d <= 3, then tail walk pairs)"
+            "dhat": ("Algorithm 3 (exact Z_1..Z_d for the 64 heaviest nodes, cost-chosen d <= 8, then tail walk pairs)"
                      if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
             "l2": "flushed (512 MB write) before each timed step", "parallelism": f"replicas x{args.gpus}"}
 
