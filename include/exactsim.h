@@ -133,6 +133,11 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "pair_budget"    largest allowed sum of R(k) (default 1e15); above it a
  *                    query returns ESIM_EBUDGET without running walks
  *   "timing"         1: record per-phase CUDA event times in the stats
+ *   "shared_walks"   batches and the server: 1 (default) samples each node's walk pairs once
+ *                    for all columns -- max_q R_q(k) pairs cut at the distinct R_q(k), each
+ *                    column counting the intervals below its own R_q(k); the walk spec keys
+ *                    pairs by (seed, k, r) only, so every column's counts are the same
+ *                    integers as with 0 (each column sampled on its own)
  *   "sparse_hist"    1: sparse linearization (Section 3.2; FP64 only): the query runs
  *                    at eps/2 (L and R_b) and keeps only the history entries
  *                    pi^l(k) > (1-sqrt c)^2 eps/2 -- fewer than 1/that many, whatever n --

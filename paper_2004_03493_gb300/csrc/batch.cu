@@ -353,6 +353,87 @@ cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, b
     return batch_level_dispatch_rev<64, false>(g, tile, s_prev, op, (f2*)partial);
 }
 
+// ---------------------------------------------------------------- shared walks
+//
+// The walk spec keys pair r of node k by (seed, k, r) alone, so column q of a batch,
+// which needs pairs 0 .. R_q(k)-1 of node k, sees the same pairs as every other
+// column.  The batch therefore samples max_q R_q(k) pairs of each node once, cut at
+// the distinct values of R_q(k) into intervals, and column q's count for node k is
+// the sum of the intervals below R_q(k) -- the same integer as sampling alone.
+// Segments are node-major: segment k*B + i is interval i of node k (zero length
+// past the node's distinct counts).
+__global__ void shared_plan_kernel(int64_t n, int B, const uint64_t* __restrict__ R, uint64_t* __restrict__ len,
+                                   uint64_t* __restrict__ rbase) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t t[kBatchMax];
+        int m = 0;
+        for (int q = 0; q < B; ++q) {  // distinct non-zero R_q(k), ascending (insertion)
+            const uint64_t v = R[(size_t)q * (size_t)n + (size_t)k];
+            if (v == 0) continue;
+            int i = m;
+            while (i > 0 && t[i - 1] > v) --i;
+            if (i > 0 && t[i - 1] == v) continue;
+            for (int j = m; j > i; --j) t[j] = t[j - 1];
+            t[i] = v;
+            ++m;
+        }
+        uint64_t prev = 0;
+        for (int i = 0; i < B; ++i) {
+            const size_t sidx = (size_t)k * (size_t)B + (size_t)i;
+            rbase[sidx] = prev;
+            if (i < m) {
+                len[sidx] = t[i] - prev;
+                prev = t[i];
+            } else {
+                len[sidx] = 0;
+            }
+        }
+    }
+}
+
+// nonmeet(q, k) = the counts of node k's intervals that end at or below R_q(k)
+__global__ void shared_columns_kernel(int64_t n, int B, const uint64_t* __restrict__ R,
+                                      const uint64_t* __restrict__ rbase, const uint64_t* __restrict__ soff,
+                                      const uint64_t* __restrict__ scount, uint64_t* __restrict__ nonmeet) {
+    const int64_t N = n * (int64_t)B;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = idx / n, k = idx % n;
+        const uint64_t Rq = R[idx];
+        uint64_t sum = 0;
+        for (int i = 0; i < B; ++i) {
+            const size_t sidx = (size_t)k * (size_t)B + (size_t)i;
+            const uint64_t len = soff[sidx + 1] - soff[sidx];
+            if (len == 0 || rbase[sidx] + len > Rq) break;
+            sum += scount[sidx];
+        }
+        (void)q;
+        nonmeet[idx] = sum;
+    }
+}
+
+__global__ void dhat_from_R_kernel(int64_t N, const uint64_t* __restrict__ nonmeet, const uint64_t* __restrict__ R,
+                                   double* __restrict__ dhat) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        dhat[i] = R[i] ? (double)nonmeet[i] / (double)R[i] : 0.0;
+}
+
+cudaError_t launch_shared_plan(const Graph& g, int B, const uint64_t* R, uint64_t* len, uint64_t* rbase) {
+    shared_plan_kernel<<<grid_cap(g, g.n, kBlock), kBlock, 0, g.stream>>>(g.n, B, R, len, rbase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shared_columns(const Graph& g, int B, const uint64_t* R, const uint64_t* rbase, const uint64_t* soff,
+                                  const uint64_t* scount, uint64_t* nonmeet) {
+    shared_columns_kernel<<<grid_cap(g, g.n * B, kBlock), kBlock, 0, g.stream>>>(g.n, B, R, rbase, soff, scount,
+                                                                                  nonmeet);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dhat_from_R(const Graph& g, int64_t N, const uint64_t* nonmeet, const uint64_t* R, double* dhat) {
+    dhat_from_R_kernel<<<grid_cap(g, N, kBlock), kBlock, 0, g.stream>>>(N, nonmeet, R, dhat);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_forward_init(const Graph& g, int W, int B, const int64_t* u, double c, float* hist0,
                                       float* x0) {
     const int blocks = grid_cap(g, g.n * W, kBlock);

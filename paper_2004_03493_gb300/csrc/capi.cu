@@ -516,6 +516,8 @@ struct BWs {
     uint64_t* R;      // B n
     uint64_t* off;    // B n + 1
     uint64_t* nonmeet;// B n
+    uint64_t* rbase;  // B n  shared walks: first pair of each (node, interval) segment
+    uint64_t* scount; // B n  shared walks: interval lengths, then interval counts
     double* dhat;     // B n
     double* s;        // B n
     int64_t* u;       // W
@@ -548,6 +550,8 @@ size_t bws_layout(int64_t n_, int W, int B, int32_t Lmax, int64_t nseg_max, int 
     t.R = (uint64_t*)take(8 * bn);
     t.off = (uint64_t*)take(8 * (bn + 1));
     t.nonmeet = (uint64_t*)take(8 * bn);
+    t.rbase = (uint64_t*)take(8 * bn);
+    t.scount = (uint64_t*)take(8 * bn);
     t.dhat = (double*)take(8 * bn);
     t.s = (double*)take(8 * bn);
     t.u = (int64_t*)take(8 * W);
@@ -638,7 +642,7 @@ esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, 
     const Status hs = *g.status_host;
     g.last_L = plan.Lmax;
     g.last_launches = 1 + plan.Lmax * (1 + (g.out.nlong > 0 ? 1 : 0)) + 1 + 3 + 1 + 1 + 1 +
-                      plan.Lmax * (1 + (g.in.nlong > 0 ? 1 : 0)) + (k > 0 ? 27 : 0);
+                      plan.Lmax * (1 + (g.in.nlong > 0 ? 1 : 0)) + (k > 0 ? 27 : 0) + (g.shared_walks ? 2 : 0);
     g.last_R_b = plan.Rb[0];
     g.last_kappa = kappa_of(g, c);
     g.last_norm2 = 0.0;
@@ -734,11 +738,23 @@ int batch_enqueue(Graph& tuner, const Graph& view, const BatchPlan& p, void* ws,
                       "batch forward level");
     if (timing) cudaEventRecord(view.ev[1], stream);
     ESIM_CUDA_TRY(launch_batch_alloc(view, W, B, w.hist, Lmax, w.Rb, view.alloc_mode, w.R), "batch allocation");
-    ESIM_CUDA_TRY(launch_scan_R(view, N, w.R, w.off, w.part_R, w.part_norm, w.part_Rd), "batch scan");
-    if (timing) cudaEventRecord(view.ev[2], stream);
-    ESIM_CUDA_TRY(launch_sample_segments(view, N, w.off, c, seed, w.nonmeet, nullptr), "batch walk pairs");
-    if (timing) cudaEventRecord(view.ev[3], stream);
-    ESIM_CUDA_TRY(launch_dhat_segments(view, N, w.nonmeet, w.off, w.dhat), "batch dhat");
+    if (view.shared_walks) {
+        // one walk set per node: intervals between the distinct R_q(k), sampled once
+        ESIM_CUDA_TRY(launch_shared_plan(view, B, w.R, w.scount, w.rbase), "shared walk plan");
+        ESIM_CUDA_TRY(launch_scan_R(view, N, w.scount, w.off, w.part_R, w.part_norm, w.part_Rd), "shared walk scan");
+        if (timing) cudaEventRecord(view.ev[2], stream);
+        ESIM_CUDA_TRY(launch_sample_segments(view, N, w.off, c, seed, w.scount, nullptr, nullptr, B, w.rbase),
+                      "batch walk pairs (shared)");
+        if (timing) cudaEventRecord(view.ev[3], stream);
+        ESIM_CUDA_TRY(launch_shared_columns(view, B, w.R, w.rbase, w.off, w.scount, w.nonmeet), "shared walk counts");
+        ESIM_CUDA_TRY(launch_dhat_from_R(view, N, w.nonmeet, w.R, w.dhat), "batch dhat");
+    } else {
+        ESIM_CUDA_TRY(launch_scan_R(view, N, w.R, w.off, w.part_R, w.part_norm, w.part_Rd), "batch scan");
+        if (timing) cudaEventRecord(view.ev[2], stream);
+        ESIM_CUDA_TRY(launch_sample_segments(view, N, w.off, c, seed, w.nonmeet, nullptr), "batch walk pairs");
+        if (timing) cudaEventRecord(view.ev[3], stream);
+        ESIM_CUDA_TRY(launch_dhat_segments(view, N, w.nonmeet, w.off, w.dhat), "batch dhat");
+    }
     double* s = s_dev ? s_dev : w.s;
     ESIM_CUDA_TRY(launch_batch_reverse_init(view, W, B, w.dhat, c, w.hist + (size_t)Lmax * nw, w.w, w.sa,
                                             Lmax == 0 ? s : nullptr),
@@ -934,6 +950,9 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "precision must be 0 (FP64) or 1 (FP32c)");
         if (value == 1.0 && g.sparse_hist) return fail(ESIM_ENOTSUP, "sparse_hist needs precision 0 (FP64)");
         g.precision = (int)value;
+    } else if (k == "shared_walks") {
+        if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "shared_walks must be 0 or 1");
+        g.shared_walks = (int)value;
     } else if (k == "sparse_hist") {
         if (value != 0.0 && value != 1.0) return fail(ESIM_EINVAL, "sparse_hist must be 0 or 1");
         if (value == 1.0 && g.precision != 0) return fail(ESIM_ENOTSUP, "sparse_hist needs precision 0 (FP64)");
@@ -975,6 +994,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "precision") *value = g.precision;
     else if (k == "diag") *value = g.diag_mode;
     else if (k == "sparse_hist") *value = g.sparse_hist;
+    else if (k == "shared_walks") *value = g.shared_walks;
     else if (k == "alg3") *value = g.alg3;
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;

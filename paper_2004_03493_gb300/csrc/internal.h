@@ -98,6 +98,7 @@ struct Graph {
     int batch_tile_fwd[3] = {-1, -1, -1};  // per width W = 16, 32, 64
     int batch_tile_rev[3] = {-1, -1, -1};
     int batch_tile_force = -1;    // option "batch_tile": -1 autotune, else 0..2
+    int shared_walks = 1;         // batches: one walk set per node for all columns
     float batch_tune_ms[3][2][3] = {};
     // workspace
     Status* status = nullptr;     // device
@@ -144,8 +145,10 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
 cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
+// shared_B > 0 with rbase: segment s covers pairs [rbase[s], rbase[s] + len) of node s / shared_B
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
-                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr);
+                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr,
+                                   int shared_B = 0, const uint64_t* rbase = nullptr);
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
                                  double* dhat);
 cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
@@ -165,6 +168,11 @@ cudaError_t launch_batch_alloc(const Graph& g, int W, int B, const float* hist, 
                                int mode, uint64_t* R);
 cudaError_t launch_batch_reverse_init(const Graph& g, int W, int B, const double* dhat, double c, const float* hL,
                                       float2* w, float2* s0, double* s_out_if_final);
+// walks shared across a batch's columns (node-major intervals between the distinct R_q(k))
+cudaError_t launch_shared_plan(const Graph& g, int B, const uint64_t* R, uint64_t* len, uint64_t* rbase);
+cudaError_t launch_shared_columns(const Graph& g, int B, const uint64_t* R, const uint64_t* rbase, const uint64_t* soff,
+                                  const uint64_t* scount, uint64_t* nonmeet);
+cudaError_t launch_dhat_from_R(const Graph& g, int64_t N, const uint64_t* nonmeet, const uint64_t* R, double* dhat);
 cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, bool final_level, double c,
                                        const float2* w, const float* h, const float2* s_prev, float2* s_next,
                                        double* s_out, void* partial);

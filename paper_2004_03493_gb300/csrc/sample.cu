@@ -242,6 +242,19 @@ __device__ __forceinline__ uint32_t pick_redraw(uint32_t d, unsigned long long m
     return (uint32_t)(m >> 32);
 }
 
+// Walks shared across the columns of a batch: segment s covers pairs
+// [rbase[s], rbase[s] + len) of node s / B (node-major, B segments per node).
+struct SharedSegs {
+    int B;                  // 0: segments are (column, node) = (s / n, s % n)
+    const uint64_t* rbase;  // first pair index of each segment (NULL unless shared)
+};
+
+__device__ __forceinline__ uint32_t segment_node(unsigned long long seg, unsigned long long n_nodes,
+                                                 const SharedSegs& sh) {
+    if (sh.B) return (uint32_t)(seg / (unsigned long long)sh.B);
+    return (uint32_t)(seg < n_nodes ? seg : seg % n_nodes);
+}
+
 // State of one walk pair stream: the thread's current node k, pair r of R(k)
 // (rk), the two walk positions, the step t, and the pairs still to run.
 // A segment is the run of pairs of one (column, node): in a single query segment k
@@ -259,7 +272,7 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
                                           const int32_t* __restrict__ col, const uint64_t* __restrict__ off,
                                           uint32_t T, const PhiloxKeys& K, unsigned long long* __restrict__ nonmeet,
                                           unsigned long long& steps, unsigned long long n_nodes,
-                                          const uint8_t* __restrict__ depth) {
+                                          const uint8_t* __restrict__ depth, const SharedSegs& sh) {
     const uint32_t rlo = (uint32_t)S.r, rhi = (uint32_t)(S.r >> 32);
     const uint4 w = philox4x32_10(make_uint4(rlo, rhi, S.k, S.t), K);
     const uint2 ra = __ldg(row + S.xa), rb = __ldg(row + S.xb);  // (first in-edge, din)
@@ -300,9 +313,9 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
         do {
             ++S.seg;
         } while (__ldg(off + S.seg + 1) <= g);
-        S.r = 0;
-        S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
-        S.k = (uint32_t)(S.seg < n_nodes ? S.seg : S.seg % n_nodes);
+        S.r = sh.rbase ? __ldg(sh.rbase + S.seg) : 0ull;
+        S.rk = S.r + (__ldg(off + S.seg + 1) - __ldg(off + S.seg));
+        S.k = segment_node(S.seg, n_nodes, sh);
         S.d = depth ? depth[S.k] : 0u;
         S.xa = S.xb = S.k;
     }
@@ -320,7 +333,8 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
                                                                  unsigned long long* __restrict__ nonmeet,
                                                                  unsigned long long* __restrict__ steps_out,
                                                                  Status* __restrict__ st,
-                                                                 const uint8_t* __restrict__ depth) {
+                                                                 const uint8_t* __restrict__ depth,
+                                                                 const SharedSegs sh) {
     __shared__ unsigned long long red[kBlock / 32];
     const unsigned long long total = off[nseg];
     if ((double)total > budget || (st->err & kErrBudget)) {
@@ -344,14 +358,15 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
             if (__ldg(off + mid) <= g0) lo = mid; else hi = mid;
         }
         S.seg = (unsigned long long)lo;
-        S.k = (uint32_t)(lo < n ? lo : lo % n);
+        S.k = segment_node(S.seg, (unsigned long long)n, sh);
         S.d = depth ? depth[S.k] : 0u;
-        S.r = g0 - __ldg(off + S.seg);
-        S.rk = __ldg(off + S.seg + 1) - __ldg(off + S.seg);
+        const unsigned long long rb = sh.rbase ? __ldg(sh.rbase + S.seg) : 0ull;
+        S.r = rb + (g0 - __ldg(off + S.seg));
+        S.rk = rb + (__ldg(off + S.seg + 1) - __ldg(off + S.seg));
         S.xa = S.xb = S.k;
         for (;;) {
             if (!S.left) break;
-            pair_step(S, row, col, off, T, K, nonmeet, steps, (unsigned long long)n, depth);
+            pair_step(S, row, col, off, T, K, nonmeet, steps, (unsigned long long)n, depth, sh);
         }
     }
     steps = block_sum(steps, red);
@@ -379,7 +394,8 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
 }
 
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
-                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth) {
+                                   uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth, int shared_B,
+                                   const uint64_t* rbase) {
     cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)nseg, g.stream);
     if (e != cudaSuccess) return e;
     unsigned long long* steps = pair_steps ? (unsigned long long*)pair_steps : &g.status->pair_steps;
@@ -396,7 +412,8 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
     sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, nseg, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
-                                                         (unsigned long long*)nonmeet, steps, g.status, depth);
+                                                         (unsigned long long*)nonmeet, steps, g.status, depth,
+                                                         SharedSegs{rbase ? shared_B : 0, rbase});
     return cudaGetLastError();
 }
 

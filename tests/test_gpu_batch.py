@@ -111,3 +111,28 @@ def test_batch_topk_and_limits(esim):
         g.query_batch([n], [1e-2], C)
     assert e.value.status == -1
     g.close()
+
+
+def test_shared_walks_give_the_same_counts_with_fewer_pairs(esim):
+    n, rp, col = synth.chung_lu(6000, 60000, gamma=2.1, seed=5)
+    srcs = synth.random_sources(rp, 40, seed=2)
+    srcs[5] = srcs[4]  # the same source twice: identical thresholds share every interval
+    eps = np.exp(np.random.default_rng(3).uniform(np.log(1e-5), np.log(1e-2), size=40))
+    eps[5] = eps[4]
+    g1 = esim.Graph(n, rp, col, kappa=0.5)
+    g0 = esim.Graph(n, rp, col, kappa=0.5, shared_walks=0)
+    assert g1.get_option("shared_walks") == 1.0
+    s1 = g1.query_batch(srcs, eps, C, seed=7)
+    st1 = g1.stats()
+    s0 = g0.query_batch(srcs, eps, C, seed=7)
+    st0 = g0.stats()
+    assert np.array_equal(s1, s0)
+    assert np.array_equal(s1[4], s1[5])
+    assert st1["sum_R"] < st0["sum_R"]
+    assert st1["pair_steps"] < st0["pair_steps"]
+    # top-k through the shared path equals the unshared one
+    ids1, v1 = g1.topk_batch(srcs[:8], eps[:8], C, 20, seed=7)
+    ids0, v0 = g0.topk_batch(srcs[:8], eps[:8], C, 20, seed=7)
+    assert np.array_equal(ids1, ids0) and np.array_equal(v1, v0)
+    g1.close()
+    g0.close()
