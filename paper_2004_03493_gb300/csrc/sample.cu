@@ -312,6 +312,10 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
         const unsigned long long g = S.g_end - S.left;
         do {
             ++S.seg;
+            if (sh.B) {  // shared layout: a node's empty intervals are its last ones; skip them at once
+                const unsigned long long i = S.seg % (unsigned long long)sh.B;
+                if (i != 0 && __ldg(off + S.seg + 1) == __ldg(off + S.seg)) S.seg += (unsigned long long)sh.B - 1 - i;
+            }
         } while (__ldg(off + S.seg + 1) <= g);
         S.r = sh.rbase ? __ldg(sh.rbase + S.seg) : 0ull;
         S.rk = S.r + (__ldg(off + S.seg + 1) - __ldg(off + S.seg));
