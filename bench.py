@@ -387,6 +387,11 @@ def run_batched(args, w):
             tb.append(a)
             ts.append(b)
             bstats.append(st)
+    # walks shared across the columns (the default) against each column sampling its own
+    gb.set_option("shared_walks", 0)
+    t_unshared = timed(batch)
+    st_unshared = gb.stats()
+    gb.set_option("shared_walks", 1)
     # accuracy of the batched form against the plain FP64 single queries on the same walks
     sb = gb.query_batch(srcs[:8], eps[:8], c, seed=1)
     diffs = [float(np.max(np.abs(sb[q] - gs.query(srcs[q], c, float(eps[q]), 1)))) for q in range(8)]
@@ -404,6 +409,12 @@ def run_batched(args, w):
             "batched_phases_ms": {p: statistics.mean(s_[f"ms_{p}"] for s_ in bstats)
                                   for p in ("forward", "allocate", "sample", "reverse", "topk")},
             "max_abs_diff_batched_vs_single_first8": max(diffs),
+            "shared_walks": {"pairs": statistics.mean(s_["sum_R"] for s_ in bstats),
+                             "pairs_unshared": st_unshared["sum_R"],
+                             "sample_ms": statistics.mean(s_["ms_sample"] for s_ in bstats),
+                             "sample_ms_unshared": st_unshared["ms_sample"], "ms_unshared": t_unshared,
+                             "note": "same per-column counts either way (the walk spec keys pairs by node and "
+                                     "index); shared: one walk set per node cut at the distinct R_q(k)"},
             "note": "both forms draw the same walk pairs (one seed); the difference is FP32c rounding plus "
                     "the sampling noise of R(k) decided from FP32 pi"}
     print(json.dumps(line), flush=True)
