@@ -206,6 +206,187 @@ __device__ __forceinline__ void probe_flush_colsum(unsigned long long v, const P
     }
 }
 
+// ---- direction-optimising probe steps
+//
+// A probe block starts from 32 single nodes, so its first steps touch few rows.
+// While the frontier F_s (the rows of x_s that may be non-zero) has few in-edges,
+// a step pushes x_s(j) to the rows i in I(j) with integer atomics into an n x 32
+// accumulator (exact, so the order of the atomics does not matter) and processes
+// only the touched rows; once the frontier's in-edges exceed (m + n) / 4 the step
+// and all later ones of the block run the dense pull above.  Both forms give the
+// same integers, so the switch changes no bit of the result.  The frontier, its
+// in-edge count and the work list of 64-entry chunks live on the device; the
+// kernels of a step read the same counters, so all agree on the form without a
+// host round trip.
+constexpr int kPushChunk = 64;
+
+struct ProbeStepCnt {
+    unsigned int fcount;      // rows in F_s
+    unsigned int wcount;      // push work items of F_s (64-entry chunks of in-rows)
+    unsigned long long push;  // in-edges of F_s
+};
+
+struct ProbeCtl {
+    ProbeStepCnt st[kAlg3MaxDepth + 2];
+    int dense_plus1;  // 0: sparse so far; s + 1: dense from step s on
+};
+
+__device__ __forceinline__ bool probe_dense_at(const ProbeCtl* ctl, int s, unsigned long long thr) {
+    const int d = *(volatile const int*)&ctl->dense_plus1;
+    return (d != 0 && d - 1 <= s) || ctl->st[s].push > thr;
+}
+
+struct ProbePush {
+    const uint32_t* in_rp;
+    const int32_t* in_col;
+    const unsigned long long* X;  // x_s (rows of F_s)
+    unsigned long long* Hn;       // accumulator of h_{s+1}, zero outside the step
+    uint32_t* mark;               // rows already in F_{s+1}
+    const int2* W;                // work items of F_s
+    int32_t* Fnext;               // F_{s+1}
+    ProbeCtl* ctl;
+    int s;
+    unsigned long long thr;
+};
+
+// One warp per work item (row j, chunk): every entry i of the chunk receives x_s(j)
+// in all 32 columns; each lane marks one entry's row and the new rows are appended
+// to F_{s+1} with one atomic per warp.
+__global__ void __launch_bounds__(kBlock) probe_push_kernel(ProbePush a) {
+    if (probe_dense_at(a.ctl, a.s, a.thr)) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned int items = a.ctl->st[a.s].wcount;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (int64_t)items; w += nwarps) {
+        const int2 it = a.W[w];
+        const int32_t j = it.x;
+        const unsigned long long xv = a.X[(size_t)j * kProbeW + lane];
+        if (!__any_sync(0xffffffffu, xv != 0ull)) continue;  // adds nothing, touches nothing
+        const uint32_t rb = __ldg(a.in_rp + j), re = __ldg(a.in_rp + j + 1);
+        const uint32_t beg = rb + (uint32_t)it.y * kPushChunk;
+        const uint32_t end = beg + kPushChunk < re ? beg + kPushChunk : re;
+        for (uint32_t p0 = beg; p0 < end; p0 += 32) {
+            const uint32_t p = p0 + lane;
+            const int32_t mine = p < end ? __ldg(a.in_col + p) : -1;
+            bool fresh = false;
+            unsigned long long din_new = 0;
+            if (mine >= 0) {
+                fresh = atomicExch(a.mark + mine, 1u) == 0u;
+                if (fresh) din_new = __ldg(a.in_rp + mine + 1) - __ldg(a.in_rp + mine);
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            unsigned int base = 0;
+            if (fm) {
+                unsigned long long dsum = din_new;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                if (lane == 0) {
+                    base = atomicAdd(&a.ctl->st[a.s + 1].fcount, (unsigned int)__popc(fm));
+                    atomicAdd(&a.ctl->st[a.s + 1].push, dsum);
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (fresh) a.Fnext[base + __popc(fm & ((1u << lane) - 1u))] = mine;
+            }
+            const int cnt = (int)(end - p0 < 32 ? end - p0 : 32);  // warp-uniform
+            for (int t = 0; t < cnt; ++t) {
+                const int32_t i = __shfl_sync(0xffffffffu, mine, t);
+                if (xv) atomicAdd(a.Hn + (size_t)i * kProbeW + lane, xv);
+            }
+        }
+    }
+}
+
+struct ProbeSparseEpi {
+    const uint32_t* in_rp;
+    unsigned long long* Hn;
+    uint32_t* mark;
+    const int32_t* Fnext;        // F_{s+1}
+    const int32_t* Fcur;         // F_s: its x_s rows are cleared
+    unsigned long long* Xcur;    // x_s
+    int2* Wnext;                 // work items of F_{s+1}
+    ProbeCtl* ctl;
+    int s;
+    int last;                    // no further step: x_{s+1} and its work items are not needed
+    unsigned long long thr;
+};
+
+// The rows of F_{s+1}: h_{s+1} from the accumulator (which is cleared), x_{s+1},
+// the epilogue terms, and the next step's work items; then x_s is cleared on F_s.
+__global__ void __launch_bounds__(kBlock) probe_sparse_epi_kernel(ProbeSparseEpi a, ProbeEpi epi) {
+    if (probe_dense_at(a.ctl, a.s, a.thr)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned int nf = a.ctl->st[a.s + 1].fcount;
+    unsigned long long nacc = 0ull;
+    for (int64_t r = w0; r < (int64_t)nf; r += nwarps) {
+        const int32_t i = a.Fnext[r];
+        const size_t at = (size_t)i * kProbeW + lane;
+        const unsigned long long H = a.Hn[at];
+        a.Hn[at] = 0ull;
+        const uint32_t d = __ldg(a.in_rp + i + 1) - __ldg(a.in_rp + i);
+        if (lane == 0) {
+            a.mark[i] = 0u;
+            if (!a.last && d) {
+                const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
+                const unsigned int base = atomicAdd(&a.ctl->st[a.s + 1].wcount, nch);
+                for (unsigned int ch = 0; ch < nch; ++ch) a.Wnext[base + ch] = make_int2(i, (int)ch);
+            }
+        }
+        if (a.last) {
+            if (epi.mode == 2) nacc += fx_sq(H);
+        } else {
+            nacc += probe_epilogue(i, H, lane, epi);
+        }
+    }
+    const unsigned int nc = a.ctl->st[a.s].fcount;
+    for (int64_t r = w0; r < (int64_t)nc; r += nwarps) a.Xcur[(size_t)a.Fcur[r] * kProbeW + lane] = 0ull;
+    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
+}
+
+// Block start: x_0 = e_{q'} / din(q') per column, F_0 = the sources, their work items.
+__global__ void probe_sparse_init_kernel(const int32_t* __restrict__ ids, int count, const uint32_t* __restrict__ in_rp,
+                                         unsigned long long* __restrict__ X, int32_t* __restrict__ F, int2* __restrict__ W,
+                                         ProbeCtl* __restrict__ ctl) {
+    const int lane = threadIdx.x;
+    int32_t q = -1;
+    uint32_t d = 0;
+    if (lane < count) {
+        q = ids[lane];
+        d = in_rp[q + 1] - in_rp[q];
+        X[(size_t)q * kProbeW + lane] = d ? kOne / d : 0ull;
+        F[lane] = q;
+    }
+    const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
+    unsigned int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned int base = incl - nch;
+    for (unsigned int ch = 0; ch < nch; ++ch) W[base + ch] = make_int2(q, (int)ch);
+    unsigned long long dsum = d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) {
+        ctl->st[0].fcount = (unsigned int)(count < 32 ? count : 32);
+        ctl->st[0].wcount = total;
+        ctl->st[0].push = dsum;
+    }
+}
+
+// After a block that went dense: both x buffers are cleared for the next block.
+__global__ void probe_cleanup_kernel(const ProbeCtl* __restrict__ ctl, unsigned long long* __restrict__ Xa,
+                                     unsigned long long* __restrict__ Xb, size_t words) {
+    if (ctl->dense_plus1 == 0) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
+        Xa[i] = 0ull;
+        Xb[i] = 0ull;
+    }
+}
+
 // One probe step: h(i, col) = sum_{j in Out(i)} X(j, col), a pull over the out-edge
 // CSR for 32 columns at once.  Short rows: one warp per row, lane = column.  Long
 // rows: one block per 4096-entry segment, each warp adding a contiguous eighth of it
@@ -216,10 +397,15 @@ __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uin
                                                             uint32_t long_min, int64_t nseg,
                                                             const Segment* __restrict__ seg,
                                                             unsigned long long* __restrict__ partial, int short_blocks,
-                                                            ProbeEpi epi) {
+                                                            ProbeEpi epi, ProbeCtl* ctl, int step,
+                                                            unsigned long long thr) {
     constexpr int kWarps = kBlock / 32;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    if (ctl) {
+        if (!probe_dense_at(ctl, step, thr)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->dense_plus1, 0, step + 1);
+    }
     if ((int)blockIdx.x >= short_blocks) {
         __shared__ unsigned long long red[kWarps][kProbeW];
         const int64_t nsb = (int64_t)gridDim.x - short_blocks;
@@ -254,7 +440,9 @@ __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uin
 __global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(int64_t nlong, const int32_t* __restrict__ long_rows,
                                                                  const int32_t* __restrict__ long_first,
                                                                  const unsigned long long* __restrict__ partial,
-                                                                 ProbeEpi epi) {
+                                                                 ProbeEpi epi, const ProbeCtl* ctl, int step,
+                                                                 unsigned long long thr) {
+    if (ctl && !probe_dense_at(ctl, step, thr)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long nacc = 0ull;
@@ -306,6 +494,11 @@ struct A3Ws {
     int32_t* ids;     // n
     unsigned long long* Xa;      // 32 n probe block (fixed point)
     unsigned long long* Xb;      // 32 n
+    unsigned long long* Hn;      // 32 n push accumulator (zero between steps)
+    uint32_t* mark;              // n (zero between steps)
+    int32_t* F[2];               // frontiers, n each
+    int2* W[2];                  // push work items, n + m/64 + 64 each
+    ProbeCtl* ctl;
     double* partial;             // kDotBlocks (dot products)
     unsigned long long* ppart;   // 32 nseg (probe segment partials)
     double* coef;                // 32
@@ -314,7 +507,7 @@ struct A3Ws {
     unsigned long long* counts;  // 64
 };
 
-size_t a3_layout(int64_t n_, int64_t nseg, void* base, A3Ws* out) {
+size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     const size_t n = (size_t)n_;
     const size_t D = (size_t)kAlg3MaxDepth;
     size_t o = 0;
@@ -335,6 +528,14 @@ size_t a3_layout(int64_t n_, int64_t nseg, void* base, A3Ws* out) {
     w.ids = (int32_t*)take(4 * n);
     w.Xa = (unsigned long long*)take(8 * kProbeW * n);
     w.Xb = (unsigned long long*)take(8 * kProbeW * n);
+    w.Hn = (unsigned long long*)take(8 * kProbeW * n);
+    w.mark = (uint32_t*)take(4 * n);
+    const size_t witems = n + (size_t)m_ / kPushChunk + 64;
+    for (int b = 0; b < 2; ++b) {
+        w.F[b] = (int32_t*)take(4 * n);
+        w.W[b] = (int2*)take(8 * witems);
+    }
+    w.ctl = (ProbeCtl*)take(sizeof(ProbeCtl));
     w.partial = (double*)take(8 * kDotBlocks);
     w.ppart = (unsigned long long*)take(8 * (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
     w.coef = (double*)take(8 * kProbeW);
@@ -354,7 +555,7 @@ cudaError_t dsum(const Graph& g, const double* a, int kind, const A3Ws& ws, doub
 
 // One probe step for the block: X_prev -> h (epilogue: X_next, accumulation).
 cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const ProbeEpi& epi,
-                       unsigned long long* partial, int* count) {
+                       unsigned long long* partial, int* count, ProbeCtl* ctl, int step, unsigned long long thr) {
     const DevCsr& A = g.out;
     const int wpb = kBlock / 32;
     int64_t sb = (g.n + wpb - 1) / wpb;
@@ -363,14 +564,14 @@ cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const P
     int64_t segb = A.nseg;  // one block per segment
     if (segb > (int64_t)g.sm_count * 8) segb = (int64_t)g.sm_count * 8;
     probe_rows_kernel<<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, X_prev, A.long_min, A.nseg,
-                                                                       A.seg, partial, (int)sb, epi);
+                                                                       A.seg, partial, (int)sb, epi, ctl, step, thr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*count;
     if (A.nlong > 0) {
         const int64_t blocks = (A.nlong * 32 + kBlock - 1) / kBlock;
         probe_long_rows_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.nlong, A.long_rows, A.long_first, partial,
-                                                                          epi);
+                                                                          epi, ctl, step, thr);
         e = cudaGetLastError();
         ++*count;
     }
@@ -379,11 +580,11 @@ cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const P
 
 }  // namespace
 
-size_t alg3_workspace_bytes(const Graph& g) { return a3_layout(g.n, g.out.nseg, nullptr, nullptr); }
+size_t alg3_workspace_bytes(const Graph& g) { return a3_layout(g.n, g.m, g.out.nseg, nullptr, nullptr); }
 
 cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* wsp, uint64_t* supp_out, int* launches) {
     A3Ws ws;
-    a3_layout(g.n, g.out.nseg, wsp, &ws);
+    a3_layout(g.n, g.m, g.out.nseg, wsp, &ws);
     const size_t n = (size_t)g.n;
     int count = 0;
     cudaError_t e = cudaMemsetAsync(ws.counts, 0, sizeof(unsigned long long) * 64, g.stream);
@@ -408,7 +609,7 @@ cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* wsp, uint
 
 cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, void* wsp, double* z_out, int* launches) {
     A3Ws ws;
-    a3_layout(g.n, g.out.nseg, wsp, &ws);
+    a3_layout(g.n, g.m, g.out.nseg, wsp, &ws);
     const size_t n = (size_t)g.n;
     const int per_sweep = 1 + (g.out.nlong > 0 ? 1 : 0);
     const int eb = eblocks(g, g.n);
@@ -419,6 +620,13 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     if ((e = cudaMemsetAsync(ws.Zv, 0, sizeof(double) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws.colsum, 0, sizeof(unsigned long long) * kProbeW, g.stream)) != cudaSuccess) return e;
+    if (depth >= 3) {  // the probe blocks, accumulator and marks start (and each block ends) all zero
+        if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.Xb, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.Hn, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.mark, 0, sizeof(uint32_t) * n, g.stream)) != cudaSuccess)
+            return e;
+    }
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
     for (int j = 1; j <= depth; ++j) {
@@ -452,16 +660,18 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                 return e;
             if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
             const int steps = depth - j;
+            const unsigned long long thr = (unsigned long long)(g.m + g.n) / 4;
+            const unsigned sparse_blocks = (unsigned)g.sm_count * 4;
             for (uint64_t b0 = 0; b0 < nsup; b0 += kProbeW) {
                 const int cnt = (int)std::min<uint64_t>(kProbeW, nsup - b0);
                 const int32_t* ids = ws.ids + b0;
-                if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess)
-                    return e;
-                probe_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.in.rp, ws.Xa);
+                if ((e = cudaMemsetAsync(ws.ctl, 0, sizeof(ProbeCtl), g.stream)) != cudaSuccess) return e;
+                probe_sparse_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.in.rp, ws.Xa, ws.F[0], ws.W[0], ws.ctl);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 ++count;
                 unsigned long long* X[2] = {ws.Xa, ws.Xb};
                 for (int lp = 1; lp <= steps; ++lp) {
+                    const int st = lp - 1;
                     ProbeEpi epi{g.in.rp, X[lp & 1], 0, nullptr, ws.Zv + (size_t)(j + lp) * n, ws.colsum};
                     if (lp == steps) {
                         epi.mode = 2;
@@ -472,12 +682,23 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                         epi.mode = 1;
                         epi.coef = ws.coef;
                     }
-                    if ((e = probe_step(g, X[(lp - 1) & 1], epi, ws.ppart, &count)) != cudaSuccess) return e;
+                    const ProbePush push{g.in.rp, g.in.col, X[st & 1], ws.Hn, ws.mark, ws.W[st & 1],
+                                         ws.F[(st + 1) & 1], ws.ctl, st, thr};
+                    probe_push_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(push);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                    ++count;
+                    if ((e = probe_step(g, X[st & 1], epi, ws.ppart, &count, ws.ctl, st, thr)) != cudaSuccess) return e;
+                    const ProbeSparseEpi se{g.in.rp, ws.Hn, ws.mark, ws.F[(st + 1) & 1], ws.F[st & 1], X[st & 1],
+                                            ws.W[(st + 1) & 1], ws.ctl, st, lp == steps ? 1 : 0, thr};
+                    probe_sparse_epi_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(se, epi);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                    ++count;
                 }
+                probe_cleanup_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(ws.ctl, ws.Xa, ws.Xb, (size_t)kProbeW * n);
                 probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)steps], ws.coef);
                 probe_norm_finish_kernel<<<1, kProbeW, 0, g.stream>>>(ws.coef, ws.colsum, ws.sums + 63);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                count += 2;
+                count += 3;
             }
         }
     }
