@@ -93,14 +93,15 @@ def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, dep
     return out
 
 
-def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int) -> float:
+def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int, w_sweep: float = 4.0, w_probe: float = 0.5,
+                 w_launch: float = 1048576.0) -> float:
     """Estimated GPU work (in sampler pair-steps) of exploiting a node to depth d.
 
     d = 0 is Algorithm 2 alone.  Walks: R_d (d + 1/(1-c)) with R_d = max(1, ceil(v c^(2d))),
-    v = R_b pi(k)^2.  Lemma 5 at depth d: 2d-1 single sweeps of m+n entries (weight 4
-    each entry), sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps (weight 0.5 per entry
-    and column), and 2^20 per kernel launch (3 per sweep; 3 per probe step and 2 per
-    block of 32 probes).  The same arithmetic, in the same order, as the library's plan,
+    v = R_b pi(k)^2.  Lemma 5 at depth d: 2d-1 single sweeps of m+n entries (weight
+    w_sweep per entry), sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps (w_probe per
+    entry and column), and w_launch per kernel launch (3 per sweep; 3 per probe step and
+    2 per block of 32 probes).  The same arithmetic, in the same order, as the library's plan,
     so that both sides pick the same depth.
     """
     r = math.ceil(v) if d == 0 else math.ceil(v * c ** (2 * d))
@@ -113,9 +114,9 @@ def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int) -> float:
         for i in range(1, d - 1):
             probe += int(supp[i]) * (d - i)
             launches += (int(supp[i]) + 31) // 32 * (3 * (d - i) + 2)
-        cost += 4.0 * edges * float(2 * d - 1)
-        cost += 0.5 * edges * float(probe)
-        cost += 1048576.0 * float(launches)
+        cost += w_sweep * edges * float(2 * d - 1)
+        cost += w_probe * edges * float(probe)
+        cost += w_launch * float(launches)
     return cost
 
 
@@ -126,7 +127,8 @@ def supports(P, k: int, levels: int) -> list[int]:
 
 
 def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 8,
-                      min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None):
+                      min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None,
+                      weights: tuple = (4.0, 0.5, 1048576.0)):
     """(depth uint8[n], R uint64[n]) of Algorithm 3 with the cost-minimising depth.
 
     Candidates: the max_nodes largest pi(k) (ties to the lower id) with pi(k) > 0,
@@ -157,7 +159,7 @@ def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: 
         if max(1.0, float(math.ceil(v))) < min_pairs:
             continue
         supp = supports(P, kk, max(0, max_depth - 2))
-        costs = [exploit_cost(dd, v, c, supp, n, m) for dd in range(max_depth + 1)]
+        costs = [exploit_cost(dd, v, c, supp, n, m, *weights) for dd in range(max_depth + 1)]
         d, best = 0, costs[0]
         for dd in range(1, max_depth + 1):
             if costs[dd] < best:

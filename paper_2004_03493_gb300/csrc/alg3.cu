@@ -51,15 +51,41 @@ __global__ void sum_partials_kernel(int count, const double* __restrict__ partia
     if (threadIdx.x == 0) *out = acc;
 }
 
-// count[0] += |{i : h(i) != 0}| (integer atomics: order-free, so exact)
-__global__ void __launch_bounds__(kBlock) support_kernel(int64_t n, const double* __restrict__ h,
-                                                         unsigned long long* __restrict__ count) {
-    __shared__ unsigned long long red[kBlock / 32];
-    unsigned long long c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        c += h[i] != 0.0 ? 1ull : 0ull;
-    c = block_sum(c, red);
-    if (threadIdx.x == 0 && c) atomicAdd(count, c);
+// Supports of the walk distributions of up to 32 nodes at once, as bit sets: bit c
+// of B_l(i) says (P^T)^l(k_c, i) != 0.  B_{l+1}(i) = OR over j in Out(i) of B_l(j)
+// (a pull over the out-edge CSR, one warp per row), and lane c of each warp counts
+// the rows with bit c set; one integer atomic per column and block gives
+// |supp h_l| for each of the 32 nodes.
+__global__ void reach_init_kernel(const int32_t* __restrict__ ks, int count, uint32_t* __restrict__ Bm) {
+    if ((int)threadIdx.x < count) atomicOr(Bm + ks[threadIdx.x], 1u << threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kBlock) reach_step_kernel(int64_t n, const uint32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const uint32_t* __restrict__ Bcur,
+                                                            uint32_t* __restrict__ Bnext,
+                                                            unsigned long long* __restrict__ counts) {
+    constexpr int kWarps = kBlock / 32;
+    __shared__ unsigned long long red[kWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kWarps;
+    unsigned long long cnt = 0ull;
+    for (int64_t row = (int64_t)blockIdx.x * kWarps + wib; row < n; row += nw) {
+        const uint32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
+        uint32_t acc = 0u;
+        for (uint32_t p = b + lane; p < e; p += 32) acc |= Bcur[__ldg(col + p)];
+        acc = __reduce_or_sync(0xffffffffu, acc);
+        if (lane == 0) Bnext[row] = acc;
+        cnt += (acc >> lane) & 1u;
+    }
+    red[wib][lane] = cnt;
+    __syncthreads();
+    if (wib == 0) {
+        unsigned long long t = 0ull;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += red[w][lane];
+        if (t) atomicAdd(counts + lane, t);
+    }
 }
 
 // flag(i) = h(i) != 0, as the uint64 counts of the offset scan
@@ -499,12 +525,14 @@ struct A3Ws {
     int32_t* F[2];               // frontiers, n each
     int2* W[2];                  // push work items, n + m/64 + 64 each
     ProbeCtl* ctl;
+    uint32_t* Ba;                // reach bit sets (32 nodes per word)
+    uint32_t* Bb;
+    unsigned long long* rcounts; // (D + 1) x 32 support sizes
     double* partial;             // kDotBlocks (dot products)
     unsigned long long* ppart;   // 32 nseg (probe segment partials)
     double* coef;                // 32
     unsigned long long* colsum;  // 32
     double* sums;                // 64: [j] = sum_q Zv_j(q); [63] = the last level's probe terms
-    unsigned long long* counts;  // 64
 };
 
 size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
@@ -536,12 +564,14 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
         w.W[b] = (int2*)take(8 * witems);
     }
     w.ctl = (ProbeCtl*)take(sizeof(ProbeCtl));
+    w.Ba = (uint32_t*)take(4 * n);
+    w.Bb = (uint32_t*)take(4 * n);
+    w.rcounts = (unsigned long long*)take(8 * 32 * (size_t)(kAlg3MaxDepth + 1));
     w.partial = (double*)take(8 * kDotBlocks);
     w.ppart = (unsigned long long*)take(8 * (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
     w.coef = (double*)take(8 * kProbeW);
     w.colsum = (unsigned long long*)take(8 * kProbeW);
     w.sums = (double*)take(8 * 64);
-    w.counts = (unsigned long long*)take(8 * 64);
     if (out) *out = w;
     return o;
 }
@@ -582,28 +612,44 @@ cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const P
 
 size_t alg3_workspace_bytes(const Graph& g) { return a3_layout(g.n, g.m, g.out.nseg, nullptr, nullptr); }
 
-cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* wsp, uint64_t* supp_out, int* launches) {
+cudaError_t alg3_supports(const Graph& g, const int32_t* ks_host, int count, int levels, void* wsp,
+                          uint64_t* supp_out, int* launches) {
     A3Ws ws;
     a3_layout(g.n, g.m, g.out.nseg, wsp, &ws);
     const size_t n = (size_t)g.n;
-    int count = 0;
-    cudaError_t e = cudaMemsetAsync(ws.counts, 0, sizeof(unsigned long long) * 64, g.stream);
-    if (e != cudaSuccess) return e;
-    if (levels > 0) {
-        if ((e = launch_walk_distributions(g, k, levels, ws.H, ws.xa, ws.xb)) != cudaSuccess) return e;
-        count += 1 + levels * (1 + (g.out.nlong > 0 ? 1 : 0));
-        for (int i = 1; i <= levels; ++i) {
-            support_kernel<<<eblocks(g, g.n), kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)i * n, ws.counts + i);
+    int nl = 0;
+    cudaError_t e = cudaSuccess;
+    for (int c0 = 0; c0 < count; c0 += 32) {
+        const int cnt = std::min(32, count - c0);
+        for (int c = 0; c < cnt; ++c) supp_out[(size_t)(c0 + c) * (kAlg3MaxDepth + 1)] = 1;
+        if (levels <= 0) continue;
+        if ((e = cudaMemsetAsync(ws.rcounts, 0, 8 * 32 * (size_t)(kAlg3MaxDepth + 1), g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.Ba, 0, 4 * n, g.stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ws.ids, ks_host + c0, sizeof(int32_t) * (size_t)cnt, cudaMemcpyHostToDevice,
+                                 g.stream)) != cudaSuccess)
+            return e;
+        reach_init_kernel<<<1, 32, 0, g.stream>>>(ws.ids, cnt, ws.Ba);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++nl;
+        uint32_t* B[2] = {ws.Ba, ws.Bb};
+        int64_t blocks = (g.n + kBlock / 32 - 1) / (kBlock / 32);
+        if (blocks > (int64_t)g.sm_count * 16) blocks = (int64_t)g.sm_count * 16;
+        for (int l = 1; l <= levels; ++l) {
+            reach_step_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(g.n, g.out.rp, g.out.col, B[(l - 1) & 1],
+                                                                         B[l & 1], ws.rcounts + (size_t)l * 32);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            ++count;
+            ++nl;
         }
+        std::vector<unsigned long long> host((size_t)32 * (kAlg3MaxDepth + 1));
+        if ((e = cudaMemcpyAsync(host.data(), ws.rcounts, 8 * host.size(), cudaMemcpyDeviceToHost, g.stream)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
+        for (int c = 0; c < cnt; ++c)
+            for (int l = 1; l <= levels; ++l)
+                supp_out[(size_t)(c0 + c) * (kAlg3MaxDepth + 1) + l] = host[(size_t)l * 32 + c];
     }
-    unsigned long long host[64] = {};
-    if ((e = cudaMemcpyAsync(host, ws.counts, sizeof(host), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-    supp_out[0] = 1;
-    for (int i = 1; i <= levels; ++i) supp_out[i] = host[i];
-    if (launches) *launches += count;
+    if (launches) *launches += nl;
     return cudaSuccess;
 }
 

@@ -271,14 +271,10 @@ esim_status ensure_a3ws(Graph& g) {
 //   walks      R_d (d + 1/(1-c)),  R_d = max(1, ceil(v c^(2d)))  (v = R_b pi(k)^2)
 //   Lemma 5    2d-1 single-vector sweeps of m+n entries (h_1..h_d and the P~ sweeps),
 //              sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps, and the launches;
-// d = 0 is Algorithm 2 alone.  The weights were measured on the bench graph: a pair-step,
-// about 4 of them per entry of a single sweep, 0.5 per entry and column of a 32-column
-// probe sweep, and 2^20 per launch.
-constexpr double kA3SweepEdge = 4.0;
-constexpr double kA3ProbeEdge = 0.5;
-constexpr double kA3Launch = 1048576.0;
-
-double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m) {
+// d = 0 is Algorithm 2 alone.  The weights (options alg3_w_sweep, alg3_w_probe,
+// alg3_w_launch: pair-steps per entry of a single sweep, per entry and column of a probe
+// sweep, and per launch) are calibrated by timing whole queries on GB300.
+double alg3_cost(const Graph& g, int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m) {
     double r = d == 0 ? ceil(v) : ceil(v * pow(c, (double)(2 * d)));
     if (r < 1.0) r = 1.0;
     double cost = r * ((double)d + 1.0 / (1.0 - c));
@@ -289,9 +285,9 @@ double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int
             probe += supp[i] * (uint64_t)(d - i);
             launches += (supp[i] + 31) / 32 * (uint64_t)(3 * (d - i) + 2);
         }
-        cost += kA3SweepEdge * edges * (double)(2 * d - 1);
-        cost += kA3ProbeEdge * edges * (double)probe;
-        cost += kA3Launch * (double)launches;
+        cost += g.alg3_w_sweep * edges * (double)(2 * d - 1);
+        cost += g.alg3_w_probe * edges * (double)probe;
+        cost += g.alg3_w_launch * (double)launches;
     }
     return cost;
 }
@@ -321,6 +317,9 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 node selection");
     const std::vector<uint32_t>& din = *g.din_host;
     int used = 0;
+    // candidates: the heaviest nodes with din >= 2 and enough Algorithm 2 pairs
+    std::vector<int32_t> cand;
+    std::vector<double> cand_v;
     for (int i = 0; i < K; ++i) {
         const int32_t kk = ids[i];
         const double p = pis[i];
@@ -330,13 +329,22 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         double r0 = ceil(v);
         if (r0 < 1.0) r0 = 1.0;
         if (r0 < g.alg3_min_pairs) continue;
-        uint64_t supp[kAlg3MaxDepth + 1] = {};
-        const int levels = std::max(0, g.alg3_max_depth - 2);
-        ESIM_CUDA_TRY(alg3_supports(g, kk, levels, g.a3ws, supp, launches), "Algorithm 3 supports");
+        cand.push_back(kk);
+        cand_v.push_back(v);
+    }
+    const int levels = std::max(0, g.alg3_max_depth - 2);
+    std::vector<uint64_t> supps(cand.size() * (kAlg3MaxDepth + 1), 0);
+    if (!cand.empty())
+        ESIM_CUDA_TRY(alg3_supports(g, cand.data(), (int)cand.size(), levels, g.a3ws, supps.data(), launches),
+                      "Algorithm 3 supports");
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+        const int32_t kk = cand[ci];
+        const double v = cand_v[ci];
+        const uint64_t* supp = supps.data() + ci * (kAlg3MaxDepth + 1);
         int d = 0;
-        double best = alg3_cost(0, v, c, supp, g.n, g.m);
+        double best = alg3_cost(g, 0, v, c, supp, g.n, g.m);
         for (int dd = 1; dd <= g.alg3_max_depth; ++dd) {
-            const double cost = alg3_cost(dd, v, c, supp, g.n, g.m);
+            const double cost = alg3_cost(g, dd, v, c, supp, g.n, g.m);
             if (cost < best) {
                 best = cost;
                 d = dd;
@@ -972,6 +980,9 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_min_pairs") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_min_pairs must be >= 0");
         g.alg3_min_pairs = value;
+    } else if (k == "alg3_w_sweep" || k == "alg3_w_probe" || k == "alg3_w_launch") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, k + " must be >= 0");
+        (k == "alg3_w_sweep" ? g.alg3_w_sweep : k == "alg3_w_probe" ? g.alg3_w_probe : g.alg3_w_launch) = value;
     } else if (k == "alg3_max_nodes") {
         if (!(value >= 1.0 && value <= 4096.0)) return fail(ESIM_EINVAL, "alg3_max_nodes must be in [1, 4096]");
         g.alg3_max_nodes = (int)value;
@@ -999,6 +1010,9 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
+    else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
+    else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
+    else if (k == "alg3_w_launch") *value = g.alg3_w_launch;
     else if (k == "batch_tile") *value = g.batch_tile_force;
     else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];
     else if (k == "batch_tile_fwd32") *value = g.batch_tile_fwd[1];

@@ -85,6 +85,10 @@ struct Graph {
     int alg3_max_depth = 8;
     double alg3_min_pairs = 1e6;
     int alg3_max_nodes = 64;
+    // Algorithm 3's cost model (pair-steps per sweep entry, per probe entry and column, per launch)
+    double alg3_w_sweep = 4.0;
+    double alg3_w_probe = 0.5;
+    double alg3_w_launch = 1048576.0;
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
@@ -180,9 +184,10 @@ cudaError_t launch_batch_reverse_level(const Graph& g, int W, int B, int tile, b
 // alg3.cu
 constexpr int kAlg3MaxDepth = 16;
 size_t alg3_workspace_bytes(const Graph& g);
-// supp_out[i] = number of nodes with (P^T)^i(k, .) != 0, i = 0..levels (levels <= kAlg3MaxDepth);
-// synchronises g.stream.
-cudaError_t alg3_supports(const Graph& g, int64_t k, int levels, void* ws, uint64_t* supp_out, int* launches);
+// supp_out[c * (kAlg3MaxDepth + 1) + i] = number of nodes with (P^T)^i(ks[c], .) != 0, for
+// i = 0..levels (levels <= kAlg3MaxDepth) and the count nodes ks (host); synchronises g.stream.
+cudaError_t alg3_supports(const Graph& g, const int32_t* ks, int count, int levels, void* ws, uint64_t* supp_out,
+                          int* launches);
 // Z_1..Z_depth of node k (Lemma 5) into z_out (host), depth <= kAlg3MaxDepth; synchronises g.stream.
 cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, void* ws, double* z_out,
                                int* launches);
