@@ -12,7 +12,8 @@ error above eps in 100 seeds (the paper's 6/(1-sqrt c)^4 is infeasible at
 eps = 1e-6).  --alg3 0 runs Algorithm 2 alone.  The graph is synthetic; the
 paper's datasets are not available.
 
-Timing: W warm-up steps, then K timed steps; the graph (8 MB) fits in L2, so
+Timing: W warm-up steps, then K timed steps (default 10: each source once); the graph
+(8 MB) fits in L2, so
 L2 is flushed (a 512 MB write) before every timed step, outside the CUDA-event
 bracket of the step.  Under torchrun each rank is an independent replica with
 its own ten sources (the path has no exchange step); value = all queries of
@@ -626,7 +627,7 @@ def config_of(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cl100k", choices=sorted(WORKLOADS))
