@@ -1,6 +1,7 @@
 // Algorithm 3 ("Improved method for estimating D(k,k)"): exact first-meeting
 // probabilities Z_1..Z_d of node k by Lemma 5, for any depth d <= kAlg3MaxDepth,
-// and the diagonal estimate that combines them with the tail walk pairs.
+// the supports that choose d, and the diagonal estimate that combines the Z with the
+// tail walk pairs.
 //
 // Notation: h_l = (P^T)^l(k, .), the distribution of a non-stop walk from k after l
 // steps (dense FP64, by pull sweeps over the out-edge CSR with no decay); Zv_l the
@@ -9,11 +10,13 @@
 //   Zv_j = c^j h_j^2 - c P~ Zv_{j-1} - sum_{l'=2}^{j-1} c^{l'} sum_{q'} Zv_{j-l'}(q') ((P^T)^{l'}(q', .))^2
 // (the l' = 1 term is one squared-weight sweep, because (P^T)(q', q)^2 = 1/din(q')^2
 // for q in I(q')).  The l' >= 2 terms need the walk distributions of every q' in
-// the support of h_{j-l'}: the "probes".  Probes run 32 at a time as an n x 32 FP64
-// block through a multi-column pull product whose epilogue subtracts
-// sum_col c^{l'} Zv_i(q'_col) h^{q'_col}_{l'}(q)^2 from Zv_{i+l'}(q) (a fixed lane tree;
-// blocks of 32 consecutive q' of the ascending support, in order).  Z_j = sum_q Zv_j(q)
-// by fixed-order block partials.  Everything is deterministic.
+// the support of h_{j-l'}: the "probes".  Probes run in blocks of 32 columns (one
+// warp lane each), up to kGroupMax blocks per launch.  A probe step maps the
+// block's x = h/din to h_next = P x; its epilogue subtracts
+// sum_col c^{l'} Zv_i(q'_col) h^{q'_col}_{l'}(q)^2 from Zv_{i+l'}(q) for a level below
+// d, or adds h^2 to per-column sums for level d itself (only Z_d's total is needed).
+// Z_j = sum_q Zv_j(q) by fixed-order block partials.  Every accumulation that
+// crosses blocks or threads is an integer one, so the result is deterministic.
 #include "common.cuh"
 #include "internal.h"
 
@@ -27,7 +30,12 @@ namespace esim {
 namespace {
 
 constexpr int kDotBlocks = 1024;
-constexpr int kProbeW = 32;  // probe columns per block (one warp lane each)
+constexpr int kProbeW = 32;      // probe columns per block (one warp lane each)
+constexpr int kGroupMax = 8;     // probe blocks per launch
+constexpr int kPushChunk = 64;   // in-edges per push work item
+constexpr size_t kProbeBudget = (size_t)2 << 30;  // device bytes for the probe groups
+
+// ---------------------------------------------------------------- dense FP64 helpers
 
 // partial[block] of sum_i a(i)^2 (kind 0) or sum_i a(i) (kind 2)
 __global__ void __launch_bounds__(kBlock) wsum_kernel(int64_t n, const double* __restrict__ a, int kind,
@@ -110,15 +118,20 @@ __global__ void sq_scale_kernel(int64_t n, const double* __restrict__ v, const d
     }
 }
 
-// Zv_j = c^j h_j^2 - c T + Zv_j, where Zv_j already holds the (negative) probe terms
-// and T = P~ Zv_{j-1} (T = NULL at j = 1)
+// Probe terms of the levels below d are summed in signed fixed point with 58 fraction
+// bits (integer atomics: exact, order-free); a row's term is at most 32 in magnitude
+// and a level's total at most 1.
+constexpr double kZOne = 288230376151711744.0;  // 2^58
+
+// Zv_j = c^j h_j^2 - c T + (probe terms), T = P~ Zv_{j-1} (T = NULL at j = 1)
 __global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double* __restrict__ h,
-                                   const double* __restrict__ T, double* __restrict__ zv) {
+                                   const double* __restrict__ T, const long long* __restrict__ zfx,
+                                   double* __restrict__ zv) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double hv = h[i];
         double z = cj * (hv * hv);
         if (T) z -= c * T[i];
-        zv[i] = z + zv[i];
+        zv[i] = z + (double)zfx[i] * (1.0 / kZOne);
     }
 }
 
@@ -139,61 +152,238 @@ __device__ __forceinline__ unsigned long long fx_sq(unsigned long long H) {
     return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
 }
 
-// Probe block start: x_0 = e_{q'} / din(q') in column col (row-major n x 32, zeroed before)
-__global__ void probe_init_kernel(const int32_t* __restrict__ ids, int count, const uint32_t* __restrict__ in_rp,
-                                  unsigned long long* __restrict__ X) {
-    const int col = threadIdx.x;
-    if (col < count) {
-        const int32_t q = ids[col];
-        const uint32_t d = in_rp[q + 1] - in_rp[q];
-        X[(size_t)q * kProbeW + col] = d ? kOne / d : 0ull;
-    }
-}
-
-// coef(col) = c^{l'} Zv_i(q'_col); 0 for unused columns
-__global__ void probe_coef_kernel(const int32_t* __restrict__ ids, int count, const double* __restrict__ zv_src,
-                                  double cl, double* __restrict__ coef) {
-    const int col = threadIdx.x;
-    if (col < kProbeW) coef[col] = col < count ? cl * zv_src[ids[col]] : 0.0;
-}
-
-// zlast += sum_col coef(col) * colsum(col) (columns in order); colsum reset for the next block
-__global__ void probe_norm_finish_kernel(const double* __restrict__ coef, unsigned long long* __restrict__ colsum,
-                                         double* __restrict__ zlast) {
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int col = 0; col < kProbeW; ++col) t += coef[col] * ((double)colsum[col] * kInvOne);
-        *zlast += t;
-    }
-    __syncthreads();
-    if (threadIdx.x < kProbeW) colsum[threadIdx.x] = 0ull;
-}
-
-struct ProbeEpi {
-    const uint32_t* in_rp;
-    unsigned long long* x_next;  // n x 32: h / din for the next step
-    int mode;                    // 0: none; 1: subtract sum_col coef h^2 from zacc(row); 2: column sums of h^2
-    const double* coef;          // 32 (mode 1)
-    double* zacc;                // n: Zv of the target level (mode 1)
-    unsigned long long* colsum;  // 32 (mode 2)
+// Direction-optimising steps.  A block starts from 32 single nodes, so its first
+// steps touch few rows.  While the frontier F_s (the rows of x_s that may be
+// non-zero) has few in-edges, a step pushes x_s(j) to the rows i in I(j) with
+// integer atomics into an n x 32 accumulator (exact, so the order of the atomics does
+// not matter) and processes only the touched rows; once the frontier's in-edges
+// exceed (m + n) / 4 the step and all later ones of the block run the dense pull.
+// Both forms give the same integers, so the switch changes no bit of the result.
+// The frontier, its in-edge count and the work list of 64-entry chunks live on the
+// device; the kernels of a step read the same counters, so all agree on the form
+// without a host round trip.
+struct ProbeStepCnt {
+    unsigned int fcount;      // rows in F_s
+    unsigned int wcount;      // push work items of F_s (64-entry chunks of in-rows)
+    unsigned long long push;  // in-edges of F_s
 };
 
-// Row `row` of h^{q'}_{l'} is H (fixed point) in lane = column.  All 32 lanes of the
-// warp call it.  Returns this lane's h^2 (fixed point) for mode 2, else 0.  The FP64
-// row term of mode 1 is a fixed butterfly over the lanes, skipped when the row is zero.
-__device__ __forceinline__ unsigned long long probe_epilogue(int64_t row, unsigned long long H, int lane,
-                                                             const ProbeEpi& e) {
-    const uint32_t d = __ldg(e.in_rp + row + 1) - __ldg(e.in_rp + row);
-    e.x_next[(size_t)row * kProbeW + lane] = (d && H) ? H / d : 0ull;
-    if (e.mode == 2) return fx_sq(H);
-    if (e.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
+struct ProbeCtl {
+    ProbeStepCnt st[kAlg3MaxDepth + 2];
+    int dense_plus1;  // 0: sparse so far; s + 1: dense from step s on
+    int pad;
+};
+
+__device__ __forceinline__ bool probe_dense_at(const ProbeCtl* ctl, int s, unsigned long long thr) {
+    const int d = *(volatile const int*)&ctl->dense_plus1;
+    return (d != 0 && d - 1 <= s) || ctl->st[s].push > thr;
+}
+
+// The buffers of a probe group: block b (blockIdx.y) owns slice b of each.
+struct ProbeGroup {
+    unsigned long long* X[2];   // x ping-pong, 32 n each
+    unsigned long long* Hn;     // push accumulator, 32 n (zero between steps)
+    uint32_t* mark;             // n (zero between steps)
+    int32_t* F[2];              // frontiers, n each
+    int2* W[2];                 // push work items, nw each
+    unsigned long long* ppart;  // dense long-row partials, 32 nseg
+    ProbeCtl* ctl;              // one per block
+    double* coef;               // 32 per block
+    unsigned long long* colsum; // 32 per block
+    size_t nx, nw, np;          // slice strides of X/Hn, W, ppart
+    int64_t n;
+};
+
+// What a step does with h_{s+1}: mode 0 nothing, 1 subtract the row terms from a level
+// below d (zfx), 2 add h^2 to the column sums (level d).
+struct ProbeStepArgs {
+    const uint32_t* in_rp;
+    const int32_t* in_col;
+    int s;               // step index (h_{s+1} is produced)
+    int src;             // which X buffer holds x_s
+    int mode;
+    int last;            // no further step: x_{s+1} is not needed
+    long long* zfx;      // mode 1 target
+    unsigned long long thr;
+};
+
+// Row `row` of h_{s+1} is H (fixed point) in lane = column.  All 32 lanes of the warp
+// call it.  Writes x_{s+1} (unless last); returns this lane's h^2 for mode 2.
+__device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigned long long H, int lane,
+                                                            const ProbeStepArgs& a, unsigned long long* xnext,
+                                                            const double* coef) {
+    if (!a.last) {
+        const uint32_t d = __ldg(a.in_rp + row + 1) - __ldg(a.in_rp + row);
+        xnext[(size_t)row * kProbeW + lane] = (d && H) ? H / d : 0ull;
+    }
+    if (a.mode == 2) return fx_sq(H);
+    if (a.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
         const double h = (double)H * kInvOne;
-        double t = e.coef[lane] * (h * h);
+        double t = coef[lane] * (h * h);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) e.zacc[row] = e.zacc[row] - t;
+        if (lane == 0 && t != 0.0)
+            atomicAdd((unsigned long long*)(a.zfx + row), (unsigned long long)(-__double2ll_rn(t * kZOne)));
     }
     return 0ull;
+}
+
+// Column sums of mode 2: lane sums of the block's warps, then one integer atomic per
+// column (order-free, so exact and deterministic).
+__device__ __forceinline__ void probe_flush_colsum(unsigned long long v, unsigned long long* colsum) {
+    constexpr int kWarps = kBlock / 32;
+    __shared__ unsigned long long red[kWarps][kProbeW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    red[wib][lane] = v;
+    __syncthreads();
+    if (wib == 0) {
+        unsigned long long t = 0ull;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += red[w][lane];
+        if (t) atomicAdd(colsum + lane, t);
+    }
+}
+
+// Group start (one warp per block): x_0 = e_{q'} / din(q') per column, F_0 = the
+// sources, their work items, fresh counters and column sums.
+__global__ void probe_init_kernel(ProbeGroup G, const int32_t* __restrict__ ids, int count,
+                                  const uint32_t* __restrict__ in_rp) {
+    const int b = blockIdx.y, lane = threadIdx.x;
+    ProbeCtl* ctl = G.ctl + b;
+    uint32_t* z = (uint32_t*)ctl;
+    for (int i = lane; i < (int)(sizeof(ProbeCtl) / 4); i += 32) z[i] = 0u;
+    __syncwarp();
+    const int left = count - b * kProbeW;
+    const int cnt = left < kProbeW ? left : kProbeW;
+    int32_t q = -1;
+    uint32_t d = 0;
+    if (lane < cnt) {
+        q = ids[b * kProbeW + lane];
+        d = in_rp[q + 1] - in_rp[q];
+        G.X[0][(size_t)b * G.nx + (size_t)q * kProbeW + lane] = d ? kOne / d : 0ull;
+        G.F[0][(size_t)b * G.n + lane] = q;
+    }
+    const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
+    unsigned int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned int base = incl - nch;
+    for (unsigned int ch = 0; ch < nch; ++ch) G.W[0][(size_t)b * G.nw + base + ch] = make_int2(q, (int)ch);
+    unsigned long long dsum = d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    if (lane == 0) {
+        ctl->st[0].fcount = (unsigned int)cnt;
+        ctl->st[0].wcount = total;
+        ctl->st[0].push = dsum;
+    }
+    G.colsum[(size_t)b * kProbeW + lane] = 0ull;
+}
+
+// coef(b, col) = c^{l'} Zv_i(q'_col); 0 for unused columns
+__global__ void probe_coef_kernel(ProbeGroup G, const int32_t* __restrict__ ids, int count,
+                                  const double* __restrict__ zv_src, double cl) {
+    const int i = blockIdx.y * kProbeW + threadIdx.x;
+    G.coef[i] = i < count ? cl * zv_src[ids[i]] : 0.0;
+}
+
+// Push step (one warp per work item): every entry i of the chunk receives x_s(j) in
+// all 32 columns; each lane marks one entry's row and the new rows are appended to
+// F_{s+1} with one atomic per warp.
+__global__ void __launch_bounds__(kBlock) probe_push_kernel(ProbeGroup G, ProbeStepArgs a) {
+    const int b = blockIdx.y;
+    ProbeCtl* ctl = G.ctl + b;
+    if (probe_dense_at(ctl, a.s, a.thr)) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* X = G.X[a.src] + (size_t)b * G.nx;
+    unsigned long long* Hn = G.Hn + (size_t)b * G.nx;
+    uint32_t* mark = G.mark + (size_t)b * G.n;
+    const int2* W = G.W[a.s & 1] + (size_t)b * G.nw;
+    int32_t* Fnext = G.F[(a.s + 1) & 1] + (size_t)b * G.n;
+    const unsigned int items = ctl->st[a.s].wcount;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (int64_t)items; w += nwarps) {
+        const int2 it = W[w];
+        const int32_t j = it.x;
+        const unsigned long long xv = X[(size_t)j * kProbeW + lane];
+        if (!__any_sync(0xffffffffu, xv != 0ull)) continue;  // adds nothing, touches nothing
+        const uint32_t rb = __ldg(a.in_rp + j), re = __ldg(a.in_rp + j + 1);
+        const uint32_t beg = rb + (uint32_t)it.y * kPushChunk;
+        const uint32_t end = beg + kPushChunk < re ? beg + kPushChunk : re;
+        for (uint32_t p0 = beg; p0 < end; p0 += 32) {
+            const uint32_t p = p0 + lane;
+            const int32_t mine = p < end ? __ldg(a.in_col + p) : -1;
+            bool fresh = false;
+            unsigned long long din_new = 0;
+            if (mine >= 0) {
+                fresh = atomicExch(mark + mine, 1u) == 0u;
+                if (fresh) din_new = __ldg(a.in_rp + mine + 1) - __ldg(a.in_rp + mine);
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            if (fm) {
+                unsigned long long dsum = din_new;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                unsigned int base = 0;
+                if (lane == 0) {
+                    base = atomicAdd(&ctl->st[a.s + 1].fcount, (unsigned int)__popc(fm));
+                    atomicAdd(&ctl->st[a.s + 1].push, dsum);
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (fresh) Fnext[base + __popc(fm & ((1u << lane) - 1u))] = mine;
+            }
+            const int cnt = (int)(end - p0 < 32 ? end - p0 : 32);  // warp-uniform
+            for (int t = 0; t < cnt; ++t) {
+                const int32_t i = __shfl_sync(0xffffffffu, mine, t);
+                if (xv) atomicAdd(Hn + (size_t)i * kProbeW + lane, xv);
+            }
+        }
+    }
+}
+
+// Sparse epilogue: the rows of F_{s+1} (h_{s+1} from the accumulator, which is
+// cleared), the next step's work items; then x_s is cleared on F_s.
+__global__ void __launch_bounds__(kBlock) probe_sparse_epi_kernel(ProbeGroup G, ProbeStepArgs a) {
+    const int b = blockIdx.y;
+    ProbeCtl* ctl = G.ctl + b;
+    if (probe_dense_at(ctl, a.s, a.thr)) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long* Hn = G.Hn + (size_t)b * G.nx;
+    uint32_t* mark = G.mark + (size_t)b * G.n;
+    const int32_t* Fnext = G.F[(a.s + 1) & 1] + (size_t)b * G.n;
+    const int32_t* Fcur = G.F[a.s & 1] + (size_t)b * G.n;
+    unsigned long long* Xcur = G.X[a.src] + (size_t)b * G.nx;
+    unsigned long long* Xnext = G.X[a.src ^ 1] + (size_t)b * G.nx;
+    int2* Wnext = G.W[(a.s + 1) & 1] + (size_t)b * G.nw;
+    const double* coef = G.coef + (size_t)b * kProbeW;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned int nf = ctl->st[a.s + 1].fcount;
+    unsigned long long nacc = 0ull;
+    for (int64_t r = w0; r < (int64_t)nf; r += nwarps) {
+        const int32_t i = Fnext[r];
+        const size_t at = (size_t)i * kProbeW + lane;
+        const unsigned long long H = Hn[at];
+        Hn[at] = 0ull;
+        if (lane == 0) {
+            mark[i] = 0u;
+            const uint32_t d = __ldg(a.in_rp + i + 1) - __ldg(a.in_rp + i);
+            if (!a.last && d) {
+                const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
+                const unsigned int base = atomicAdd(&ctl->st[a.s + 1].wcount, nch);
+                for (unsigned int ch = 0; ch < nch; ++ch) Wnext[base + ch] = make_int2(i, (int)ch);
+            }
+        }
+        nacc += probe_row_out(i, H, lane, a, Xnext, coef);
+    }
+    const unsigned int nc = ctl->st[a.s].fcount;
+    for (int64_t r = w0; r < (int64_t)nc; r += nwarps) Xcur[(size_t)Fcur[r] * kProbeW + lane] = 0ull;
+    if (a.mode == 2) probe_flush_colsum(nacc, G.colsum + (size_t)b * kProbeW);
 }
 
 // Sum of X(col[p], lane) over entries [b, e), eight gathers in flight (integer adds).
@@ -216,232 +406,34 @@ __device__ __forceinline__ unsigned long long probe_range(const int32_t* __restr
     return acc;
 }
 
-// Column sums of mode 2: lane sums of the block's warps, then one integer atomic per
-// column (integer addition is order-free, so the result is exact and deterministic).
-__device__ __forceinline__ void probe_flush_colsum(unsigned long long v, const ProbeEpi& e) {
+// Dense step: h(i, col) = sum_{j in Out(i)} x_s(j, col), a pull over the out-edge CSR
+// for 32 columns at once.  Short rows: one warp per row, lane = column.  Long rows:
+// one block per 4096-entry segment, each warp adding a contiguous eighth of it into
+// the segment's partial; probe_long_rows_kernel adds a row's partials.
+__global__ void __launch_bounds__(kBlock) probe_rows_kernel(ProbeGroup G, ProbeStepArgs a,
+                                                            const uint32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col, uint32_t long_min,
+                                                            int64_t nseg, const Segment* __restrict__ seg,
+                                                            int short_blocks) {
     constexpr int kWarps = kBlock / 32;
-    __shared__ unsigned long long red[kWarps][kProbeW];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    red[wib][lane] = v;
-    __syncthreads();
-    if (wib == 0) {
-        unsigned long long t = 0ull;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) t += red[w][lane];
-        if (t) atomicAdd(e.colsum + lane, t);
-    }
-}
-
-// ---- direction-optimising probe steps
-//
-// A probe block starts from 32 single nodes, so its first steps touch few rows.
-// While the frontier F_s (the rows of x_s that may be non-zero) has few in-edges,
-// a step pushes x_s(j) to the rows i in I(j) with integer atomics into an n x 32
-// accumulator (exact, so the order of the atomics does not matter) and processes
-// only the touched rows; once the frontier's in-edges exceed (m + n) / 4 the step
-// and all later ones of the block run the dense pull above.  Both forms give the
-// same integers, so the switch changes no bit of the result.  The frontier, its
-// in-edge count and the work list of 64-entry chunks live on the device; the
-// kernels of a step read the same counters, so all agree on the form without a
-// host round trip.
-constexpr int kPushChunk = 64;
-
-struct ProbeStepCnt {
-    unsigned int fcount;      // rows in F_s
-    unsigned int wcount;      // push work items of F_s (64-entry chunks of in-rows)
-    unsigned long long push;  // in-edges of F_s
-};
-
-struct ProbeCtl {
-    ProbeStepCnt st[kAlg3MaxDepth + 2];
-    int dense_plus1;  // 0: sparse so far; s + 1: dense from step s on
-};
-
-__device__ __forceinline__ bool probe_dense_at(const ProbeCtl* ctl, int s, unsigned long long thr) {
-    const int d = *(volatile const int*)&ctl->dense_plus1;
-    return (d != 0 && d - 1 <= s) || ctl->st[s].push > thr;
-}
-
-struct ProbePush {
-    const uint32_t* in_rp;
-    const int32_t* in_col;
-    const unsigned long long* X;  // x_s (rows of F_s)
-    unsigned long long* Hn;       // accumulator of h_{s+1}, zero outside the step
-    uint32_t* mark;               // rows already in F_{s+1}
-    const int2* W;                // work items of F_s
-    int32_t* Fnext;               // F_{s+1}
-    ProbeCtl* ctl;
-    int s;
-    unsigned long long thr;
-};
-
-// One warp per work item (row j, chunk): every entry i of the chunk receives x_s(j)
-// in all 32 columns; each lane marks one entry's row and the new rows are appended
-// to F_{s+1} with one atomic per warp.
-__global__ void __launch_bounds__(kBlock) probe_push_kernel(ProbePush a) {
-    if (probe_dense_at(a.ctl, a.s, a.thr)) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned int items = a.ctl->st[a.s].wcount;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (int64_t)items; w += nwarps) {
-        const int2 it = a.W[w];
-        const int32_t j = it.x;
-        const unsigned long long xv = a.X[(size_t)j * kProbeW + lane];
-        if (!__any_sync(0xffffffffu, xv != 0ull)) continue;  // adds nothing, touches nothing
-        const uint32_t rb = __ldg(a.in_rp + j), re = __ldg(a.in_rp + j + 1);
-        const uint32_t beg = rb + (uint32_t)it.y * kPushChunk;
-        const uint32_t end = beg + kPushChunk < re ? beg + kPushChunk : re;
-        for (uint32_t p0 = beg; p0 < end; p0 += 32) {
-            const uint32_t p = p0 + lane;
-            const int32_t mine = p < end ? __ldg(a.in_col + p) : -1;
-            bool fresh = false;
-            unsigned long long din_new = 0;
-            if (mine >= 0) {
-                fresh = atomicExch(a.mark + mine, 1u) == 0u;
-                if (fresh) din_new = __ldg(a.in_rp + mine + 1) - __ldg(a.in_rp + mine);
-            }
-            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-            unsigned int base = 0;
-            if (fm) {
-                unsigned long long dsum = din_new;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-                if (lane == 0) {
-                    base = atomicAdd(&a.ctl->st[a.s + 1].fcount, (unsigned int)__popc(fm));
-                    atomicAdd(&a.ctl->st[a.s + 1].push, dsum);
-                }
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (fresh) a.Fnext[base + __popc(fm & ((1u << lane) - 1u))] = mine;
-            }
-            const int cnt = (int)(end - p0 < 32 ? end - p0 : 32);  // warp-uniform
-            for (int t = 0; t < cnt; ++t) {
-                const int32_t i = __shfl_sync(0xffffffffu, mine, t);
-                if (xv) atomicAdd(a.Hn + (size_t)i * kProbeW + lane, xv);
-            }
-        }
-    }
-}
-
-struct ProbeSparseEpi {
-    const uint32_t* in_rp;
-    unsigned long long* Hn;
-    uint32_t* mark;
-    const int32_t* Fnext;        // F_{s+1}
-    const int32_t* Fcur;         // F_s: its x_s rows are cleared
-    unsigned long long* Xcur;    // x_s
-    int2* Wnext;                 // work items of F_{s+1}
-    ProbeCtl* ctl;
-    int s;
-    int last;                    // no further step: x_{s+1} and its work items are not needed
-    unsigned long long thr;
-};
-
-// The rows of F_{s+1}: h_{s+1} from the accumulator (which is cleared), x_{s+1},
-// the epilogue terms, and the next step's work items; then x_s is cleared on F_s.
-__global__ void __launch_bounds__(kBlock) probe_sparse_epi_kernel(ProbeSparseEpi a, ProbeEpi epi) {
-    if (probe_dense_at(a.ctl, a.s, a.thr)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned int nf = a.ctl->st[a.s + 1].fcount;
-    unsigned long long nacc = 0ull;
-    for (int64_t r = w0; r < (int64_t)nf; r += nwarps) {
-        const int32_t i = a.Fnext[r];
-        const size_t at = (size_t)i * kProbeW + lane;
-        const unsigned long long H = a.Hn[at];
-        a.Hn[at] = 0ull;
-        const uint32_t d = __ldg(a.in_rp + i + 1) - __ldg(a.in_rp + i);
-        if (lane == 0) {
-            a.mark[i] = 0u;
-            if (!a.last && d) {
-                const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
-                const unsigned int base = atomicAdd(&a.ctl->st[a.s + 1].wcount, nch);
-                for (unsigned int ch = 0; ch < nch; ++ch) a.Wnext[base + ch] = make_int2(i, (int)ch);
-            }
-        }
-        if (a.last) {
-            if (epi.mode == 2) nacc += fx_sq(H);
-        } else {
-            nacc += probe_epilogue(i, H, lane, epi);
-        }
-    }
-    const unsigned int nc = a.ctl->st[a.s].fcount;
-    for (int64_t r = w0; r < (int64_t)nc; r += nwarps) a.Xcur[(size_t)a.Fcur[r] * kProbeW + lane] = 0ull;
-    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
-}
-
-// Block start: x_0 = e_{q'} / din(q') per column, F_0 = the sources, their work items.
-__global__ void probe_sparse_init_kernel(const int32_t* __restrict__ ids, int count, const uint32_t* __restrict__ in_rp,
-                                         unsigned long long* __restrict__ X, int32_t* __restrict__ F, int2* __restrict__ W,
-                                         ProbeCtl* __restrict__ ctl) {
-    const int lane = threadIdx.x;
-    int32_t q = -1;
-    uint32_t d = 0;
-    if (lane < count) {
-        q = ids[lane];
-        d = in_rp[q + 1] - in_rp[q];
-        X[(size_t)q * kProbeW + lane] = d ? kOne / d : 0ull;
-        F[lane] = q;
-    }
-    const unsigned int nch = (d + kPushChunk - 1) / kPushChunk;
-    unsigned int incl = nch;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const unsigned int base = incl - nch;
-    for (unsigned int ch = 0; ch < nch; ++ch) W[base + ch] = make_int2(q, (int)ch);
-    unsigned long long dsum = d;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane == 0) {
-        ctl->st[0].fcount = (unsigned int)(count < 32 ? count : 32);
-        ctl->st[0].wcount = total;
-        ctl->st[0].push = dsum;
-    }
-}
-
-// After a block that went dense: both x buffers are cleared for the next block.
-__global__ void probe_cleanup_kernel(const ProbeCtl* __restrict__ ctl, unsigned long long* __restrict__ Xa,
-                                     unsigned long long* __restrict__ Xb, size_t words) {
-    if (ctl->dense_plus1 == 0) return;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
-        Xa[i] = 0ull;
-        Xb[i] = 0ull;
-    }
-}
-
-// One probe step: h(i, col) = sum_{j in Out(i)} X(j, col), a pull over the out-edge
-// CSR for 32 columns at once.  Short rows: one warp per row, lane = column.  Long
-// rows: one block per 4096-entry segment, each warp adding a contiguous eighth of it
-// into the segment's partial; probe_long_rows_kernel adds a row's partials.
-__global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uint32_t* __restrict__ rp,
-                                                            const int32_t* __restrict__ col,
-                                                            const unsigned long long* __restrict__ X,
-                                                            uint32_t long_min, int64_t nseg,
-                                                            const Segment* __restrict__ seg,
-                                                            unsigned long long* __restrict__ partial, int short_blocks,
-                                                            ProbeEpi epi, ProbeCtl* ctl, int step,
-                                                            unsigned long long thr) {
-    constexpr int kWarps = kBlock / 32;
+    const int b = blockIdx.y;
+    ProbeCtl* ctl = G.ctl + b;
+    if (!probe_dense_at(ctl, a.s, a.thr)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->dense_plus1, 0, a.s + 1);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    if (ctl) {
-        if (!probe_dense_at(ctl, step, thr)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->dense_plus1, 0, step + 1);
-    }
+    const unsigned long long* X = G.X[a.src] + (size_t)b * G.nx;
     if ((int)blockIdx.x >= short_blocks) {
         __shared__ unsigned long long red[kWarps][kProbeW];
+        unsigned long long* partial = G.ppart + (size_t)b * G.np;
         const int64_t nsb = (int64_t)gridDim.x - short_blocks;
         for (int64_t s = (int64_t)blockIdx.x - short_blocks; s < nseg; s += nsb) {  // uniform per block
             const Segment sg = seg[s];
             const uint32_t per = (sg.end - sg.beg + kWarps - 1) / kWarps;
-            uint32_t b = sg.beg + (uint32_t)wib * per;
-            if (b > sg.end) b = sg.end;
-            const uint32_t e = b + per < sg.end ? b + per : sg.end;
-            red[wib][lane] = probe_range(col, X, b, e, lane);
+            uint32_t bb = sg.beg + (uint32_t)wib * per;
+            if (bb > sg.end) bb = sg.end;
+            const uint32_t e = bb + per < sg.end ? bb + per : sg.end;
+            red[wib][lane] = probe_range(col, X, bb, e, lane);
             __syncthreads();
             if (wib == 0) {
                 unsigned long long t = 0ull;
@@ -453,31 +445,54 @@ __global__ void __launch_bounds__(kBlock) probe_rows_kernel(int64_t n, const uin
         }
         return;
     }
+    unsigned long long* Xnext = G.X[a.src ^ 1] + (size_t)b * G.nx;
+    const double* coef = G.coef + (size_t)b * kProbeW;
     unsigned long long nacc = 0ull;
     const int64_t nw = (int64_t)short_blocks * kWarps;
-    for (int64_t row = (int64_t)blockIdx.x * kWarps + wib; row < n; row += nw) {
-        const uint32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
-        if (e - b >= long_min) continue;  // warp-uniform: a long row
-        nacc += probe_epilogue(row, probe_range(col, X, b, e, lane), lane, epi);
+    for (int64_t row = (int64_t)blockIdx.x * kWarps + wib; row < G.n; row += nw) {
+        const uint32_t rb = __ldg(rp + row), re = __ldg(rp + row + 1);
+        if (re - rb >= long_min) continue;  // warp-uniform: a long row
+        nacc += probe_row_out(row, probe_range(col, X, rb, re, lane), lane, a, Xnext, coef);
     }
-    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
+    if (a.mode == 2) probe_flush_colsum(nacc, G.colsum + (size_t)b * kProbeW);
 }
 
-__global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(int64_t nlong, const int32_t* __restrict__ long_rows,
-                                                                 const int32_t* __restrict__ long_first,
-                                                                 const unsigned long long* __restrict__ partial,
-                                                                 ProbeEpi epi, const ProbeCtl* ctl, int step,
-                                                                 unsigned long long thr) {
-    if (ctl && !probe_dense_at(ctl, step, thr)) return;
+__global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(ProbeGroup G, ProbeStepArgs a, int64_t nlong,
+                                                                 const int32_t* __restrict__ long_rows,
+                                                                 const int32_t* __restrict__ long_first) {
+    const int b = blockIdx.y;
+    if (!probe_dense_at(G.ctl + b, a.s, a.thr)) return;
     const int lane = threadIdx.x & 31;
+    const unsigned long long* partial = G.ppart + (size_t)b * G.np;
+    unsigned long long* Xnext = G.X[a.src ^ 1] + (size_t)b * G.nx;
+    const double* coef = G.coef + (size_t)b * kProbeW;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long nacc = 0ull;
     if (w < nlong) {  // warp-uniform
         unsigned long long acc = 0ull;
         for (int32_t s = long_first[w]; s < long_first[w + 1]; ++s) acc += partial[(size_t)s * kProbeW + lane];
-        nacc = probe_epilogue(long_rows[w], acc, lane, epi);
+        nacc = probe_row_out(long_rows[w], acc, lane, a, Xnext, coef);
     }
-    if (epi.mode == 2) probe_flush_colsum(nacc, epi);
+    if (a.mode == 2) probe_flush_colsum(nacc, G.colsum + (size_t)b * kProbeW);
+}
+
+// Group end: zlast += the sum over blocks and columns, in order, of
+// c^{steps} Zv_i(q'_col) colsum(b, col); blocks that went dense clear both x buffers.
+__global__ void probe_end_kernel(ProbeGroup G, const int32_t* __restrict__ ids, int count,
+                                 const double* __restrict__ zv_src, double cl, double* __restrict__ zlast) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < count; ++i) t += (cl * zv_src[ids[i]]) * ((double)G.colsum[i] * kInvOne);
+        *zlast += t;
+    }
+    const int b = blockIdx.y;
+    if (G.ctl[b].dense_plus1 == 0) return;
+    unsigned long long* xa = G.X[0] + (size_t)b * G.nx;
+    unsigned long long* xb = G.X[1] + (size_t)b * G.nx;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < G.nx; i += (size_t)gridDim.x * blockDim.x) {
+        xa[i] = 0ull;
+        xb[i] = 0ull;
+    }
 }
 
 // D^ of Algorithm 3 for exploited nodes (depth > 0), of Algorithm 2 for the others,
@@ -508,9 +523,25 @@ int eblocks(const Graph& g, int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
+size_t witems_of(int64_t n, int64_t m) { return (size_t)n + (size_t)m / kPushChunk + 64; }
+
+// Bytes of one probe block's slices
+size_t probe_block_bytes(int64_t n, int64_t m, int64_t nseg) {
+    const size_t nn = (size_t)n;
+    return 8 * 3 * kProbeW * nn + 4 * 3 * nn + 2 * 8 * witems_of(n, m) +
+           8 * (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1) + sizeof(ProbeCtl) + 8 * 2 * kProbeW + 4096;
+}
+
+int group_size(int64_t n, int64_t m, int64_t nseg) {
+    const size_t per = probe_block_bytes(n, m, nseg);
+    const size_t gmax = kProbeBudget / per;
+    return (int)std::max<size_t>(1, std::min<size_t>(kGroupMax, gmax));
+}
+
 struct A3Ws {
     double* H;        // (D+1) n: h_0 .. h_D from k
     double* Zv;       // (D+1) n: Zv_1 .. Zv_D at rows 1..D (row 0 unused)
+    long long* Zfx;   // (D+1) n: fixed-point probe terms per level
     double* T;        // n: P~ Zv_{j-1}
     double* x;        // n: sweep input
     double* xa;       // n
@@ -518,21 +549,13 @@ struct A3Ws {
     uint64_t* flag;   // n
     uint64_t* off;    // n + 1
     int32_t* ids;     // n
-    unsigned long long* Xa;      // 32 n probe block (fixed point)
-    unsigned long long* Xb;      // 32 n
-    unsigned long long* Hn;      // 32 n push accumulator (zero between steps)
-    uint32_t* mark;              // n (zero between steps)
-    int32_t* F[2];               // frontiers, n each
-    int2* W[2];                  // push work items, n + m/64 + 64 each
-    ProbeCtl* ctl;
-    uint32_t* Ba;                // reach bit sets (32 nodes per word)
+    uint32_t* Ba;     // reach bit sets (32 nodes per word)
     uint32_t* Bb;
-    unsigned long long* rcounts; // (D + 1) x 32 support sizes
-    double* partial;             // kDotBlocks (dot products)
-    unsigned long long* ppart;   // 32 nseg (probe segment partials)
-    double* coef;                // 32
-    unsigned long long* colsum;  // 32
-    double* sums;                // 64: [j] = sum_q Zv_j(q); [63] = the last level's probe terms
+    unsigned long long* rcounts;  // (D + 1) x 32 support sizes
+    double* partial;  // kDotBlocks (dot products)
+    double* sums;     // 64: [j] = sum_q Zv_j(q); [63] = the last level's probe terms
+    ProbeGroup G;
+    int group;        // probe blocks per launch
 };
 
 size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
@@ -547,6 +570,7 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     A3Ws w{};
     w.H = (double*)take(8 * (D + 1) * n);
     w.Zv = (double*)take(8 * (D + 1) * n);
+    w.Zfx = (long long*)take(8 * (D + 1) * n);
     w.T = (double*)take(8 * n);
     w.x = (double*)take(8 * n);
     w.xa = (double*)take(8 * n);
@@ -554,24 +578,31 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     w.flag = (uint64_t*)take(8 * n);
     w.off = (uint64_t*)take(8 * (n + 1));
     w.ids = (int32_t*)take(4 * n);
-    w.Xa = (unsigned long long*)take(8 * kProbeW * n);
-    w.Xb = (unsigned long long*)take(8 * kProbeW * n);
-    w.Hn = (unsigned long long*)take(8 * kProbeW * n);
-    w.mark = (uint32_t*)take(4 * n);
-    const size_t witems = n + (size_t)m_ / kPushChunk + 64;
-    for (int b = 0; b < 2; ++b) {
-        w.F[b] = (int32_t*)take(4 * n);
-        w.W[b] = (int2*)take(8 * witems);
-    }
-    w.ctl = (ProbeCtl*)take(sizeof(ProbeCtl));
     w.Ba = (uint32_t*)take(4 * n);
     w.Bb = (uint32_t*)take(4 * n);
-    w.rcounts = (unsigned long long*)take(8 * 32 * (size_t)(kAlg3MaxDepth + 1));
+    w.rcounts = (unsigned long long*)take(8 * 32 * (D + 1));
     w.partial = (double*)take(8 * kDotBlocks);
-    w.ppart = (unsigned long long*)take(8 * (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1));
-    w.coef = (double*)take(8 * kProbeW);
-    w.colsum = (unsigned long long*)take(8 * kProbeW);
     w.sums = (double*)take(8 * 64);
+    const int G = group_size(n_, m_, nseg);
+    const size_t gz = (size_t)G;
+    w.group = G;
+    ProbeGroup& P = w.G;
+    P.n = n_;
+    P.nx = (size_t)kProbeW * n;
+    P.nw = witems_of(n_, m_);
+    P.np = (size_t)kProbeW * (size_t)std::max<int64_t>(nseg, 1);
+    P.X[0] = (unsigned long long*)take(8 * P.nx * gz);
+    P.X[1] = (unsigned long long*)take(8 * P.nx * gz);
+    P.Hn = (unsigned long long*)take(8 * P.nx * gz);
+    P.mark = (uint32_t*)take(4 * n * gz);
+    for (int b = 0; b < 2; ++b) {
+        P.F[b] = (int32_t*)take(4 * n * gz);
+        P.W[b] = (int2*)take(8 * P.nw * gz);
+    }
+    P.ppart = (unsigned long long*)take(8 * P.np * gz);
+    P.ctl = (ProbeCtl*)take(sizeof(ProbeCtl) * gz);
+    P.coef = (double*)take(8 * kProbeW * gz);
+    P.colsum = (unsigned long long*)take(8 * kProbeW * gz);
     if (out) *out = w;
     return o;
 }
@@ -583,29 +614,34 @@ cudaError_t dsum(const Graph& g, const double* a, int kind, const A3Ws& ws, doub
     return cudaGetLastError();
 }
 
-// One probe step for the block: X_prev -> h (epilogue: X_next, accumulation).
-cudaError_t probe_step(const Graph& g, const unsigned long long* X_prev, const ProbeEpi& epi,
-                       unsigned long long* partial, int* count, ProbeCtl* ctl, int step, unsigned long long thr) {
+// One probe step for a group of nb blocks: push, dense pull (whichever the counters
+// pick), sparse epilogue.
+cudaError_t probe_step(const Graph& g, const A3Ws& ws, const ProbeStepArgs& a, int nb, int* count) {
     const DevCsr& A = g.out;
+    const unsigned sparse_blocks = (unsigned)std::max(1, g.sm_count * 4 / nb);
+    probe_push_kernel<<<dim3(sparse_blocks, (unsigned)nb), kBlock, 0, g.stream>>>(ws.G, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const int wpb = kBlock / 32;
     int64_t sb = (g.n + wpb - 1) / wpb;
     if (sb > (int64_t)g.sm_count * 16) sb = (int64_t)g.sm_count * 16;
     if (sb < 1) sb = 1;
     int64_t segb = A.nseg;  // one block per segment
     if (segb > (int64_t)g.sm_count * 8) segb = (int64_t)g.sm_count * 8;
-    probe_rows_kernel<<<(unsigned)(sb + segb), kBlock, 0, g.stream>>>(g.n, A.rp, A.col, X_prev, A.long_min, A.nseg,
-                                                                       A.seg, partial, (int)sb, epi, ctl, step, thr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    ++*count;
+    probe_rows_kernel<<<dim3((unsigned)(sb + segb), (unsigned)nb), kBlock, 0, g.stream>>>(
+        ws.G, a, A.rp, A.col, A.long_min, A.nseg, A.seg, (int)sb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *count += 2;
     if (A.nlong > 0) {
         const int64_t blocks = (A.nlong * 32 + kBlock - 1) / kBlock;
-        probe_long_rows_kernel<<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.nlong, A.long_rows, A.long_first, partial,
-                                                                          epi, ctl, step, thr);
-        e = cudaGetLastError();
+        probe_long_rows_kernel<<<dim3((unsigned)blocks, (unsigned)nb), kBlock, 0, g.stream>>>(ws.G, a, A.nlong,
+                                                                                              A.long_rows, A.long_first);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*count;
     }
-    return e;
+    probe_sparse_epi_kernel<<<dim3(sparse_blocks, (unsigned)nb), kBlock, 0, g.stream>>>(ws.G, a);
+    ++*count;
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -663,18 +699,20 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     cudaError_t e = launch_walk_distributions(g, k, depth, ws.H, ws.xa, ws.xb);
     if (e != cudaSuccess) return e;
     count += 1 + depth * per_sweep;
-    if ((e = cudaMemsetAsync(ws.Zv, 0, sizeof(double) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.Zfx, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess)
+        return e;
     if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ws.colsum, 0, sizeof(unsigned long long) * kProbeW, g.stream)) != cudaSuccess) return e;
-    if (depth >= 3) {  // the probe blocks, accumulator and marks start (and each block ends) all zero
-        if ((e = cudaMemsetAsync(ws.Xa, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.Xb, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.Hn, 0, sizeof(unsigned long long) * kProbeW * n, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.mark, 0, sizeof(uint32_t) * n, g.stream)) != cudaSuccess)
+    if (depth >= 3) {  // the probe buffers start (and each group ends) all zero
+        const size_t gz = (size_t)ws.group;
+        if ((e = cudaMemsetAsync(ws.G.X[0], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.G.X[1], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.G.Hn, 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ws.G.mark, 0, 4 * n * gz, g.stream)) != cudaSuccess)
             return e;
     }
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
+    const unsigned long long thr = (unsigned long long)(g.m + g.n) / 4;
     for (int j = 1; j <= depth; ++j) {
         double* zv = ws.Zv + (size_t)j * n;
         const double* T = nullptr;
@@ -685,67 +723,53 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             count += 1 + per_sweep;
             T = ws.T;
         }
-        zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cpow[(size_t)j], c, ws.H + (size_t)j * n, T, zv);
+        zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cpow[(size_t)j], c, ws.H + (size_t)j * n, T,
+                                                        ws.Zfx + (size_t)j * n, zv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++count;
         if ((e = dsum(g, zv, 2, ws, ws.sums + j, &count)) != cudaSuccess) return e;
-        // probes from the support of h_j feed the levels j+2 .. depth: the vector Zv of
-        // a level below depth, only the sum for the last level
-        if (j <= depth - 2) {
-            flag_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)j * n, ws.flag);
+        // probes from the support of h_j feed the levels j+2 .. depth: the row terms of a
+        // level below depth, only the column sums for the last level
+        if (j > depth - 2) continue;
+        flag_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)j * n, ws.flag);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_scan_R(g, g.n, ws.flag, ws.off, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n))) !=
+            cudaSuccess)
+            return e;
+        scatter_ids_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.flag, ws.off, ws.ids);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count += 5;
+        uint64_t nsup = 0;
+        if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
+        const int steps = depth - j;
+        const uint64_t per_group = (uint64_t)kProbeW * (uint64_t)ws.group;
+        for (uint64_t g0 = 0; g0 < nsup; g0 += per_group) {
+            const int cnt = (int)std::min<uint64_t>(per_group, nsup - g0);
+            const int nb = (cnt + kProbeW - 1) / kProbeW;
+            const int32_t* ids = ws.ids + g0;
+            probe_init_kernel<<<dim3(1, (unsigned)nb), kProbeW, 0, g.stream>>>(ws.G, ids, cnt, g.in.rp);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = launch_scan_R(g, g.n, ws.flag, ws.off, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n))) !=
-                cudaSuccess)
-                return e;
-            scatter_ids_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.flag, ws.off, ws.ids);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            count += 5;
-            uint64_t nsup = 0;
-            if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) !=
-                cudaSuccess)
-                return e;
-            if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-            const int steps = depth - j;
-            const unsigned long long thr = (unsigned long long)(g.m + g.n) / 4;
-            const unsigned sparse_blocks = (unsigned)g.sm_count * 4;
-            for (uint64_t b0 = 0; b0 < nsup; b0 += kProbeW) {
-                const int cnt = (int)std::min<uint64_t>(kProbeW, nsup - b0);
-                const int32_t* ids = ws.ids + b0;
-                if ((e = cudaMemsetAsync(ws.ctl, 0, sizeof(ProbeCtl), g.stream)) != cudaSuccess) return e;
-                probe_sparse_init_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, g.in.rp, ws.Xa, ws.F[0], ws.W[0], ws.ctl);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                ++count;
-                unsigned long long* X[2] = {ws.Xa, ws.Xb};
-                for (int lp = 1; lp <= steps; ++lp) {
-                    const int st = lp - 1;
-                    ProbeEpi epi{g.in.rp, X[lp & 1], 0, nullptr, ws.Zv + (size_t)(j + lp) * n, ws.colsum};
-                    if (lp == steps) {
-                        epi.mode = 2;
-                    } else if (lp >= 2) {
-                        probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)lp], ws.coef);
-                        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                        ++count;
-                        epi.mode = 1;
-                        epi.coef = ws.coef;
-                    }
-                    const ProbePush push{g.in.rp, g.in.col, X[st & 1], ws.Hn, ws.mark, ws.W[st & 1],
-                                         ws.F[(st + 1) & 1], ws.ctl, st, thr};
-                    probe_push_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(push);
+            ++count;
+            for (int lp = 1; lp <= steps; ++lp) {
+                ProbeStepArgs a{g.in.rp, g.in.col, lp - 1, (lp - 1) & 1, 0, lp == steps ? 1 : 0,
+                                ws.Zfx + (size_t)(j + lp) * n, thr};
+                if (lp == steps) {
+                    a.mode = 2;
+                } else if (lp >= 2) {
+                    probe_coef_kernel<<<dim3(1, (unsigned)nb), kProbeW, 0, g.stream>>>(ws.G, ids, cnt, zv,
+                                                                                       cpow[(size_t)lp]);
                     if ((e = cudaGetLastError()) != cudaSuccess) return e;
                     ++count;
-                    if ((e = probe_step(g, X[st & 1], epi, ws.ppart, &count, ws.ctl, st, thr)) != cudaSuccess) return e;
-                    const ProbeSparseEpi se{g.in.rp, ws.Hn, ws.mark, ws.F[(st + 1) & 1], ws.F[st & 1], X[st & 1],
-                                            ws.W[(st + 1) & 1], ws.ctl, st, lp == steps ? 1 : 0, thr};
-                    probe_sparse_epi_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(se, epi);
-                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                    ++count;
+                    a.mode = 1;
                 }
-                probe_cleanup_kernel<<<sparse_blocks, kBlock, 0, g.stream>>>(ws.ctl, ws.Xa, ws.Xb, (size_t)kProbeW * n);
-                probe_coef_kernel<<<1, kProbeW, 0, g.stream>>>(ids, cnt, zv, cpow[(size_t)steps], ws.coef);
-                probe_norm_finish_kernel<<<1, kProbeW, 0, g.stream>>>(ws.coef, ws.colsum, ws.sums + 63);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                count += 3;
+                if ((e = probe_step(g, ws, a, nb, &count)) != cudaSuccess) return e;
             }
+            probe_end_kernel<<<dim3((unsigned)g.sm_count, (unsigned)nb), kBlock, 0, g.stream>>>(
+                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++count;
         }
     }
     double sums[64] = {};
