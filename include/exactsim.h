@@ -162,7 +162,7 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_max_depth" deepest exploitation, 1..16 (default 8)
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the depth's cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per
- *                    entry and column of a 32-column probe sweep (0.5), per kernel launch
+ *                    entry and column of a 32-column probe sweep (0.2), per kernel launch
  *                    (2^19).  The estimate of depth d is R_d (d + 1/(1-c)) walks plus
  *                    w_sweep (m+n)(2d-1) + w_probe (m+n) sum_{i<=d-2} |supp h_i|(d-i) +
  *                    w_launch (3(2d-1) + sum_i ceil(|supp h_i|/32)(3(d-i)+2))

@@ -93,7 +93,7 @@ def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, dep
     return out
 
 
-def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int, w_sweep: float = 4.0, w_probe: float = 0.5,
+def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int, w_sweep: float = 4.0, w_probe: float = 0.2,
                  w_launch: float = 524288.0) -> float:
     """Estimated GPU work (in sampler pair-steps) of exploiting a node to depth d.
 
@@ -128,7 +128,7 @@ def supports(P, k: int, levels: int) -> list[int]:
 
 def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 8,
                       min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None,
-                      weights: tuple = (4.0, 0.5, 524288.0)):
+                      weights: tuple = (4.0, 0.2, 524288.0)):
     """(depth uint8[n], R uint64[n]) of Algorithm 3 with the cost-minimising depth.
 
     Candidates: the max_nodes largest pi(k) (ties to the lower id) with pi(k) > 0,

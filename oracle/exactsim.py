@@ -38,7 +38,7 @@ class QueryResult:
 def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
           kappa: float | None = None, mode: str = "pi2", threads: int = 0, alg3: bool = False,
           alg3_max_depth: int = 8, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64,
-          sparse: bool = False, diag: str = "estimated", alg3_weights: tuple = (4.0, 0.5, 524288.0)) -> QueryResult:
+          sparse: bool = False, diag: str = "estimated", alg3_weights: tuple = (4.0, 0.2, 524288.0)) -> QueryResult:
     """One single-source query.  ``sparse``: sparse Linearization (Sec. 3.2) -- the
     query runs at eps/2 and the reverse loop reads the history with entries at or
     below (1 - sqrt(c))^2 eps/2 dropped (pi for the allocation is the full sum).

@@ -87,7 +87,7 @@ struct Graph {
     int alg3_max_nodes = 64;
     // Algorithm 3's cost model (pair-steps per sweep entry, per probe entry and column, per launch)
     double alg3_w_sweep = 4.0;
-    double alg3_w_probe = 0.5;
+    double alg3_w_probe = 0.2;
     double alg3_w_launch = 524288.0;
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
