@@ -128,13 +128,13 @@ def supports(P, k: int, levels: int) -> list[int]:
 
 def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 8,
                       min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None,
-                      weights: tuple = (4.0, 0.2, 524288.0)):
+                      weights: tuple = (4.0, 0.2, 524288.0), mode: str = "pi2"):
     """(depth uint8[n], R uint64[n]) of Algorithm 3 with the cost-minimising depth.
 
     Candidates: the max_nodes largest pi(k) (ties to the lower id) with pi(k) > 0,
-    din(k) >= 2 and an Algorithm 2 count max(1, ceil(R_b pi(k)^2)) >= min_pairs.  Each
-    takes the depth d in 0..max_depth of least ``exploit_cost`` (the first on ties);
-    d > 0 gives R(k) = max(1, ceil(R_b pi(k)^2 c^(2d))).  Nodes with din <= 1 take the
+    din(k) >= 2 and an Algorithm 2 count max(1, ceil(v)) >= min_pairs, v = R_b pi(k)^2
+    (R_b pi(k) for the basic allocation).  Each takes the depth d in 0..max_depth of
+    least ``exploit_cost`` (the first on ties); d > 0 gives R(k) = max(1, ceil(v c^(2d))).  Nodes with din <= 1 take the
     exact D and no samples.  ``stats["min_gap"]`` (if given) receives the smallest
     relative gap between a chosen cost and another depth's cost: the margin of the
     floating-point depth decisions.
@@ -144,7 +144,7 @@ def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: 
     m = int(np.asarray(in_rowptr)[-1])
     P = transition_matrix(n, in_rowptr, in_col)
     pi = np.asarray(pi, dtype=np.float64)
-    R = np.ceil(R_b * (pi * pi)).astype(np.uint64)
+    R = np.ceil(R_b * (pi * pi) if mode == "pi2" else R_b * pi).astype(np.uint64)
     R[(pi > 0) & (R == 0)] = 1
     depth = np.zeros(n, dtype=np.uint8)
     R[din <= 1] = 0  # exact D for din 0 and 1
@@ -155,7 +155,7 @@ def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: 
             break
         if din[kk] < 2:
             continue
-        v = R_b * (pi[kk] * pi[kk])
+        v = R_b * (pi[kk] * pi[kk]) if mode == "pi2" else R_b * pi[kk]
         if max(1.0, float(math.ceil(v))) < min_pairs:
             continue
         supp = supports(P, kk, max(0, max_depth - 2))

@@ -64,7 +64,7 @@ def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0
     # Algorithm 3 for the heaviest nodes (pi^2 allocation)
     plan = {}
     depth, R = a3.exploitation_plan(n, in_rowptr, in_col, pi, R_b, c, alg3_max_depth, alg3_min_pairs,
-                                    alg3_max_nodes, stats=plan, weights=alg3_weights)
+                                    alg3_max_nodes, stats=plan, weights=alg3_weights, mode=mode)
     zsum = np.zeros(n)
     for k in np.nonzero(depth)[0]:
         zsum[k] = sum(a3.first_meeting_lemma5(n, in_rowptr, in_col, int(k), c, int(depth[k])))

@@ -219,3 +219,34 @@ def test_alg3_rejects_repeated_in_edges(esim):
         g.alg3_first_meeting(2, 2, C)
     assert e.value.status == -6
     g.close()
+
+
+def test_alg3_with_basic_allocation_and_fp32c(esim, oracle_walks):
+    from oracle import exactsim
+    n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
+    g = esim.Graph(n, rp, col, alloc=1, alg3=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6)
+    eps = 2e-2
+    checked = 0
+    for u, seed in ((5, 1), (1234, 2), (2999, 3)):
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, mode="basic", alg3=True, alg3_max_depth=6,
+                           alg3_min_pairs=1e3, alg3_max_nodes=16)
+        v = q.R_b * q.pi
+        vv = np.concatenate([v, v * C ** (2.0 * q.depth)])
+        frac = np.abs(vv - np.round(vv))
+        if not np.all((frac > 1e-12 * vv) | (vv == 0)) or q.plan_gap <= 1e-9:
+            continue
+        s = g.query(u, C, eps, seed)
+        st = g.stats()
+        assert st["alg3_nodes"] == int(np.count_nonzero(q.depth)) > 0
+        assert st["sum_R"] == int(q.R.sum()) and st["pair_steps"] == q.pair_steps
+        assert np.max(np.abs(s - q.s)) <= TOL
+        checked += 1
+    assert checked >= 2
+    # FP32c precision with Algorithm 3: same pairs and D^ decisions as FP64 up to FP32 pi,
+    # scores within the precision form's bound of FP64
+    g.set_option("alloc", 0)
+    s64 = g.query(5, C, 1e-3, 4)
+    g.set_option("precision", 1)
+    s32 = g.query(5, C, 1e-3, 4)
+    assert np.max(np.abs(s32 - s64)) < 1e-4
+    g.close()
