@@ -733,8 +733,8 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         if (j > depth - 2) continue;
         flag_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.H + (size_t)j * n, ws.flag);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_scan_R(g, g.n, ws.flag, ws.off, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n))) !=
-            cudaSuccess)
+        if ((e = launch_scan_R(g, g.n, ws.flag, ws.off, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n),
+                               false)) != cudaSuccess)
             return e;
         scatter_ids_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.flag, ws.off, ws.ids);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -92,6 +92,7 @@ struct Graph {
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
+    uint64_t* samp_w = nullptr;   // 2n+1: weighted pair shares of the sampler (Algorithm 3 depths)
     size_t a3ws_bytes = 0;
     int32_t last_alg3_nodes = 0;
     uint64_t last_hist_entries = 0;
@@ -155,8 +156,9 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
                                    int shared_B = 0, const uint64_t* rbase = nullptr);
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
                                  double* dhat);
+// record = false: an auxiliary scan that leaves the status block (sum of R, budget) alone
 cudaError_t launch_scan_R(const Graph& g, int64_t N, const uint64_t* R, uint64_t* off, unsigned long long* part_R,
-                          double* part_norm, double* part_Rd);
+                          double* part_norm, double* part_Rd, bool record = true);
 uint32_t walk_threshold(double c);
 
 // capi.cu: record a message for esim_last_error() and return `status` (as an esim_status int)
