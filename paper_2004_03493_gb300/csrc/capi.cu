@@ -120,7 +120,6 @@ void release(Graph& g) {
     cudaFree(g.ws);
     cudaFree(g.bws);
     cudaFree(g.a3ws);
-    cudaFree(g.samp_w);
     cudaFree(g.partial);
     cudaFree(g.scan_part);
     cudaFree(g.norm_part);
@@ -251,13 +250,6 @@ esim_status check_graph(const esim_graph* h) {
 }
 
 esim_status ensure_a3ws(Graph& g) {
-    if (!g.samp_w) {
-        if (cudaMalloc(&g.samp_w, sizeof(uint64_t) * (size_t)(2 * g.n + 1)) != cudaSuccess) {
-            cudaGetLastError();
-            g.samp_w = nullptr;
-            return fail(ESIM_ENOMEM, "cudaMalloc(sampler shares)");
-        }
-    }
     const size_t need = alg3_workspace_bytes(g);
     if (g.a3ws && g.a3ws_bytes >= need) return ESIM_OK;
     cudaStreamSynchronize(g.stream);

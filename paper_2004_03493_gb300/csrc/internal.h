@@ -92,7 +92,6 @@ struct Graph {
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
-    uint64_t* samp_w = nullptr;   // 2n+1: weighted pair shares of the sampler (Algorithm 3 depths)
     size_t a3ws_bytes = 0;
     int32_t last_alg3_nodes = 0;
     uint64_t last_hist_entries = 0;

@@ -327,30 +327,6 @@ __device__ __forceinline__ void pair_step(PairState& S, const uint2* __restrict_
     }
 }
 
-// Expected pair-steps of one pair of a node of Algorithm 3 depth d, in half-steps: the
-// d forced steps and about 1/(1-c) = 2.5 more (d = 0: Algorithm 2).  Only the balance of
-// the threads' shares depends on it, never a result.
-__device__ __forceinline__ unsigned long long pair_weight(unsigned d) { return 2ull * d + 5ull; }
-
-// Global pair index at weighted position u (offw: exclusive scan of R(k) pair_weight(d(k))).
-__device__ __forceinline__ unsigned long long weighted_to_pair(unsigned long long u, const uint64_t* __restrict__ offw,
-                                                               const uint64_t* __restrict__ off, int64_t nseg,
-                                                               const uint8_t* __restrict__ depth) {
-    if (u >= offw[nseg]) return off[nseg];
-    int64_t lo = 0, hi = nseg;  // offw[lo] <= u < offw[lo+1]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(offw + mid) <= u) lo = mid; else hi = mid;
-    }
-    return __ldg(off + lo) + (u - __ldg(offw + lo)) / pair_weight(depth[lo]);
-}
-
-__global__ void pair_weight_kernel(int64_t n, const uint64_t* __restrict__ off, const uint8_t* __restrict__ depth,
-                                   uint64_t* __restrict__ rw) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        rw[k] = (off[k + 1] - off[k]) * pair_weight(depth[k]);
-}
-
 // Persistent walk-pair sampler.  Thread t takes a contiguous run of global pair
 // indices (about total / #threads of them) and advances its current pair by one
 // step per loop iteration, so a lane whose pair ended starts its next pair at
@@ -364,8 +340,7 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
                                                                  unsigned long long* __restrict__ steps_out,
                                                                  Status* __restrict__ st,
                                                                  const uint8_t* __restrict__ depth,
-                                                                 const SharedSegs sh,
-                                                                 const uint64_t* __restrict__ offw) {
+                                                                 const SharedSegs sh) {
     __shared__ unsigned long long red[kBlock / 32];
     const unsigned long long total = off[nseg];
     if ((double)total > budget || (st->err & kErrBudget)) {
@@ -374,19 +349,9 @@ __global__ void __launch_bounds__(kBlock, 6) sample_pairs_kernel(int64_t n, int6
     }
     const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long g0, g1;
-    if (offw) {  // equal shares of the expected pair-steps rather than of the pairs
-        const unsigned long long tw = offw[nseg];
-        const unsigned long long perw = tw / nthreads, remw = tw % nthreads;
-        const unsigned long long u0 = tid * perw + (tid < remw ? tid : remw);
-        const unsigned long long u1 = u0 + perw + (tid < remw ? 1ull : 0ull);
-        g0 = weighted_to_pair(u0, offw, off, nseg, depth);
-        g1 = weighted_to_pair(u1, offw, off, nseg, depth);
-    } else {
-        const unsigned long long per = total / nthreads, rem = total % nthreads;
-        g0 = tid * per + (tid < rem ? tid : rem);
-        g1 = g0 + per + (tid < rem ? 1ull : 0ull);
-    }
+    const unsigned long long per = total / nthreads, rem = total % nthreads;
+    const unsigned long long g0 = tid * per + (tid < rem ? tid : rem);
+    const unsigned long long g1 = g0 + per + (tid < rem ? 1ull : 0ull);
     PairState S;
     S.left = g1 - g0;
     S.g_end = g1;
@@ -452,23 +417,10 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
         g_sample_blocks_per_sm = b > 0 ? b : 1;
     }
     const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
-    // with Algorithm 3 depths the threads take equal shares of the expected pair-steps
-    const uint64_t* offw = nullptr;
-    if (depth && !rbase && nseg == g.n && g.samp_w) {
-        uint64_t* rw = g.samp_w;
-        uint64_t* ow = g.samp_w + g.n;
-        int64_t b = (g.n + kBlock - 1) / kBlock;
-        if (b > (int64_t)g.sm_count * 8) b = (int64_t)g.sm_count * 8;
-        pair_weight_kernel<<<(unsigned)b, kBlock, 0, g.stream>>>(g.n, off, depth, rw);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int64_t nb = allocate_blocks(g.n);
-        if ((e = launch_scan_R(g, g.n, rw, ow, g.scan_part, nullptr, g.norm_part + nb, false)) != cudaSuccess) return e;
-        offw = ow;
-    }
     sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, nseg, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
                                                          (unsigned long long*)nonmeet, steps, g.status, depth,
-                                                         SharedSegs{rbase ? shared_B : 0, rbase}, offw);
+                                                         SharedSegs{rbase ? shared_B : 0, rbase});
     return cudaGetLastError();
 }
 
