@@ -127,6 +127,12 @@ void release(Graph& g) {
     for (auto& ev : g.ev)
         if (ev) cudaEventDestroy(ev);
     if (g.own_stream) cudaStreamDestroy(g.own_stream);
+    if (g.side_stream) {
+        cudaStreamSynchronize(g.side_stream);
+        cudaStreamDestroy(g.side_stream);
+    }
+    for (auto& ev : g.side_ev)
+        if (ev) cudaEventDestroy(ev);
     g = Graph{};
 }
 
@@ -161,6 +167,12 @@ struct Ws {
     double* s;         // n
     uint8_t* depth;    // n  Algorithm 3 depth per node (0: Algorithm 2)
     double* zsum;      // n  Algorithm 3: sum of the exact Z_l(k)
+    uint8_t* cand;     // n  Algorithm 3 candidates (their walks wait for the plan)
+    uint64_t* R2;      // n  R of the other nodes, then of the candidates
+    uint64_t* off2;    // n+1  offsets of the other nodes' walks (read by the side stream)
+    uint64_t* offc;    // n+1  offsets of the candidates' walks
+    uint64_t* nm2;     // n  counts of the other nodes
+    int32_t* cand_ids; // 4096
     // sparse linearization (FP64): rolling pi^l, the running pi, the kept entries
     double* lev;       // n
     double* pirun;     // n
@@ -215,6 +227,12 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
     t.s = (double*)take(8 * n);
     t.depth = (uint8_t*)take(n);
     t.zsum = (double*)take(8 * n);
+    t.cand = (uint8_t*)take(n);
+    t.R2 = (uint64_t*)take(8 * n);
+    t.off2 = (uint64_t*)take(8 * (n + 1));
+    t.offc = (uint64_t*)take(8 * (n + 1));
+    t.nm2 = (uint64_t*)take(8 * n);
+    t.cand_ids = (int32_t*)take(4 * 4096);
     if (precision == 0 && sparse_cap > 0) {
         // last, so that the layout for a smaller capacity is a prefix of this one
         t.sh.lvl = (uint64_t*)take(8 * (size_t)(L + 2));
@@ -298,7 +316,31 @@ double alg3_cost(const Graph& g, int d, double v, double c, const uint64_t* supp
 // max(1, ceil(R_b pi(k)^2 c^(2d))) (pi(k) for the basic allocation): the tail
 // estimator's variance and range are c^(2d) and c^d of Algorithm 2's.  Nodes with
 // din <= 1 already got no pairs from the allocation.  Then the offsets are rescanned.
-esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches) {
+// Starts, on the side stream, the walks of every node that is not an Algorithm 3
+// candidate: their R(k) is final, and the walk spec keys a pair by (seed, k, r), so
+// splitting the nodes between two sampler launches changes no count.  The side
+// sampler takes two thirds of each SM, leaving room for the planning's kernels.
+esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& cand, double c, uint64_t seed,
+                             int* launches) {
+    ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand_ids, cand.data(), sizeof(int32_t) * cand.size(), cudaMemcpyHostToDevice,
+                                  g.stream), "upload candidates");
+    ESIM_CUDA_TRY(launch_mark(g, w.cand_ids, (int)cand.size(), w.cand), "mark candidates");
+    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 0, w.R2), "other nodes' R");
+    const int64_t nb = allocate_blocks(g.n);
+    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.off2, g.scan_part, nullptr, g.norm_part + nb, false), "other nodes' scan");
+    ESIM_CUDA_TRY(cudaEventRecord(g.side_ev[0], g.stream), "record");
+    ESIM_CUDA_TRY(cudaStreamWaitEvent(g.side_stream, g.side_ev[0], 0), "side wait");
+    Graph view = g;
+    view.stream = g.side_stream;
+    view.sample_block_cap = 4;
+    ESIM_CUDA_TRY(launch_sample(view, w.off2, c, seed, w.nm2, nullptr, nullptr), "other nodes' walk pairs");
+    ESIM_CUDA_TRY(cudaEventRecord(g.side_ev[1], g.side_stream), "record");
+    *launches += 6;
+    return ESIM_OK;
+}
+
+esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches, uint64_t seed, bool* side) {
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
     esim_status a3 = ensure_a3ws(g);
     if (a3 != ESIM_OK) return a3;
@@ -331,6 +373,16 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         if (r0 < g.alg3_min_pairs) continue;
         cand.push_back(kk);
         cand_v.push_back(v);
+    }
+    // The budget applies to the pairs actually drawn: drop the verdict on the
+    // Algorithm 2 counts (no other error can be raised before the walks); the side
+    // sampler judges the other nodes' pairs and the rescan below all of them.
+    ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
+    *side = false;
+    if (!cand.empty() && g.side_stream) {
+        esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
+        if (ss != ESIM_OK) return ss;
+        *side = true;
     }
     const int levels = std::max(0, g.alg3_max_depth - 2);
     std::vector<uint64_t> supps(cand.size() * (kAlg3MaxDepth + 1), 0);
@@ -367,10 +419,6 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         ++used;
     }
     g.last_alg3_nodes = used;
-    // The budget applies to the pairs actually drawn: drop the verdict on the
-    // Algorithm 2 counts (no other error can be raised before the walks) and let
-    // the rescan judge the new ones.
-    ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
     const int64_t nb = allocate_blocks(g.n);
     ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R, w.off, g.scan_part, nullptr, g.norm_part + nb), "Algorithm 3 rescan");
     *launches += 3;
@@ -443,12 +491,29 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
         else
             ESIM_CUDA_TRY(launch_allocate32(g, w.hist32, L, R_b, g.alloc_mode, w.pi, w.R, w.off),
                           "allocation (FP32c)");
+        bool side = false;
         if (g.alg3) {
-            esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches);
-            if (a3 != ESIM_OK) return a3;
+            esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches, seed, &side);
+            if (a3 != ESIM_OK) {
+                if (side) cudaStreamSynchronize(g.side_stream);  // no walks left running into the next query
+                return a3;
+            }
         }
         if (g.timing) cudaEventRecord(g.ev[2], g.stream);
-        ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr), "walk pairs");
+        if (side) {
+            // the candidates' walks here; the other nodes' counts come from the side stream
+            ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 1, w.R2), "candidates' R");
+            ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.offc, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n),
+                                        false),
+                          "candidates' scan");
+            ESIM_CUDA_TRY(launch_sample(g, w.offc, c, seed, w.nonmeet, nullptr, w.depth), "candidates' walk pairs");
+            ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.side_ev[1], 0), "wait for the other nodes' walks");
+            ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nonmeet), "merge counts");
+            extra_launches += 5;
+        } else {
+            ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr),
+                          "walk pairs");
+        }
         if (g.timing) cudaEventRecord(g.ev[3], g.stream);
         if (g.alg3)
             ESIM_CUDA_TRY(launch_dhat_alg3(g, w.nonmeet, w.off, w.depth, w.zsum, c, w.dhat), "dhat (Algorithm 3)");
@@ -900,7 +965,10 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
               dev_alloc(&g.partial, npart) == cudaSuccess && dev_alloc(&g.scan_part, (size_t)nb) == cudaSuccess &&
               dev_alloc(&g.norm_part, 2 * (size_t)nb) == cudaSuccess &&
               cudaMalloc(&g.topk_ws, topk_stage_offset(n) + (sizeof(double) + sizeof(int32_t)) * kTopkMax) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&g.side_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g.side_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g.side_ev[1], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(g);

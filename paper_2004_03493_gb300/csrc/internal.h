@@ -71,6 +71,9 @@ struct Graph {
     double* inv_din = nullptr;  // n: 1/din(i) (0 where din = 0), for the FP64 sweeps
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // Algorithm 3: walks of the other nodes during the planning
+    cudaEvent_t side_ev[2] = {};
+    int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     // options
     double kappa = 0.0;
     int alloc_mode = 0;
@@ -148,6 +151,12 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
                           uint64_t* pair_steps, const uint8_t* depth = nullptr);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
 cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out);
+// R_out(k) = R(k) where keep(k) == want, else 0
+cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want, uint64_t* R_out);
+// counts(k) = side(k) where cand(k) == 0
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts);
+// cand(k) = 1 for the listed nodes
+cudaError_t launch_mark(const Graph& g, const int32_t* ids, int count, uint8_t* mark);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
 // shared_B > 0 with rbase: segment s covers pairs [rbase[s], rbase[s] + len) of node s / shared_B
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,

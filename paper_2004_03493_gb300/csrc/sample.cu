@@ -393,6 +393,43 @@ __global__ void fill_kernel(int64_t n, double value, double* __restrict__ out) {
         out[k] = value;
 }
 
+__global__ void mask_R_kernel(int64_t n, const uint64_t* __restrict__ R, const uint8_t* __restrict__ keep,
+                              uint8_t want, uint64_t* __restrict__ R_out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        R_out[k] = keep[k] == want ? R[k] : 0ull;
+}
+
+__global__ void merge_counts_kernel(int64_t n, const uint8_t* __restrict__ cand, const uint64_t* __restrict__ side,
+                                    uint64_t* __restrict__ counts) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (!cand[k]) counts[k] = side[k];
+}
+
+__global__ void mark_kernel(const int32_t* __restrict__ ids, int count, uint8_t* __restrict__ mark) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) mark[ids[i]] = 1u;
+}
+
+static int eb_cap(const Graph& g, int64_t n) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    if (b > (int64_t)g.sm_count * 8) b = (int64_t)g.sm_count * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want, uint64_t* R_out) {
+    mask_R_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, R, keep, want, R_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts) {
+    merge_counts_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, cand, side, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark(const Graph& g, const int32_t* ids, int count, uint8_t* mark) {
+    mark_kernel<<<1, kBlock, 0, g.stream>>>(ids, count, mark);
+    return cudaGetLastError();
+}
+
 static int g_sample_blocks_per_sm = 0;
 
 cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
@@ -416,7 +453,9 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
         if (e != cudaSuccess) return e;
         g_sample_blocks_per_sm = b > 0 ? b : 1;
     }
-    const unsigned blocks = (unsigned)(g.sm_count * g_sample_blocks_per_sm);
+    const int per_sm = g.sample_block_cap > 0 && g.sample_block_cap < g_sample_blocks_per_sm ? g.sample_block_cap
+                                                                                              : g_sample_blocks_per_sm;
+    const unsigned blocks = (unsigned)(g.sm_count * per_sm);
     sample_pairs_kernel<<<blocks, kBlock, 0, g.stream>>>(g.n, nseg, g.in.info, g.in.col, off, walk_threshold(c),
                                                          philox_keys(seed), g.pair_budget,
                                                          (unsigned long long*)nonmeet, steps, g.status, depth,
