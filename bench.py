@@ -751,8 +751,12 @@ def main():
 
     # roofline of the dominant kernel (the walk-pair sampler): pair-steps per second against
     # the integer-issue limit of one Philox-4x32-10 block plus the step logic
+    # the sampler's launches: with Algorithm 3 one on the side stream (the other nodes' walks,
+    # overlapping the planning) and one after the planning; achieved = pair-steps / the sum
+    # of the launches' durations (CUDA events on each launch's own stream)
     steps_total = sum(s["pair_steps"] for s in stats)
-    ms_sample = sum(s["ms_sample"] for s in stats)
+    ms_sample = sum(s["ms_sample_kernel"] + s["ms_sample_side"] for s in stats)
+    sampler_launches = sum(1 + (1 if s["pair_steps_side"] else 0) for s in stats)
     ms_phase = {p: sum(s[f"ms_{p}"] for s in stats) for p in ("forward", "allocate", "sample", "reverse", "topk")}
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -787,7 +791,9 @@ def main():
                 "d2h_bytes_per_step": k * (4 + 8),
                 "note": "host clock around esim_topk with host output buffers; query parameters pass by value"},
         "gpu_launches": launches,
-        "roofline": {"kernel": "sample_pairs_kernel", "bound": "alu", "achieved": achieved / 1e9,
+        "roofline": {"kernel": "sample_pairs_kernel", "launches": sampler_launches,
+                     "ms_per_launch": ms_sample / max(sampler_launches, 1),
+                     "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak_steps / 1e9, "unit": "G pair-steps/s", "frac": achieved / peak_steps,
                      "traffic": traffic,
                      "peak_source": f"{sm_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz ({pk_src} clock) / "

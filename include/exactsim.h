@@ -85,6 +85,13 @@ typedef struct {
     int32_t reserved2;
     uint64_t hist_entries;    /* stored history entries: (L+1) n dense, kept entries sparse */
     uint64_t workspace_bytes; /* device bytes of the last query's workspace layout */
+    /* With Algorithm 3 the walks of the nodes that are not exploitation candidates run on
+     * a second stream while the candidates are planned: ms_sample_kernel is the main
+     * sampler launch alone, ms_sample_side the side launch (overlapping the planning),
+     * pair_steps_side its share of pair_steps (which counts both). */
+    float ms_sample_kernel;
+    float ms_sample_side;
+    uint64_t pair_steps_side;
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */

@@ -33,7 +33,9 @@ class QueryStats(ctypes.Structure):
                 ("pair_steps", ctypes.c_uint64), ("ms_forward", ctypes.c_float), ("ms_allocate", ctypes.c_float),
                 ("ms_sample", ctypes.c_float), ("ms_reverse", ctypes.c_float), ("ms_topk", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("alg3_nodes", ctypes.c_int32), ("reserved2", ctypes.c_int32),
-                ("hist_entries", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+                ("hist_entries", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
+                ("ms_sample_kernel", ctypes.c_float), ("ms_sample_side", ctypes.c_float),
+                ("pair_steps_side", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved2"}

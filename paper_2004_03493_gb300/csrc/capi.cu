@@ -133,6 +133,8 @@ void release(Graph& g) {
     }
     for (auto& ev : g.side_ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto& ev : g.side_tev)
+        if (ev) cudaEventDestroy(ev);
     g = Graph{};
 }
 
@@ -334,7 +336,14 @@ esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& 
     Graph view = g;
     view.stream = g.side_stream;
     view.sample_block_cap = 4;
-    ESIM_CUDA_TRY(launch_sample(view, w.off2, c, seed, w.nm2, nullptr, nullptr), "other nodes' walk pairs");
+    if (g.timing) {
+        for (auto& ev : g.side_tev)
+            if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
+        cudaEventRecord(g.side_tev[0], g.side_stream);
+    }
+    ESIM_CUDA_TRY(launch_sample(view, w.off2, c, seed, w.nm2, (uint64_t*)&g.status->pair_steps_side, nullptr),
+                  "other nodes' walk pairs");
+    if (g.timing) cudaEventRecord(g.side_tev[1], g.side_stream);
     ESIM_CUDA_TRY(cudaEventRecord(g.side_ev[1], g.side_stream), "record");
     *launches += 6;
     return ESIM_OK;
@@ -476,11 +485,16 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     if (g.timing) cudaEventRecord(g.ev[1], g.stream);
     // kernels of the allocation, sampling and D^ phases (the default counts 3 + 1 + 1)
     int extra_launches = 0;
+    bool side_used = false;
     g.last_alg3_nodes = 0;
     if (g.diag_mode == 1) {
         // ParSim's approximation D = (1-c) I: no allocation and no walk pairs
-        if (g.timing) cudaEventRecord(g.ev[2], g.stream);
-        if (g.timing) cudaEventRecord(g.ev[3], g.stream);
+        if (g.timing) {
+            cudaEventRecord(g.ev[2], g.stream);
+            cudaEventRecord(g.ev[6], g.stream);
+            cudaEventRecord(g.ev[7], g.stream);
+            cudaEventRecord(g.ev[3], g.stream);
+        }
         ESIM_CUDA_TRY(launch_fill(g, g.n, 1.0 - c, w.dhat), "dhat (ParSim)");
         extra_launches -= 4;
     } else {
@@ -506,14 +520,19 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
             ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.offc, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n),
                                         false),
                           "candidates' scan");
+            if (g.timing) cudaEventRecord(g.ev[6], g.stream);
             ESIM_CUDA_TRY(launch_sample(g, w.offc, c, seed, w.nonmeet, nullptr, w.depth), "candidates' walk pairs");
+            if (g.timing) cudaEventRecord(g.ev[7], g.stream);
             ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.side_ev[1], 0), "wait for the other nodes' walks");
             ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nonmeet), "merge counts");
             extra_launches += 5;
         } else {
+            if (g.timing) cudaEventRecord(g.ev[6], g.stream);
             ESIM_CUDA_TRY(launch_sample(g, w.off, c, seed, w.nonmeet, nullptr, g.alg3 ? w.depth : nullptr),
                           "walk pairs");
+            if (g.timing) cudaEventRecord(g.ev[7], g.stream);
         }
+        side_used = side;
         if (g.timing) cudaEventRecord(g.ev[3], g.stream);
         if (g.alg3)
             ESIM_CUDA_TRY(launch_dhat_alg3(g, w.nonmeet, w.off, w.depth, w.zsum, c, w.dhat), "dhat (Algorithm 3)");
@@ -561,11 +580,15 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     g.last_kappa = kappa;
     g.last_norm2 = hs.pi_norm2;
     g.last_sum_R = hs.sum_R;
-    g.last_steps = hs.pair_steps;
+    g.last_steps = hs.pair_steps + (side_used ? hs.pair_steps_side : 0ull);
+    g.last_steps_side = side_used ? hs.pair_steps_side : 0ull;
     for (float& x : g.last_ms) x = 0.f;
+    g.last_ms_kernel = g.last_ms_side = 0.f;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
         cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
+        cudaEventElapsedTime(&g.last_ms_kernel, g.ev[6], g.ev[7]);
+        if (side_used) cudaEventElapsedTime(&g.last_ms_side, g.side_tev[0], g.side_tev[1]);
     }
     if (hs.err & kErrBudget)
         return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
@@ -722,9 +745,12 @@ esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, 
     g.last_sum_R = hs.sum_R;
     g.last_steps = hs.pair_steps;
     for (float& x : g.last_ms) x = 0.f;
+    g.last_ms_kernel = g.last_ms_side = 0.f;
+    g.last_steps_side = 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
         cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
+        g.last_ms_kernel = g.last_ms[2];
     }
     if (hs.err & kErrBudget)
         return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
@@ -1138,6 +1164,9 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->ms_reverse = g.last_ms[3];
     out->ms_topk = g.last_ms[4];
     out->ms_total = g.last_ms[5];
+    out->ms_sample_kernel = g.last_ms_kernel;
+    out->ms_sample_side = g.last_ms_side;
+    out->pair_steps_side = g.last_steps_side;
     out->alg3_nodes = g.last_alg3_nodes;
     out->hist_entries = g.last_hist_entries;
     out->workspace_bytes = g.last_ws_bytes;

@@ -28,6 +28,7 @@ struct Status {
     int err;
     unsigned int ticket;             // last-block ticket of the sparse-history compaction
     unsigned long long hist_count;   // sparse history entries so far
+    unsigned long long pair_steps_side;  // pair-steps of the side-stream sampler launch
 };
 
 // Sparse history of one query (sparse linearization): entries [lvl[l], lvl[l+1]) are
@@ -73,6 +74,7 @@ struct Graph {
     cudaStream_t stream = nullptr;
     cudaStream_t side_stream = nullptr;  // Algorithm 3: walks of the other nodes during the planning
     cudaEvent_t side_ev[2] = {};
+    cudaEvent_t side_tev[2] = {};        // timing of the side sampler (option timing)
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     // options
     double kappa = 0.0;
@@ -125,6 +127,8 @@ struct Graph {
     double last_R_b = 0, last_kappa = 0, last_norm2 = 0;
     unsigned long long last_sum_R = 0, last_steps = 0;
     float last_ms[6] = {};
+    float last_ms_kernel = 0.f, last_ms_side = 0.f;  // sampler launches alone (main, side)
+    unsigned long long last_steps_side = 0;
 };
 
 // sweep.cu
