@@ -167,6 +167,9 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_max_nodes" heaviest nodes (by pi) considered, 1..4096 (default 64)
  *   "alg3_min_pairs" smallest Algorithm 2 pair count worth considering (default 1e6)
  *   "alg3_max_depth" deepest exploitation, 1..16 (default 8)
+ *   "alg3_overlap"   sampler blocks per SM for the walks of the nodes that are not
+ *                    candidates, run on a second stream during the planning (default 4;
+ *                    0: all walks after the planning).  Counts do not depend on it.
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the depth's cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per
  *                    entry and column of a 32-column probe sweep (0.2), per kernel launch

@@ -335,7 +335,7 @@ esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& 
     ESIM_CUDA_TRY(cudaStreamWaitEvent(g.side_stream, g.side_ev[0], 0), "side wait");
     Graph view = g;
     view.stream = g.side_stream;
-    view.sample_block_cap = 4;
+    view.sample_block_cap = g.alg3_overlap;
     if (g.timing) {
         for (auto& ev : g.side_tev)
             if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
@@ -388,7 +388,7 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     // sampler judges the other nodes' pairs and the rescan below all of them.
     ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
     *side = false;
-    if (!cand.empty() && g.side_stream) {
+    if (!cand.empty() && g.side_stream && g.alg3_overlap > 0) {
         esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
         if (ss != ESIM_OK) return ss;
         *side = true;
@@ -1077,6 +1077,10 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_w_sweep" || k == "alg3_w_probe" || k == "alg3_w_launch") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, k + " must be >= 0");
         (k == "alg3_w_sweep" ? g.alg3_w_sweep : k == "alg3_w_probe" ? g.alg3_w_probe : g.alg3_w_launch) = value;
+    } else if (k == "alg3_overlap") {
+        if (!(value >= 0.0 && value <= 64.0) || value != floor(value))
+            return fail(ESIM_EINVAL, "alg3_overlap must be an integer in [0, 64]");
+        g.alg3_overlap = (int)value;
     } else if (k == "alg3_max_nodes") {
         if (!(value >= 1.0 && value <= 4096.0)) return fail(ESIM_EINVAL, "alg3_max_nodes must be in [1, 4096]");
         g.alg3_max_nodes = (int)value;
@@ -1104,6 +1108,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
+    else if (k == "alg3_overlap") *value = g.alg3_overlap;
     else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
     else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
     else if (k == "alg3_w_launch") *value = g.alg3_w_launch;
