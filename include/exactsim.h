@@ -167,6 +167,9 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_max_nodes" heaviest nodes (by pi) considered, 1..4096 (default 64)
  *   "alg3_min_pairs" smallest Algorithm 2 pair count worth considering (default 1e6)
  *   "alg3_max_depth" deepest exploitation, 1..16 (default 8)
+ *   "alg3_push_div"  a probe step pushes from its frontier while the frontier's in-edges are
+ *                    at most (m+n)/alg3_push_div, else pulls over all rows (default 4);
+ *                    both give the same integers
  *   "alg3_overlap"   sampler blocks per SM for the walks of the nodes that are not
  *                    candidates, run on a second stream during the planning (default 4;
  *                    0: all walks after the planning).  Counts do not depend on it.

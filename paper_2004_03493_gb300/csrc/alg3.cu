@@ -157,7 +157,8 @@ __device__ __forceinline__ unsigned long long fx_sq(unsigned long long H) {
 // non-zero) has few in-edges, a step pushes x_s(j) to the rows i in I(j) with
 // integer atomics into an n x 32 accumulator (exact, so the order of the atomics does
 // not matter) and processes only the touched rows; once the frontier's in-edges
-// exceed (m + n) / 4 the step and all later ones of the block run the dense pull.
+// exceed (m + n) / alg3_push_div (default 4) the step and all later ones of the block
+// run the dense pull.
 // Both forms give the same integers, so the switch changes no bit of the result.
 // The frontier, its in-edge count and the work list of 64-entry chunks live on the
 // device; the kernels of a step read the same counters, so all agree on the form
@@ -712,7 +713,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     }
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
-    const unsigned long long thr = (unsigned long long)(g.m + g.n) / 4;
+    const unsigned long long thr = (unsigned long long)(g.m + g.n) / (unsigned long long)std::max(1, g.alg3_push_div);
     for (int j = 1; j <= depth; ++j) {
         double* zv = ws.Zv + (size_t)j * n;
         const double* T = nullptr;

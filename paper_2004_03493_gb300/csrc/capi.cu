@@ -1077,6 +1077,10 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_w_sweep" || k == "alg3_w_probe" || k == "alg3_w_launch") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, k + " must be >= 0");
         (k == "alg3_w_sweep" ? g.alg3_w_sweep : k == "alg3_w_probe" ? g.alg3_w_probe : g.alg3_w_launch) = value;
+    } else if (k == "alg3_push_div") {
+        if (!(value >= 1.0 && value <= 1e6) || value != floor(value))
+            return fail(ESIM_EINVAL, "alg3_push_div must be an integer in [1, 1e6]");
+        g.alg3_push_div = (int)value;
     } else if (k == "alg3_overlap") {
         if (!(value >= 0.0 && value <= 64.0) || value != floor(value))
             return fail(ESIM_EINVAL, "alg3_overlap must be an integer in [0, 64]");
@@ -1109,6 +1113,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
     else if (k == "alg3_overlap") *value = g.alg3_overlap;
+    else if (k == "alg3_push_div") *value = g.alg3_push_div;
     else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
     else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
     else if (k == "alg3_w_launch") *value = g.alg3_w_launch;
