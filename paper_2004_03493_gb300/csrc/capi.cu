@@ -135,6 +135,11 @@ void release(Graph& g) {
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : g.side_tev)
         if (ev) cudaEventDestroy(ev);
+    if (g.early_stream) {
+        cudaStreamSynchronize(g.early_stream);
+        cudaStreamDestroy(g.early_stream);
+    }
+    if (g.early_ev) cudaEventDestroy(g.early_ev);
     g = Graph{};
 }
 
@@ -174,6 +179,8 @@ struct Ws {
     uint64_t* off2;    // n+1  offsets of the other nodes' walks (read by the side stream)
     uint64_t* offc;    // n+1  offsets of the candidates' walks
     uint64_t* nm2;     // n  counts of the other nodes
+    uint64_t* nme;     // n  counts of the heavy candidates sampled during the planning
+    uint64_t* offe;    // n+1  offsets of one such candidate
     int32_t* cand_ids; // 4096
     // sparse linearization (FP64): rolling pi^l, the running pi, the kept entries
     double* lev;       // n
@@ -234,6 +241,8 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
     t.off2 = (uint64_t*)take(8 * (n + 1));
     t.offc = (uint64_t*)take(8 * (n + 1));
     t.nm2 = (uint64_t*)take(8 * n);
+    t.nme = (uint64_t*)take(8 * n);
+    t.offe = (uint64_t*)take(8 * (n + 1));
     t.cand_ids = (int32_t*)take(4 * 4096);
     if (precision == 0 && sparse_cap > 0) {
         // last, so that the layout for a smaller capacity is a prefix of this one
@@ -349,6 +358,27 @@ esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& 
     return ESIM_OK;
 }
 
+// A planned candidate whose walks are at least this many pairs starts them at once.
+constexpr uint64_t kEarlyPairs = 1ull << 24;
+
+// The walks of one planned candidate k on the early stream: its offsets alone (the other
+// nodes have none), counts added to nme, pair-steps to the status block.
+esim_status start_early_walks(Graph& g, const Ws& w, int32_t k, uint64_t R1, double c, uint64_t seed, bool started,
+                              int* launches) {
+    Graph view = g;
+    view.stream = g.early_stream;
+    view.sample_block_cap = g.alg3_overlap;
+    if (!started) ESIM_CUDA_TRY(cudaMemsetAsync(w.nme, 0, 8 * (size_t)g.n, g.early_stream), "reset counts");
+    ESIM_CUDA_TRY(launch_single_offsets(view, k, R1, w.offe), "one node's offsets");
+    ESIM_CUDA_TRY(launch_sample_segments(view, g.n, w.offe, c, seed, w.nme, nullptr, w.depth, 0, nullptr, false),
+                  "heavy candidate's walk pairs");
+    const uint8_t two = 2;
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand + k, &two, 1, cudaMemcpyHostToDevice, g.stream), "mark early");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "mark early");  // the host byte is a local
+    *launches += 2;
+    return ESIM_OK;
+}
+
 esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches, uint64_t seed, bool* side) {
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
     esim_status a3 = ensure_a3ws(g);
@@ -388,6 +418,7 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     // sampler judges the other nodes' pairs and the rescan below all of them.
     ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
     *side = false;
+    bool early_started = false;
     if (!cand.empty() && g.side_stream && g.alg3_overlap > 0) {
         esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
         if (ss != ESIM_OK) return ss;
@@ -426,8 +457,19 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum + kk, &zs, sizeof(double), cudaMemcpyHostToDevice, g.stream), "set zsum");
         ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // host values above are locals
         ++used;
+        if (*side && R1 >= kEarlyPairs) {
+            // this node's R(k) and depth are final: its walks start now, during the rest
+            // of the planning (the host synchronised the writes above)
+            esim_status es = start_early_walks(g, w, kk, R1, c, seed, early_started, launches);
+            if (es != ESIM_OK) return es;
+            early_started = true;
+        }
     }
     g.last_alg3_nodes = used;
+    if (*side) {  // the early walks are done when this event is
+        if (!early_started) ESIM_CUDA_TRY(cudaMemsetAsync(w.nme, 0, 8 * (size_t)g.n, g.early_stream), "reset counts");
+        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.early_stream), "record");
+    }
     const int64_t nb = allocate_blocks(g.n);
     ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R, w.off, g.scan_part, nullptr, g.norm_part + nb), "Algorithm 3 rescan");
     *launches += 3;
@@ -509,7 +551,10 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
         if (g.alg3) {
             esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches, seed, &side);
             if (a3 != ESIM_OK) {
-                if (side) cudaStreamSynchronize(g.side_stream);  // no walks left running into the next query
+                if (side) {  // no walks left running into the next query
+                    cudaStreamSynchronize(g.side_stream);
+                    cudaStreamSynchronize(g.early_stream);
+                }
                 return a3;
             }
         }
@@ -524,7 +569,8 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
             ESIM_CUDA_TRY(launch_sample(g, w.offc, c, seed, w.nonmeet, nullptr, w.depth), "candidates' walk pairs");
             if (g.timing) cudaEventRecord(g.ev[7], g.stream);
             ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.side_ev[1], 0), "wait for the other nodes' walks");
-            ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nonmeet), "merge counts");
+            ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.early_ev, 0), "wait for the heavy candidates' walks");
+            ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nme, w.nonmeet), "merge counts");
             extra_launches += 5;
         } else {
             if (g.timing) cudaEventRecord(g.ev[6], g.stream);
@@ -994,7 +1040,9 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
               cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g.side_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&g.side_ev[0], cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&g.side_ev[1], cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&g.side_ev[1], cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&g.early_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g.early_ev, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(g);

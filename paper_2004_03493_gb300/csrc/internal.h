@@ -74,6 +74,8 @@ struct Graph {
     cudaStream_t stream = nullptr;
     cudaStream_t side_stream = nullptr;  // Algorithm 3: walks of the other nodes during the planning
     cudaEvent_t side_ev[2] = {};
+    cudaStream_t early_stream = nullptr; // Algorithm 3: walks of each planned heavy node during the rest
+    cudaEvent_t early_ev = nullptr;
     cudaEvent_t side_tev[2] = {};        // timing of the side sampler (option timing)
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     int alg3_overlap = 4;                // side sampler blocks per SM during the planning (0: no overlap)
@@ -159,15 +161,18 @@ cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t*
 cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out);
 // R_out(k) = R(k) where keep(k) == want, else 0
 cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want, uint64_t* R_out);
-// counts(k) = side(k) where cand(k) == 0
-cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts);
+// counts(k) = side(k) where cand(k) == 0, early(k) where cand(k) == 2
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, const uint64_t* early,
+                                uint64_t* counts);
 // cand(k) = 1 for the listed nodes
 cudaError_t launch_mark(const Graph& g, const int32_t* ids, int count, uint8_t* mark);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
 // shared_B > 0 with rbase: segment s covers pairs [rbase[s], rbase[s] + len) of node s / shared_B
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
                                    uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr,
-                                   int shared_B = 0, const uint64_t* rbase = nullptr);
+                                   int shared_B = 0, const uint64_t* rbase = nullptr, bool zero_counts = true);
+// off(i) = 0 for i <= k, R for i > k: the offsets of one node's R pairs
+cudaError_t launch_single_offsets(const Graph& g, int64_t k, uint64_t R, uint64_t* off);
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
                                  double* dhat);
 // record = false: an auxiliary scan that leaves the status block (sum of R, budget) alone

@@ -400,9 +400,17 @@ __global__ void mask_R_kernel(int64_t n, const uint64_t* __restrict__ R, const u
 }
 
 __global__ void merge_counts_kernel(int64_t n, const uint8_t* __restrict__ cand, const uint64_t* __restrict__ side,
-                                    uint64_t* __restrict__ counts) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        if (!cand[k]) counts[k] = side[k];
+                                    const uint64_t* __restrict__ early, uint64_t* __restrict__ counts) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t m = cand[k];
+        if (m == 0) counts[k] = side[k];
+        else if (m == 2) counts[k] = early[k];
+    }
+}
+
+__global__ void single_offsets_kernel(int64_t n, int64_t k, uint64_t R, uint64_t* __restrict__ off) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] = i <= k ? 0ull : R;
 }
 
 __global__ void mark_kernel(const int32_t* __restrict__ ids, int count, uint8_t* __restrict__ mark) {
@@ -420,8 +428,14 @@ cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts) {
-    merge_counts_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, cand, side, counts);
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, const uint64_t* early,
+                                uint64_t* counts) {
+    merge_counts_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, cand, side, early, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_single_offsets(const Graph& g, int64_t k, uint64_t R, uint64_t* off) {
+    single_offsets_kernel<<<eb_cap(g, g.n + 1), kBlock, 0, g.stream>>>(g.n, k, R, off);
     return cudaGetLastError();
 }
 
@@ -439,9 +453,10 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
 
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
                                    uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth, int shared_B,
-                                   const uint64_t* rbase) {
-    cudaError_t e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)nseg, g.stream);
-    if (e != cudaSuccess) return e;
+                                   const uint64_t* rbase, bool zero_counts) {
+    cudaError_t e = cudaSuccess;
+    if (zero_counts && (e = cudaMemsetAsync(nonmeet, 0, sizeof(uint64_t) * (size_t)nseg, g.stream)) != cudaSuccess)
+        return e;
     unsigned long long* steps = pair_steps ? (unsigned long long*)pair_steps : &g.status->pair_steps;
     if (pair_steps) {
         e = cudaMemsetAsync(pair_steps, 0, sizeof(uint64_t), g.stream);
