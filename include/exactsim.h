@@ -86,12 +86,16 @@ typedef struct {
     uint64_t hist_entries;    /* stored history entries: (L+1) n dense, kept entries sparse */
     uint64_t workspace_bytes; /* device bytes of the last query's workspace layout */
     /* With Algorithm 3 the walks of the nodes that are not exploitation candidates run on
-     * a second stream while the candidates are planned: ms_sample_kernel is the main
-     * sampler launch alone, ms_sample_side the side launch (overlapping the planning),
-     * pair_steps_side its share of pair_steps (which counts both). */
+     * a second stream while the candidates are planned, and each heavy candidate's walks
+     * on a third as soon as its plan is final: ms_sample_kernel is the last sampler launch
+     * alone, ms_sample_side the side launch, ms_sample_early the sum of the early_launches
+     * early ones (all with option timing); pair_steps_side is the side launch's share of
+     * pair_steps, which counts every launch. */
     float ms_sample_kernel;
     float ms_sample_side;
     uint64_t pair_steps_side;
+    float ms_sample_early;
+    int32_t early_launches;
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */

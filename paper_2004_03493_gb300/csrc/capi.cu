@@ -135,6 +135,8 @@ void release(Graph& g) {
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : g.side_tev)
         if (ev) cudaEventDestroy(ev);
+    for (auto& ev : g.early_tev)
+        if (ev) cudaEventDestroy(ev);
     if (g.early_stream) {
         cudaStreamSynchronize(g.early_stream);
         cudaStreamDestroy(g.early_stream);
@@ -370,8 +372,19 @@ esim_status start_early_walks(Graph& g, const Ws& w, int32_t k, uint64_t R1, dou
     view.sample_block_cap = g.alg3_overlap;
     if (!started) ESIM_CUDA_TRY(cudaMemsetAsync(w.nme, 0, 8 * (size_t)g.n, g.early_stream), "reset counts");
     ESIM_CUDA_TRY(launch_single_offsets(view, k, R1, w.offe), "one node's offsets");
+    const size_t ti = 2 * (size_t)g.early_launches;
+    if (g.timing) {
+        while (g.early_tev.size() < ti + 2) {
+            cudaEvent_t ev = nullptr;
+            ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
+            g.early_tev.push_back(ev);
+        }
+        cudaEventRecord(g.early_tev[ti], g.early_stream);
+    }
     ESIM_CUDA_TRY(launch_sample_segments(view, g.n, w.offe, c, seed, w.nme, nullptr, w.depth, 0, nullptr, false),
                   "heavy candidate's walk pairs");
+    if (g.timing) cudaEventRecord(g.early_tev[ti + 1], g.early_stream);
+    ++g.early_launches;
     const uint8_t two = 2;
     ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand + k, &two, 1, cudaMemcpyHostToDevice, g.stream), "mark early");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "mark early");  // the host byte is a local
@@ -419,6 +432,7 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
     *side = false;
     bool early_started = false;
+    g.early_launches = 0;
     if (!cand.empty() && g.side_stream && g.alg3_overlap > 0) {
         esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
         if (ss != ESIM_OK) return ss;
@@ -629,12 +643,18 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     g.last_steps = hs.pair_steps + (side_used ? hs.pair_steps_side : 0ull);
     g.last_steps_side = side_used ? hs.pair_steps_side : 0ull;
     for (float& x : g.last_ms) x = 0.f;
-    g.last_ms_kernel = g.last_ms_side = 0.f;
+    g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
+    g.last_early = side_used ? g.early_launches : 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
         cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
         cudaEventElapsedTime(&g.last_ms_kernel, g.ev[6], g.ev[7]);
         if (side_used) cudaEventElapsedTime(&g.last_ms_side, g.side_tev[0], g.side_tev[1]);
+        for (int i = 0; i < g.last_early; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, g.early_tev[2 * (size_t)i], g.early_tev[2 * (size_t)i + 1]);
+            g.last_ms_early += ms;
+        }
     }
     if (hs.err & kErrBudget)
         return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
@@ -791,7 +811,8 @@ esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, 
     g.last_sum_R = hs.sum_R;
     g.last_steps = hs.pair_steps;
     for (float& x : g.last_ms) x = 0.f;
-    g.last_ms_kernel = g.last_ms_side = 0.f;
+    g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
+    g.last_early = 0;
     g.last_steps_side = 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
@@ -1225,6 +1246,8 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->ms_sample_kernel = g.last_ms_kernel;
     out->ms_sample_side = g.last_ms_side;
     out->pair_steps_side = g.last_steps_side;
+    out->ms_sample_early = g.last_ms_early;
+    out->early_launches = g.last_early;
     out->alg3_nodes = g.last_alg3_nodes;
     out->hist_entries = g.last_hist_entries;
     out->workspace_bytes = g.last_ws_bytes;

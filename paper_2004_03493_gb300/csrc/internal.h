@@ -76,6 +76,8 @@ struct Graph {
     cudaEvent_t side_ev[2] = {};
     cudaStream_t early_stream = nullptr; // Algorithm 3: walks of each planned heavy node during the rest
     cudaEvent_t early_ev = nullptr;
+    std::vector<cudaEvent_t> early_tev;  // timing of the early launches (start, end pairs)
+    int early_launches = 0;
     cudaEvent_t side_tev[2] = {};        // timing of the side sampler (option timing)
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     int alg3_overlap = 4;                // side sampler blocks per SM during the planning (0: no overlap)
@@ -132,6 +134,8 @@ struct Graph {
     unsigned long long last_sum_R = 0, last_steps = 0;
     float last_ms[6] = {};
     float last_ms_kernel = 0.f, last_ms_side = 0.f;  // sampler launches alone (main, side)
+    float last_ms_early = 0.f;
+    int last_early = 0;
     unsigned long long last_steps_side = 0;
 };
 
