@@ -277,7 +277,9 @@ def run_precision(args, w):
     L = esim.esim_levels(c, eps)
     kappa = args.kappa
     g = esim.Graph(n, rp, col, kappa=kappa)
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the library's launches and the CUDA events must share one
+    # (torch's legacy default stream would not order the library's work)
+    stream = torch.cuda.Stream()
     g.set_stream(stream)
     hist64 = torch.empty((L + 1) * n, dtype=torch.float64, device="cuda")
     hist32 = torch.empty((L + 1) * n, dtype=torch.float32, device="cuda")
@@ -352,7 +354,7 @@ def run_batched(args, w):
     c, k = w["c"], w["k"]
     gb = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
     gs = esim.Graph(n, rp, col, kappa=args.kappa, timing=1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # shared by the library's launches and the CUDA events
     gb.set_stream(stream)
     gs.set_stream(stream)
     B = len(srcs)
@@ -364,6 +366,7 @@ def run_batched(args, w):
 
     def timed(fn):
         flush.zero_()
+        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -694,7 +697,7 @@ def main():
     srcs = sources_for(w, rp, world, rank)
     c, eps, k = w["c"], w["eps"], w["k"]
     g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)  # shared by the library's launches and the CUDA events
     g.set_stream(stream)
     ids = torch.empty(k, dtype=torch.int32, device=dev)
     vals = torch.empty(k, dtype=torch.float64, device=dev)
