@@ -89,15 +89,15 @@ struct ForwardOp {  // FP64
     }
 };
 
-struct ReverseOp {  // FP64
+struct ReverseOp {  // FP64; 1/a is a host constant (an FP64 division per row is costly on GB300)
     double sc;
-    double a;
+    double inv_a;
     const double* __restrict__ inv_din;
     const double* __restrict__ dhat;
     const double* __restrict__ h;  // pi^{L-l}
     double* __restrict__ s_out;
     __device__ __forceinline__ void operator()(int64_t row, double acc) const {
-        s_out[row] = (sc * acc) * inv_din[row] + dhat[row] * h[row] / a;
+        s_out[row] = (sc * acc) * inv_din[row] + dhat[row] * h[row] * inv_a;
     }
 };
 
@@ -233,10 +233,10 @@ __global__ void forward_init32_kernel(int64_t n, int64_t u, float a, const uint3
     }
 }
 
-__global__ void reverse_init_kernel(int64_t n, double a, const double* __restrict__ dhat,
+__global__ void reverse_init_kernel(int64_t n, double inv_a, const double* __restrict__ dhat,
                                     const double* __restrict__ h, double* __restrict__ s0) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s0[i] = dhat[i] * h[i] / a;
+        s0[i] = dhat[i] * h[i] * inv_a;
 }
 
 // w = D^ / a as two-floats, and s^0 = w pi^L (float2, or FP64 when L = 0)
@@ -304,17 +304,18 @@ __global__ void __launch_bounds__(kBlock) compact_level_kernel(int64_t n, const 
     }
 }
 
-// s(k) += D^(k) pi^level(k) / a over the sparse entries of one level (unique nodes).
+// s(k) += D^(k) pi^level(k) / a (times the host's 1/a) over the sparse entries of one
+// level (unique nodes).
 __global__ void __launch_bounds__(kBlock) scatter_level_kernel(const uint64_t* __restrict__ lvl, int level,
                                                                const int32_t* __restrict__ idx,
                                                                const double* __restrict__ val,
-                                                               const double* __restrict__ dhat, double a,
+                                                               const double* __restrict__ dhat, double inv_a,
                                                                double* __restrict__ s) {
     const uint64_t beg = lvl[level], end = lvl[level + 1];
     for (uint64_t p = beg + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end;
          p += (uint64_t)gridDim.x * blockDim.x) {
         const int32_t k = idx[p];
-        s[k] = s[k] + dhat[k] * val[p] / a;
+        s[k] = s[k] + dhat[k] * val[p] * inv_a;
     }
 }
 
@@ -390,14 +391,15 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
     const double a = 1.0 - sc;
     // level l writes buf[(L - l) & 1]; buf[0] = s_out, so level L lands in s_out
     double* buf[2] = {s_out, sa};
-    reverse_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, a, dhat, hist + (size_t)L * g.n,
-                                                                             buf[L & 1]);
+    const double inv_a = 1.0 / a;
+    reverse_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, inv_a, dhat,
+                                                                             hist + (size_t)L * g.n, buf[L & 1]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int32_t l = 1; l <= L; ++l) {
         const double* sp = buf[(L - l + 1) & 1];
         double* sn = buf[(L - l) & 1];
-        ReverseOp op{sc, a, g.inv_din, dhat, hist + (size_t)(L - l) * g.n, sn};
+        ReverseOp op{sc, inv_a, g.inv_din, dhat, hist + (size_t)(L - l) * g.n, sn};
         e = sweep_level<Pol64>(g, g.in, sp, op);
         if (e != cudaSuccess) return e;
     }
@@ -439,13 +441,13 @@ cudaError_t launch_reverse_sparse(const Graph& g, const SparseHist& h, int32_t L
     const unsigned sb = (unsigned)g.sm_count * 4;
     cudaError_t e = launch_fill(g, g.n, 0.0, buf[L & 1]);
     if (e != cudaSuccess) return e;
-    scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L, h.idx, h.val, dhat, a, buf[L & 1]);
+    scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L, h.idx, h.val, dhat, 1.0 / a, buf[L & 1]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int32_t l = 1; l <= L; ++l) {
         double* sn = buf[(L - l) & 1];
         ReverseSparseOp op{sc, g.inv_din, sn};
         if ((e = sweep_level<Pol64>(g, g.in, buf[(L - l + 1) & 1], op)) != cudaSuccess) return e;
-        scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L - l, h.idx, h.val, dhat, a, sn);
+        scatter_level_kernel<<<sb, kBlock, 0, g.stream>>>(h.lvl, L - l, h.idx, h.val, dhat, 1.0 / a, sn);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
