@@ -345,6 +345,14 @@ esim_status esim_reverse_f32(esim_graph* g, const float* hist, int32_t L, double
  * step d.  esim_dhat_alg3 gives D^ = counts/R for depth 0, 1 - zsum - c^d counts/R
  * for depth d > 0, and 1 (din 0) or 1-c (din 1) exactly. */
 esim_status esim_alg3_first_meeting(esim_graph* g, int64_t k, int32_t depth, double c, double* z_out);
+/* Algorithm 3's depth choice for one node, host arithmetic only (no device): the d in
+ * 0..max_depth (<= 16) of least estimated work R_d (d + 1/(1-c)) + w_sweep (m+n)(2d-1) +
+ * w_probe (m+n) sum_{i=1}^{d-2} supp[i](d-i) + w_launch launches(d), R_d = max(1,
+ * ceil(v c^(2d))), v = R_b pi(k)^2 (R_b pi(k) for the basic allocation), supp[i] =
+ * |supp (P^T)^i(k, .)| for i = 0..max(0, max_depth-2); the first on ties.  The option
+ * "alg3" decides every node with it.  Returns -1 on invalid arguments. */
+int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_depth, int64_t n, int64_t m,
+                        double w_sweep, double w_probe, double w_launch);
 esim_status esim_sample_depth(esim_graph* g, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
                               uint64_t* counts, uint64_t* pair_steps);
 esim_status esim_dhat_alg3(esim_graph* g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,

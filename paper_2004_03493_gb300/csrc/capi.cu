@@ -305,7 +305,8 @@ esim_status ensure_a3ws(Graph& g) {
 // d = 0 is Algorithm 2 alone.  The weights (options alg3_w_sweep, alg3_w_probe,
 // alg3_w_launch: pair-steps per entry of a single sweep, per entry and column of a probe
 // sweep, and per launch) are calibrated by timing whole queries on GB300.
-double alg3_cost(const Graph& g, int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m) {
+double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m, double w_sweep,
+                 double w_probe, double w_launch) {
     double r = d == 0 ? ceil(v) : ceil(v * pow(c, (double)(2 * d)));
     if (r < 1.0) r = 1.0;
     double cost = r * ((double)d + 1.0 / (1.0 - c));
@@ -316,11 +317,26 @@ double alg3_cost(const Graph& g, int d, double v, double c, const uint64_t* supp
             probe += supp[i] * (uint64_t)(d - i);
             launches += (supp[i] + 31) / 32 * (uint64_t)(3 * (d - i) + 2);
         }
-        cost += g.alg3_w_sweep * edges * (double)(2 * d - 1);
-        cost += g.alg3_w_probe * edges * (double)probe;
-        cost += g.alg3_w_launch * (double)launches;
+        cost += w_sweep * edges * (double)(2 * d - 1);
+        cost += w_probe * edges * (double)probe;
+        cost += w_launch * (double)launches;
     }
     return cost;
+}
+
+// The depth of least estimated work, 0..max_depth (the first on ties).
+int alg3_depth(double v, double c, const uint64_t* supp, int max_depth, int64_t n, int64_t m, double w_sweep,
+               double w_probe, double w_launch) {
+    int d = 0;
+    double best = alg3_cost(0, v, c, supp, n, m, w_sweep, w_probe, w_launch);
+    for (int dd = 1; dd <= max_depth; ++dd) {
+        const double cost = alg3_cost(dd, v, c, supp, n, m, w_sweep, w_probe, w_launch);
+        if (cost < best) {
+            best = cost;
+            d = dd;
+        }
+    }
+    return d;
 }
 
 // Algorithm 3 for the heaviest nodes (by pi, at most alg3_max_nodes, with din >= 2
@@ -447,15 +463,8 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         const int32_t kk = cand[ci];
         const double v = cand_v[ci];
         const uint64_t* supp = supps.data() + ci * (kAlg3MaxDepth + 1);
-        int d = 0;
-        double best = alg3_cost(g, 0, v, c, supp, g.n, g.m);
-        for (int dd = 1; dd <= g.alg3_max_depth; ++dd) {
-            const double cost = alg3_cost(g, dd, v, c, supp, g.n, g.m);
-            if (cost < best) {
-                best = cost;
-                d = dd;
-            }
-        }
+        const int d = alg3_depth(v, c, supp, g.alg3_max_depth, g.n, g.m, g.alg3_w_sweep, g.alg3_w_probe,
+                                 g.alg3_w_launch);
         if (d < 1) continue;
         double z[kAlg3MaxDepth] = {};
         ESIM_CUDA_TRY(alg3_first_meeting(g, kk, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
@@ -1415,6 +1424,14 @@ esim_status esim_alg3_first_meeting(esim_graph* h, int64_t k, int32_t depth, dou
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(alg3_first_meeting(g, k, depth, c, g.a3ws, z_out, nullptr), "Algorithm 3 first meetings");
     return ESIM_OK;
+}
+
+int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_depth, int64_t n, int64_t m,
+                        double w_sweep, double w_probe, double w_launch) {
+    if (!supp || !(c > 0.0 && c < 1.0) || max_depth < 0 || max_depth > kAlg3MaxDepth || n < 1 || m < 0 ||
+        !(v >= 0.0) || !(w_sweep >= 0.0) || !(w_probe >= 0.0) || !(w_launch >= 0.0))
+        return -1;
+    return alg3_depth(v, c, supp, max_depth, n, m, w_sweep, w_probe, w_launch);
 }
 
 esim_status esim_sample_depth(esim_graph* h, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,

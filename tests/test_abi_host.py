@@ -93,3 +93,31 @@ def test_null_handle_is_rejected(native):
     with pytest.raises(native.EsimError) as e:
         native.esim_query(None, 0, 0.6, 1e-3, 0, out)
     assert e.value.status == -1
+
+
+def test_alg3_depth_choice_matches_the_oracle(native):
+    """The library's depth choice (host arithmetic) and the oracle's exploit_cost argmin
+    pick the same depth, bit for bit, over random work estimates and real supports."""
+    from oracle import alg3 as a3
+    rng = np.random.default_rng(5)
+    n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
+    m = int(rp[-1])
+    P = a3.transition_matrix(n, rp, col)
+    supps = [a3.supports(P, int(k), 14) for k in rng.choice(n, 12, replace=False)]
+    checked = 0
+    for trial in range(400):
+        supp = supps[trial % len(supps)]
+        v = float(10 ** rng.uniform(2, 15))
+        c = float(rng.choice([0.6, 0.8, 0.5]))
+        max_depth = int(rng.integers(0, 17))
+        weights = (float(rng.choice([4.0, 1.0])), float(rng.choice([0.2, 0.5, 0.05])),
+                   float(rng.choice([524288.0, 2.0 ** 16])))
+        costs = [a3.exploit_cost(d, v, c, supp, n, m, *weights) for d in range(max_depth + 1)]
+        want = min(range(max_depth + 1), key=lambda d: (costs[d], d))
+        got = native.esim_alg3_depth(v, c, supp[:max(1, max_depth - 1)] + [0] * 2, max_depth, n, m, weights)
+        assert got == want, (v, c, max_depth, weights, costs)
+        checked += want > 0
+    assert checked > 50  # exploitation is chosen often enough to matter
+    # invalid arguments
+    assert native.esim_alg3_depth(1e9, 1.5, [1, 2, 3], 3, n, m) == -1
+    assert native.esim_alg3_depth(1e9, 0.6, [1, 2, 3], 17, n, m) == -1
