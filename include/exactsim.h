@@ -26,10 +26,15 @@
  * with key = (seed low 32 bits, seed high 32 bits) and counter (r_lo, r_hi, k, t)
  * for pair r of node k at step t.  One call per step gives (w0, w1, w2, w3); with
  * T = floor(sqrt(c) 2^32) walk A moves iff w0 < T and din > 0 and goes to
- * in-neighbour number (w1 * din) >> 32; walk B likewise with w2, w3.  A pair ends
- * as "no meeting" as soon as either walk stops, and as "meeting" when both move
- * to the same node.  A pair still running after 65536 steps ends as "no meeting".
- * A walk pair therefore depends only on (seed, k, r), not on the query.
+ * in-neighbour number (w1 * din) >> 32, exactly uniform by Lemire's rejection: when
+ * the low 32 bits of w1 * din fall below (2^32 - din) mod din, the word is redrawn
+ * from the side stream, counter (r_lo, r_hi, k, 2^31 | W 2^30 | j 2^16 | t) for the
+ * j-th block of redraws of walk W (A = 0, B = 1); walk B likewise with w2, w3.  A
+ * pair ends as "no meeting" as soon as either walk stops, and as "meeting" when
+ * both move to the same node.  A pair still running after 65536 steps ends as "no
+ * meeting".  With Algorithm 3 a node of depth d moves its pairs for d steps without
+ * the continuation test.  A walk pair therefore depends only on (seed, k, r), not on
+ * the query, its batch or the launch that runs it.
  *
  * Conventions
  *  - Every call returns an esim_status; ESIM_OK is 0.  On failure
@@ -44,6 +49,10 @@
  *  - No call falls back to the CPU.  Without a usable CUDA device every call
  *    that needs one returns ESIM_ECUDA.
  *  - Node ids are int32 in [0, n); n < 2^31 and m < 2^32.
+ *  - One graph handle serves one call at a time: calls on the same handle from
+ *    several threads must be serialised by the caller (the server has its own
+ *    scheduler thread and takes requests from any thread).  Several handles may
+ *    share a device.
  */
 #ifndef EXACTSIM_H
 #define EXACTSIM_H
