@@ -186,6 +186,9 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_overlap"   sampler blocks per SM for the walks of the nodes that are not
  *                    candidates, run on a second stream during the planning (default 4;
  *                    0: all walks after the planning).  Counts do not depend on it.
+ *   "alg3_early_pairs"  a candidate whose plan is final and whose pairs number at least
+ *                    this (default 2^24) starts its walks at once on a third stream,
+ *                    during the rest of the planning (with "alg3_overlap" > 0)
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the depth's cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per
  *                    entry and column of a 32-column probe sweep (0.2), per kernel launch

@@ -376,9 +376,6 @@ esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& 
     return ESIM_OK;
 }
 
-// A planned candidate whose walks are at least this many pairs starts them at once.
-constexpr uint64_t kEarlyPairs = 1ull << 24;
-
 // The walks of one planned candidate k on the early stream: its offsets alone (the other
 // nodes have none), counts added to nme, pair-steps to the status block.
 esim_status start_early_walks(Graph& g, const Ws& w, int32_t k, uint64_t R1, double c, uint64_t seed, bool started,
@@ -480,7 +477,7 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum + kk, &zs, sizeof(double), cudaMemcpyHostToDevice, g.stream), "set zsum");
         ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // host values above are locals
         ++used;
-        if (*side && R1 >= kEarlyPairs) {
+        if (*side && (double)R1 >= g.alg3_early_pairs) {
             // this node's R(k) and depth are final: its walks start now, during the rest
             // of the planning (the host synchronised the writes above)
             esim_status es = start_early_walks(g, w, kk, R1, c, seed, early_started, launches);
@@ -1155,6 +1152,9 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_w_sweep" || k == "alg3_w_probe" || k == "alg3_w_launch") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, k + " must be >= 0");
         (k == "alg3_w_sweep" ? g.alg3_w_sweep : k == "alg3_w_probe" ? g.alg3_w_probe : g.alg3_w_launch) = value;
+    } else if (k == "alg3_early_pairs") {
+        if (!(value >= 1.0)) return fail(ESIM_EINVAL, "alg3_early_pairs must be >= 1");
+        g.alg3_early_pairs = value;
     } else if (k == "alg3_push_div") {
         if (!(value >= 1.0 && value <= 1e6) || value != floor(value))
             return fail(ESIM_EINVAL, "alg3_push_div must be an integer in [1, 1e6]");
@@ -1192,6 +1192,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
     else if (k == "alg3_overlap") *value = g.alg3_overlap;
     else if (k == "alg3_push_div") *value = g.alg3_push_div;
+    else if (k == "alg3_early_pairs") *value = g.alg3_early_pairs;
     else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
     else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
     else if (k == "alg3_w_launch") *value = g.alg3_w_launch;

@@ -82,6 +82,7 @@ struct Graph {
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     int alg3_overlap = 4;                // side sampler blocks per SM during the planning (0: no overlap)
     int alg3_push_div = 4;               // probe steps push while the frontier's in-edges <= (m+n)/this
+    double alg3_early_pairs = 16777216.0; // a planned candidate with this many pairs walks at once
     // options
     double kappa = 0.0;
     int alloc_mode = 0;

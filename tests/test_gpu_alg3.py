@@ -250,3 +250,29 @@ def test_alg3_with_basic_allocation_and_fp32c(esim, oracle_walks):
     s32 = g.query(5, C, 1e-3, 4)
     assert np.max(np.abs(s32 - s64)) < 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("overlap,early", [(0, 1e30), (4, 1e30), (4, 1.0), (2, 1e4)])
+def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, early):
+    """The walks split over the side stream (non-candidates), the early stream (each
+    planned candidate) and the main stream give the oracle's counts and scores."""
+    from oracle import exactsim
+    n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
+    g = esim.Graph(n, rp, col, alg3=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6,
+                   alg3_overlap=overlap, alg3_early_pairs=early)
+    eps = 3e-3
+    checked = 0
+    for u, seed in ((5, 1), (1234, 2), (2999, 3)):
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, alg3=True, alg3_max_depth=6, alg3_min_pairs=1e3,
+                           alg3_max_nodes=16)
+        if not _clean(q.pi, q.R_b, q.depth.astype(np.float64), 16) or q.plan_gap <= 1e-9:
+            continue
+        s = g.query(u, C, eps, seed)
+        st = g.stats()
+        assert st["sum_R"] == int(q.R.sum()) and st["pair_steps"] == q.pair_steps
+        assert np.max(np.abs(s - q.s)) <= TOL
+        if overlap and early <= 1.0:
+            assert st["early_launches"] == st["alg3_nodes"] > 0
+        checked += 1
+    assert checked >= 2
+    g.close()
