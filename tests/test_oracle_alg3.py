@@ -28,8 +28,8 @@ def test_lemma5_matches_bruteforce(seed):
     for k in range(n):
         if din[k] == 0:
             continue
-        z = a3.first_meeting_lemma5(nn, rp, col, k, C, 6)
-        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), 6)]
+        z = a3.first_meeting_lemma5(nn, rp, col, k, C, 8)
+        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), 8)]
         assert np.max(np.abs(np.array(z) - np.array(zb))) < 1e-14, (k, z, zb)
 
 
@@ -53,12 +53,12 @@ def test_tail_walks_estimate_the_remainder(oracle_walks):
     S = power.power_method(n, rp, col, C)
     D = power.exact_diagonal(n, rp, col, C, S)
     din = np.diff(rp)
-    ks = [int(k) for k in np.nonzero(din >= 2)[0][:6]]
+    ks = [int(k) for k in np.nonzero(din >= 2)[0][:8]]
     R = np.zeros(n, dtype=np.uint64)
     depth = np.zeros(n, dtype=np.uint8)
     zsum = np.zeros(n)
     for i, k in enumerate(ks):
-        d = 1 + i  # depths 1..6
+        d = 1 + i  # depths 1..8
         depth[k] = d
         R[k] = 300_000
         zsum[k] = sum(a3.first_meeting_lemma5(n, rp, col, k, C, d))
