@@ -252,7 +252,8 @@ def test_alg3_with_basic_allocation_and_fp32c(esim, oracle_walks):
     g.close()
 
 
-@pytest.mark.parametrize("overlap,early", [(0, 1e30), (4, 1e30), (4, 1.0), (2, 1e4)])
+# (2, 1.5e6) splits the exploited nodes of each source between the early and the main stream
+@pytest.mark.parametrize("overlap,early", [(0, 1e30), (4, 1e30), (4, 1.0), (2, 1.5e6)])
 def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, early):
     """The walks split over the side stream (non-candidates), the early stream (each
     planned candidate) and the main stream give the oracle's counts and scores."""
@@ -273,6 +274,9 @@ def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, ea
         assert np.max(np.abs(s - q.s)) <= TOL
         if overlap and early <= 1.0:
             assert st["early_launches"] == st["alg3_nodes"] > 0
+        if overlap and early == 1.5e6:  # exploited R(k) of these sources lie on both sides of 1.5e6
+            n_early = int(np.count_nonzero(q.R[q.depth > 0] >= early))
+            assert 0 < st["early_launches"] == n_early < st["alg3_nodes"]
         checked += 1
     assert checked >= 2
     g.close()
