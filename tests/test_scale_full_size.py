@@ -1,0 +1,191 @@
+"""GPU parity at the full size of the timed workload: the directed Chung-Lu graph with
+n = 100,000, m = 1,000,000 (gamma 2.1, graph seed 1), c = 0.6, eps = 1e-6 (L = 29),
+kappa = 4 with Algorithm 3, top-50, on the sources that bench.py times.
+
+A whole query is out of the oracle's reach at this size (Algorithm 2 alone would draw
+2.5e12 walk pairs), so each step is checked against the oracle where it can compute
+the step, and the whole query through properties that hold at any size:
+
+* forward sweeps (Algorithm 1, L = 29) within 1e-12; pi, R(k) and offsets bit for bit;
+* the walk-pair sampler, Algorithm 2's and Algorithm 3's depth form, bit for bit on a
+  sample of nodes with their R(k) of this query.  The walk spec keys a pair by
+  (seed, k, r), so a node's counts do not depend on which other nodes are walked;
+* Z_1..Z_d of heavy nodes (Lemma 5) within 1e-12; reverse sweeps within 1e-12 on a
+  given D; top-k selection exact;
+* the whole query in the timed configuration: its top-k is the top-k of its scores;
+  L and R_b; Algorithm 3 draws fewer pairs than Algorithm 2 would; s(u, u) lies
+  within 3 eps of S(u, u) = 1 (Theorem 1: truncation at most c^(L+1) <= eps/2, and
+  the sampling sigma of this entry is below 4e-7 at kappa = 4); and the convergence
+  check of the paper's large-graph experiments (Sec. 4): every node of the top-50
+  at 10 eps scores, at eps, within 2 (10 eps + eps) of the 50th best.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import alg3 as a3
+from oracle import linearization as lin
+
+pytestmark = pytest.mark.gpu
+
+C = 0.6
+EPS = 1e-6
+KAPPA = 4.0
+K = 50
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for gpu tests")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def esim(torch_cuda):
+    import paper_2004_03493_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def workload(esim):
+    n, rp, col = synth.chung_lu(100_000, 1_000_000, gamma=2.1, seed=1)
+    srcs = [int(x) for x in synth.random_sources(rp, 10, seed=7)]
+    g = esim.Graph(n, rp, col, kappa=KAPPA, alg3=1)
+    yield (n, rp, col), srcs, g
+    g.close()
+
+
+def _dev(torch, arr):
+    return torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+
+
+def _u64(torch, n):
+    return torch.zeros(n, dtype=torch.uint64, device="cuda")
+
+
+def _offsets(R):
+    return np.concatenate([[0], np.cumsum(R, dtype=np.uint64)]).astype(np.uint64)
+
+
+def test_forward_and_allocation_at_full_size(torch_cuda, workload):
+    torch = torch_cuda
+    (n, rp, col), srcs, g = workload
+    L = lin.levels(C, EPS)
+    assert L == 29
+    R_b = lin.sample_base(n, C, EPS, KAPPA)
+    for u in srcs[:2]:
+        H = lin.hop_vectors(n, rp, col, u, C, L)
+        hist = torch.full(((L + 1) * n,), float("nan"), dtype=torch.float64, device="cuda")
+        g.forward(u, C, L, hist)
+        g.sync()
+        assert np.max(np.abs(hist.view(L + 1, n).cpu().numpy() - H)) <= TOL
+        # the allocation from the oracle's history: the same FP64 operations on both sides
+        pi_ref = lin.ppr(H)
+        pi = torch.empty(n, dtype=torch.float64, device="cuda")
+        R = _u64(torch, n)
+        off = _u64(torch, n + 1)
+        g.allocate(_dev(torch, H.reshape(-1)), L, R_b, 0, pi, R, off)
+        g.sync()
+        assert np.array_equal(pi.cpu().numpy(), pi_ref)
+        R_ref = lin.allocate(pi_ref, R_b, "pi2")
+        assert np.array_equal(R.cpu().numpy(), R_ref)
+        assert np.array_equal(off.cpu().numpy(), _offsets(R_ref))
+
+
+def test_sampler_on_sampled_nodes_at_full_size(torch_cuda, workload, oracle_walks):
+    torch = torch_cuda
+    (n, rp, col), srcs, g = workload
+    L = lin.levels(C, EPS)
+    R_full = lin.allocate(lin.ppr(lin.hop_vectors(n, rp, col, srcs[0], C, L)), lin.sample_base(n, C, EPS, KAPPA),
+                          "pi2")
+    rng = np.random.default_rng(31)
+    light = np.nonzero((R_full > 0) & (R_full <= 200_000))[0]
+    mid = np.nonzero((R_full > 1000) & (R_full <= 200_000))[0]
+    heavy = np.nonzero((R_full > 200_000) & (R_full <= 5_000_000))[0]  # pairs spread over many threads
+    picks = np.unique(np.concatenate([rng.choice(light, size=48, replace=False),
+                                      rng.choice(mid, size=16, replace=False),
+                                      rng.choice(heavy, size=4, replace=False)]))
+    R = np.zeros(n, dtype=np.uint64)
+    R[picks] = R_full[picks]
+    off = _offsets(R)
+    for seed in (0, 7, 2 ** 63 + 1):  # 7: the seed of one timed step
+        ref, steps_ref = oracle_walks.walk_pairs(n, rp, col, R, C, seed)
+        nonmeet = _u64(torch, n)
+        steps = _u64(torch, 1)
+        g.sample(_dev(torch, off), C, seed, nonmeet, steps)
+        g.sync()
+        assert np.array_equal(nonmeet.cpu().numpy(), ref)
+        assert int(steps.cpu().numpy()[0]) == steps_ref
+    # Algorithm 3's form: depth d gives d forced non-stop steps, then the tail walk
+    depth = np.zeros(n, dtype=np.uint8)
+    depth[picks] = rng.integers(0, 9, size=picks.size).astype(np.uint8)
+    ref, steps_ref = oracle_walks.walk_pairs_depth(n, rp, col, R, depth, C, 3)
+    counts = _u64(torch, n)
+    steps = _u64(torch, 1)
+    g.sample_depth(_dev(torch, off), _dev(torch, depth), C, 3, counts, steps)
+    g.sync()
+    assert np.array_equal(counts.cpu().numpy(), ref)
+    assert int(steps.cpu().numpy()[0]) == steps_ref
+
+
+def test_first_meetings_of_heavy_nodes_at_full_size(workload):
+    (n, rp, col), srcs, g = workload
+    # among the 16 largest pi of the first timed source: its own node (din 14, supports
+    # 1, 14, 83, 1731 over three steps) and two hubs of smaller reach; depth 3 is the
+    # first with Lemma 5's l' >= 2 terms
+    for k, d in ((srcs[0], 3), (24958, 3), (39246, 4)):
+        ref = a3.first_meeting_lemma5(n, rp, col, k, C, d)
+        z = g.alg3_first_meeting(k, d, C)
+        assert z.shape == (d,)
+        assert np.max(np.abs(z - np.array(ref))) <= TOL, (k, d, z, ref)
+
+
+def test_reverse_and_topk_at_full_size(torch_cuda, workload):
+    torch = torch_cuda
+    (n, rp, col), srcs, g = workload
+    L = lin.levels(C, EPS)
+    H = lin.hop_vectors(n, rp, col, srcs[1], C, L)
+    D = synth.uniform_diagonal(n, C, seed=3)
+    s_ref = lin.reverse(n, rp, col, H, D, C)
+    s = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    g.reverse(_dev(torch, H.reshape(-1)), L, C, _dev(torch, D), s)
+    g.sync()
+    assert np.max(np.abs(s.cpu().numpy() - s_ref)) <= TOL
+    ids_ref, vals_ref = lin.topk(s_ref, K, exclude=srcs[1])
+    ids = torch.empty(K, dtype=torch.int32, device="cuda")
+    vals = torch.empty(K, dtype=torch.float64, device="cuda")
+    g.select_topk(_dev(torch, s_ref), srcs[1], K, ids, vals)
+    g.sync()
+    assert np.array_equal(ids.cpu().numpy(), ids_ref)
+    assert np.array_equal(vals.cpu().numpy(), vals_ref)
+
+
+def test_timed_configuration_query_properties(workload):
+    (n, rp, col), srcs, g = workload
+    L = lin.levels(C, EPS)
+    for i, u in enumerate(srcs[:2]):
+        s = g.query(u, C, EPS, i)
+        st = g.stats()
+        assert st["L"] == L
+        assert st["R_b"] == pytest.approx(lin.sample_base(n, C, EPS, KAPPA), rel=1e-15)
+        assert st["alg3_nodes"] >= 1
+        R2 = lin.allocate(lin.ppr(lin.hop_vectors(n, rp, col, u, C, L)), st["R_b"], "pi2")
+        assert st["sum_R"] < int(R2.sum())  # Algorithm 3 replaces most of Algorithm 2's pairs
+        assert st["pair_steps"] >= st["sum_R"]  # every pair takes at least one step
+        assert np.all(np.isfinite(s))
+        assert abs(s[u] - 1.0) <= 3 * EPS, s[u]
+        # the timed call (top-k, host buffers) returns the top-k of the same scores
+        ids, vals = g.topk(u, C, EPS, K, i)
+        ids_ref, vals_ref = lin.topk(s, K, exclude=u)
+        assert np.array_equal(ids, ids_ref) and np.array_equal(vals, vals_ref)
+        # convergence: the top-50 at 10 eps against the scores at eps.  If both are
+        # within their eps of S, a node of the coarse top-50 scores at least the 50th
+        # best fine score minus 2 (10 eps + eps)
+        coarse_ids, _ = g.topk(u, C, 10 * EPS, K, i + 100)
+        fine = np.delete(s, u)
+        t50 = np.sort(fine)[::-1][K - 1]
+        assert np.all(s[coarse_ids] >= t50 - 2 * (10 * EPS + EPS))
