@@ -324,7 +324,11 @@ esim_status esim_allocate(esim_graph* g, const double* hist, int32_t L, double R
 /* Walk pairs (Algorithm 2): nonmeet[n] (uint64) receives, for each k, how many
  * of its off[k+1] - off[k] pairs never meet.  pair_steps (one uint64, may be
  * NULL) receives the number of Philox calls.  If off[n] exceeds the option
- * "pair_budget" no walk runs and esim_sync returns ESIM_EBUDGET. */
+ * "pair_budget" no walk runs and esim_sync returns ESIM_EBUDGET.
+ * off[n+1] must be nondecreasing with off[0] = 0, as esim_allocate writes it.  The
+ * library does not check this on the device: other arrays give undefined results,
+ * including reads past the end of off.  The same holds for every step call below
+ * that takes off. */
 esim_status esim_sample(esim_graph* g, const uint64_t* off, double c, uint64_t seed, uint64_t* nonmeet,
                         uint64_t* pair_steps);
 
