@@ -121,3 +121,23 @@ def test_alg3_depth_choice_matches_the_oracle(native):
     # invalid arguments
     assert native.esim_alg3_depth(1e9, 1.5, [1, 2, 3], 3, n, m) == -1
     assert native.esim_alg3_depth(1e9, 0.6, [1, 2, 3], 17, n, m) == -1
+
+
+def test_no_cpu_fallback_without_a_device(native):
+    """Without a usable CUDA device the device calls report ESIM_ECUDA: no call computes
+    on the CPU instead."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    n, rp, col = synth.erdos_renyi(50, 200, seed=1)
+    with pytest.raises(native.EsimError) as e:
+        native.esim_load_graph(n, rp, col)
+    assert e.value.status == -3
+
+
+def test_missing_library_raises(native, monkeypatch):
+    """The binding refuses to run when the CUDA library was not built."""
+    monkeypatch.setattr(native, "_lib", None)
+    monkeypatch.setattr(native, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libexactsim.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        native.lib()
