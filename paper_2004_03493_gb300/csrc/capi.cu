@@ -111,7 +111,11 @@ esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::ve
 
 void release(Graph& g) {
     cudaSetDevice(g.device);
+    // no work of this handle may still use its buffers: its own streams drain first (a
+    // caller's stream set by esim_set_stream is the caller's to drain)
     if (g.own_stream) cudaStreamSynchronize(g.own_stream);
+    if (g.side_stream) cudaStreamSynchronize(g.side_stream);
+    if (g.early_stream) cudaStreamSynchronize(g.early_stream);
     free_csr(g.in);
     free_csr(g.out);
     cudaFree(g.inv_din);
@@ -127,20 +131,14 @@ void release(Graph& g) {
     for (auto& ev : g.ev)
         if (ev) cudaEventDestroy(ev);
     if (g.own_stream) cudaStreamDestroy(g.own_stream);
-    if (g.side_stream) {
-        cudaStreamSynchronize(g.side_stream);
-        cudaStreamDestroy(g.side_stream);
-    }
+    if (g.side_stream) cudaStreamDestroy(g.side_stream);
     for (auto& ev : g.side_ev)
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : g.side_tev)
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : g.early_tev)
         if (ev) cudaEventDestroy(ev);
-    if (g.early_stream) {
-        cudaStreamSynchronize(g.early_stream);
-        cudaStreamDestroy(g.early_stream);
-    }
+    if (g.early_stream) cudaStreamDestroy(g.early_stream);
     if (g.early_ev) cudaEventDestroy(g.early_ev);
     g = Graph{};
 }
