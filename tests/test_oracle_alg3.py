@@ -128,3 +128,80 @@ def test_alg3_query_within_eps_of_power_method(oracle_walks):
         q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=2000.0, alg3=True, alg3_min_pairs=1e3)
         assert np.count_nonzero(q.depth) > 0 and q.depth.max() >= 3
         assert np.max(np.abs(q.s - S[:, u])) <= eps
+
+
+def _lemma5_gap(g, depth=5):
+    """Largest |Lemma 5 - rational brute force| over the nodes of a small graph."""
+    nn, rp, col = g
+    din = np.diff(rp)
+    gap = 0.0
+    for k in range(nn):
+        if din[k] == 0:
+            continue
+        z = a3.first_meeting_lemma5(nn, rp, col, k, C, depth)
+        zb = [float(x) for x in a3.first_meeting_bruteforce(nn, rp, col, k, Fraction(3, 5), depth)]
+        gap = max(gap, float(np.max(np.abs(np.array(z) - np.array(zb)))))
+    return gap
+
+
+def test_planted_mistakes_in_lemma5_are_caught(monkeypatch):
+    """Plausible mistakes planted in the oracle's Lemma 5 fail the brute-force pin."""
+    g = synth.random_small(7, p=0.45, seed=1)
+    assert _lemma5_gap(g) < 1e-14
+    true_walk = a3.walk_distribution
+    # (1) a transposed operand: the walks follow out-edges instead of in-edges
+    true_tm = a3.transition_matrix
+    monkeypatch.setattr(a3, "transition_matrix", lambda *args: true_tm(*args).T.tocsr())
+    assert _lemma5_gap(g) > 1e-3
+    monkeypatch.setattr(a3, "transition_matrix", true_tm)
+    # (2) the l' >= 2 terms dropped: every walk distribution but the source's loses its
+    # steps beyond the first
+    calls = {"n": 0}
+
+    def truncated(P, k, steps):
+        H = true_walk(P, k, steps)
+        calls["n"] += 1
+        if calls["n"] > 1:
+            H[2:] = 0.0
+        return H
+
+    def per_node(*args, **kw):
+        calls["n"] = 0
+        return lemma5(*args, **kw)
+
+    lemma5 = a3.first_meeting_lemma5
+    monkeypatch.setattr(a3, "walk_distribution", truncated)
+    monkeypatch.setattr(a3, "first_meeting_lemma5", per_node)
+    assert _lemma5_gap(g) > 1e-4
+    monkeypatch.setattr(a3, "first_meeting_lemma5", lemma5)
+    # (3) one step off: the distributions of the meeting terms taken a step early
+    monkeypatch.setattr(a3, "walk_distribution",
+                        lambda P, k, steps: np.vstack([true_walk(P, k, steps)[:1], true_walk(P, k, steps)[:-1]]))
+    assert _lemma5_gap(g) > 1e-3
+
+
+def test_planted_sign_in_the_tail_estimator_is_caught(oracle_walks):
+    """D^ = 1 - sum Z - c^d tail/R (Algorithm 3); with the tail term's sign flipped the
+    z-test against the Power Method's D fails."""
+    g = synth.chung_lu(60, 500, gamma=2.1, seed=6)
+    n, rp, col = g
+    S = power.power_method(n, rp, col, C)
+    D = power.exact_diagonal(n, rp, col, C, S)
+    din = np.diff(rp)
+    ks = [int(k) for k in np.nonzero(din >= 2)[0][:4]]
+    R = np.zeros(n, dtype=np.uint64)
+    depth = np.zeros(n, dtype=np.uint8)
+    zsum = np.zeros(n)
+    for k in ks:
+        depth[k] = 1
+        R[k] = 300_000
+        zsum[k] = sum(a3.first_meeting_lemma5(n, rp, col, k, C, 1))
+    counts, _ = oracle_walks.walk_pairs_depth(n, rp, col, R, depth, C, seed=3)
+    right = a3.dhat_alg3(counts, R, depth, zsum, din, C)
+    tail = C * counts.astype(np.float64) / np.maximum(R, 1).astype(np.float64)
+    wrong = np.where(depth > 0, 1.0 - zsum + tail, right)
+    for k in ks:
+        p = (1 - D[k] - zsum[k]) / C
+        sd = C * np.sqrt(max(p * (1 - p), 1e-300) / 300_000)
+        assert abs(right[k] - D[k]) < 5 * sd + 1e-12
+        assert abs(wrong[k] - D[k]) > 5 * sd
