@@ -92,3 +92,18 @@ def test_parsim_diagonal():
     assert np.max(np.abs(D - (1 - C))) > 0.05
     q = exactsim.query(n, rp, col, 0, C, 1e-4, diag="parsim")
     assert np.max(np.abs(q.s - S[:, 0])) > 1e-3
+
+
+def test_planted_threshold_without_the_square_factor_is_caught():
+    """A threshold of eps (the (1 - sqrt c)^2 factor dropped) breaks the lemma's bound."""
+    n, rp, col = synth.chung_lu(300, 2400, gamma=2.1, seed=12)
+    S = power.power_method(n, rp, col, C)
+    D = power.exact_diagonal(n, rp, col, C, S)
+    eps = 3e-3
+    L = lin.levels(C, eps)
+    worst = 0.0
+    for u in (0, 17, 123):
+        H = lin.hop_vectors(n, rp, col, u, C, L)
+        dense = lin.reverse(n, rp, col, H, D, C)
+        worst = max(worst, float(np.max(dense - lin.reverse(n, rp, col, lin.sparsify(H, eps), D, C))))
+    assert worst > eps
