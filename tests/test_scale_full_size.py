@@ -14,8 +14,9 @@ the step, and the whole query through properties that hold at any size:
   given D; top-k selection exact;
 * the whole query in the timed configuration: its top-k is the top-k of its scores;
   L and R_b; Algorithm 3 draws fewer pairs than Algorithm 2 would; s(u, u) lies
-  within 3 eps of S(u, u) = 1 (Theorem 1: truncation at most c^(L+1) <= eps/2, and
-  the sampling sigma of this entry is below 4e-7 at kappa = 4); and the convergence
+  within 3 eps of S(u, u) = 1 (the levels beyond L add at most c^(L+1)/(1-c) = 5.5e-7,
+  and Lemma 2 bounds the sampling sigma of this entry below 4e-7 at kappa = 4, so the
+  margin is above 7 sigma); and the convergence
   check of the paper's large-graph experiments (Sec. 4): every node of the top-50
   at 10 eps scores, at eps, within 2 (10 eps + eps) of the 50th best.
 """
