@@ -34,3 +34,24 @@ def test_cpu_exactsim_power_law_graph(oracle_walks):
     u = int(synth.random_sources(rp, 1, seed=3)[0])
     q = exactsim.query(n, rp, col, u, C, eps, seed=7)
     assert np.max(np.abs(q.s - S[:, u])) <= eps
+
+
+def test_lemma2_variance_bound_holds_empirically(oracle_walks):
+    """Lemma 2 with the pi^2 allocation bounds Var s(v) by ||pi_v||^2 / (4 a^4 R_b)
+    (a = 1 - sqrt c): the bound the benchmark reports as its sampling sigma.  The
+    variance over 200 seeds stays under it, and is not zero (the test has power)."""
+    from oracle import linearization as lin
+    n, rp, col = synth.chung_lu(300, 2400, gamma=2.1, seed=12)
+    u, eps, kappa = 5, 1e-2, 0.5
+    a = 1.0 - np.sqrt(C)
+    runs = np.array([exactsim.query(n, rp, col, u, C, eps, seed=s, kappa=kappa).s for s in range(200)])
+    R_b = lin.sample_base(n, C, eps, kappa)
+    L = lin.levels(C, eps)
+    var = runs.var(axis=0, ddof=1)
+    checked = 0
+    for v in [u] + [int(x) for x in np.argsort(-runs.mean(axis=0))[1:6]]:
+        norm_v = float(np.sum(lin.ppr(lin.hop_vectors(n, rp, col, v, C, L)) ** 2))
+        bound = norm_v / (4 * a ** 4 * R_b)
+        assert 0 < var[v] <= 1.3 * bound, (v, var[v], bound)
+        checked += 1
+    assert checked == 6
