@@ -55,3 +55,22 @@ def test_lemma2_variance_bound_holds_empirically(oracle_walks):
         assert 0 < var[v] <= 1.3 * bound, (v, var[v], bound)
         checked += 1
     assert checked == 6
+
+
+def test_topk_convergence_protocol_against_the_power_method(oracle_walks):
+    """The top-k check the large-graph tests use (Sec. 4): with both queries within their
+    eps, every node of the top-k at the coarse eps scores, in the fine query, at least the
+    fine k-th best minus 2 (eps_c + eps_f); against the exact S, every returned node has
+    S(u, v) >= S_k - 2 eps_c (Precision@k up to ties within the error)."""
+    from oracle import linearization as lin
+    n, rp, col = synth.chung_lu(400, 4000, gamma=2.1, seed=13)
+    S = power.power_method(n, rp, col, C)
+    k, eps_c, eps_f = 20, 1e-2, 1e-3
+    for u in [int(x) for x in synth.random_sources(rp, 3, seed=5)]:
+        coarse = exactsim.query(n, rp, col, u, C, eps_c, seed=1, kappa=16.0).s
+        fine = exactsim.query(n, rp, col, u, C, eps_f, seed=2, kappa=16.0).s
+        ids, _ = lin.topk(coarse, k, exclude=u)
+        t_fine = np.sort(np.delete(fine, u))[::-1][k - 1]
+        assert np.all(fine[ids] >= t_fine - 2 * (eps_c + eps_f))
+        s_k = np.sort(np.delete(S[:, u], u))[::-1][k - 1]
+        assert np.all(S[ids, u] >= s_k - 2 * eps_c)
