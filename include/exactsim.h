@@ -316,8 +316,9 @@ esim_status esim_forward(esim_graph* g, int64_t u, double c, int32_t L, double* 
 /* Allocation (Lemma 4 / Algorithm 1): pi(k) = sum_{l=0..L} hist[l*n + k] added in
  * level order; R(k) = ceil(R_b * (pi(k) * pi(k))) (mode 0) or ceil(R_b * pi(k))
  * (mode 1); off[0] = 0, off[k+1] = off[k] + R(k).  pi_out may be NULL.
- * R_out[n], off[n+1] (uint64).  A value of R_b * pi^2 at or above 2^63 makes
- * esim_sync return ESIM_EBUDGET. */
+ * R_out[n], off[n+1] (uint64).  With option "alg3" = 1 the nodes with din <= 1 get
+ * R(k) = 0 (Algorithm 3 gives their D exactly: 1 at din 0, 1-c at din 1).  A value of
+ * R_b * pi^2 at or above 2^63 makes esim_sync return ESIM_EBUDGET. */
 esim_status esim_allocate(esim_graph* g, const double* hist, int32_t L, double R_b, int32_t mode,
                           double* pi_out, uint64_t* R_out, uint64_t* off);
 
@@ -393,7 +394,9 @@ esim_status esim_select_topk(esim_graph* g, const double* scores, int64_t exclud
  * and 4096 candidates), resident on every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current); make that first call before
- * any stream capture.  All calls share the array: calls whose work overlaps on
+ * any stream capture.  The address is kept with the id of the CUDA context it was
+ * taken in; after a device reset (a new context) the next call looks it up again.
+ * All calls share the array: calls whose work overlaps on
  * the GPU race and must be serialised by the caller.  Limits: 1 <= k <= 4096
  * (ESIM_ENOTSUP above), 1 <= n < 2^31.  Calls no cudaMalloc or cudaFree. */
 esim_status esim_select_topk_static(const double* scores, int64_t n, int64_t exclude, int32_t k, int32_t* ids_out,

@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "exactsim.h"
+#include <cuda.h>
 
 #include <mutex>
 #include <string>
@@ -286,9 +287,12 @@ cudaError_t launch_topk_batch(const Graph& g, int32_t B, const double* scores, c
 // silently use the wrong memory.  The device address is taken once per device
 // with cudaGetSymbolAddress (the first call on a device does this, with that
 // device current; make that first call before any stream capture) and passed to
-// the kernels.  All calls share the array and it keeps the last call's contents;
-// topk_init_kernel clears the state every call.  Calls whose work overlaps on the
-// GPU (different streams, or several host threads) race on the array.
+// the kernels.  The address is remembered together with the unique id of the CUDA
+// context it was taken in: after a device reset the device has a new context (and
+// the array a new address), so the next call takes the address again.  All calls
+// share the array and it keeps the last call's contents; topk_init_kernel clears
+// the state every call.  Calls whose work overlaps on the GPU (different streams,
+// or several host threads) race on the array.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -302,19 +306,58 @@ constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
 int g_static_sms[kStaticMaxDevices] = {};
+unsigned long long g_static_ctx[kStaticMaxDevices] = {};  // context id the address belongs to
 
-// Device address of the scratch array and the SM count of the current device.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the CUDA context current on this thread, from the driver's entry points.
+// With no context current yet, the device's primary context is made current first (the
+// context the runtime would use); a context the caller made current is left alone.
+cudaError_t current_context_id(int dev, unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorNotSupported;
+        get_current = (CtxGetCurrentFn)f0;
+        get_id = (CtxGetIdFn)f1;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) {
+        cudaError_t e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    }
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of the scratch array and the SM count of the current device, taken
+// again whenever the device's context differs from the one they were taken in.
 cudaError_t static_scratch(int dev, void** ptr, int* sms) {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    unsigned long long ctx = 0;
+    cudaError_t e = current_context_id(dev, &ctx);
+    if (e != cudaSuccess) return e;
+    if (!g_static_ptr[dev] || g_static_ctx[dev] != ctx) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_topk_static_scratch);
+        e = cudaGetSymbolAddress(&p, g_topk_static_scratch);
         if (e != cudaSuccess) return e;
         int s = 0;
         e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         g_static_sms[dev] = s;
         g_static_ptr[dev] = p;
+        g_static_ctx[dev] = ctx;
     }
     *ptr = g_static_ptr[dev];
     *sms = g_static_sms[dev];
