@@ -53,7 +53,7 @@ WORKLOADS = {
     "rmat25": dict(kind="rmat_torch", scale=25, n=1 << 25, m=500_000_000, graph_seed=1, c=0.6,
                    eps_set=(1e-5, 1e-6, 1e-7), eps=1e-6, sources=4096, source_seed=7, k=100),
     # precision form: FP32c against FP64 sweeps on the same sources and the same D^
-    "cl4m": dict(kind="chung_lu", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
+    "cl4m": dict(kind="chung_lu_torch", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
                  sources=4, source_seed=7, k=50),
 }
 METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6, top-50)"
@@ -61,10 +61,9 @@ METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6,
 # multiplies + 2 three-input XORs); step logic = 2 threshold compares, 2 multiply-shift picks,
 # 2 row loads, 2 neighbour loads
 INSTR_PER_PAIR_STEP = 48.0
-# DRAM bytes per sampler launch from the ncu capture named in profiles/ (None once the kernel changes):
-# dram__bytes_read.sum + dram__bytes_write.sum of the bench query's sampler launch, 6.63 MB read and
-# 0 B written; the graph stays in L2, so this is its compulsory read
-KERNEL_TRAFFIC = {"sample_pairs_kernel": 6.63e6}
+# Accuracy of the timed configuration, measured by tests/test_gpu_exceed.py (the same options
+# on the n = 2e4 graph of the same recipe, against the Power Method); filled from its GB300 run
+ACCURACY = None
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -86,6 +85,8 @@ def make_graph(w):
         return synth.rmat_torch(w["scale"], w["m"], seed=w["graph_seed"], device="cuda")
     if w["kind"] == "chung_lu":
         return synth.chung_lu(w["n"], w["m"], gamma=w["gamma"], seed=w["graph_seed"])
+    if w["kind"] == "chung_lu_torch":
+        return synth.chung_lu_torch(w["n"], w["m"], gamma=w["gamma"], seed=w["graph_seed"], device="cuda")
     return synth.erdos_renyi(w["n"], w["m"], seed=w["graph_seed"])
 
 
@@ -175,9 +176,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0, alg3=False, z_budget_s=20.0):
-    """Time one bounded sample of the CPU oracle query; return (seconds per full query, info)."""
-    from oracle import alg3 as a3
+def cpu_oracle_step(w, n, rp, col, u, kappa, pair_cap, threads=0):
+    """One bounded sample of the CPU oracle's query for source u; returns (seconds of the
+    sample, estimated seconds of the full query, info).
+
+    The oracle runs Algorithm 1 with Algorithm 2 (its Algorithm 3 follows the paper's
+    adaptive depth, whose exploration costs at least as much as the walks it replaces
+    and keeps n x n supports: out of a CPU's reach at this size): forward sweeps, the
+    allocation, reverse sweeps and top-k in full; the walk pairs on a sample of
+    pair_cap pairs in the same per-node proportions.  Walk time is linear in the number
+    of pairs, so the full query is estimated as the rest plus the sampled walk time
+    times (all pairs / sampled pairs).
+    """
     from oracle import linearization as lin
     from oracle import walks
     c, eps = w["c"], w["eps"]
@@ -186,61 +196,67 @@ def cpu_reference_sample(w, n, rp, col, u, kappa, pair_cap, threads=0, alg3=Fals
     H = lin.hop_vectors(n, rp, col, u, c, L)
     pi = lin.ppr(H)
     R_b = lin.sample_base(n, c, eps, kappa)
-    depth = None
-    z_note = ""
-    if alg3:
-        depth, R = a3.exploitation_plan(n, rp, col, pi, R_b, c)
-        # Lemma 5 term by term grows with the supports of the walk distributions; time the
-        # exploited nodes in increasing order of that work (walk distributions of
-        # sum_i |supp h_i| (d - i) probes) until z_budget_s, then scale by the work left
-        P = a3.transition_matrix(n, rp, col)
-        work = {}
-        for k in np.nonzero(depth)[0]:
-            d = int(depth[k])
-            supp = a3.supports(P, int(k), max(0, d - 2))
-            work[int(k)] = 2 * d - 1 + sum(supp[i] * (d - i) for i in range(1, d - 1))
-        t_z0 = time.perf_counter()
-        done = 0
-        for k in sorted(work, key=lambda x: (work[x], x)):
-            spent = time.perf_counter() - t_z0
-            # a node's Lemma 5 cannot be stopped half-way: start the next one only while its
-            # time, estimated from the work timed so far, fits in what is left of the budget
-            if done and spent + spent / done * work[k] > z_budget_s:
-                break
-            sum(a3.first_meeting_lemma5(n, rp, col, k, c, int(depth[k])))
-            done += work[k]
-        t_z = time.perf_counter() - t_z0
-        total_work = sum(work.values())
-        if done < total_work:
-            t0 -= t_z * (total_work / max(done, 1) - 1.0)  # scale the Lemma 5 time to all nodes
-            z_note = f"; Lemma 5 for {done / total_work:.2g} of the exploitation work, time scaled"
-    else:
-        R = lin.allocate(pi, R_b, "pi2")
-    t_sweep_fwd = time.perf_counter() - t0
+    R = lin.allocate(pi, R_b, "pi2")
+    t_fwd = time.perf_counter() - t0
     total = int(R.sum())
-    # bounded sample of the walk pairs: the same per-node proportions, scaled down
     scale = min(1.0, pair_cap / max(total, 1))
     R_s = np.floor(R.astype(np.float64) * scale).astype(np.uint64)
     t1 = time.perf_counter()
-    if alg3:
-        nonmeet, steps = walks.walk_pairs_depth(n, rp, col, R_s, depth, c, 1, threads)
-    else:
-        nonmeet, steps = walks.walk_pairs(n, rp, col, R_s, c, 1, threads)
+    nonmeet, _ = walks.walk_pairs(n, rp, col, R_s, c, 1, threads)
     t_walk = time.perf_counter() - t1
-    D = lin.dhat(nonmeet, R_s)
     t2 = time.perf_counter()
+    D = lin.dhat(nonmeet, R_s)
     s = lin.reverse(n, rp, col, H, D, c)
     lin.topk(s, w["k"], exclude=u)
     t_rev = time.perf_counter() - t2
     sampled = int(R_s.sum())
-    walk_full = t_walk * (total / max(sampled, 1))
-    return t_sweep_fwd + walk_full + t_rev, {"pairs_total": total, "pairs_sampled": sampled,
-                                             "t_sweeps_s": t_sweep_fwd + t_rev, "t_walk_sample_s": t_walk,
-                                             "z_note": z_note}
+    factor = total / max(sampled, 1)
+    t_step = t_fwd + t_walk + t_rev
+    return t_step, t_fwd + t_rev + t_walk * factor, {"pairs_total": total, "pairs_sampled": sampled,
+                                                     "walk_scale": factor, "t_sweeps_s": t_fwd + t_rev,
+                                                     "t_walk_sample_s": t_walk}
+
+
+def cpu_oracle_scaling_check(w, n, rp, col, u, pair_cap, threads=0):
+    """A whole oracle query with no sampling (kappa small enough that all its walk pairs
+    are pair_cap), against the estimate from a tenth of its pairs: the check that the
+    sampled walk time scales linearly."""
+    from oracle import linearization as lin
+    c, eps = w["c"], w["eps"]
+    L = lin.levels(c, eps)
+    pi = lin.ppr(lin.hop_vectors(n, rp, col, u, c, L))
+    norm_R = float(lin.allocate(pi, lin.sample_base(n, c, eps, 1.0), "pi2").sum())
+    kappa = pair_cap / norm_R  # about pair_cap pairs in all
+    t_full, est_full, info = cpu_oracle_step(w, n, rp, col, u, kappa, 1e30, threads)
+    _, est, info_s = cpu_oracle_step(w, n, rp, col, u, kappa, info["pairs_total"] / 10.0, threads)
+    return {"kappa": kappa, "pairs": info["pairs_total"], "measured_full_s": t_full,
+            "estimated_from_tenth_s": est, "ratio": est / t_full}
+
+
+def cpu_baseline_of(w, n, rp, col, srcs, kappa, pair_cap):
+    """The oracle timed on the host cores over the workload's sources, one bounded sample
+    each: (queries/s of the estimated full queries, seconds of the samples, cores, info)."""
+    from oracle import walks
+    walks.build()
+    t_samples, t_full, infos = [], [], []
+    for u in srcs:
+        ts, tf, info = cpu_oracle_step(w, n, rp, col, u, kappa, pair_cap)
+        t_samples.append(ts)
+        t_full.append(tf)
+        infos.append(info)
+    return len(srcs) / sum(t_full), t_samples, walks.max_threads(), infos
+
+
+def cpu_sample_note(srcs, pair_cap, infos, kappa):
+    scale = statistics.mean(i["walk_scale"] for i in infos)
+    return (f"oracle Algorithm 1 + Algorithm 2 at kappa={kappa:g} (the GPU path's Algorithm 3 only lowers "
+            f"the variance), sources {srcs} one query each: sweeps, allocation, D^ and top-k in full, "
+            f"{pair_cap:.3g} of {statistics.mean(i['pairs_total'] for i in infos):.3g} walk pairs per query on "
+            f"average (same per-node proportions), walk time scaled by {scale:.3g}x to the full pair count")
 
 
 def run_reference(args, w, rank, world):
-    """--impl reference: the CPU oracle on the host cores."""
+    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
     from oracle import walks
@@ -248,27 +264,91 @@ def run_reference(args, w, rank, world):
     n, rp, col = make_graph(w)
     srcs = sources_for(w, rp, 1, 0)
     cores = walks.max_threads()
-    per_query = []
-    info = None
+    t_step, t_full, infos, used = [], [], [], []
     for i in range(args.warmup + args.steps):
         u = srcs[i % len(srcs)]
-        t, info = cpu_reference_sample(w, n, rp, col, u, args.kappa, args.ref_pairs, alg3=bool(args.alg3),
-                                       z_budget_s=6.0)
+        ts, tf, info = cpu_oracle_step(w, n, rp, col, u, args.kappa, args.ref_pairs)
         if i >= args.warmup:
-            per_query.append(t)
-    q_per_s = 1.0 / statistics.mean(per_query)
-    sample = (f"one query per step (sources cycled), all forward/reverse sweeps and allocation in full, "
-              f"{info['pairs_sampled']:.3g} of {info['pairs_total']:.3g} walk pairs (same per-node proportions), "
-              f"walk time scaled to the full pair count{info['z_note']}")
+            t_step.append(ts)
+            t_full.append(tf)
+            infos.append(info)
+            used.append(u)
+    q_per_s = len(t_full) / sum(t_full)
+    check = cpu_oracle_scaling_check(w, n, rp, col, srcs[0], args.ref_pairs)
     line = {
         "impl": "reference", "metric": METRIC, "value": q_per_s, "unit": "queries/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / q_per_s,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(t_step),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args, w),
-        "cpu_baseline": {"value": q_per_s, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": q_per_s, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": cpu_sample_note(used, args.ref_pairs, infos, args.kappa),
+                         "ms_per_full_query_estimated": 1000.0 * statistics.mean(t_full),
+                         "scaling_check": check},
         "e2e": {"value": q_per_s, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "ms_per_step is the measured time of one sample step; value is 1 / the estimated time of the "
+                "full query (scaling_check: a whole unsampled oracle query against its estimate)",
     }
     print(json.dumps(line), flush=True)
+
+
+def sweep_roofline(esim, torch, stream, reps=5):
+    """Sweep HBM GB/s on the directed Chung-Lu graph n = 4e6, m = 7e7 (gamma 2.2), FP64 and
+    FP32c: forward plus reverse sweeps of one query at eps = 1e-7 (L = 33) from a seeded
+    source, timed with CUDA events on the library's stream, D given (its values do not
+    change the sweep's work).  The graph (0.56 GB of CSR, vectors 16-32 MB) is drawn on
+    the GPU; its sweeps read more than L2 holds."""
+    import synth
+    wl = WORKLOADS["cl4m"]
+    t0 = time.perf_counter()
+    n, rp, col = synth.chung_lu_torch(wl["n"], wl["m"], gamma=wl["gamma"], seed=wl["graph_seed"], device="cuda")
+    t_gen = time.perf_counter() - t0
+    m = len(col)
+    c = wl["c"]
+    L = esim.esim_levels(c, wl["eps"])
+    u = int(synth.random_sources(rp, 1, seed=wl["source_seed"])[0])
+    g = esim.Graph(n, rp, col)
+    g.set_stream(stream)
+    del rp, col
+    hist64 = torch.empty((L + 1) * n, dtype=torch.float64, device="cuda")
+    hist32 = torch.empty((L + 1) * n, dtype=torch.float32, device="cuda")
+    dh = torch.from_numpy(synth.uniform_diagonal(n, c, seed=3)).cuda()
+    s64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    s32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    out = {}
+    pk, pk_src = peaks()
+    for prec in ("fp64", "fp32c"):
+        fwd, rev = [], []
+        for i in range(reps + 1):
+            ev[0].record(stream)
+            if prec == "fp64":
+                g.forward(u, c, L, hist64)
+                ev[1].record(stream)
+                g.reverse(hist64, L, c, dh, s64)
+            else:
+                g.forward_f32(u, c, L, hist32)
+                ev[1].record(stream)
+                g.reverse_f32(hist32, L, c, dh, s32)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            if i > 0:  # the first pass warms up
+                fwd.append(ev[0].elapsed_time(ev[1]))
+                rev.append(ev[1].elapsed_time(ev[2]))
+        g.sync()
+        ms = statistics.mean(fwd) + statistics.mean(rev)
+        gbs = L * sweep_level_bytes(n, m, prec) / (ms / 1000.0) / 1e9
+        out[prec] = {"ms_forward": statistics.mean(fwd), "ms_reverse": statistics.mean(rev), "ms_query_sweeps": ms,
+                     "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
+    err = float((s32 - s64).abs().max().item())
+    g.close()
+    del hist64, hist32
+    torch.cuda.empty_cache()
+    return {"graph": f"chung_lu n={n} m={m} gamma={wl['gamma']} (torch generator, seed {wl['graph_seed']})",
+            "L": L, "source": u, "bytes_per_level": {p: sweep_level_bytes(n, m, p) for p in ("fp64", "fp32c")},
+            "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_src, "graph_gen_s": t_gen,
+            "fp64": out["fp64"], "fp32c": out["fp32c"], "max_abs_diff_fp32c_vs_fp64": err,
+            "note": "achieved = compulsory bytes of L forward + L reverse levels / CUDA-event time; "
+                    "frac of the measured copy bandwidth"}
 
 
 def run_precision(args, w):
@@ -512,126 +592,14 @@ def synth_sources(rp, count, seed):
     return synth.random_sources(rp, count, seed=seed)
 
 
-def run_exceed(args, w):
-    """Theorem 1 check: max_v |s(v) - S(u, v)| over many seeds on the small ER workload.
-
-    The Power Method (CPU oracle) gives S; each seed is one GPU query with the
-    stated kappa (the paper's 6/(1-sqrt c)^4 by default).  Reports the exceed rate
-    (fraction of seeds with max error > eps) and the error distribution.
-    """
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2004_03493_gb300 as esim
-    from oracle import power
-    n, rp, col = make_graph(w)
-    c, eps = w["c"], w["eps"]
-    S = power.power_method(n, rp, col, c)
-    g = esim.Graph(n, rp, col, kappa=args.kappa, precision=args.precision, alg3=args.alg3)
-    us = [0] + [int(x) for x in synth_sources(rp, 4, 3)]
-    errs = []
-    t0 = time.perf_counter()
-    for seed in range(args.seeds):
-        u = us[seed % len(us)]
-        s = g.query(u, c, eps, seed)
-        errs.append(float(np.max(np.abs(s - S[:, u]))))
-    wall = time.perf_counter() - t0
-    st = g.stats()
-    errs = np.array(errs)
-    line = {"metric": "exceed rate of max_v |s(v) - S(u,v)| > eps over seeds (Theorem 1)", "value": float(np.mean(errs > eps)),
-            "unit": "fraction", "n_gpus": 1, "higher_is_better": False, "dtype": "f64" if args.precision == 0 else "fp32c",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "graph": w["kind"], "n": n, "m": len(col), "c": c, "eps": eps,
-                       "kappa": args.kappa if args.kappa > 0 else "6/(1-sqrt c)^4", "seeds": args.seeds,
-                       "sources": us, "oracle": "Power Method (FP64 CPU)",
-                       "dhat": "Algorithm 3" if args.alg3 else "Algorithm 2", "alg3_nodes_last": st["alg3_nodes"]},
-            "max_err": {"max": float(errs.max()), "p50": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
-                        "mean": float(errs.mean())},
-            "pairs_per_query": st["sum_R"], "queries_per_s": args.seeds / wall}
-    print(json.dumps(line), flush=True)
-    g.close()
-
-
-ABLATION_VARIANTS = (
-    # name, options: the paper's basic ExactSim, each optimization added in turn, and ParSim
-    ("basic", dict(alloc=1, alg3=0, sparse_hist=0)),
-    ("pi2", dict(alloc=0, alg3=0, sparse_hist=0)),
-    ("pi2+alg3", dict(alloc=0, alg3=1, sparse_hist=0)),
-    ("optimized", dict(alloc=0, alg3=1, sparse_hist=1)),
-    ("parsim", dict(diag=1)),
-)
-
-
-def run_ablation(args, w):
-    """The paper's ablation (Sec. 4): basic vs optimized ExactSim, plus ParSim's D.
-
-    Time/error part: the small ER graph (the Power Method gives S), eps in
-    {1e-2, 1e-3, 1e-4}, five sources, one seeded query each per variant; per
-    variant and eps the median device ms per query, the max error over all
-    nodes and over v != u, and the walk pairs per query.  Memory part: the
-    Chung-Lu n=4e6 graph, one query per eps in {1e-5, 1e-6, 1e-7}: the device
-    workspace of the dense history against the sparse one (the walk count does
-    not change the workspace, so these queries run at kappa = 1e-6).
-    """
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2004_03493_gb300 as esim
-    from oracle import power
-    n, rp, col = make_graph(WORKLOADS["er2000"])
-    c = 0.6
-    S = power.power_method(n, rp, col, c)
-    us = [0] + [int(x) for x in synth_sources(rp, 4, 3)]
-    rows = []
-    for name, opts in ABLATION_VARIANTS:
-        g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, **opts)
-        for eps in (1e-2, 1e-3, 1e-4):
-            g.query(us[0], c, eps, 99)  # warm-up
-            ms, err, err_off, pairs = [], 0.0, 0.0, []
-            for i, u in enumerate(us):
-                s = g.query(u, c, eps, i)
-                st = g.stats()
-                ms.append(st["ms_total"])
-                pairs.append(st["sum_R"])
-                d = np.abs(s - S[:, u])
-                err = max(err, float(d.max()))
-                d[u] = 0.0
-                err_off = max(err_off, float(d.max()))
-            rows.append({"variant": name, "eps": eps, "ms_per_query": float(np.median(ms)), "max_err": err,
-                         "max_err_off_source": err_off, "pairs_per_query": float(np.mean(pairs)),
-                         "within_eps": err <= eps})
-        g.close()
-    wl = WORKLOADS["cl4m"]
-    n4, rp4, col4 = make_graph(wl)
-    u4 = sources_for(wl, rp4, 1, 0)[0]
-    mem = []
-    for sparse in (0, 1):
-        g = esim.Graph(n4, rp4, col4, kappa=1e-6, sparse_hist=sparse, alg3=0)
-        for eps in (1e-5, 1e-6, 1e-7):
-            g.query(u4, c, eps, 0)
-            st = g.stats()
-            mem.append({"sparse_hist": sparse, "eps": eps, "L": st["L"], "hist_entries": st["hist_entries"],
-                        "workspace_bytes": st["workspace_bytes"]})
-        g.close()
-    graph_bytes = 2 * (4 * len(col4) + 4 * (n4 + 1))
-    line = {"metric": "ablation: basic vs optimized ExactSim (time, max error) and history memory",
-            "unit": "rows", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
-            "config": {"time_error_graph": "erdos_renyi n=2000 m=20000", "c": c, "kappa": args.kappa,
-                       "sources": us, "oracle": "Power Method (FP64 CPU)",
-                       "memory_graph": f"chung_lu n={n4} m={len(col4)} gamma=2.2", "memory_source": u4,
-                       "graph_csr_bytes": graph_bytes},
-            "time_error": rows, "memory": mem}
-    print(json.dumps(line), flush=True)
-
-
 def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources": w["sources"], "queries_per_step": 1,
             "top_k": w["k"], "kappa": args.kappa, "alloc": "pi^2 (Lemma 4)",
-            "dhat": ("Algorithm 3 (exact Z_1..Z_d for the 64 heaviest nodes, cost-chosen d <= 8, then tail walk pairs)"
-                     if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
+            "dhat": ("Algorithm 3, the library's cost-model rule (alg3_rule 1): exact Z_1..Z_d for the 64 heaviest "
+                     "nodes at a cost-chosen d <= 8, max(1, ceil(R_b pi^2 c^(2d))) tail walk pairs; the others "
+                     "Algorithm 2" if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
+            "accuracy": ACCURACY,
             "l2": "flushed (512 MB write) before each timed step", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -644,13 +612,10 @@ def main():
     ap.add_argument("--workload", default="cl100k", choices=sorted(WORKLOADS))
     ap.add_argument("--kappa", type=float, default=4.0,
                     help="sample constant: R_b = kappa ln(n) / eps^2 (<= 0: the paper's 6/(1-sqrt c)^4)")
-    ap.add_argument("--ref-pairs", type=float, default=2e8, help="walk pairs per CPU reference sample")
+    ap.add_argument("--ref-pairs", type=float, default=5e7, help="walk pairs per CPU oracle sample")
+    ap.add_argument("--no-sweeps", action="store_true", help="leave out the n=4e6 sweep roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--exceed", action="store_true", help="Theorem 1 exceed rate over --seeds seeds (small workloads)")
-    ap.add_argument("--seeds", type=int, default=100)
     ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
-    ap.add_argument("--ablation", action="store_true",
-                    help="basic vs optimized ExactSim and ParSim: time/error on the small ER graph, memory on cl4m")
     ap.add_argument("--alg3", type=int, default=1,
                     help="1 (default): Algorithm 3 D^ estimator for the heaviest nodes; 0: Algorithm 2 only")
     ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
@@ -676,12 +641,6 @@ def main():
     if args.workload == "rmat25":
         run_serving(args, w)
         return
-    if args.exceed:
-        run_exceed(args, w)
-        return
-    if args.ablation:
-        run_ablation(args, w)
-        return
 
     import torch
     import torch.distributed as dist
@@ -704,7 +663,7 @@ def main():
     n, rp, col = make_graph(w)
     srcs = sources_for(w, rp, world, rank)
     c, eps, k = w["c"], w["eps"], w["k"]
-    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3)
+    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3, alg3_rule=1, alg3_max_depth=8)
     stream = torch.cuda.Stream(device=dev)  # shared by the library's launches and the CUDA events
     g.set_stream(stream)
     ids = torch.empty(k, dtype=torch.int32, device=dev)
@@ -792,8 +751,6 @@ def main():
     norm_u = statistics.mean(s["pi_norm2"] for s in stats) if stats else 0.0
     sigma_u = math.sqrt(norm_u / (4 * a ** 4 * R_b)) if R_b > 0 else None
     sigma_any = math.sqrt(1.0 / (4 * a ** 4 * R_b)) if R_b > 0 else None
-    traffic = KERNEL_TRAFFIC.get("sample_pairs_kernel")
-
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -807,7 +764,7 @@ def main():
                      "ms_per_launch": ms_sample / max(sampler_launches, 1),
                      "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak_steps / 1e9, "unit": "G pair-steps/s", "frac": achieved / peak_steps,
-                     "traffic": traffic,
+                     "traffic": None,
                      "peak_source": f"{sm_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz ({pk_src} clock) / "
                                     f"{INSTR_PER_PAIR_STEP:.0f} integer instructions per pair-step"},
         "phases_ms": {p: v / max(len(stats), 1) for p, v in ms_phase.items()},
@@ -816,16 +773,18 @@ def main():
         "error_bound": {"sigma_source": sigma_u, "sigma_any_node": sigma_any, "eps": eps,
                         "note": "Lemma 2 variance bound with the pi^2 allocation at this kappa; "
                                 "kappa = 6/(1-sqrt c)^4 carries Theorem 1's guarantee"},
-        "sweep_hbm_gbs": sweep_gbs,
+        "sweep_hbm_gbs_cl100k": sweep_gbs,
         "wall_s": wall,
     }
+    if rank == 0 and world == 1 and not args.no_sweeps:
+        line["sweep_roofline"] = sweep_roofline(esim, torch, stream)
+        line["sweep_hbm_gbs_fp64"] = line["sweep_roofline"]["fp64"]["gbs"]
+        line["sweep_hbm_gbs_fp32c"] = line["sweep_roofline"]["fp32c"]["gbs"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import walks
-        walks.build()
-        t, info = cpu_reference_sample(w, n, rp, col, srcs[0], args.kappa, args.ref_pairs, alg3=bool(args.alg3))
-        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "queries/s", "cores": walks.max_threads(), "kind": "oracle",
-                                "sample": f"one query (u={srcs[0]}): sweeps in full, {info['pairs_sampled']:.3g} of "
-                                          f"{info['pairs_total']:.3g} walk pairs, walk time scaled{info['z_note']}"}
+        qps, t_samples, cores, infos = cpu_baseline_of(w, n, rp, col, srcs, args.kappa, args.ref_pairs)
+        line["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                "sample": cpu_sample_note(srcs, args.ref_pairs, infos, args.kappa),
+                                "sample_s": sum(t_samples)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()

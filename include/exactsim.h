@@ -167,19 +167,32 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "diag"           0: D^ estimated by walk pairs (default); 1: ParSim's approximation
  *                    D = (1-c) I (Section 2, related work), no allocation and no walk pairs -- the
  *                    baseline of the paper's comparison of diagonal corrections
- *   "alg3"           1: Algorithm 3 (local deterministic exploitation) for the
- *                    heaviest nodes; nodes with din <= 1 take the exact D (1 at din 0,
- *                    1-c at din 1) and no walk pairs.  An exploited node k of depth d
- *                    gets the exact Z_1..Z_d (Lemma 5) and max(1, ceil(R_b pi(k)^2
- *                    c^(2d))) special pairs that move for d steps without the
+ *   "alg3"           1: Algorithm 3 (local deterministic exploitation); nodes with
+ *                    din <= 1 take the exact D (1 at din 0, 1-c at din 1) and no walk
+ *                    pairs.  An exploited node k of depth d gets the exact Z_1..Z_d
+ *                    (Lemma 5) and special pairs that move for d steps without the
  *                    continuation draw; D^(k) = 1 - sum Z - c^d (pairs meeting after step
- *                    d)/R.  The depth minimises an estimate of the GPU work (walks plus
- *                    the sweeps of Lemma 5, which grow with the supports of
- *                    (P^T)^i(k, .)); depth 0 leaves the node to Algorithm 2.
+ *                    d)/R.  How d and the pair count are chosen is option "alg3_rule".
  *                    Needs a graph without repeated in-edges (else ESIM_ENOTSUP).
- *   "alg3_max_nodes" heaviest nodes (by pi) considered, 1..4096 (default 64)
- *   "alg3_min_pairs" smallest Algorithm 2 pair count worth considering (default 1e6)
- *   "alg3_max_depth" deepest exploitation, 1..16 (default 8)
+ *   "alg3_rule"      0 (default): the paper's adaptive depth (Algorithm 3).  Every node
+ *                    with R(k) > 0 explores level by level, counting each edge the
+ *                    listing traverses when it extends a walk distribution
+ *                    (P^T)^(l')(q', .) by one step, and stops at the level during which
+ *                    the count reaches 2 R(k)/sqrt(c), at a level that adds no edge, or at
+ *                    alg3_max_depth; it keeps its R(k) pairs.  The count keeps n x n
+ *                    support bit sets: graphs with 2 n ceil(n/32) 4-byte words above
+ *                    4 GiB (n > 131072) return ESIM_ENOTSUP.
+ *                    1: a cost model for speed -- only the heaviest nodes (by pi, at most
+ *                    alg3_max_nodes, with din >= 2 and an Algorithm 2 count of at least
+ *                    alg3_min_pairs) are exploited, at the depth that minimises an
+ *                    estimate of the GPU work (walks plus the sweeps of Lemma 5, which
+ *                    grow with the supports of (P^T)^i(k, .)), with
+ *                    max(1, ceil(R_b pi(k)^2 c^(2d))) pairs: the tail estimator's variance
+ *                    bound at depth d is c^(2d) times Algorithm 2's, so the variance bound
+ *                    of R(k) Algorithm 2 pairs is kept; depth 0 leaves a node to Algorithm 2
+ *   "alg3_max_nodes" cost model: heaviest nodes (by pi) considered, 1..4096 (default 64)
+ *   "alg3_min_pairs" cost model: smallest Algorithm 2 pair count worth considering (default 1e6)
+ *   "alg3_max_depth" deepest exploitation, 1..16 (default 16)
  *   "alg3_push_div"  a probe step pushes from its frontier while the frontier's in-edges are
  *                    at most (m+n)/alg3_push_div, else pulls over all rows (default 4);
  *                    both give the same integers
@@ -189,7 +202,7 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_early_pairs"  a candidate whose plan is final and whose pairs number at least
  *                    this (default 2^24) starts its walks at once on a third stream,
  *                    during the rest of the planning (with "alg3_overlap" > 0)
- *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the depth's cost model, in
+ *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per
  *                    entry and column of a 32-column probe sweep (0.2), per kernel launch
  *                    (2^19).  The estimate of depth d is R_d (d + 1/(1-c)) walks plus
@@ -366,10 +379,21 @@ esim_status esim_alg3_first_meeting(esim_graph* g, int64_t k, int32_t depth, dou
  * 0..max_depth (<= 16) of least estimated work R_d (d + 1/(1-c)) + w_sweep (m+n)(2d-1) +
  * w_probe (m+n) sum_{i=1}^{d-2} supp[i](d-i) + w_launch launches(d), R_d = max(1,
  * ceil(v c^(2d))), v = R_b pi(k)^2 (R_b pi(k) for the basic allocation), supp[i] =
- * |supp (P^T)^i(k, .)| for i = 0..max(0, max_depth-2); the first on ties.  The option
- * "alg3" decides every node with it.  Returns -1 on invalid arguments. */
+ * |supp (P^T)^i(k, .)| for i = 0..max(0, max_depth-2); the first on ties.  Option
+ * "alg3_rule" = 1 decides every candidate with it.  Returns -1 on invalid arguments. */
 int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_depth, int64_t n, int64_t m,
                         double w_sweep, double w_probe, double w_launch);
+/* Algorithm 3's adaptive depth as the paper gives it ("Local deterministic exploitation
+ * for D"): depth[n] (device, uint8) receives, for every node with R[k] > 0 (R: device,
+ * uint64[n]), the level l during which its explored-edge count E_k reaches
+ * 2 R(k)/sqrt(c), compared in FP64; a level that adds no edge, or max_depth
+ * (0..16), ends the exploration earlier.  E_k adds, at level l, for every l' = 0..l and
+ * every q' in supp (P^T)^(l-l')(k, .), the in-degrees of the nodes in
+ * supp (P^T)^(l')(q', .): the edges the listing traverses when it extends that walk
+ * distribution by one step.  Nodes with R[k] = 0 get depth 0.  Synchronises the
+ * graph's stream once per level.  Errors: ESIM_ENOTSUP for n > 131072 (the support
+ * bit sets), ESIM_EINVAL, ESIM_ENOMEM, ESIM_ECUDA. */
+esim_status esim_alg3_paper_depth(esim_graph* g, const uint64_t* R, double c, int32_t max_depth, uint8_t* depth);
 esim_status esim_sample_depth(esim_graph* g, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
                               uint64_t* counts, uint64_t* pair_steps);
 esim_status esim_dhat_alg3(esim_graph* g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,

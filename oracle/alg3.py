@@ -13,19 +13,23 @@ Test infrastructure only (see ``oracle/__init__.py``).
   (rational) distribution of two non-stop walks from k over pairs of nodes, step by
   step, removing the pairs that have met; Z_l = c^l * (mass that first meets at
   step l).  An independent formulation that pins the lemma's recursion.
-* ``exploitation_plan`` -- the exploitation the library uses: the heaviest nodes (by
-  pi(k), at most ``max_nodes``, with R(k) >= ``min_pairs`` and din(k) >= 2) take the
-  depth that minimises ``exploit_cost`` (the paper stops its adaptive exploration
-  when the explored edges reach the walk work; the cost here weighs the library's
-  dense sweeps against its walks); their sample count becomes
-  max(1, ceil(R_b pi(k)^2 c^(2 depth))).  Nodes with din <= 1 take the exact values of
-  Algorithm 3 (D = 1 at din = 0, 1 - c at din = 1) and no samples.
+* ``explored_edges`` / ``explored_edges_literal`` -- the counter E_k of Algorithm 3:
+  every edge the exploration traverses when it extends a walk distribution
+  (P^T)^(l')(q', .) by one step, level by level (a vectorised form over all nodes,
+  and the listing's loops written out for small graphs).
+* ``paper_depth`` / ``exploitation_plan`` -- Algorithm 3's adaptive depth: node k
+  stops at the level during which E_k reaches 2 R(k)/sqrt(c), the expected step
+  count of its R(k) walk pairs; nodes with din <= 1 take the exact D and no pairs.
+* ``first_meeting_sums`` -- sum_{l <= depth(k)} Z_l(k) for every node at once (Lemma 5
+  with the sum over q' as a matrix product).
 * ``dhat_alg3`` -- D^(k) = 1 - sum_{l <= depth} Z_l(k) - c^depth * tailmeet(k) / R(k)
   for exploited nodes (Algorithm 3), nonmeet / R for the others.
 
-Pinned by: the rational brute force (Z to 1e-14), the identity
+Pinned by: the rational brute force (Z to 1e-14); the identity
 sum_l Z_l(k) = 1 - D(k) against the Power Method's exact D (the truncated sum stays
-below it and the tail estimator closes the gap), and z-tests of the tail walks.
+below it, an exhausted exploration reaches it, and the tail estimator closes the gap
+without bias: z-tests); the counter against the listing's loops on small graphs and
+against its closed form on the complete digraph.
 """
 from __future__ import annotations
 
@@ -93,87 +97,147 @@ def first_meeting_bruteforce(n: int, in_rowptr, in_col, k: int, c: Fraction, dep
     return out
 
 
-def exploit_cost(d: int, v: float, c: float, supp, n: int, m: int, w_sweep: float = 4.0, w_probe: float = 0.2,
-                 w_launch: float = 524288.0) -> float:
-    """Estimated GPU work (in sampler pair-steps) of exploiting a node to depth d.
+def explored_edges_literal(n: int, in_rowptr, in_col, k: int, levels: int) -> list[int]:
+    """E_k at the end of each level l = 0..levels, by the loops of Algorithm 3 as printed.
 
-    d = 0 is Algorithm 2 alone.  Walks: R_d (d + 1/(1-c)) with R_d = max(1, ceil(v c^(2d))),
-    v = R_b pi(k)^2.  Lemma 5 at depth d: 2d-1 single sweeps of m+n entries (weight
-    w_sweep per entry), sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps (w_probe per
-    entry and column), and w_launch per kernel launch (3 per sweep; 3 per probe step and
-    2 per block of 32 probes).  The same arithmetic, in the same order, as the library's plan,
-    so that both sides pick the same depth.
+    At level l, for every l' = 0..l, every q' with (P^T)^(l-l')(k, q') != 0 and every x
+    with (P^T)^(l')(q', x) != 0, the step to each q in I(x) adds one explored edge.
+    Walk distributions are kept per (q', l') and extended one step at a time.  Pure
+    Python, for small graphs: it pins ``explored_edges``.
     """
-    r = math.ceil(v) if d == 0 else math.ceil(v * c ** (2 * d))
-    r = max(1.0, float(r))
-    cost = r * (d + 1.0 / (1.0 - c))
-    if d > 0:
-        edges = float(m + n)
-        probe = 0
-        launches = 3 * (2 * d - 1)
-        for i in range(1, d - 1):
-            probe += int(supp[i]) * (d - i)
-            launches += (int(supp[i]) + 31) // 32 * (3 * (d - i) + 2)
-        cost += w_sweep * edges * float(2 * d - 1)
-        cost += w_probe * edges * float(probe)
-        cost += w_launch * float(launches)
-    return cost
+    rp = [int(x) for x in in_rowptr]
+    col = [int(x) for x in in_col]
+    inn = [col[rp[j]:rp[j + 1]] for j in range(n)]
+    dists: dict[int, list[dict[int, Fraction]]] = {}
+
+    def dist(q: int, ell: int) -> dict[int, Fraction]:
+        if q not in dists:
+            dists[q] = [{q: Fraction(1)}]
+        d = dists[q]
+        while len(d) <= ell:
+            nxt: dict[int, Fraction] = {}
+            for x, w in d[-1].items():
+                for y in inn[x]:
+                    nxt[y] = nxt.get(y, Fraction(0)) + w / len(inn[x])
+            d.append(nxt)
+        return d[ell]
+
+    E = 0
+    out = []
+    for ell in range(levels + 1):
+        for lp in range(ell + 1):
+            for qp, wq in dist(k, ell - lp).items():
+                if wq == 0:
+                    continue
+                for x, wx in dist(qp, lp).items():
+                    if wx != 0:
+                        E += len(inn[x])
+        out.append(E)
+    return out
 
 
-def supports(P, k: int, levels: int) -> list[int]:
-    """|supp h_i| for i = 0..levels, h_i the non-stop walk distribution from k."""
-    H = walk_distribution(P, k, levels)
-    return [int(np.count_nonzero(H[i])) for i in range(levels + 1)]
+def explored_edges(n: int, in_rowptr, in_col, levels: int) -> np.ndarray:
+    """E[l, k]: explored edges of Algorithm 3 from node k at the end of level l.
 
-
-def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 8,
-                      min_pairs: float = 1e6, max_nodes: int = 64, stats: dict | None = None,
-                      weights: tuple = (4.0, 0.2, 524288.0), mode: str = "pi2"):
-    """(depth uint8[n], R uint64[n]) of Algorithm 3 with the cost-minimising depth.
-
-    Candidates: the max_nodes largest pi(k) (ties to the lower id) with pi(k) > 0,
-    din(k) >= 2 and an Algorithm 2 count max(1, ceil(v)) >= min_pairs, v = R_b pi(k)^2
-    (R_b pi(k) for the basic allocation).  Each takes the depth d in 0..max_depth of
-    least ``exploit_cost`` (the first on ties); d > 0 gives R(k) = max(1, ceil(v c^(2d))).  Nodes with din <= 1 take the
-    exact D and no samples.  ``stats["min_gap"]`` (if given) receives the smallest
-    relative gap between a chosen cost and another depth's cost: the margin of the
-    floating-point depth decisions.
+    supp (P^T)^j(q, .) is row q of the boolean j-th power of A, A(q, x) = [x in I(q)]
+    (a library matrix product per power).  e_j(q) = sum of din(x) over that support
+    is the number of edges the listing traverses when it extends (P^T)^j(q', .) by a
+    step; level l adds W_l(k) = sum_{l'=0..l} sum_{q' in supp (P^T)^(l-l')(k, .)} e_l'(q').
+    Dense n x n matrices: small graphs only.
     """
-    min_gap = math.inf
+    # 0/1 matrices and integer sums below 2^53 multiply exactly in FP64 (BLAS)
+    din = in_degrees(in_rowptr).astype(np.float64)
+    rp = np.asarray(in_rowptr, dtype=np.int64)
+    col = np.asarray(in_col, dtype=np.int64)
+    A = np.zeros((n, n))
+    A[np.repeat(np.arange(n), np.diff(rp)), col] = 1.0
+    supp = [np.eye(n)]
+    for _ in range(levels):
+        supp.append(((supp[-1] @ A) > 0).astype(np.float64))
+    e = [S @ din for S in supp]  # e[j][q]
+    E = np.zeros((levels + 1, n), dtype=np.int64)
+    run = np.zeros(n, dtype=np.int64)
+    for ell in range(levels + 1):
+        W = np.zeros(n, dtype=np.int64)
+        for lp in range(ell + 1):
+            W += np.rint(supp[ell - lp] @ e[lp]).astype(np.int64)
+        run = run + W
+        E[ell] = run
+    return E
+
+
+def paper_depth(E_k, R_k: int, c: float, max_depth: int) -> int:
+    """l(k) of Algorithm 3: the level during which E_k reaches 2 R(k)/sqrt(c).
+
+    E_k[l] is the count at the end of level l.  Two readings where the listing gives
+    no stop: a level that adds no edge (every node reached at that level has din 0,
+    so no walk pair can meet later and the Z up to that level give D exactly) stops
+    the exploration at that level, and so does ``max_depth``.
+    """
+    T = 2.0 * float(R_k) / math.sqrt(c)
+    prev = 0
+    for ell in range(max_depth + 1):
+        cur = int(E_k[ell])
+        if float(cur) >= T:
+            return ell
+        if ell > 0 and cur == prev:
+            return ell
+        prev = cur
+    return max_depth
+
+
+def exploitation_plan(n: int, in_rowptr, in_col, pi: np.ndarray, R_b: float, c: float, max_depth: int = 16,
+                      mode: str = "pi2"):
+    """(depth uint8[n], R uint64[n]) of Algorithm 3 with the paper's adaptive depth.
+
+    R(k) is the allocation of Lemma 4 (pi2) or Algorithm 1 (basic).  Nodes with din 0
+    or 1 take the exact D (Algorithm 3's first cases) and no pairs.  Every other node
+    with R(k) > 0 explores until E_k >= 2 R(k)/sqrt(c) (``paper_depth``) and keeps its
+    R(k) pairs, which move without stopping for l(k) steps.
+    """
     din = in_degrees(in_rowptr)
-    m = int(np.asarray(in_rowptr)[-1])
-    P = transition_matrix(n, in_rowptr, in_col)
     pi = np.asarray(pi, dtype=np.float64)
     R = np.ceil(R_b * (pi * pi) if mode == "pi2" else R_b * pi).astype(np.uint64)
     R[(pi > 0) & (R == 0)] = 1
+    R[din <= 1] = 0
     depth = np.zeros(n, dtype=np.uint8)
-    R[din <= 1] = 0  # exact D for din 0 and 1
-    order = np.lexsort((np.arange(n), -pi))[:max_nodes]
-    for kk in order:
-        kk = int(kk)
-        if not pi[kk] > 0:
-            break
-        if din[kk] < 2:
-            continue
-        v = R_b * (pi[kk] * pi[kk]) if mode == "pi2" else R_b * pi[kk]
-        if max(1.0, float(math.ceil(v))) < min_pairs:
-            continue
-        supp = supports(P, kk, max(0, max_depth - 2))
-        costs = [exploit_cost(dd, v, c, supp, n, m, *weights) for dd in range(max_depth + 1)]
-        d, best = 0, costs[0]
-        for dd in range(1, max_depth + 1):
-            if costs[dd] < best:
-                d, best = dd, costs[dd]
-        for dd, cost in enumerate(costs):
-            if dd != d:
-                min_gap = min(min_gap, abs(cost - best) / best)
-        if d == 0:
-            continue
-        depth[kk] = d
-        R[kk] = max(1, int(math.ceil(v * c ** (2 * d))))
-    if stats is not None:
-        stats["min_gap"] = min_gap
+    cand = np.nonzero(R > 0)[0]
+    if cand.size:
+        E = explored_edges(n, in_rowptr, in_col, max_depth)
+        for k in cand:
+            depth[k] = paper_depth(E[:, k], int(R[k]), c, max_depth)
     return depth, R
+
+
+def first_meeting_sums(n: int, in_rowptr, in_col, depth: np.ndarray, c: float) -> np.ndarray:
+    """zsum(k) = sum_{l=1..depth(k)} Z_l(k) for every node, Lemma 5 in matrix form.
+
+    With M_j = (P^T)^j (dense) and Q_j = M_j * M_j (element-wise), row k of
+    Z_l = c^l Q_l - sum_{l'=1..l-1} c^l' Z_(l-l') Q_l' is Lemma 5 for node k: the sum
+    over q' is a library matrix product.  Rows are kept only while l <= depth(k).
+    Small graphs only; ``first_meeting_lemma5`` is the term-by-term form that pins it.
+    """
+    depth = np.asarray(depth)
+    D = int(depth.max()) if depth.size else 0
+    zsum = np.zeros(n)
+    if D == 0:
+        return zsum
+    P = transition_matrix(n, in_rowptr, in_col)
+    PT = P.T.toarray()
+    M = [np.eye(n)]
+    for _ in range(D):
+        M.append(M[-1] @ PT)  # (P^T)^j: row k is the walk distribution from k after j steps
+    Q = [x * x for x in M]
+    rows = np.nonzero(depth > 0)[0]
+    Z = [None]  # Z[l]: Z_l restricted to `rows`
+    for ell in range(1, D + 1):
+        z = c ** ell * Q[ell][rows]
+        for lp in range(1, ell):
+            z = z - c ** lp * (Z[ell - lp] @ Q[lp])
+        Z.append(z)
+        keep = depth[rows] >= ell
+        zsum[rows[keep]] += z[keep].sum(axis=1)
+    return zsum
 
 
 def dhat_alg3(counts: np.ndarray, R: np.ndarray, depth: np.ndarray, zsum: np.ndarray, din: np.ndarray,

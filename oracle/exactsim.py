@@ -1,4 +1,4 @@
-"""The whole CPU ExactSim query: Algorithm 1 with Algorithm 2 as its D estimator.
+"""The whole CPU ExactSim query: Algorithm 1 with Algorithm 2 (or 3) as its D estimator.
 
 Test infrastructure only (see ``oracle/__init__.py``).  It runs the steps in the
 paper's order -- L, hop vectors, allocation, walk pairs, D^, reverse
@@ -32,17 +32,18 @@ class QueryResult:
     pair_steps: int
     depth: np.ndarray | None = None
     zsum: np.ndarray | None = None
-    plan_gap: float = float("inf")  # margin of Algorithm 3's depth decisions (relative cost gap)
 
 
 def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0,
           kappa: float | None = None, mode: str = "pi2", threads: int = 0, alg3: bool = False,
-          alg3_max_depth: int = 8, alg3_min_pairs: float = 1e6, alg3_max_nodes: int = 64,
-          sparse: bool = False, diag: str = "estimated", alg3_weights: tuple = (4.0, 0.2, 524288.0)) -> QueryResult:
+          alg3_max_depth: int = 16, alg3_plan=None, sparse: bool = False, diag: str = "estimated") -> QueryResult:
     """One single-source query.  ``sparse``: sparse Linearization (Sec. 3.2) -- the
     query runs at eps/2 and the reverse loop reads the history with entries at or
     below (1 - sqrt(c))^2 eps/2 dropped (pi for the allocation is the full sum).
-    ``diag="parsim"``: D = (1 - c) I with no walks, ParSim's approximation (Sec. 2)."""
+    ``diag="parsim"``: D = (1 - c) I with no walks, ParSim's approximation (Sec. 2).
+    ``alg3``: Algorithm 3 with the paper's adaptive depth (explore until the explored
+    edges reach 2 R(k)/sqrt(c), at most ``alg3_max_depth`` levels), or with a given
+    ``alg3_plan`` = (depth uint8[n], R uint64[n]) chosen by the caller."""
     if sparse:
         eps = 0.5 * eps
     L = lin.levels(c, eps)
@@ -61,16 +62,15 @@ def query(n: int, in_rowptr, in_col, u: int, c: float, eps: float, seed: int = 0
         D = lin.dhat(nonmeet, R)
         s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
         return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=nonmeet, D=D, L=L, R_b=R_b, pair_steps=steps)
-    # Algorithm 3 for the heaviest nodes (pi^2 allocation)
-    plan = {}
-    depth, R = a3.exploitation_plan(n, in_rowptr, in_col, pi, R_b, c, alg3_max_depth, alg3_min_pairs,
-                                    alg3_max_nodes, stats=plan, weights=alg3_weights, mode=mode)
-    zsum = np.zeros(n)
-    for k in np.nonzero(depth)[0]:
-        zsum[k] = sum(a3.first_meeting_lemma5(n, in_rowptr, in_col, int(k), c, int(depth[k])))
+    if alg3_plan is None:
+        depth, R = a3.exploitation_plan(n, in_rowptr, in_col, pi, R_b, c, alg3_max_depth, mode)
+    else:
+        depth = np.asarray(alg3_plan[0], dtype=np.uint8)
+        R = np.asarray(alg3_plan[1], dtype=np.uint64)
+    zsum = a3.first_meeting_sums(n, in_rowptr, in_col, depth, c)
     counts, steps = walks.walk_pairs_depth(n, in_rowptr, in_col, R, depth, c, seed, threads)
     din = np.diff(np.asarray(in_rowptr, dtype=np.int64))
     D = a3.dhat_alg3(counts, R, depth, zsum, din, c)
     s = lin.reverse(n, in_rowptr, in_col, Hr, D, c)
     return QueryResult(s=s, H=Hr, pi=pi, R=R, nonmeet=counts, D=D, L=L, R_b=R_b, pair_steps=steps,
-                       depth=depth, zsum=zsum, plan_gap=plan["min_gap"])
+                       depth=depth, zsum=zsum)

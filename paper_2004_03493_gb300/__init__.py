@@ -15,6 +15,7 @@ from ._native import (  # noqa: F401
     EsimError,
     esim_allocate,
     esim_alg3_first_meeting,
+    esim_alg3_paper_depth,
     esim_sample_depth,
     esim_dhat_alg3,
     esim_dhat,
@@ -160,6 +161,9 @@ class Graph:
 
     def alg3_first_meeting(self, k, depth, c):
         return esim_alg3_first_meeting(self.handle, k, depth, c)
+
+    def alg3_paper_depth(self, R, c, max_depth, depth):
+        esim_alg3_paper_depth(self.handle, R, c, max_depth, depth)
 
     def sample_depth(self, off, depth, c, seed, counts, pair_steps=None):
         esim_sample_depth(self.handle, off, depth, c, seed, counts, pair_steps)

@@ -106,6 +106,7 @@ SIGNATURES = {
     "esim_server_destroy": (None, [_P]),
     "esim_alg3_first_meeting": (_ST, [_P, _I64, _I32, _D, _P]),
     "esim_alg3_depth": (_I32, [_D, _D, _P, _I32, _I64, _I64, _D, _D, _D]),
+    "esim_alg3_paper_depth": (_ST, [_P, _P, _D, _I32, _P]),
     "esim_sample_depth": (_ST, [_P, _P, _P, _D, _U64, _P, _P]),
     "esim_dhat_alg3": (_ST, [_P, _P, _P, _P, _P, _D, _P]),
 }
@@ -365,6 +366,11 @@ def esim_alg3_depth(v: float, c: float, supp, max_depth: int, n: int, m: int,
     sp = np.ascontiguousarray(supp, dtype=np.uint64)
     return int(lib().esim_alg3_depth(float(v), float(c), sp.ctypes.data, int(max_depth), int(n), int(m),
                                      *[float(x) for x in weights]))
+
+
+def esim_alg3_paper_depth(g: int, R, c: float, max_depth: int, depth) -> None:
+    _check(lib().esim_alg3_paper_depth(g, _ptr(R, "uint64", device=True), c, int(max_depth),
+                                       _ptr(depth, "uint8", device=True)))
 
 
 def esim_sample_depth(g: int, off, depth, c: float, seed: int, counts, pair_steps=None) -> None:

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libexactsim.so")
 
-SOURCES = ["capi.cu", "sweep.cu", "sample.cu", "topk.cu", "batch.cu", "server.cu", "alg3.cu"]
+SOURCES = ["capi.cu", "sweep.cu", "sample.cu", "topk.cu", "batch.cu", "server.cu", "alg3.cu", "alg3_paper.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

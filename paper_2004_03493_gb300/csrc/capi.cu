@@ -124,6 +124,7 @@ void release(Graph& g) {
     cudaFree(g.ws);
     cudaFree(g.bws);
     cudaFree(g.a3ws);
+    cudaFree(g.a3pws);
     cudaFree(g.partial);
     cudaFree(g.scan_part);
     cudaFree(g.norm_part);
@@ -403,8 +404,74 @@ esim_status start_early_walks(Graph& g, const Ws& w, int32_t k, uint64_t R1, dou
     return ESIM_OK;
 }
 
+esim_status ensure_a3pws(Graph& g) {
+    if (!alg3_paper_fits(g.n))
+        return fail(ESIM_ENOTSUP, "the paper's Algorithm 3 depth rule keeps n x n support bit sets; n = " +
+                                      std::to_string(g.n) + " is above its 4 GiB budget (option alg3_rule = 1 "
+                                      "chooses depths by the cost model)");
+    const size_t need = alg3_paper_bytes(g.n, kAlg3MaxDepth);
+    if (g.a3pws && g.a3pws_bytes >= need) return ESIM_OK;
+    cudaStreamSynchronize(g.stream);
+    cudaFree(g.a3pws);
+    g.a3pws = nullptr;
+    g.a3pws_bytes = 0;
+    if (cudaMalloc(&g.a3pws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 depth-rule workspace of " + std::to_string(need) + " bytes)");
+    }
+    g.a3pws_bytes = need;
+    return ESIM_OK;
+}
+
+// Algorithm 3 with the paper's adaptive depth: every node with R(k) > 0 (din >= 2; the
+// allocation gave the others none) explores until its explored edges reach
+// 2 R(k)/sqrt(c), at most alg3_max_depth levels (alg3_paper.cu); it keeps its R(k)
+// pairs, which move without the continuation draw for depth(k) steps.  Z_1 is c/din(k);
+// deeper nodes get Z_1..Z_d from alg3_first_meeting, one node at a time.
+esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
+    esim_status a3 = ensure_a3pws(g);
+    if (a3 != ESIM_OK) return a3;
+    ESIM_CUDA_TRY(cudaMemsetAsync(w.zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
+    ESIM_CUDA_TRY(alg3_paper_depths(g, w.R, c, g.alg3_max_depth, g.a3pws, w.depth, launches),
+                  "Algorithm 3 depths (explored edges)");
+    ESIM_CUDA_TRY(alg3_paper_z1(g, w.depth, c, w.zsum), "Algorithm 3 Z_1");
+    *launches += 1;
+    std::vector<uint8_t> depth((size_t)g.n);
+    std::vector<double> zs((size_t)g.n);
+    ESIM_CUDA_TRY(cudaMemcpyAsync(depth.data(), w.depth, (size_t)g.n, cudaMemcpyDeviceToHost, g.stream), "copy depth");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(zs.data(), w.zsum, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
+                  "copy zsum");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depths");
+    int used = 0;
+    bool deep = false;
+    for (int64_t k = 0; k < g.n; ++k) {
+        const int d = depth[(size_t)k];
+        if (d == 0) continue;
+        ++used;
+        if (d == 1) continue;
+        if (!deep) {
+            a3 = ensure_a3ws(g);
+            if (a3 != ESIM_OK) return a3;
+            deep = true;
+        }
+        double z[kAlg3MaxDepth] = {};
+        ESIM_CUDA_TRY(alg3_first_meeting(g, k, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
+        double sum = 0.0;
+        for (int j = 0; j < d; ++j) sum += z[j];
+        zs[(size_t)k] = sum;
+    }
+    if (deep)
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum, zs.data(), sizeof(double) * (size_t)g.n, cudaMemcpyHostToDevice, g.stream),
+                      "upload zsum");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // zs is a local
+    g.last_alg3_nodes = used;
+    return ESIM_OK;
+}
+
 esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches, uint64_t seed, bool* side) {
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
+    *side = false;
+    if (g.alg3_rule == 0) return plan_alg3_paper(g, w, c, launches);
     esim_status a3 = ensure_a3ws(g);
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(cudaMemsetAsync(w.depth, 0, (size_t)g.n, g.stream), "reset depth");
@@ -1140,6 +1207,10 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
         if (value == 1.0 && g.has_duplicates)
             return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
         g.alg3 = (int)value;
+    } else if (k == "alg3_rule") {
+        if (value != 0.0 && value != 1.0)
+            return fail(ESIM_EINVAL, "alg3_rule must be 0 (the paper's explored-edge rule) or 1 (cost model)");
+        g.alg3_rule = (int)value;
     } else if (k == "alg3_max_depth") {
         if (!(value >= 1.0 && value <= (double)kAlg3MaxDepth) || value != floor(value))
             return fail(ESIM_EINVAL, "alg3_max_depth must be an integer in [1, 16]");
@@ -1185,6 +1256,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "sparse_hist") *value = g.sparse_hist;
     else if (k == "shared_walks") *value = g.shared_walks;
     else if (k == "alg3") *value = g.alg3;
+    else if (k == "alg3_rule") *value = g.alg3_rule;
     else if (k == "alg3_max_depth") *value = g.alg3_max_depth;
     else if (k == "alg3_min_pairs") *value = g.alg3_min_pairs;
     else if (k == "alg3_max_nodes") *value = g.alg3_max_nodes;
@@ -1422,6 +1494,19 @@ esim_status esim_alg3_first_meeting(esim_graph* h, int64_t k, int32_t depth, dou
     esim_status a3 = ensure_a3ws(g);
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(alg3_first_meeting(g, k, depth, c, g.a3ws, z_out, nullptr), "Algorithm 3 first meetings");
+    return ESIM_OK;
+}
+
+esim_status esim_alg3_paper_depth(esim_graph* h, const uint64_t* R, double c, int32_t max_depth, uint8_t* depth) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!R || !depth) return fail(ESIM_EINVAL, "NULL argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (max_depth < 0 || max_depth > kAlg3MaxDepth) return fail(ESIM_EINVAL, "need 0 <= max_depth <= 16");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    esim_status a3 = ensure_a3pws(g);
+    if (a3 != ESIM_OK) return a3;
+    ESIM_CUDA_TRY(alg3_paper_depths(g, R, c, max_depth, g.a3pws, depth, nullptr), "Algorithm 3 depths (explored edges)");
     return ESIM_OK;
 }
 

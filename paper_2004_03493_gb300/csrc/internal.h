@@ -94,7 +94,8 @@ struct Graph {
     // Algorithm 3 (local deterministic exploitation)
     int alg3 = 0;
     int diag_mode = 0;  // 0: D^ from walk pairs (Algorithm 2 / 3); 1: ParSim's D = (1-c) I
-    int alg3_max_depth = 8;
+    int alg3_rule = 0;       // 0: the paper's depth (explored edges reach 2 R(k)/sqrt c); 1: cost model
+    int alg3_max_depth = 16;
     double alg3_min_pairs = 1e6;
     int alg3_max_nodes = 64;
     // Algorithm 3's cost model (pair-steps per sweep entry, per probe entry and column, per launch)
@@ -105,6 +106,8 @@ struct Graph {
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)
     size_t a3ws_bytes = 0;
+    void* a3pws = nullptr;        // the paper's depth rule: support bit sets and edge tables
+    size_t a3pws_bytes = 0;
     int32_t last_alg3_nodes = 0;
     uint64_t last_hist_entries = 0;
     uint64_t last_ws_bytes = 0;
@@ -219,6 +222,15 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                                int* launches);
 cudaError_t launch_dhat_alg3(const Graph& g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,
                              const double* zsum, double c, double* dhat);
+
+// alg3_paper.cu: the paper's adaptive depth (Algorithm 3).  depth[k] for every node with
+// R(k) > 0 (device arrays; the others get 0); synchronises g.stream once per level.
+size_t alg3_paper_bytes(int64_t n, int max_depth);
+bool alg3_paper_fits(int64_t n);
+cudaError_t alg3_paper_depths(const Graph& g, const uint64_t* R, double c, int max_depth, void* ws, uint8_t* depth,
+                              int* launches);
+// zsum(k) = Z_1(k) = c / din(k) for the nodes of depth 1 (others untouched)
+cudaError_t alg3_paper_z1(const Graph& g, const uint8_t* depth, double c, double* zsum);
 
 // topk.cu
 constexpr int kTopkMax = 4096;

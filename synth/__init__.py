@@ -10,6 +10,7 @@ from .graphs import (  # noqa: F401
     chung_lu,
     rmat,
     rmat_torch,
+    chung_lu_torch,
     random_sources,
     uniform_diagonal,
     out_star,

@@ -15,6 +15,8 @@ Generators:
   (a, b, c, d), duplicates and loops removed, seeded random vertex permutation;
   ``rmat_torch`` draws the same kind of graph with torch on a GPU for the
   largest sizes.
+* ``chung_lu_torch`` -- the Chung-Lu recipe with torch on a GPU (the n = 4e6 graph
+  of the precision form, generated in seconds).
 
 Small named graphs (stars, cycle, complete digraph, ...) serve the closed-form
 checks.  Nothing here computes any part of SimRank.
@@ -167,6 +169,65 @@ def rmat_torch(scale: int, m: int, a=0.57, b=0.19, c=0.19, d=0.05, seed: int = 1
                 dst = (dst << 1) | (q & 1)
             keep = src != dst
             parts.append(perm[src[keep]] * n + perm[dst[keep]])
+            del src, dst, keep
+        keys = torch.unique(torch.cat([keys] + parts))
+        del parts
+        if keys.numel() >= m:
+            break
+        draw = int((m - keys.numel()) * 2) + 4096
+    if keys.numel() < m:
+        raise RuntimeError("could not reach the requested number of distinct edges")
+    pick = torch.randperm(keys.numel(), generator=gen, device=device)[:m]
+    keys = keys[pick]
+    src = keys // n
+    dst = keys % n
+    del keys, pick
+    order = torch.argsort(dst * n + src)
+    src = src[order]
+    dst = dst[order]
+    counts = torch.bincount(dst, minlength=n)
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(counts, 0)
+    return n, rowptr.cpu().numpy(), src.to(torch.int32).cpu().numpy()
+
+
+def chung_lu_torch(n: int, m: int, gamma: float = 2.2, seed: int = 1, device: str = "cuda"):
+    """Directed Chung-Lu graph generated with torch on `device` (for the largest sizes).
+
+    Same recipe as ``chung_lu`` (independent Pareto in- and out-weights
+    w = (1-U)^(-1/(gamma-1)), endpoints drawn proportionally to the weights, loops and
+    duplicates removed, exactly m distinct edges) with torch's generator: deterministic
+    for a given seed, device type and torch version, but a different graph than the
+    NumPy ``chung_lu``.  Surplus edges are drawn, deduplicated, and m of them are kept by
+    a seeded permutation.
+    """
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+
+    def cdf():
+        u = torch.rand(n, generator=gen, device=device, dtype=torch.float64)
+        w = (1.0 - u) ** (-1.0 / (gamma - 1.0))
+        c = torch.cumsum(w, 0)
+        return c / c[-1]
+
+    c_out = cdf()
+    c_in = cdf()
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    draw = int(m * 1.25) + 4096
+    for _ in range(20):
+        chunk = 1 << 26
+        parts = []
+        left = draw
+        while left > 0:
+            k = min(chunk, left)
+            left -= k
+            src = torch.searchsorted(c_out, torch.rand(k, generator=gen, device=device, dtype=torch.float64),
+                                     right=True).clamp_(max=n - 1)
+            dst = torch.searchsorted(c_in, torch.rand(k, generator=gen, device=device, dtype=torch.float64),
+                                     right=True).clamp_(max=n - 1)
+            keep = src != dst
+            parts.append(src[keep] * n + dst[keep])
             del src, dst, keep
         keys = torch.unique(torch.cat([keys] + parts))
         del parts

@@ -95,15 +95,17 @@ def test_null_handle_is_rejected(native):
     assert e.value.status == -1
 
 
-def test_alg3_depth_choice_matches_the_oracle(native):
-    """The library's depth choice (host arithmetic) and the oracle's exploit_cost argmin
-    pick the same depth, bit for bit, over random work estimates and real supports."""
-    from oracle import alg3 as a3
+def test_alg3_cost_model_depth_is_the_documented_argmin(native):
+    """The library's cost-model depth choice (host arithmetic, option alg3_rule = 1) is the
+    argmin of the cost its header documents, restated in tests/alg3_cost_plan.py, bit for
+    bit over random work estimates and real supports."""
+    import alg3_cost_plan as cp
+    from oracle import power
     rng = np.random.default_rng(5)
     n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
     m = int(rp[-1])
-    P = a3.transition_matrix(n, rp, col)
-    supps = [a3.supports(P, int(k), 14) for k in rng.choice(n, 12, replace=False)]
+    P = power.transition_matrix(n, rp, col)
+    supps = [cp.supports(P, int(k), 14) for k in rng.choice(n, 12, replace=False)]
     checked = 0
     for trial in range(400):
         supp = supps[trial % len(supps)]
@@ -112,7 +114,7 @@ def test_alg3_depth_choice_matches_the_oracle(native):
         max_depth = int(rng.integers(0, 17))
         weights = (float(rng.choice([4.0, 1.0])), float(rng.choice([0.2, 0.5, 0.05])),
                    float(rng.choice([524288.0, 2.0 ** 16])))
-        costs = [a3.exploit_cost(d, v, c, supp, n, m, *weights) for d in range(max_depth + 1)]
+        costs = [cp.cost(d, v, c, supp, n, m, *weights) for d in range(max_depth + 1)]
         want = min(range(max_depth + 1), key=lambda d: (costs[d], d))
         got = native.esim_alg3_depth(v, c, supp[:max(1, max_depth - 1)] + [0] * 2, max_depth, n, m, weights)
         assert got == want, (v, c, max_depth, weights, costs)

@@ -4,9 +4,14 @@
   1e-12 (FP64 sums in different orders).
 * The depth-aware sampler (special tail pairs) bit for bit against the oracle's
   C walks, counts and pair steps.
+* The paper's adaptive depth (explored edges reach 2 R(k)/sqrt(c)) node for node
+  against the oracle's counter.
 * D^ of Algorithm 3 against the oracle, and the whole query against the CPU
-  ExactSim with Algorithm 3 (integers exact, scores within 1e-12) and against the
-  Power Method within eps.
+  ExactSim with Algorithm 3 under the paper's rule (integers exact, scores within
+  1e-12) and against the Power Method within eps.
+* The library's cost-model rule (a speed choice, option alg3_rule = 1): the whole
+  query against the oracle run on the plan that the tests' restatement of the
+  documented cost model picks, with the walks split over streams or not.
 """
 import numpy as np
 import pytest
@@ -125,47 +130,74 @@ def test_dhat_alg3(torch_cuda, graph):
     assert np.all(got[din == 0] == 1.0) and np.all(got[din == 1] == 1.0 - C)
 
 
-def _clean(pi, R_b, plan_depth, K):
-    """The integer decisions are stable under the ~1e-15 relative gap between the
-    GPU's and the oracle's pi: no ceil() argument within rounding of an integer,
-    and no near-tie in pi at the edge of the K heaviest nodes."""
-    v = R_b * (pi * pi)
-    for vv in (v, v * C ** (2.0 * plan_depth)):
+def _clean_R(pi, R_b, mode="pi2", scale=None):
+    """No ceil() argument of the allocation lies within rounding of an integer: the GPU's
+    pi differs from the oracle's by summation order (~1e-15 relative)."""
+    v = R_b * (pi * pi) if mode == "pi2" else R_b * pi
+    vs = [v] if scale is None else [v, v * scale]
+    for vv in vs:
         frac = np.abs(vv - np.round(vv))
         if not np.all((frac > 1e-12 * vv) | (vv == 0)):
             return False
-    srt = np.sort(pi)[::-1]
-    if K < len(srt) and srt[K] > 0 and (srt[K - 1] - srt[K]) <= 1e-12 * srt[K - 1]:
-        return False
     return True
 
 
-@pytest.mark.parametrize("graph_name,kappa,min_pairs,max_nodes", [
-    ("cl3000", None, 1e3, 16),
-    ("er2000", 2000.0, 1e2, 8),
-    ("dang2000", None, 1e3, 24),
+PAPER_GRAPHS = {
+    "er2000": lambda: synth.erdos_renyi(2000, 16000, seed=4),
+    "cl3000": lambda: synth.chung_lu(3000, 30000, gamma=2.1, seed=9),
+    "dang2000": lambda: synth.with_dangling(2000, 12000, seed=6),
+}
+
+
+@pytest.mark.parametrize("graph_name", list(PAPER_GRAPHS))
+def test_paper_depth_rule_step_bit_exact(torch_cuda, esim, graph_name):
+    """esim_alg3_paper_depth against the oracle's counter and rule, node for node, for
+    sample counts from 1 to 1e12 and several depth caps."""
+    torch = torch_cuda
+    n, rp, col = PAPER_GRAPHS[graph_name]()
+    din = np.diff(rp)
+    g = esim.Graph(n, rp, col)
+    E = a3.explored_edges(n, rp, col, 16)
+    rng = np.random.default_rng(17)
+    for max_depth in (16, 5, 0):
+        R = np.floor(10.0 ** rng.uniform(0, 12, size=n)).astype(np.uint64)
+        R[rng.random(n) < 0.2] = 0
+        R[din <= 1] = 0
+        want = np.zeros(n, dtype=np.uint8)
+        for k in np.nonzero(R)[0]:
+            want[k] = a3.paper_depth(E[:, k], int(R[k]), C, max_depth)
+        depth = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+        g.alg3_paper_depth(_dev(torch, R), C, max_depth, depth)
+        g.sync()
+        got = depth.cpu().numpy()
+        assert np.array_equal(got, want), (graph_name, max_depth, np.nonzero(got != want)[0][:10])
+        if max_depth == 16:
+            assert want.max() >= 5 and len(np.unique(want)) >= 5
+    g.close()
+
+
+@pytest.mark.parametrize("graph_name,kappa,eps", [
+    ("er2000", 2000.0, 3e-3),
+    ("cl3000", None, 3e-3),
+    ("dang2000", None, 3e-3),
+    ("er2000", 4.0, 1e-4),
 ])
-def test_alg3_query_matches_cpu_exactsim(esim, oracle_walks, graph_name, kappa, min_pairs, max_nodes):
+def test_alg3_paper_rule_query_matches_cpu_exactsim(esim, oracle_walks, graph_name, kappa, eps):
+    """The whole query with the paper's adaptive depth (the library's default rule)
+    against the oracle's Algorithm 3: depths, pair counts and pair steps exact, scores
+    within 1e-12."""
     from oracle import exactsim
-    n, rp, col = {
-        "cl3000": lambda: synth.chung_lu(3000, 30000, gamma=2.1, seed=9),
-        "er2000": lambda: synth.erdos_renyi(2000, 16000, seed=4),
-        "dang2000": lambda: synth.with_dangling(2000, 12000, seed=6),
-    }[graph_name]()
+    n, rp, col = PAPER_GRAPHS[graph_name]()
     g = esim.Graph(n, rp, col) if kappa is None else esim.Graph(n, rp, col, kappa=kappa)
     g.set_option("alg3", 1)
-    g.set_option("alg3_min_pairs", min_pairs)
-    g.set_option("alg3_max_nodes", max_nodes)
-    g.set_option("alg3_max_depth", 6)
-    eps = 3e-3
+    assert g.get_option("alg3_rule") == 0 and g.get_option("alg3_max_depth") == 16
     checked = 0
     deepest = 0
     for u, seed in ((5, 1), (1234, 2), (n - 1, 3)):
-        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=kappa, alg3=True, alg3_max_depth=6,
-                           alg3_min_pairs=min_pairs, alg3_max_nodes=max_nodes)
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=kappa, alg3=True)
         deepest = max(deepest, int(q.depth.max()))
-        if not _clean(q.pi, q.R_b, q.depth.astype(np.float64), max_nodes) or q.plan_gap <= 1e-9:
-            continue  # an integer or depth decision sits within rounding of its boundary
+        if not _clean_R(q.pi, q.R_b):
+            continue  # an integer decision sits within rounding of its boundary
         s = g.query(u, C, eps, seed)
         st = g.stats()
         assert st["alg3_nodes"] == int(np.count_nonzero(q.depth))
@@ -175,6 +207,91 @@ def test_alg3_query_matches_cpu_exactsim(esim, oracle_walks, graph_name, kappa, 
         checked += 1
     assert checked >= 2
     assert deepest >= 3  # probes (Lemma 5's l' >= 2 terms) were exercised
+    g.close()
+
+
+def test_alg3_paper_rule_with_basic_allocation(esim, oracle_walks):
+    from oracle import exactsim
+    n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
+    g = esim.Graph(n, rp, col, alloc=1, alg3=1)
+    eps = 2e-2
+    checked = 0
+    for u, seed in ((5, 1), (1234, 2), (2999, 3)):
+        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, mode="basic", alg3=True)
+        if not _clean_R(q.pi, q.R_b, "basic"):
+            continue
+        s = g.query(u, C, eps, seed)
+        st = g.stats()
+        assert st["alg3_nodes"] == int(np.count_nonzero(q.depth)) > 0
+        assert st["sum_R"] == int(q.R.sum()) and st["pair_steps"] == q.pair_steps
+        assert np.max(np.abs(s - q.s)) <= TOL
+        checked += 1
+    assert checked >= 2
+    g.close()
+
+
+def test_alg3_paper_rule_refuses_graphs_beyond_its_bit_sets(esim):
+    # a 131,073-node cycle: the support bit sets would need 2 n ceil(n/32) words > 4 GiB
+    n = 131_073
+    rp = np.arange(n + 1, dtype=np.int64)
+    col = ((np.arange(n) + 1) % n).astype(np.int32)
+    g = esim.Graph(n, rp, col, alg3=1)
+    with pytest.raises(esim.EsimError) as e:
+        g.query(0, C, 1e-2, 0)
+    assert e.value.status == -6 and "alg3_rule" in str(e.value)
+    g.set_option("alg3_rule", 1)  # the cost model has no such limit
+    s = g.query(0, C, 1e-2, 0)
+    assert abs(s[0] - (1 - C) * (1 - C ** (esim.esim_levels(C, 1e-2) + 1)) / (1 - C)) < 1e-12
+    g.close()
+
+
+def _cost_plan_query(n, rp, col, u, eps, seed, kappa=None, mode="pi2", **kw):
+    """The oracle's query under the cost-model plan that tests/alg3_cost_plan.py restates."""
+    import alg3_cost_plan as cp
+    from oracle import exactsim
+    L = lin.levels(C, eps)
+    pi = lin.ppr(lin.hop_vectors(n, rp, col, u, C, L))
+    R_b = lin.sample_base(n, C, eps, kappa)
+    depth, R, gap = cp.plan(n, rp, col, pi, R_b, C, mode=mode, **kw)
+    q = exactsim.query(n, rp, col, u, C, eps, seed=seed, kappa=kappa, mode=mode, alg3=True, alg3_plan=(depth, R))
+    return q, gap
+
+
+@pytest.mark.parametrize("graph_name,kappa,min_pairs,max_nodes", [
+    ("cl3000", None, 1e3, 16),
+    ("er2000", 2000.0, 1e2, 8),
+    ("dang2000", None, 1e3, 24),
+])
+def test_alg3_cost_model_query_matches_oracle_on_its_plan(esim, oracle_walks, graph_name, kappa, min_pairs,
+                                                          max_nodes):
+    """Option alg3_rule = 1 (the cost model, a speed choice of the library): the oracle
+    runs the plan that the tests' restatement of the documented cost model chooses, and
+    the library's whole query matches it (integers exact, scores within 1e-12)."""
+    n, rp, col = PAPER_GRAPHS[graph_name]()
+    g = esim.Graph(n, rp, col) if kappa is None else esim.Graph(n, rp, col, kappa=kappa)
+    for key, val in (("alg3", 1), ("alg3_rule", 1), ("alg3_min_pairs", min_pairs), ("alg3_max_nodes", max_nodes),
+                     ("alg3_max_depth", 6)):
+        g.set_option(key, val)
+    eps = 3e-3
+    checked = 0
+    deepest = 0
+    for u, seed in ((5, 1), (1234, 2), (n - 1, 3)):
+        q, gap = _cost_plan_query(n, rp, col, u, eps, seed, kappa, max_depth=6, min_pairs=min_pairs,
+                                  max_nodes=max_nodes)
+        deepest = max(deepest, int(q.depth.max()))
+        srt = np.sort(q.pi)[::-1]
+        tie = max_nodes < n and srt[max_nodes] > 0 and srt[max_nodes - 1] - srt[max_nodes] <= 1e-12 * srt[max_nodes - 1]
+        if not _clean_R(q.pi, q.R_b, scale=C ** (2.0 * q.depth)) or gap <= 1e-9 or tie:
+            continue
+        s = g.query(u, C, eps, seed)
+        st = g.stats()
+        assert st["alg3_nodes"] == int(np.count_nonzero(q.depth))
+        assert st["sum_R"] == int(q.R.sum())
+        assert st["pair_steps"] == q.pair_steps
+        assert np.max(np.abs(s - q.s)) <= TOL
+        checked += 1
+    assert checked >= 2
+    assert deepest >= 3
     g.close()
 
 
@@ -188,6 +305,11 @@ def test_alg3_within_eps_and_fewer_pairs(esim):
     s2 = g.query(u, C, eps, 0)
     base = g.stats()
     g.set_option("alg3", 1)
+    sp = g.query(u, C, eps, 0)  # the paper's depth rule keeps R(k) pairs
+    stp = g.stats()
+    assert stp["alg3_nodes"] > 0 and stp["sum_R"] <= base["sum_R"]
+    assert np.max(np.abs(sp - S[:, u])) <= eps
+    g.set_option("alg3_rule", 1)  # the cost model spends fewer pairs
     g.set_option("alg3_min_pairs", 1e4)
     s3 = g.query(u, C, eps, 0)
     st = g.stats()
@@ -221,19 +343,16 @@ def test_alg3_rejects_repeated_in_edges(esim):
     g.close()
 
 
-def test_alg3_with_basic_allocation_and_fp32c(esim, oracle_walks):
-    from oracle import exactsim
+def test_alg3_cost_model_with_basic_allocation_and_fp32c(esim, oracle_walks):
     n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
-    g = esim.Graph(n, rp, col, alloc=1, alg3=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6)
+    g = esim.Graph(n, rp, col, alloc=1, alg3=1, alg3_rule=1, alg3_min_pairs=1e3, alg3_max_nodes=16,
+                   alg3_max_depth=6)
     eps = 2e-2
     checked = 0
     for u, seed in ((5, 1), (1234, 2), (2999, 3)):
-        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, mode="basic", alg3=True, alg3_max_depth=6,
-                           alg3_min_pairs=1e3, alg3_max_nodes=16)
-        v = q.R_b * q.pi
-        vv = np.concatenate([v, v * C ** (2.0 * q.depth)])
-        frac = np.abs(vv - np.round(vv))
-        if not np.all((frac > 1e-12 * vv) | (vv == 0)) or q.plan_gap <= 1e-9:
+        q, gap = _cost_plan_query(n, rp, col, u, eps, seed, mode="basic", max_depth=6, min_pairs=1e3,
+                                  max_nodes=16)
+        if not _clean_R(q.pi, q.R_b, "basic", scale=C ** (2.0 * q.depth)) or gap <= 1e-9:
             continue
         s = g.query(u, C, eps, seed)
         st = g.stats()
@@ -255,18 +374,17 @@ def test_alg3_with_basic_allocation_and_fp32c(esim, oracle_walks):
 # (2, 1.5e6) splits the exploited nodes of each source between the early and the main stream
 @pytest.mark.parametrize("overlap,early", [(0, 1e30), (4, 1e30), (4, 1.0), (2, 1.5e6)])
 def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, early):
-    """The walks split over the side stream (non-candidates), the early stream (each
-    planned candidate) and the main stream give the oracle's counts and scores."""
-    from oracle import exactsim
+    """Cost model: the walks split over the side stream (non-candidates), the early stream
+    (each planned candidate) and the main stream give the oracle's counts and scores on
+    the same plan."""
     n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
-    g = esim.Graph(n, rp, col, alg3=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6,
+    g = esim.Graph(n, rp, col, alg3=1, alg3_rule=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6,
                    alg3_overlap=overlap, alg3_early_pairs=early)
     eps = 3e-3
     checked = 0
     for u, seed in ((5, 1), (1234, 2), (2999, 3)):
-        q = exactsim.query(n, rp, col, u, C, eps, seed=seed, alg3=True, alg3_max_depth=6, alg3_min_pairs=1e3,
-                           alg3_max_nodes=16)
-        if not _clean(q.pi, q.R_b, q.depth.astype(np.float64), 16) or q.plan_gap <= 1e-9:
+        q, gap = _cost_plan_query(n, rp, col, u, eps, seed, max_depth=6, min_pairs=1e3, max_nodes=16)
+        if not _clean_R(q.pi, q.R_b, scale=C ** (2.0 * q.depth)) or gap <= 1e-9:
             continue
         s = g.query(u, C, eps, seed)
         st = g.stats()

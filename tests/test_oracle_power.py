@@ -1,6 +1,7 @@
 """Pins of the Power Method oracle (O1) and of the exact diagonal correction D.
 
-Every check here compares against something other than the oracle itself:
+Every check here compares against something other than the oracle itself (and runs
+for both the NumPy/SciPy Power Method and its C restatement):
 closed forms derived from the SimRank definition (Eq. intro-simrank), an exact
 rational solve of the walk-meeting chain (Eq. scwwalk), and the invariants the
 paper states for D (Eq. def-lsim2: 1-c <= D <= 1; Algorithm 3: din=0 -> 1,
@@ -17,8 +18,21 @@ from oracle import pair_chain, power
 C = 0.6
 
 
+_IMPL = {"name": "python"}
+
+
+@pytest.fixture(autouse=True, params=["python", "c"])
+def impl(request):
+    """Every pin runs against both implementations of the Power Method (NumPy/SciPy and
+    the C one with OpenMP that the larger tests use)."""
+    _IMPL["name"] = request.param
+    yield request.param
+
+
 def _S(g, c=C):
     n, rp, col = g
+    if _IMPL["name"] == "c":
+        return power.power_method_c(n, rp, col, c)
     return power.power_method(n, rp, col, c)
 
 

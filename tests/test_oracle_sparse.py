@@ -72,7 +72,7 @@ def test_sparse_query_within_eps_of_power_method(oracle_walks):
     assert q.R_b == lin.sample_base(n, C, eps / 2, 16.0)
     assert np.max(np.abs(q.s - S[:, 5])) <= eps
     # with Algorithm 3 as well
-    q3 = exactsim.query(n, rp, col, 5, C, eps, seed=2, kappa=400.0, sparse=True, alg3=True, alg3_min_pairs=1e3)
+    q3 = exactsim.query(n, rp, col, 5, C, eps, seed=2, kappa=400.0, sparse=True, alg3=True)
     assert np.count_nonzero(q3.depth) > 0
     assert np.max(np.abs(q3.s - S[:, 5])) <= eps
 

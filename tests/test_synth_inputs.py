@@ -66,6 +66,21 @@ def test_chung_lu_recipe(gamma):
     assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
 
 
+def test_chung_lu_torch_recipe():
+    """The torch generator of the largest Chung-Lu graph keeps the recipe (run on the CPU)."""
+    pytest.importorskip("torch")
+    gamma = 2.2
+    n, rp, col = synth.chung_lu_torch(200_000, 2_000_000, gamma=gamma, seed=2, device="cpu")
+    _check_csr(n, rp, col, 2_000_000)
+    din = np.diff(rp)
+    dout = np.bincount(col, minlength=n)
+    for deg in (din, dout):
+        assert abs(_hill_tail_exponent(deg) - (gamma - 1.0)) < 0.3
+        assert _top_share(deg) > 0.25
+    _, rp2, col2 = synth.chung_lu_torch(200_000, 2_000_000, gamma=gamma, seed=2, device="cpu")
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+
+
 def test_rmat_recipe():
     n, rp, col = synth.rmat(14, 200_000, seed=1)
     assert n == 1 << 14
