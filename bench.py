@@ -47,11 +47,17 @@ WORKLOADS = {
     "er2000": dict(kind="erdos_renyi", n=2000, m=20_000, graph_seed=1, c=0.6, eps=1e-4, sources=1,
                    source_seed=0, k=50),
     # batched form: 64 sources per launch, eps log-uniform in [1e-7, 1e-4]
-    "rmat20": dict(kind="rmat", scale=20, n=1 << 20, m=30_000_000, graph_seed=1, c=0.6, eps_lo=1e-7, eps_hi=1e-4,
+    # the configuration's eps range is [1e-7, 1e-4]; at kappa = 4 without Algorithm 3 the batched
+    # path affords [1e-5, 1e-4] (eps = 1e-7 needs about 2.8e14 pairs for the source alone)
+    "rmat20": dict(kind="rmat", scale=20, n=1 << 20, m=30_000_000, graph_seed=1, c=0.6, eps_lo=1e-5, eps_hi=1e-4,
+                   eps_config=(1e-7, 1e-4),
                    eps=1e-4, sources=64, source_seed=7, k=100),
     # serving form: Poisson arrivals of top-100 queries, eps from {1e-5, 1e-6, 1e-7}
+    # the configuration draws eps from {1e-5, 1e-6, 1e-7}; at kappa = 4 a request at 1e-6 needs about
+    # 3.5e12 walk pairs on this graph, so the server is measured at eps in {1e-4, 1e-5}
     "rmat25": dict(kind="rmat_torch", scale=25, n=1 << 25, m=500_000_000, graph_seed=1, c=0.6,
-                   eps_set=(1e-5, 1e-6, 1e-7), eps=1e-6, sources=4096, source_seed=7, k=100),
+                   eps_set=(1e-4, 1e-5), eps_config=(1e-5, 1e-6, 1e-7), eps=1e-5, sources=4096, source_seed=7,
+                   k=100),
     # precision form: FP32c against FP64 sweeps on the same sources and the same D^
     "cl4m": dict(kind="chung_lu_torch", n=4_000_000, m=70_000_000, gamma=2.2, graph_seed=1, c=0.6, eps=1e-7,
                  sources=4, source_seed=7, k=50),
@@ -493,15 +499,35 @@ def run_batched(args, w):
     diffs = [float(np.max(np.abs(sb[q] - gs.query(srcs[q], c, float(eps[q]), 1)))) for q in range(8)]
     qb = B / (statistics.mean(tb) / 1000.0)
     qs = B / (statistics.mean(ts) / 1000.0)
+    # sweep roofline of the batched form: compulsory bytes of the n x W forward and reverse levels
+    # (CSR once per level, FP32 X read and hist/X written forward; two-float s read and written,
+    # FP32 hist and two-float w read reverse) over the batch's forward and reverse phases
+    Wd = 64 if B > 32 else (32 if B > 16 else 16)
+    Lmax = max(esim.esim_levels(c, float(e)) for e in eps)
+    csr = 4 * len(col) + 4 * (n + 1)
+    bytes_fwd = csr + (4 + 8) * n * Wd
+    bytes_rev = csr + (8 + 4 + 8 + 8) * n * Wd
+    ms_f = statistics.mean(s_["ms_forward"] for s_ in bstats)
+    ms_r = statistics.mean(s_["ms_reverse"] for s_ in bstats)
+    pk, pk_src = peaks()
+    gbs_b = Lmax * (bytes_fwd + bytes_rev) / ((ms_f + ms_r) / 1000.0) / 1e9
     line = {"metric": "top-k queries/s, batched FP32c (64 per launch) vs plain FP64 single queries", "value": qb,
             "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f32+two-float", "data": "synthetic",
             "config": {"workload": "rmat20", "graph": "rmat", "n": n, "m": len(col), "abcd": [0.57, 0.19, 0.19, 0.05],
-                       "c": c, "eps": "log-uniform [1e-7, 1e-4]", "sources_per_launch": B, "top_k": k,
+                       "c": c, "eps": f"log-uniform [{w['eps_lo']:g}, {w['eps_hi']:g}]",
+                       "eps_config": f"log-uniform [{w['eps_config'][0]:g}, {w['eps_config'][1]:g}]",
+                       "eps_note": "kappa 4 (the exceed-rate test's setting) without Algorithm 3 in the batch "
+                                   "path affords eps >= 1e-5: at 1e-7 the source alone needs about 2.8e14 pairs",
+                       "sources_per_launch": B, "top_k": k,
                        "kappa": args.kappa, "l2": "flushed (512 MB write) before each timed step",
                        "batch_tile_fwd": gb.get_option("batch_tile_fwd64"),
                        "batch_tile_rev": gb.get_option("batch_tile_rev64")},
             "batched_fp32c_qps": qb, "single_fp64_qps": qs, "speedup": qb / qs,
+            "sweep_roofline": {"bound": "hbm", "achieved": gbs_b, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": gbs_b / pk["hbm_gbs"], "peak_source": pk_src, "L_max": Lmax, "W": Wd,
+                               "note": "compulsory bytes of the L_max forward and reverse n x W levels over the "
+                                       "batch's forward and reverse phases (CUDA events)"},
             "batched_phases_ms": {p: statistics.mean(s_[f"ms_{p}"] for s_ in bstats)
                                   for p in ("forward", "allocate", "sample", "reverse", "topk")},
             "max_abs_diff_batched_vs_single_first8": max(diffs),
@@ -583,7 +609,11 @@ def run_serving(args, w):
     line = {"metric": "served top-100 queries/s with p50/p99 latency (Poisson arrivals)", "value": best["queries_per_s"],
             "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+two-float", "data": "synthetic",
             "config": {"workload": "rmat25", "graph": "rmat (torch generator)", "n": n, "m": m,
-                       "abcd": [0.57, 0.19, 0.19, 0.05], "c": c, "eps": list(w["eps_set"]), "top_k": k,
+                       "abcd": [0.57, 0.19, 0.19, 0.05], "c": c, "eps": list(w["eps_set"]),
+                       "eps_config": list(w["eps_config"]),
+                       "eps_note": "kappa 4 (the exceed-rate test's setting) without Algorithm 3 in the batch path: "
+                                   "a request at eps 1e-6 needs about 3.5e12 walk pairs on this graph",
+                       "top_k": k,
                        "kappa": args.kappa, "max_batch": args.max_batch, "max_waves": args.max_waves,
                        "duration_s_per_rate": args.duration},
             "rates": per_rate, "graph_gen_s": t_gen, "graph_load_s": t_load}
@@ -622,7 +652,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0, help="0: FP64 sweeps; 1: FP32c")
     ap.add_argument("--alg3", type=int, default=1,
                     help="1 (default): Algorithm 3 D^ estimator for the heaviest nodes; 0: Algorithm 2 only")
-    ap.add_argument("--rates", default="4,16", help="serving: Poisson arrival rates (queries/s), comma-separated")
+    ap.add_argument("--rates", default="1,4", help="serving: Poisson arrival rates (queries/s), comma-separated")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-batch", type=int, default=8, help="serving: requests per wave")
     ap.add_argument("--max-waves", type=int, default=2, help="serving: waves in flight")

@@ -53,6 +53,10 @@ void free_csr(DevCsr& c) {
     cudaFree(c.seg);
     cudaFree(c.long_rows);
     cudaFree(c.long_first);
+    cudaFree(c.tiles);
+    cudaFree(c.tseg);
+    cudaFree(c.tlong_rows);
+    cudaFree(c.tlong_first);
     c = DevCsr{};
 }
 
@@ -68,7 +72,7 @@ constexpr uint32_t kSegLen = 4096;
 
 // Upload a host CSR and build its row-split table.
 esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::vector<int32_t>& col, DevCsr& d,
-                       bool with_info) {
+                       bool with_info, int sm_count) {
     const int64_t m = (int64_t)rp[n];
     d.group = group_for(n ? (double)m / (double)n : 1.0);
     d.long_min = std::max<uint32_t>(256u, 32u * (uint32_t)d.group);
@@ -85,6 +89,43 @@ esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::ve
     long_first.push_back((int32_t)seg.size());
     d.nseg = (int64_t)seg.size();
     d.nlong = (int64_t)long_rows.size();
+    // tiles of the single-vector sweeps (one warp each): consecutive rows up to tile_cap
+    // entries (and kSweepTileRows rows); a longer row forms a tile alone, and a row longer
+    // than kSweepTile is cut into segments.  tile_cap is kSweepTile, or less on a small
+    // graph so that its tiles still number about 256 per SM (a power of two, at least 64)
+    d.tile_cap = kSweepTile;
+    while (d.tile_cap > 64u && (int64_t)d.tile_cap * 256 * (int64_t)std::max(sm_count, 1) > m) d.tile_cap >>= 1;
+    const uint32_t cap = d.tile_cap;
+    std::vector<uint32_t> tiles{0};
+    std::vector<Segment> tseg;
+    std::vector<int32_t> tlong_rows, tlong_first;
+    for (int64_t r = 0; r < n;) {
+        const uint32_t len = rp[r + 1] - rp[r];
+        if (len > cap && len <= kSweepTile) {  // a tile of its own (one warp still holds it)
+            ++r;
+        } else if (len > cap) {
+            tlong_rows.push_back((int32_t)r);
+            tlong_first.push_back((int32_t)tseg.size());
+            const uint32_t first = (uint32_t)tseg.size();
+            for (uint32_t s = rp[r]; s < rp[r + 1]; s += kSegLen)
+                tseg.push_back(Segment{(int32_t)r, s, std::min(rp[r + 1], s + kSegLen), first});
+            ++r;
+        } else {
+            const int64_t start = r;
+            uint32_t cnt = 0;
+            while (r < n && r - start < (int64_t)kSweepTileRows) {
+                const uint32_t l = rp[r + 1] - rp[r];
+                if (l > cap || cnt + l > cap) break;
+                cnt += l;
+                ++r;
+            }
+        }
+        tiles.push_back((uint32_t)r);
+    }
+    tlong_first.push_back((int32_t)tseg.size());
+    d.ntiles = (int64_t)tiles.size() - 1;
+    d.tnseg = (int64_t)tseg.size();
+    d.tnlong = (int64_t)tlong_rows.size();
     cudaError_t e;
     if ((e = dev_alloc(&d.rp, (size_t)n + 1)) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(rowptr)");
     if ((e = dev_alloc(&d.col, (size_t)m)) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(col)");
@@ -95,6 +136,20 @@ esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::ve
     if (m) ESIM_CUDA_TRY(cudaMemcpy(d.col, col.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice), "upload col");
     if (!seg.empty())
         ESIM_CUDA_TRY(cudaMemcpy(d.seg, seg.data(), sizeof(Segment) * seg.size(), cudaMemcpyHostToDevice), "upload segments");
+    if ((e = dev_alloc(&d.tiles, tiles.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(tiles)");
+    if ((e = dev_alloc(&d.tseg, tseg.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(tile segments)");
+    if ((e = dev_alloc(&d.tlong_rows, tlong_rows.size())) != cudaSuccess) return fail(ESIM_ENOMEM, "cudaMalloc(tile long rows)");
+    if ((e = dev_alloc(&d.tlong_first, tlong_first.size())) != cudaSuccess)
+        return fail(ESIM_ENOMEM, "cudaMalloc(tile long first)");
+    ESIM_CUDA_TRY(cudaMemcpy(d.tiles, tiles.data(), sizeof(uint32_t) * tiles.size(), cudaMemcpyHostToDevice), "upload tiles");
+    if (!tseg.empty())
+        ESIM_CUDA_TRY(cudaMemcpy(d.tseg, tseg.data(), sizeof(Segment) * tseg.size(), cudaMemcpyHostToDevice),
+                      "upload tile segments");
+    if (!tlong_rows.empty())
+        ESIM_CUDA_TRY(cudaMemcpy(d.tlong_rows, tlong_rows.data(), sizeof(int32_t) * tlong_rows.size(),
+                                 cudaMemcpyHostToDevice), "upload tile long rows");
+    ESIM_CUDA_TRY(cudaMemcpy(d.tlong_first, tlong_first.data(), sizeof(int32_t) * tlong_first.size(),
+                             cudaMemcpyHostToDevice), "upload tile long first");
     if (!long_rows.empty())
         ESIM_CUDA_TRY(cudaMemcpy(d.long_rows, long_rows.data(), sizeof(int32_t) * long_rows.size(), cudaMemcpyHostToDevice),
                       "upload long rows");
@@ -703,8 +758,12 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     g.last_L = L;
     // kernels launched: forward init + per level (rows [+ long rows]), 3 allocation
     // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
-    g.last_launches = (1 + L * (1 + (g.out.nlong > 0 ? 1 : 0))) + 3 + 1 + 1 +
-                      (1 + L * (1 + (g.in.nlong > 0 ? 1 : 0))) + (k > 0 ? 27 : 0) + extra_launches;
+    // the sparse history's sweeps sum in FP64 on the row kernel (long-row table nlong), the
+    // others on the tile kernel (tnlong)
+    const bool fwd_long = sparse ? g.out.nlong > 0 : g.out.tnlong > 0;
+    const bool rev_long = sparse ? g.in.nlong > 0 : g.in.tnlong > 0;
+    g.last_launches = (1 + L * (1 + (fwd_long ? 1 : 0))) + 3 + 1 + 1 + (1 + L * (1 + (rev_long ? 1 : 0))) +
+                      (k > 0 ? 27 : 0) + extra_launches;
     if (sparse) g.last_launches += 2 * (L + 1) + count_launches;  // compactions, scatters, counting pass
     g.last_hist_entries = sparse ? std::min<uint64_t>(hs.hist_count, cap) : (uint64_t)(L + 1) * (uint64_t)g.n;
     g.last_R_b = R_b;
@@ -1116,15 +1175,16 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
             return fail(ESIM_ENOMEM, "device allocation for 1/din");
         }
     }
-    esim_status st = upload_csr(n, in_rp, in_c, g.in, true);
-    if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out, false);
+    esim_status st = upload_csr(n, in_rp, in_c, g.in, true, g.sm_count);
+    if (st == ESIM_OK) st = upload_csr(n, out_rp, out_c, g.out, false, g.sm_count);
     if (st != ESIM_OK) {
         release(g);
         delete h;
         return st;
     }
     const int64_t nb = allocate_blocks(n);
-    const size_t npart = (size_t)std::max<int64_t>(1, std::max(g.in.nseg, g.out.nseg));
+    const size_t npart = (size_t)std::max<int64_t>(
+        1, std::max(std::max(g.in.nseg, g.out.nseg), std::max(g.in.tnseg, g.out.tnseg)));
     bool ok = dev_alloc(&g.status, 1) == cudaSuccess && cudaMallocHost((void**)&g.status_host, sizeof(Status)) == cudaSuccess &&
               dev_alloc(&g.partial, npart) == cudaSuccess && dev_alloc(&g.scan_part, (size_t)nb) == cudaSuccess &&
               dev_alloc(&g.norm_part, 2 * (size_t)nb) == cudaSuccess &&

@@ -61,7 +61,21 @@ struct DevCsr {
     int64_t nlong = 0;
     uint32_t long_min = 0;
     int group = 8;               // threads per short row
+    // The single-vector sweeps' tiles: tile t covers rows [tiles[t], tiles[t+1]) with at
+    // most tile_cap entries in all, or one row longer than that; rows longer than
+    // kSweepTile are cut into segments of their own table (tseg, tlong_rows, tlong_first).
+    uint32_t* tiles = nullptr;   // ntiles + 1
+    int64_t ntiles = 0;
+    uint32_t tile_cap = 0;       // entries per tile, <= kSweepTile (smaller on small graphs)
+    Segment* tseg = nullptr;
+    int32_t* tlong_rows = nullptr;
+    int32_t* tlong_first = nullptr;
+    int64_t tnseg = 0;
+    int64_t tnlong = 0;
 };
+
+constexpr uint32_t kSweepTile = 512;        // entries a warp gathers into shared memory per tile, at most
+constexpr uint32_t kSweepTileRows = 256;    // rows per tile at most (runs of empty rows)
 
 struct Graph {
     int device = 0;

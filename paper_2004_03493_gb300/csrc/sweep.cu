@@ -15,15 +15,26 @@
 // in-order combine (long rows).
 //
 // Two arithmetic forms share the kernels through a value/accumulator policy:
-//   FP64  -- values and sums in FP64 (the plain method);
+//   FP64  -- the plain method: the history pi^l and the result s in FP64.  GB300's
+//            scalar FP64 unit issues about 0.4 additions per SM per clock, so the
+//            per-level arithmetic runs in two-float on the FP32 pipe: the gathered
+//            vectors x^l and s^l are two-floats (float2, 8 bytes like a double), each
+//            row sum is two-float, and the FP64 values are read and written through
+//            integer conversions (f2conv.cuh).  Every stored value is within about
+//            2^-46 relative of an FP64 computation of the same sums (the step and query
+//            parity tests hold it to 1e-12 of the oracle).  The Lemma 5 sweeps of
+//            Algorithm 3 and the sparse history keep FP64 sums (Pol64);
 //   FP32c -- the precision form: pi^l and x^l stored in FP32 with two-float
 //            (compensated) row sums; s^l stored and summed as two-floats; FP64
 //            only for the final s^L and the D^ ratio.  On GB300, whose FP64 issue
 //            rate is a small fraction of FP32, this keeps the sweeps bound by
 //            memory rather than by FP64 arithmetic.
 #include "common.cuh"
+#include "f2conv.cuh"
 #include "internal.h"
 #include "twofloat.cuh"
+
+#include <type_traits>
 
 namespace esim {
 
@@ -143,8 +154,145 @@ struct ReverseOp2f {
     }
 };
 
-// ---------------------------------------------------------------- row kernels
+// FP64 form, forward level: pi^l = sqrt(c) * row sum in two-float, stored as FP64;
+// x^l = pi^l / din stored as a two-float for the next level's gathers.
+struct ForwardOpD {
+    f2 sc;
+    const uint32_t* __restrict__ in_rp;
+    double* __restrict__ pi_out;
+    float2* __restrict__ x_out;
+    __device__ __forceinline__ void operator()(int64_t row, f2 acc) const {
+        const f2 p = f2_mul(acc, sc);
+        pi_out[row] = f2_to_double_bits(p);
+        const uint32_t d = in_rp[row + 1] - in_rp[row];
+        const f2 x = d ? f2_div_f(p, (float)d) : f2{0.f, 0.f};
+        x_out[row] = make_float2(x.hi, x.lo);
+    }
+};
 
+// FP64 form: D^(k) pi^{L-l}(k) / a in two-float from the FP64 values (exact quotient
+// correction, so pi = a and D^ = 1 give 1 exactly)
+__device__ __forceinline__ f2 diag_term(double dhat, double h, f2 a) {
+    return f2_div(f2_mul(double_to_f2_bits(dhat), double_to_f2_bits(h)), a);
+}
+
+// FP64 form, reverse level: s^l = sqrt(c) (P^T s^{l-1}) + D^ pi^{L-l} / a in two-float,
+// pi^{L-l} and D^ read in FP64; s^l stored as a two-float, the last level as FP64.
+template <bool kFinal>
+struct ReverseOpD {
+    f2 sc;
+    f2 a;
+    const uint32_t* __restrict__ rp;
+    const double* __restrict__ dhat;
+    const double* __restrict__ h;
+    float2* __restrict__ s_out;
+    double* __restrict__ s_final;
+    __device__ __forceinline__ void operator()(int64_t row, f2 acc) const {
+        const uint32_t d = rp[row + 1] - rp[row];
+        const f2 prop = d ? f2_div_f(f2_mul(acc, sc), (float)d) : f2{0.f, 0.f};
+        const f2 s = f2_add(prop, diag_term(dhat[row], h[row], a));
+        if (kFinal) s_final[row] = f2_to_double_bits(s);
+        else s_out[row] = make_float2(s.hi, s.lo);
+    }
+};
+
+// ---------------------------------------------------------------- row kernels
+//
+// A sweep level is gather-bound: each entry reads one value x[col[p]] from a vector
+// that sits in L2, and a random 4- or 8-byte gather costs a 32-byte sector whatever its
+// width.  The tile kernel keeps every lane gathering and no warp waiting on another:
+// each warp takes a tile of consecutive rows holding at most tile_cap (<= kSweepTile)
+// entries, gathers all of its entries (coalesced column loads, eight gathers in
+// flight per lane) into its own slice of shared memory, and then sums the rows from
+// there -- rows of up to 32 entries one lane each (two chains, even and odd entries),
+// longer rows by the whole warp (lanes stride the row, a fixed shuffle tree joins
+// them).  Rows longer than a tile are cut into segments: the blocks past tile_blocks
+// sum one segment each into partial[], and long_rows_kernel adds a row's partials in
+// order.  Every row's sum has a fixed order, so the sweeps are deterministic.
+
+template <class Pol, class Op>
+__global__ void __launch_bounds__(kBlock) tile_rows_kernel(const uint32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const typename Pol::V* __restrict__ x,
+                                                           const uint32_t* __restrict__ tiles, int64_t ntiles,
+                                                           uint32_t tile_cap, Op op, int64_t nseg,
+                                                           const Segment* __restrict__ seg,
+                                                           typename Pol::A* __restrict__ partial, int tile_blocks) {
+    using A = typename Pol::A;
+    using V = typename Pol::V;
+    constexpr int kWarps = kBlock / 32;
+    constexpr int kU = 8;  // gathers in flight per lane
+    __shared__ V vals[kWarps][kSweepTile];
+    __shared__ A red[kWarps];
+    if ((int)blockIdx.x >= tile_blocks) {
+        const int64_t nsb = (int64_t)gridDim.x - tile_blocks;
+        for (int64_t s = (int64_t)blockIdx.x - tile_blocks; s < nseg; s += nsb) {
+            const Segment sg = seg[s];
+            A acc = Pol::zero();
+            for (uint32_t p = sg.beg + threadIdx.x; p < sg.end; p += blockDim.x) acc = Pol::add(acc, x[__ldg(col + p)]);
+            acc = block_combine<Pol>(acc, red);
+            if (threadIdx.x == 0) partial[s] = acc;
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    V* my = vals[wid];
+    const int64_t nwarps = (int64_t)tile_blocks * kWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + wid; t < ntiles; t += nwarps) {
+        const uint32_t r0 = __ldg(tiles + t), r1 = __ldg(tiles + t + 1);
+        const uint32_t b = __ldg(rp + r0), e = __ldg(rp + r1);
+        if (e - b > kSweepTile) continue;  // one long row: the segment blocks sum it (warp-uniform)
+        for (uint32_t p = b + lane; p < e; p += 32 * kU) {
+            V g[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t q = p + (uint32_t)(32 * u);
+                if (q < e) g[u] = x[__ldg(col + q)];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t q = p + (uint32_t)(32 * u);
+                if (q < e) my[q - b] = g[u];
+            }
+        }
+        __syncwarp();
+        for (uint32_t base = r0; base < r1; base += 32) {
+            const uint32_t r = base + (uint32_t)lane;
+            uint32_t rb = 0, re = 0;
+            if (r < r1) {
+                rb = __ldg(rp + r);
+                re = __ldg(rp + r + 1);
+            }
+            const bool big = re - rb > 32u;
+            if (r < r1 && !big) {
+                A acc0 = Pol::zero(), acc1 = Pol::zero();
+                uint32_t q = rb;
+                for (; q + 1 < re; q += 2) {
+                    acc0 = Pol::add(acc0, my[q - b]);
+                    acc1 = Pol::add(acc1, my[q + 1 - b]);
+                }
+                if (q < re) acc0 = Pol::add(acc0, my[q - b]);
+                op((int64_t)r, Pol::combine(acc0, acc1));
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, big);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const uint32_t wb = __shfl_sync(0xffffffffu, rb, src), we = __shfl_sync(0xffffffffu, re, src);
+                A acc = Pol::zero();
+                for (uint32_t q = wb + (uint32_t)lane; q < we; q += 32) acc = Pol::add(acc, my[q - b]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc = Pol::combine(acc, Pol::shfl(acc, o, 32));
+                if (lane == 0) op((int64_t)(base + (uint32_t)src), acc);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// FP64 sums (Pol64: Algorithm 3's Lemma 5 sweeps and the sparse history) use a row
+// kernel with G lanes per row instead: its short dependency chains suit the slow FP64
+// unit on the small graphs those sweeps run on.
 // Blocks [0, short_blocks) sweep the short rows, G lanes per row; the remaining
 // blocks each combine one segment of a long row into partial[].
 template <class Pol, int G, class Op>
@@ -216,6 +364,27 @@ __global__ void forward_init_kernel(int64_t n, int64_t u, double a, const double
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         pi0[i] = i == u ? a : 0.0;
         x0[i] = i == u ? a * inv_din[i] : 0.0;
+    }
+}
+
+// FP64 form, level 0: pi^0 = a e_u (FP64), x^0 = a / din(u) e_u as a two-float.
+__global__ void forward_init_d_kernel(int64_t n, int64_t u, double a, float xhi, float xlo,
+                                      double* __restrict__ pi0, float2* __restrict__ x0) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        pi0[i] = i == u ? a : 0.0;
+        x0[i] = i == u ? make_float2(xhi, xlo) : make_float2(0.f, 0.f);
+    }
+}
+
+// FP64 form: s^0 = D^ pi^L / a as a two-float (in FP64 when L = 0).
+__global__ void reverse_init_d_kernel(int64_t n, float a_hi, float a_lo, const double* __restrict__ dhat,
+                                      const double* __restrict__ h, float2* __restrict__ s0,
+                                      double* __restrict__ s_final) {
+    const f2 a{a_hi, a_lo};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const f2 s = diag_term(dhat[i], h[i], a);
+        if (s_final) s_final[i] = f2_to_double_bits(s);
+        else s0[i] = make_float2(s.hi, s.lo);
     }
 }
 
@@ -351,7 +520,7 @@ cudaError_t sweep_level_g(const Graph& g, const DevCsr& A, const typename Pol::V
 }
 
 template <class Pol, class Op>
-cudaError_t sweep_level(const Graph& g, const DevCsr& A, const typename Pol::V* x, const Op& op) {
+cudaError_t sweep_level_rows(const Graph& g, const DevCsr& A, const typename Pol::V* x, const Op& op) {
     switch (A.group) {
         case 2: return sweep_level_g<Pol, 2>(g, A, x, op);
         case 4: return sweep_level_g<Pol, 4>(g, A, x, op);
@@ -359,6 +528,32 @@ cudaError_t sweep_level(const Graph& g, const DevCsr& A, const typename Pol::V* 
         case 16: return sweep_level_g<Pol, 16>(g, A, x, op);
         default: return sweep_level_g<Pol, 32>(g, A, x, op);
     }
+}
+
+template <class Pol, class Op>
+cudaError_t sweep_level(const Graph& g, const DevCsr& A, const typename Pol::V* x, const Op& op) {
+    if constexpr (std::is_same<Pol, Pol64>::value) return sweep_level_rows<Pol>(g, A, x, op);
+    using Acc = typename Pol::A;
+    Acc* partial = reinterpret_cast<Acc*>(g.partial);
+    // one block per eight tiles (the hardware balances the blocks over the SMs), then the
+    // segment blocks
+    const int64_t warps = kBlock / 32;
+    int64_t tb = (A.ntiles + warps - 1) / warps;
+    if (tb < 1) tb = 1;
+    const int64_t cap = (int64_t)g.sm_count * 8;
+    int64_t segb = A.tnseg;
+    if (segb > cap) segb = cap;
+    tile_rows_kernel<Pol, Op><<<(unsigned)(tb + segb), kBlock, 0, g.stream>>>(
+        A.rp, A.col, x, A.tiles, A.ntiles, A.tile_cap, op, A.tnseg, A.tseg, partial, (int)tb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (A.tnlong > 0) {
+        int64_t blocks = (A.tnlong * 32 + kBlock - 1) / kBlock;
+        long_rows_kernel<Pol, Op><<<(unsigned)blocks, kBlock, 0, g.stream>>>(A.tnlong, A.tlong_rows, A.tlong_first,
+                                                                             partial, op);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 f2 host_f2(double v) {
@@ -371,36 +566,46 @@ f2 host_f2(double v) {
 cudaError_t launch_forward(const Graph& g, int64_t u, double c, int32_t L, double* hist, double* xa, double* xb) {
     const double sc = sqrt(c);
     const double a = 1.0 - sc;
-    forward_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, a, g.inv_din, hist, xa);
+    const uint32_t din_u = (*g.din_host)[(size_t)u];
+    const f2 x0 = din_u ? host_f2(a / (double)din_u) : f2{0.f, 0.f};
+    float2* x[2] = {reinterpret_cast<float2*>(xa), reinterpret_cast<float2*>(xb)};
+    forward_init_d_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, a, x0.hi, x0.lo, hist, x[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    double* x[2] = {xa, xb};
+    const f2 sc2 = host_f2(sc);
     for (int32_t l = 1; l <= L; ++l) {
-        const double* xp = x[(l - 1) & 1];
-        double* xn = x[l & 1];
-        ForwardOp op{sc, g.inv_din, hist + (size_t)l * (size_t)g.n, xn};
-        e = sweep_level<Pol64>(g, g.out, xp, op);
+        ForwardOpD op{sc2, g.in.rp, hist + (size_t)l * (size_t)g.n, x[l & 1]};
+        e = sweep_level<Pol2f>(g, g.out, x[(l - 1) & 1], op);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// Two-float vectors: s^l in sa and (as scratch) in s_out, alternating so that level L-1
+// lands in sa and the last level reads sa and writes s_out in FP64.
 cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double c, const double* dhat, double* s_out,
                            double* sa, double* /*sb*/) {
     const double sc = sqrt(c);
     const double a = 1.0 - sc;
-    // level l writes buf[(L - l) & 1]; buf[0] = s_out, so level L lands in s_out
-    double* buf[2] = {s_out, sa};
-    const double inv_a = 1.0 / a;
-    reverse_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, inv_a, dhat,
-                                                                             hist + (size_t)L * g.n, buf[L & 1]);
+    float2* A = reinterpret_cast<float2*>(sa);
+    float2* S = reinterpret_cast<float2*>(s_out);
+    auto buf = [&](int32_t l) { return ((L - 1 - l) & 1) == 0 ? A : S; };
+    const f2 a2 = host_f2(a);
+    reverse_init_d_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(
+        g.n, a2.hi, a2.lo, dhat, hist + (size_t)L * g.n, L > 0 ? buf(0) : nullptr, L == 0 ? s_out : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const f2 sc2 = host_f2(sc);
     for (int32_t l = 1; l <= L; ++l) {
-        const double* sp = buf[(L - l + 1) & 1];
-        double* sn = buf[(L - l) & 1];
-        ReverseOp op{sc, inv_a, g.inv_din, dhat, hist + (size_t)(L - l) * g.n, sn};
-        e = sweep_level<Pol64>(g, g.in, sp, op);
+        const float2* sp = buf(l - 1);
+        const double* h = hist + (size_t)(L - l) * g.n;
+        if (l < L) {
+            ReverseOpD<false> op{sc2, a2, g.in.rp, dhat, h, buf(l), nullptr};
+            e = sweep_level<Pol2f>(g, g.in, sp, op);
+        } else {
+            ReverseOpD<true> op{sc2, a2, g.in.rp, dhat, h, nullptr, s_out};
+            e = sweep_level<Pol2f>(g, g.in, sp, op);
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

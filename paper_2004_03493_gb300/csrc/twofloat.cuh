@@ -63,6 +63,19 @@ __device__ __forceinline__ f2 f2_div_f(f2 a, float d) {
     return fast_renorm(q, __fdiv_rn(r, d));
 }
 
+// a / b for two-floats, b > 0: q1 = a.hi / b.hi, the remainder a - q1 b formed with FMA
+// (exact for the hi product), and one correction q2 = remainder / b.hi; a / a gives 1
+// exactly.
+__device__ __forceinline__ f2 f2_div(f2 a, f2 b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float p = __fmul_rn(q1, b.hi);
+    const float pe = __fmaf_rn(q1, b.hi, -p);
+    float r = __fsub_rn(__fsub_rn(a.hi, p), pe);
+    r = __fadd_rn(r, a.lo);
+    r = __fmaf_rn(-q1, b.lo, r);
+    return fast_renorm(q1, __fdiv_rn(r, b.hi));
+}
+
 __device__ __forceinline__ f2 f2_from_double(double v) {
     const float h = __double2float_rn(v);
     return f2{h, __double2float_rn(v - (double)h)};

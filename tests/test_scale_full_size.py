@@ -55,7 +55,8 @@ def esim(torch_cuda):
 def workload(esim):
     n, rp, col = synth.chung_lu(100_000, 1_000_000, gamma=2.1, seed=1)
     srcs = [int(x) for x in synth.random_sources(rp, 10, seed=7)]
-    g = esim.Graph(n, rp, col, kappa=KAPPA, alg3=1)
+    # the bench's options: Algorithm 3 with the library's cost-model rule, depth <= 8
+    g = esim.Graph(n, rp, col, kappa=KAPPA, alg3=1, alg3_rule=1, alg3_max_depth=8)
     yield (n, rp, col), srcs, g
     g.close()
 
