@@ -67,6 +67,9 @@ METRIC = "single-source SimRank top-k queries/s (Chung-Lu n=1e5 m=1e6, eps=1e-6,
 # multiplies + 2 three-input XORs); step logic = 2 threshold compares, 2 multiply-shift picks,
 # 2 row loads, 2 neighbour loads
 INSTR_PER_PAIR_STEP = 48.0
+# DRAM bytes of one sampler launch of the bench query, one-pass ncu capture of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum; the graph once, it stays in L2)
+SAMPLER_TRAFFIC = 6.09e6
 # Accuracy of the timed configuration as tests/test_gpu_exceed.py measured it on GB300: the same
 # options (eps 1e-6, kappa 4, FP64, Algorithm 3 cost-model rule, depth <= 8) on the directed
 # Chung-Lu graph of the same recipe at n = 2e4, m = 2e5 (where the Power Method gives S), 100
@@ -798,7 +801,7 @@ def main():
                      "ms_per_launch": ms_sample / max(sampler_launches, 1),
                      "bound": "alu", "achieved": achieved / 1e9,
                      "peak": peak_steps / 1e9, "unit": "G pair-steps/s", "frac": achieved / peak_steps,
-                     "traffic": None,
+                     "traffic": SAMPLER_TRAFFIC,
                      "peak_source": f"{sm_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz ({pk_src} clock) / "
                                     f"{INSTR_PER_PAIR_STEP:.0f} integer instructions per pair-step"},
         "phases_ms": {p: v / max(len(stats), 1) for p, v in ms_phase.items()},

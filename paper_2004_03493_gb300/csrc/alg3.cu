@@ -147,6 +147,26 @@ __global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double*
 constexpr unsigned long long kOne = 1ull << 63;
 constexpr double kInvOne = 1.0 / 9223372036854775808.0;  // 2^-63
 
+// floor(H / d) for 1 <= d < 2^32, with M = floor((2^64 - 1) / d) precomputed per node
+// (Graph::din_magic): the high word of H M never exceeds the quotient and falls short of
+// it by at most two, which the remainder corrects.  The GPU has no 64-bit integer divide;
+// this replaces its long software sequence by a multiply-high and a few adds.
+__host__ __device__ __forceinline__ unsigned long long div_by_magic(unsigned long long H, uint32_t d,
+                                                                     unsigned long long M) {
+    if (d == 1u) return H;
+#ifdef __CUDA_ARCH__
+    unsigned long long q = __umul64hi(H, M);
+#else
+    unsigned long long q = (unsigned long long)(((unsigned __int128)H * M) >> 64);
+#endif
+    unsigned long long r = H - q * d;
+    while (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
+
 // floor(H^2 / 2^63) for H <= 2^63
 __device__ __forceinline__ unsigned long long fx_sq(unsigned long long H) {
     return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
@@ -200,6 +220,7 @@ struct ProbeGroup {
 struct ProbeStepArgs {
     const uint32_t* in_rp;
     const int32_t* in_col;
+    const unsigned long long* magic;  // floor((2^64 - 1) / din) per node (division by din)
     int s;               // step index (h_{s+1} is produced)
     int src;             // which X buffer holds x_s
     int mode;
@@ -215,7 +236,7 @@ __device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigne
                                                             const double* coef) {
     if (!a.last) {
         const uint32_t d = __ldg(a.in_rp + row + 1) - __ldg(a.in_rp + row);
-        xnext[(size_t)row * kProbeW + lane] = (d && H) ? H / d : 0ull;
+        xnext[(size_t)row * kProbeW + lane] = (d && H) ? div_by_magic(H, d, __ldg(a.magic + row)) : 0ull;
     }
     if (a.mode == 2) return fx_sq(H);
     if (a.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
@@ -754,7 +775,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
             for (int lp = 1; lp <= steps; ++lp) {
-                ProbeStepArgs a{g.in.rp, g.in.col, lp - 1, (lp - 1) & 1, 0, lp == steps ? 1 : 0,
+                ProbeStepArgs a{g.in.rp, g.in.col, g.din_magic, lp - 1, (lp - 1) & 1, 0, lp == steps ? 1 : 0,
                                 ws.Zfx + (size_t)(j + lp) * n, thr};
                 if (lp == steps) {
                     a.mode = 2;

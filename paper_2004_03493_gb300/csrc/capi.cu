@@ -174,6 +174,7 @@ void release(Graph& g) {
     free_csr(g.in);
     free_csr(g.out);
     cudaFree(g.inv_din);
+    cudaFree(g.din_magic);
     cudaFree(g.status);
     if (g.status_host) cudaFreeHost(g.status_host);
     cudaFree(g.ws);
@@ -1167,8 +1168,16 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
             const int64_t d = in_rowptr[j + 1] - in_rowptr[j];
             inv[j] = d ? 1.0 / (double)d : 0.0;
         }
+        std::vector<unsigned long long> magic((size_t)n);
+        for (int64_t j = 0; j < n; ++j) {
+            const int64_t d = in_rowptr[j + 1] - in_rowptr[j];
+            magic[j] = d >= 2 ? ~0ull / (unsigned long long)d : 0ull;
+        }
         if (dev_alloc(&g.inv_din, (size_t)n) != cudaSuccess ||
-            cudaMemcpy(g.inv_din, inv.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(g.inv_din, inv.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            dev_alloc(&g.din_magic, (size_t)n) != cudaSuccess ||
+            cudaMemcpy(g.din_magic, magic.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
             cudaGetLastError();
             release(g);
             delete h;

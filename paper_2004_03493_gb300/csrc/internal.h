@@ -84,6 +84,7 @@ struct Graph {
     DevCsr in;    // rows = nodes, entries = in-neighbours (walks, reverse sweep)
     DevCsr out;   // rows = nodes, entries = out-neighbours (forward sweep)
     double* inv_din = nullptr;  // n: 1/din(i) (0 where din = 0), for the FP64 sweeps
+    unsigned long long* din_magic = nullptr;  // n: floor((2^64 - 1) / din(i)) (0 where din <= 1), exact division
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t side_stream = nullptr;  // Algorithm 3: walks of the other nodes during the planning

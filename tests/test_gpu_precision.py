@@ -95,6 +95,41 @@ def test_allocate_f32_sums_levels(torch_cuda, graph):
     assert np.array_equal(R.cpu().numpy()[clean], R_ref[clean])
 
 
+def test_fp32c_pair_counts_stay_within_their_rounding_of_fp64(torch_cuda, graph):
+    """The FP32c query draws R(k) from FP32 hop vectors: pi within (2L+2) u relative of the
+    FP64 form's pi (the forward bound, summed over levels), so R(k) = ceil(R_b pi(k)^2) moves by
+    at most 2 (2L+2) u R(k) + 1 pairs, and only where R_b pi(k)^2 lies that close to an
+    integer.  Checked node by node on the same source, with the share of nodes whose count
+    differs reported."""
+    torch = torch_cuda
+    name, (n, rp, col), g = graph
+    L = 24
+    R_b = lin.sample_base(n, C, 1e-4, 4.0)
+    out = {}
+    for prec in ("fp64", "fp32c"):
+        pi = torch.empty(n, dtype=torch.float64, device="cuda")
+        R = torch.zeros(n, dtype=torch.uint64, device="cuda")
+        off = torch.zeros(n + 1, dtype=torch.uint64, device="cuda")
+        if prec == "fp64":
+            hist = torch.empty((L + 1) * n, dtype=torch.float64, device="cuda")
+            g.forward(3, C, L, hist)
+            g.allocate(hist, L, R_b, 0, pi, R, off)
+        else:
+            hist = torch.empty((L + 1) * n, dtype=torch.float32, device="cuda")
+            g.forward_f32(3, C, L, hist)
+            g.allocate_f32(hist, L, R_b, 0, pi, R, off)
+        g.sync()
+        out[prec] = (pi.cpu().numpy(), R.cpu().numpy().astype(np.float64))
+    (p64, R64), (p32, R32) = out["fp64"], out["fp32c"]
+    delta = (2 * L + 2) * U32
+    assert np.all(np.abs(p32 - p64) <= delta * p64 + 1e-300)
+    assert np.all(np.abs(R32 - R64) <= np.ceil(2 * delta * R64) + 1)
+    share = float(np.mean(R32 != R64))
+    print(f"{name}: FP32c pair counts differ from FP64 on {share:.2%} of the nodes, "
+          f"{abs(R32.sum() - R64.sum()) / R64.sum():.2e} of the pairs")
+    assert abs(R32.sum() - R64.sum()) <= 2 * delta * R64.sum() + n
+
+
 def test_reverse_f32_matches_fp64_on_same_inputs(torch_cuda, graph):
     torch = torch_cuda
     name, (n, rp, col), g = graph
