@@ -483,7 +483,9 @@ esim_status ensure_a3pws(Graph& g) {
 // allocation gave the others none) explores until its explored edges reach
 // 2 R(k)/sqrt(c), at most alg3_max_depth levels (alg3_paper.cu); it keeps its R(k)
 // pairs, which move without the continuation draw for depth(k) steps.  Z_1 is c/din(k);
-// deeper nodes get Z_1..Z_d from alg3_first_meeting, one node at a time.
+// depth 2 has a closed form over the two-hop neighbourhood (one warp per node); deeper
+// nodes, and depth-2 nodes with a large two-hop neighbourhood, get Z_1..Z_d from
+// alg3_first_meeting, one node at a time.
 esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
     esim_status a3 = ensure_a3pws(g);
     if (a3 != ESIM_OK) return a3;
@@ -493,11 +495,23 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
     ESIM_CUDA_TRY(alg3_paper_z1(g, w.depth, c, w.zsum), "Algorithm 3 Z_1");
     *launches += 1;
     std::vector<uint8_t> depth((size_t)g.n);
-    std::vector<double> zs((size_t)g.n);
     ESIM_CUDA_TRY(cudaMemcpyAsync(depth.data(), w.depth, (size_t)g.n, cudaMemcpyDeviceToHost, g.stream), "copy depth");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depths");
+    // depth 2: the closed form, one warp per node (ids staged in the bit-set area, free now)
+    std::vector<int32_t> d2;
+    for (int64_t k = 0; k < g.n; ++k)
+        if (depth[(size_t)k] == 2) d2.push_back((int32_t)k);
+    if (!d2.empty()) {
+        int32_t* ids = (int32_t*)g.a3pws;
+        ESIM_CUDA_TRY(cudaMemcpyAsync(ids, d2.data(), sizeof(int32_t) * d2.size(), cudaMemcpyHostToDevice, g.stream),
+                      "upload depth-2 nodes");
+        ESIM_CUDA_TRY(alg3_paper_z2(g, ids, (int)d2.size(), c, w.zsum), "Algorithm 3 Z_1 + Z_2");
+        *launches += 1;
+    }
+    std::vector<double> zs((size_t)g.n);
     ESIM_CUDA_TRY(cudaMemcpyAsync(zs.data(), w.zsum, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
                   "copy zsum");
-    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depths");
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depth-2 terms");  // d2 and zs are locals
     int used = 0;
     bool deep = false;
     for (int64_t k = 0; k < g.n; ++k) {
@@ -505,6 +519,7 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
         if (d == 0) continue;
         ++used;
         if (d == 1) continue;
+        if (d == 2 && zs[(size_t)k] == zs[(size_t)k]) continue;  // the closed form took it (NaN: too large)
         if (!deep) {
             a3 = ensure_a3ws(g);
             if (a3 != ESIM_OK) return a3;
@@ -761,10 +776,9 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     // kernels, the sampler, D^, reverse init + per level, and 27 for top-k
     // the sparse history's sweeps sum in FP64 on the row kernel (long-row table nlong), the
     // others on the tile kernel (tnlong)
-    const bool fwd_long = sparse ? g.out.nlong > 0 : g.out.tnlong > 0;
-    const bool rev_long = sparse ? g.in.nlong > 0 : g.in.tnlong > 0;
-    g.last_launches = (1 + L * (1 + (fwd_long ? 1 : 0))) + 3 + 1 + 1 + (1 + L * (1 + (rev_long ? 1 : 0))) +
-                      (k > 0 ? 27 : 0) + extra_launches;
+    const int fwd_per = 1 + (sparse ? (g.out.nlong > 0) : (g.out.tnlong > 0));
+    const int rev_per = 1 + (sparse ? (g.in.nlong > 0) : (g.in.tnlong > 0));
+    g.last_launches = (1 + L * fwd_per) + 3 + 1 + 1 + (1 + L * rev_per) + (k > 0 ? 27 : 0) + extra_launches;
     if (sparse) g.last_launches += 2 * (L + 1) + count_launches;  // compactions, scatters, counting pass
     g.last_hist_entries = sparse ? std::min<uint64_t>(hs.hist_count, cap) : (uint64_t)(L + 1) * (uint64_t)g.n;
     g.last_R_b = R_b;

@@ -246,6 +246,9 @@ cudaError_t alg3_paper_depths(const Graph& g, const uint64_t* R, double c, int m
                               int* launches);
 // zsum(k) = Z_1(k) = c / din(k) for the nodes of depth 1 (others untouched)
 cudaError_t alg3_paper_z1(const Graph& g, const uint8_t* depth, double c, double* zsum);
+// zsum(k) = Z_1(k) + Z_2(k) for the listed nodes (device ids), by the closed form of depth 2;
+// NaN where the two-hop neighbourhood is too large for the kernel's table
+cudaError_t alg3_paper_z2(const Graph& g, const int32_t* ids, int count, double c, double* zsum);
 
 // topk.cu
 constexpr int kTopkMax = 4096;
