@@ -394,6 +394,15 @@ int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_de
  * graph's stream once per level.  Errors: ESIM_ENOTSUP for n > 131072 (the support
  * bit sets), ESIM_EINVAL, ESIM_ENOMEM, ESIM_ECUDA. */
 esim_status esim_alg3_paper_depth(esim_graph* g, const uint64_t* R, double c, int32_t max_depth, uint8_t* depth);
+/* Algorithm 3's exact part for given depths (Lemma 5): zsum[k] = Z_1(k) + ... + Z_d(k) with
+ * d = depth[k] (device uint8[n], 0..16), 0 where d = 0; zsum is device double[n].  Depth 1
+ * is c/din(k); depth 2 uses Lemma 5's closed form over the two-hop neighbourhood (one warp
+ * per node, 63-bit fixed point); deeper nodes, and depth-2 nodes with more than 512
+ * two-hop entries, run esim_alg3_first_meeting's kernels one node at a time.  The query
+ * with option "alg3_rule" = 0 uses this for the depths esim_alg3_paper_depth gives.
+ * Synchronous.  Needs a graph without repeated in-edges (else ESIM_ENOTSUP); ESIM_ENOTSUP
+ * also for n > 131072 (the work space is the depth rule's). */
+esim_status esim_alg3_zsum(esim_graph* g, const uint8_t* depth, double c, double* zsum);
 esim_status esim_sample_depth(esim_graph* g, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
                               uint64_t* counts, uint64_t* pair_steps);
 esim_status esim_dhat_alg3(esim_graph* g, const uint64_t* counts, const uint64_t* off, const uint8_t* depth,

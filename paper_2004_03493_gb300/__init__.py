@@ -16,6 +16,7 @@ from ._native import (  # noqa: F401
     esim_allocate,
     esim_alg3_first_meeting,
     esim_alg3_paper_depth,
+    esim_alg3_zsum,
     esim_sample_depth,
     esim_dhat_alg3,
     esim_dhat,
@@ -164,6 +165,9 @@ class Graph:
 
     def alg3_paper_depth(self, R, c, max_depth, depth):
         esim_alg3_paper_depth(self.handle, R, c, max_depth, depth)
+
+    def alg3_zsum(self, depth, c, zsum):
+        esim_alg3_zsum(self.handle, depth, c, zsum)
 
     def sample_depth(self, off, depth, c, seed, counts, pair_steps=None):
         esim_sample_depth(self.handle, off, depth, c, seed, counts, pair_steps)

@@ -107,6 +107,7 @@ SIGNATURES = {
     "esim_alg3_first_meeting": (_ST, [_P, _I64, _I32, _D, _P]),
     "esim_alg3_depth": (_I32, [_D, _D, _P, _I32, _I64, _I64, _D, _D, _D]),
     "esim_alg3_paper_depth": (_ST, [_P, _P, _D, _I32, _P]),
+    "esim_alg3_zsum": (_ST, [_P, _P, _D, _P]),
     "esim_sample_depth": (_ST, [_P, _P, _P, _D, _U64, _P, _P]),
     "esim_dhat_alg3": (_ST, [_P, _P, _P, _P, _P, _D, _P]),
 }
@@ -371,6 +372,10 @@ def esim_alg3_depth(v: float, c: float, supp, max_depth: int, n: int, m: int,
 def esim_alg3_paper_depth(g: int, R, c: float, max_depth: int, depth) -> None:
     _check(lib().esim_alg3_paper_depth(g, _ptr(R, "uint64", device=True), c, int(max_depth),
                                        _ptr(depth, "uint8", device=True)))
+
+
+def esim_alg3_zsum(g: int, depth, c: float, zsum) -> None:
+    _check(lib().esim_alg3_zsum(g, _ptr(depth, "uint8", device=True), c, _ptr(zsum, "float64", device=True)))
 
 
 def esim_sample_depth(g: int, off, depth, c: float, seed: int, counts, pair_steps=None) -> None:

@@ -143,6 +143,10 @@ __global__ void paper_z1_kernel(int64_t n, const uint8_t* __restrict__ depth, co
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         if (depth[k] != 1) continue;
         const double d = (double)(rp[k + 1] - rp[k]);
+        if (d == 0.0) {  // no in-neighbour: the walks stop at once and never meet
+            zsum[k] = 0.0;
+            continue;
+        }
         const double w = 1.0 / d;
         zsum[k] = c * (d * (w * w));
     }
@@ -178,6 +182,10 @@ __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, cons
         const int32_t k = ids[i];
         const uint32_t kb = rp[k], ke = rp[k + 1];
         const uint32_t dk = ke - kb;
+        if (dk == 0) {  // no in-neighbour: the walks stop at once and never meet
+            if (lane == 0) zsum[k] = 0.0;
+            continue;
+        }
         // size of the two-hop multiset, and T = sum over in-neighbours of 1/din (fixed lane order)
         unsigned long long e1 = 0;
         double T = 0.0;

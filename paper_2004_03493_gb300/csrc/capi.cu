@@ -479,25 +479,21 @@ esim_status ensure_a3pws(Graph& g) {
     return ESIM_OK;
 }
 
-// Algorithm 3 with the paper's adaptive depth: every node with R(k) > 0 (din >= 2; the
-// allocation gave the others none) explores until its explored edges reach
-// 2 R(k)/sqrt(c), at most alg3_max_depth levels (alg3_paper.cu); it keeps its R(k)
-// pairs, which move without the continuation draw for depth(k) steps.  Z_1 is c/din(k);
-// depth 2 has a closed form over the two-hop neighbourhood (one warp per node); deeper
-// nodes, and depth-2 nodes with a large two-hop neighbourhood, get Z_1..Z_d from
-// alg3_first_meeting, one node at a time.
-esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
+// zsum(k) = sum_{l <= depth(k)} Z_l(k) for every node (0 at depth 0), from a device depth
+// array: Z_1 = c/din(k) for depth 1, the closed form for depth 2 (alg3_paper.cu), and
+// Z_1..Z_d from alg3_first_meeting, one node at a time, beyond (and for depth-2 nodes
+// whose two-hop neighbourhood is too large for the closed form's table).  Returns the
+// number of nodes with depth >= 1 in *used.  Synchronises g.stream.
+esim_status alg3_zsums(Graph& g, const uint8_t* depth_dev, double c, double* zsum, int* launches, int* used_out) {
     esim_status a3 = ensure_a3pws(g);
     if (a3 != ESIM_OK) return a3;
-    ESIM_CUDA_TRY(cudaMemsetAsync(w.zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
-    ESIM_CUDA_TRY(alg3_paper_depths(g, w.R, c, g.alg3_max_depth, g.a3pws, w.depth, launches),
-                  "Algorithm 3 depths (explored edges)");
-    ESIM_CUDA_TRY(alg3_paper_z1(g, w.depth, c, w.zsum), "Algorithm 3 Z_1");
+    ESIM_CUDA_TRY(cudaMemsetAsync(zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
+    ESIM_CUDA_TRY(alg3_paper_z1(g, depth_dev, c, zsum), "Algorithm 3 Z_1");
     *launches += 1;
     std::vector<uint8_t> depth((size_t)g.n);
-    ESIM_CUDA_TRY(cudaMemcpyAsync(depth.data(), w.depth, (size_t)g.n, cudaMemcpyDeviceToHost, g.stream), "copy depth");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(depth.data(), depth_dev, (size_t)g.n, cudaMemcpyDeviceToHost, g.stream), "copy depth");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depths");
-    // depth 2: the closed form, one warp per node (ids staged in the bit-set area, free now)
+    // depth 2: the closed form, one warp per node (ids staged in the bit-set area)
     std::vector<int32_t> d2;
     for (int64_t k = 0; k < g.n; ++k)
         if (depth[(size_t)k] == 2) d2.push_back((int32_t)k);
@@ -505,11 +501,11 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
         int32_t* ids = (int32_t*)g.a3pws;
         ESIM_CUDA_TRY(cudaMemcpyAsync(ids, d2.data(), sizeof(int32_t) * d2.size(), cudaMemcpyHostToDevice, g.stream),
                       "upload depth-2 nodes");
-        ESIM_CUDA_TRY(alg3_paper_z2(g, ids, (int)d2.size(), c, w.zsum), "Algorithm 3 Z_1 + Z_2");
+        ESIM_CUDA_TRY(alg3_paper_z2(g, ids, (int)d2.size(), c, zsum), "Algorithm 3 Z_1 + Z_2");
         *launches += 1;
     }
     std::vector<double> zs((size_t)g.n);
-    ESIM_CUDA_TRY(cudaMemcpyAsync(zs.data(), w.zsum, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
+    ESIM_CUDA_TRY(cudaMemcpyAsync(zs.data(), zsum, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
                   "copy zsum");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depth-2 terms");  // d2 and zs are locals
     int used = 0;
@@ -532,9 +528,26 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
         zs[(size_t)k] = sum;
     }
     if (deep)
-        ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum, zs.data(), sizeof(double) * (size_t)g.n, cudaMemcpyHostToDevice, g.stream),
+        ESIM_CUDA_TRY(cudaMemcpyAsync(zsum, zs.data(), sizeof(double) * (size_t)g.n, cudaMemcpyHostToDevice, g.stream),
                       "upload zsum");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // zs is a local
+    *used_out = used;
+    return ESIM_OK;
+}
+
+// Algorithm 3 with the paper's adaptive depth: every node with R(k) > 0 (din >= 2; the
+// allocation gave the others none) explores until its explored edges reach
+// 2 R(k)/sqrt(c), at most alg3_max_depth levels (alg3_paper.cu); it keeps its R(k)
+// pairs, which move without the continuation draw for depth(k) steps; then the sums of
+// its exact Z (alg3_zsums).
+esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
+    esim_status a3 = ensure_a3pws(g);
+    if (a3 != ESIM_OK) return a3;
+    ESIM_CUDA_TRY(alg3_paper_depths(g, w.R, c, g.alg3_max_depth, g.a3pws, w.depth, launches),
+                  "Algorithm 3 depths (explored edges)");
+    int used = 0;
+    a3 = alg3_zsums(g, w.depth, c, w.zsum, launches, &used);
+    if (a3 != ESIM_OK) return a3;
     g.last_alg3_nodes = used;
     return ESIM_OK;
 }
@@ -1591,6 +1604,17 @@ esim_status esim_alg3_paper_depth(esim_graph* h, const uint64_t* R, double c, in
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(alg3_paper_depths(g, R, c, max_depth, g.a3pws, depth, nullptr), "Algorithm 3 depths (explored edges)");
     return ESIM_OK;
+}
+
+esim_status esim_alg3_zsum(esim_graph* h, const uint8_t* depth, double c, double* zsum) {
+    if (check_graph(h)) return ESIM_EINVAL;
+    Graph& g = h->g;
+    if (!depth || !zsum) return fail(ESIM_EINVAL, "NULL argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(ESIM_EINVAL, "need 0 < c < 1");
+    if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
+    ESIM_CUDA_TRY(cudaSetDevice(g.device), "cudaSetDevice");
+    int launches = 0, used = 0;
+    return alg3_zsums(g, depth, c, zsum, &launches, &used);
 }
 
 int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_depth, int64_t n, int64_t m,

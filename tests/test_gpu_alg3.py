@@ -176,6 +176,31 @@ def test_paper_depth_rule_step_bit_exact(torch_cuda, esim, graph_name):
     g.close()
 
 
+@pytest.mark.parametrize("graph_name", list(PAPER_GRAPHS))
+def test_zsum_step_matches_lemma5_sums(torch_cuda, esim, graph_name):
+    """esim_alg3_zsum (depth 1 and 2 in closed form, deeper nodes by the Lemma 5 kernels)
+    against the oracle's Lemma 5 sums, node for node, on random depth vectors 0..4 that
+    include nodes with din 0 and 1."""
+    torch = torch_cuda
+    n, rp, col = PAPER_GRAPHS[graph_name]()
+    din = np.diff(rp)
+    g = esim.Graph(n, rp, col)
+    rng = np.random.default_rng(41)
+    depth = np.zeros(n, dtype=np.uint8)
+    picks = rng.choice(n, size=400, replace=False)
+    depth[picks] = rng.integers(1, 5, size=picks.size).astype(np.uint8)
+    depth[picks[:40]] = 2  # many depth-2 nodes: the closed form's table
+    want = a3.first_meeting_sums(n, rp, col, depth, C)
+    zsum = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    g.alg3_zsum(_dev(torch, depth), C, zsum)
+    got = zsum.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - want)) <= TOL, (graph_name, np.argmax(np.abs(got - want)))
+    assert np.all(got[depth == 0] == 0.0)
+    assert np.any((depth == 2) & (din >= 2)) and np.any((depth >= 1) & (din <= 1))
+    g.close()
+
+
 @pytest.mark.parametrize("graph_name,kappa,eps", [
     ("er2000", 2000.0, 3e-3),
     ("cl3000", None, 3e-3),
