@@ -94,17 +94,22 @@ typedef struct {
     int32_t reserved2;
     uint64_t hist_entries;    /* stored history entries: (L+1) n dense, kept entries sparse */
     uint64_t workspace_bytes; /* device bytes of the last query's workspace layout */
-    /* With Algorithm 3 the walks of the nodes that are not exploitation candidates run on
-     * a second stream while the candidates are planned, and each heavy candidate's walks
-     * on a third as soon as its plan is final: ms_sample_kernel is the last sampler launch
-     * alone, ms_sample_side the side launch, ms_sample_early the sum of the early_launches
-     * early ones (all with option timing); pair_steps_side is the side launch's share of
-     * pair_steps, which counts every launch. */
+    /* With Algorithm 3's cost-model rule the walks of the nodes that are not exploitation
+     * candidates run on a second stream while the candidates are planned, and the walks of
+     * the candidates with at least "alg3_early_pairs" pairs on a third, in one launch, as
+     * soon as every depth is chosen (before the first-meeting terms).  With the paper's
+     * rule every node's walks run on the second stream once the depths are known, while
+     * the first-meeting sums are computed.  ms_sample_kernel is the last sampler launch
+     * alone, ms_sample_side the side launch, ms_sample_early the early launch (all with
+     * option timing); early_launches is 0 or 1 and early_nodes the candidates it walked;
+     * pair_steps_side is the side launch's share of pair_steps, which counts every
+     * launch. */
     float ms_sample_kernel;
     float ms_sample_side;
     uint64_t pair_steps_side;
     float ms_sample_early;
     int32_t early_launches;
+    int32_t early_nodes;  /* candidates whose walks ran in the early launch */
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */
@@ -199,9 +204,10 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_overlap"   sampler blocks per SM for the walks of the nodes that are not
  *                    candidates, run on a second stream during the planning (default 4;
  *                    0: all walks after the planning).  Counts do not depend on it.
- *   "alg3_early_pairs"  a candidate whose plan is final and whose pairs number at least
- *                    this (default 2^24) starts its walks at once on a third stream,
- *                    during the rest of the planning (with "alg3_overlap" > 0)
+ *   "alg3_early_pairs"  with "alg3_overlap" > 0, the candidates with at least this many
+ *                    pairs (default 2^24) walk on a third stream, in one launch, as soon
+ *                    as every depth is chosen, while the first-meeting terms are
+ *                    computed; the others after the planning.  Counts do not depend on it.
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per
  *                    entry and column of a 32-column probe sweep (0.2), per kernel launch

@@ -19,6 +19,7 @@
 // crosses blocks or threads is an integer one, so the result is deterministic.
 #include "common.cuh"
 #include "internal.h"
+#include "twohop.cuh"
 
 #include <math.h>
 
@@ -167,10 +168,6 @@ __host__ __device__ __forceinline__ unsigned long long div_by_magic(unsigned lon
     return q;
 }
 
-// floor(H^2 / 2^63) for H <= 2^63
-__device__ __forceinline__ unsigned long long fx_sq(unsigned long long H) {
-    return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
-}
 
 // Direction-optimising steps.  A block starts from 32 single nodes, so its first
 // steps touch few rows.  While the frontier F_s (the rows of x_s that may be
@@ -238,7 +235,7 @@ __device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigne
         const uint32_t d = __ldg(a.in_rp + row + 1) - __ldg(a.in_rp + row);
         xnext[(size_t)row * kProbeW + lane] = (d && H) ? div_by_magic(H, d, __ldg(a.magic + row)) : 0ull;
     }
-    if (a.mode == 2) return fx_sq(H);
+    if (a.mode == 2) return twohop_sq(H);  // floor(H^2 / 2^63)
     if (a.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
         const double h = (double)H * kInvOne;
         double t = coef[lane] * (h * h);
@@ -501,11 +498,16 @@ __global__ void __launch_bounds__(kBlock) probe_long_rows_kernel(ProbeGroup G, P
 // Group end: zlast += the sum over blocks and columns, in order, of
 // c^{steps} Zv_i(q'_col) colsum(b, col); blocks that went dense clear both x buffers.
 __global__ void probe_end_kernel(ProbeGroup G, const int32_t* __restrict__ ids, int count,
-                                 const double* __restrict__ zv_src, double cl, double* __restrict__ zlast) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < count; ++i) t += (cl * zv_src[ids[i]]) * ((double)G.colsum[i] * kInvOne);
-        *zlast += t;
+                                 const double* __restrict__ zv_src, double cl, double* __restrict__ zlast,
+                                 const int32_t* __restrict__ pos, unsigned long long* __restrict__ colsum_out) {
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        if (colsum_out) {  // the caller sums the terms: hand over the column sums
+            for (int i = threadIdx.x; i < count; i += blockDim.x) colsum_out[pos[i]] = G.colsum[i];
+        } else if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < count; ++i) t += (cl * zv_src[ids[i]]) * ((double)G.colsum[i] * kInvOne);
+            *zlast += t;
+        }
     }
     const int b = blockIdx.y;
     if (G.ctl[b].dense_plus1 == 0) return;
@@ -515,6 +517,64 @@ __global__ void probe_end_kernel(ProbeGroup G, const int32_t* __restrict__ ids, 
         xa[i] = 0ull;
         xb[i] = 0ull;
     }
+}
+
+// The last probe level (probes of length 2 from the support of h_{d-2}) needs of each
+// node q' only g_2(q') = sum_q ((P^T)^2(q', .))(q)^2, its column sum.  One warp per node
+// computes it from the two-hop hash table (twohop.cuh: the same integers as the dense
+// probe's two steps); a node whose two-hop multiset is too large for the table is
+// appended to (big_ids, big_pos) for the dense probes, which write its column sum at
+// big_pos.  The order of the appends does not matter: each column sum is exact.
+constexpr int kG2Warps = 4;
+constexpr int kG2Table = 1024;  // slots per warp: 4 warps x 12 KB of shared memory
+
+__global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t* __restrict__ count_dev,
+                                                                 const int32_t* __restrict__ ids,
+                                                                 const uint32_t* __restrict__ rp,
+                                                                 const int32_t* __restrict__ col,
+                                                                 unsigned long long* __restrict__ colsum,
+                                                                 int32_t* __restrict__ big_ids,
+                                                                 int32_t* __restrict__ big_pos,
+                                                                 unsigned int* __restrict__ nbig) {
+    __shared__ int32_t key[kG2Warps][kG2Table];
+    __shared__ unsigned long long val[kG2Warps][kG2Table];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t count = (int64_t)*count_dev;
+    const int64_t nw = (int64_t)gridDim.x * kG2Warps;
+    for (int64_t i = (int64_t)blockIdx.x * kG2Warps + wid; i < count; i += nw) {
+        double T;
+        uint32_t dk;
+        const unsigned long long sq = twohop_sq_sum<kG2Table>(ids[i], rp, col, key[wid], val[wid], T, dk);
+        if (lane != 0) continue;
+        if (sq == kTwoHopTooLarge) {
+            const unsigned int slot = atomicAdd(nbig, 1u);
+            big_ids[slot] = ids[i];
+            big_pos[slot] = (int32_t)i;
+            colsum[i] = 0ull;
+        } else {
+            colsum[i] = sq;
+        }
+    }
+}
+
+// *zlast += sum_i (cl Zv(ids[i])) (colsum[i] 2^-63), i < count, in a fixed order: thread t
+// takes i = t, t + 1024, ... and a fixed tree adds the threads' partials.
+__global__ void __launch_bounds__(1024) probe_g2_total_kernel(const uint64_t* __restrict__ count_dev,
+                                                              const int32_t* __restrict__ ids,
+                                                              const double* __restrict__ zv_src, double cl,
+                                                              const unsigned long long* __restrict__ colsum,
+                                                              double* __restrict__ zlast) {
+    __shared__ double red[1024];
+    const int64_t count = (int64_t)*count_dev;
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += 1024) t += (cl * zv_src[ids[i]]) * ((double)colsum[i] * kInvOne);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *zlast += red[0];
 }
 
 // D^ of Algorithm 3 for exploited nodes (depth > 0), of Algorithm 2 for the others,
@@ -576,6 +636,10 @@ struct A3Ws {
     unsigned long long* rcounts;  // (D + 1) x 32 support sizes
     double* partial;  // kDotBlocks (dot products)
     double* sums;     // 64: [j] = sum_q Zv_j(q); [63] = the last level's probe terms
+    unsigned long long* g2;  // n: column sums g_2 of the last probe level, by support position
+    int32_t* big_ids;        // n: support nodes too large for the two-hop table
+    int32_t* big_pos;        // n: their support positions
+    unsigned int* nbig;      // 1
     ProbeGroup G;
     int group;        // probe blocks per launch
 };
@@ -605,6 +669,10 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     w.rcounts = (unsigned long long*)take(8 * 32 * (D + 1));
     w.partial = (double*)take(8 * kDotBlocks);
     w.sums = (double*)take(8 * 64);
+    w.g2 = (unsigned long long*)take(8 * n);
+    w.big_ids = (int32_t*)take(4 * n);
+    w.big_pos = (int32_t*)take(4 * n);
+    w.nbig = (unsigned int*)take(256);
     const int G = group_size(n_, m_, nseg);
     const size_t gz = (size_t)G;
     w.group = G;
@@ -724,14 +792,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     if ((e = cudaMemsetAsync(ws.Zfx, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
-    if (depth >= 3) {  // the probe buffers start (and each group ends) all zero
-        const size_t gz = (size_t)ws.group;
-        if ((e = cudaMemsetAsync(ws.G.X[0], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.G.X[1], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.G.Hn, 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ws.G.mark, 0, 4 * n * gz, g.stream)) != cudaSuccess)
-            return e;
-    }
+    bool cleared = false;  // the probe buffers start (and each group ends) all zero
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
     const unsigned long long thr = (unsigned long long)(g.m + g.n) / (unsigned long long)std::max(1, g.alg3_push_div);
@@ -761,16 +822,40 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         scatter_ids_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.flag, ws.off, ws.ids);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count += 5;
+        const int steps = depth - j;
+        const bool last = steps == 2;  // these probes feed only Z_depth's total: g_2 per node
+        if (last) {
+            if ((e = cudaMemsetAsync(ws.nbig, 0, sizeof(unsigned int), g.stream)) != cudaSuccess) return e;
+            probe_g2_kernel<<<(unsigned)(g.sm_count * 4), kG2Warps * 32, 0, g.stream>>>(
+                ws.off + n, ws.ids, g.in.rp, g.in.col, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++count;
+        }
         uint64_t nsup = 0;
+        unsigned int nbig = 0;
         if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
             return e;
+        if (last && (e = cudaMemcpyAsync(&nbig, ws.nbig, sizeof(unsigned int), cudaMemcpyDeviceToHost, g.stream)) !=
+                        cudaSuccess)
+            return e;
         if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-        const int steps = depth - j;
+        // dense probes: every support node of a level below the last, the large ones of the last
+        const uint64_t nprobe = last ? (uint64_t)nbig : nsup;
+        const int32_t* probe_ids = last ? ws.big_ids : ws.ids;
         const uint64_t per_group = (uint64_t)kProbeW * (uint64_t)ws.group;
-        for (uint64_t g0 = 0; g0 < nsup; g0 += per_group) {
-            const int cnt = (int)std::min<uint64_t>(per_group, nsup - g0);
+        if (nprobe > 0 && !cleared) {
+            const size_t gz = (size_t)ws.group;
+            if ((e = cudaMemsetAsync(ws.G.X[0], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.X[1], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.Hn, 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.mark, 0, 4 * n * gz, g.stream)) != cudaSuccess)
+                return e;
+            cleared = true;
+        }
+        for (uint64_t g0 = 0; g0 < nprobe; g0 += per_group) {
+            const int cnt = (int)std::min<uint64_t>(per_group, nprobe - g0);
             const int nb = (cnt + kProbeW - 1) / kProbeW;
-            const int32_t* ids = ws.ids + g0;
+            const int32_t* ids = probe_ids + g0;
             probe_init_kernel<<<dim3(1, (unsigned)nb), kProbeW, 0, g.stream>>>(ws.G, ids, cnt, g.in.rp);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
@@ -789,7 +874,13 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                 if ((e = probe_step(g, ws, a, nb, &count)) != cudaSuccess) return e;
             }
             probe_end_kernel<<<dim3((unsigned)g.sm_count, (unsigned)nb), kBlock, 0, g.stream>>>(
-                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63);
+                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63, last ? ws.big_pos + g0 : nullptr,
+                last ? ws.g2 : nullptr);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++count;
+        }
+        if (last && nsup > 0) {
+            probe_g2_total_kernel<<<1, 1024, 0, g.stream>>>(ws.off + n, ws.ids, zv, cpow[2], ws.g2, ws.sums + 63);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
         }

@@ -20,6 +20,7 @@
 // whose bit sets fit kPaperBitsBudget.
 #include "common.cuh"
 #include "internal.h"
+#include "twohop.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -156,17 +157,11 @@ __global__ void paper_z1_kernel(int64_t n, const uint8_t* __restrict__ depth, co
 // h_2 = (P^T)^2(k, .), Lemma 5 gives Z_1(k) = c / din(k) and
 //   Z_2(k) = c^2 sum_q h_2(q)^2 - c sum_{q'} Z_1(k, q') sum_q (P^T)(q', q)^2
 //          = c^2 (sum_q h_2(q)^2 - (1/din(k)^2) sum_{q' in I(k), din(q') > 0} 1/din(q')).
-// One warp per node builds h_2 over the two-hop neighbourhood in a shared-memory hash
-// table in 63-bit fixed point (integer atomics: exact and order-free), then sums the
-// squares in fixed point.  A node whose two-hop multiset exceeds half the table gets
-// NaN and is left to the one-node Lemma 5 path.
+// One warp per node builds h_2 over the two-hop neighbourhood and sums its squares in
+// 63-bit fixed point (twohop.cuh).  A node whose two-hop multiset exceeds half the table
+// gets NaN and is left to the one-node Lemma 5 path.
 constexpr int kD2Warps = 4;
 constexpr int kD2Table = 1024;  // slots per warp (power of two): 4 warps x 12 KB of shared memory
-constexpr unsigned long long kD2One = 1ull << 63;
-
-__device__ __forceinline__ unsigned long long d2_sq(unsigned long long H) {  // floor(H^2 / 2^63)
-    return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
-}
 
 __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, const int32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ rp,
@@ -175,68 +170,27 @@ __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, cons
     __shared__ int32_t key[kD2Warps][kD2Table];
     __shared__ unsigned long long val[kD2Warps][kD2Table];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int32_t* K = key[wid];
-    unsigned long long* V = val[wid];
     const int nw = gridDim.x * kD2Warps;
     for (int i = blockIdx.x * kD2Warps + wid; i < count; i += nw) {
         const int32_t k = ids[i];
-        const uint32_t kb = rp[k], ke = rp[k + 1];
-        const uint32_t dk = ke - kb;
-        if (dk == 0) {  // no in-neighbour: the walks stop at once and never meet
-            if (lane == 0) zsum[k] = 0.0;
-            continue;
-        }
-        // size of the two-hop multiset, and T = sum over in-neighbours of 1/din (fixed lane order)
-        unsigned long long e1 = 0;
-        double T = 0.0;
-        for (uint32_t p = kb + lane; p < ke; p += 32) {
-            const int32_t q1 = col[p];
-            const uint32_t d1 = rp[q1 + 1] - rp[q1];
-            e1 += d1;
-            if (d1) T += 1.0 / (double)d1;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
-            T += __shfl_xor_sync(0xffffffffu, T, o);
-        }
-        if (e1 > (unsigned long long)(kD2Table / 2)) {
-            if (lane == 0) zsum[k] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: the one-node path
-            continue;
-        }
-        for (int s = lane; s < kD2Table; s += 32) {
-            K[s] = -1;
-            V[s] = 0ull;
-        }
-        __syncwarp();
-        for (uint32_t p1 = kb; p1 < ke; ++p1) {  // q' in I(k), then its in-neighbours across the lanes
-            const int32_t q1 = col[p1];
-            const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
-            if (b1 == e1r) continue;
-            const unsigned long long w = kD2One / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
-            for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) {
-                const int32_t q = col[p2];
-                uint32_t slot = ((uint32_t)q * 2654435761u) & (kD2Table - 1);
-                for (;;) {  // at most half the slots are taken: a free or matching slot exists
-                    const int32_t prev = atomicCAS(&K[slot], -1, q);
-                    if (prev == -1 || prev == q) break;
-                    slot = (slot + 1) & (kD2Table - 1);
-                }
-                atomicAdd(&V[slot], w);
-            }
-        }
-        __syncwarp();
-        unsigned long long sq = 0;
-        for (int s = lane; s < kD2Table; s += 32) sq += d2_sq(V[s]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) {
+        double T;
+        uint32_t dk;
+        const unsigned long long sq = twohop_sq_sum<kD2Table>(k, rp, col, key[wid], val[wid], T, dk);
+        if (lane != 0) continue;
+        if (dk == 0) zsum[k] = 0.0;  // no in-neighbour: the walks stop at once and never meet
+        else if (sq == kTwoHopTooLarge) zsum[k] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: one-node path
+        else {
             const double S2 = (double)sq * (1.0 / 9223372036854775808.0);
             const double inv = 1.0 / (double)dk;
             zsum[k] = c * inv + c * c * (S2 - T * inv * inv);
         }
-        __syncwarp();
     }
+}
+
+// dst[i] = src[ids[i]]
+__global__ void gather_f64_kernel(int count, const int32_t* __restrict__ ids, const double* __restrict__ src,
+                                  double* __restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) dst[i] = src[ids[i]];
 }
 
 int grid_for(const Graph& g, int64_t items_per_warp_rows) {
@@ -335,6 +289,13 @@ cudaError_t alg3_paper_z2(const Graph& g, const int32_t* ids, int count, double 
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + kD2Warps - 1) / kD2Warps,
                                                                    (int64_t)g.sm_count * 8));
     paper_z2_kernel<<<blocks, kD2Warps * 32, 0, g.stream>>>(count, ids, g.in.rp, g.in.col, c, zsum);
+    return cudaGetLastError();
+}
+
+cudaError_t alg3_gather_f64(const Graph& g, const int32_t* ids, int count, const double* src, double* dst) {
+    if (count <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)g.sm_count * 4);
+    gather_f64_kernel<<<blocks, 256, 0, g.stream>>>(count, ids, src, dst);
     return cudaGetLastError();
 }
 

@@ -181,6 +181,7 @@ void release(Graph& g) {
     cudaFree(g.bws);
     cudaFree(g.a3ws);
     cudaFree(g.a3pws);
+    cudaFree(g.zstage);
     cudaFree(g.partial);
     cudaFree(g.scan_part);
     cudaFree(g.norm_part);
@@ -236,9 +237,10 @@ struct Ws {
     uint64_t* off2;    // n+1  offsets of the other nodes' walks (read by the side stream)
     uint64_t* offc;    // n+1  offsets of the candidates' walks
     uint64_t* nm2;     // n  counts of the other nodes
-    uint64_t* nme;     // n  counts of the heavy candidates sampled during the planning
-    uint64_t* offe;    // n+1  offsets of one such candidate
+    uint64_t* nme;     // n  counts of the candidates sampled during the planning
+    uint64_t* offe;    // n+1  offsets of their walks
     int32_t* cand_ids; // 4096
+    PlanEntry* plan;   // 4096  the cost model's plan, staged for the scatter
     // sparse linearization (FP64): rolling pi^l, the running pi, the kept entries
     double* lev;       // n
     double* pirun;     // n
@@ -301,6 +303,7 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
     t.nme = (uint64_t*)take(8 * n);
     t.offe = (uint64_t*)take(8 * (n + 1));
     t.cand_ids = (int32_t*)take(4 * 4096);
+    t.plan = (PlanEntry*)take(sizeof(PlanEntry) * 4096);
     if (precision == 0 && sparse_cap > 0) {
         // last, so that the layout for a smaller capacity is a prefix of this one
         t.sh.lvl = (uint64_t*)take(8 * (size_t)(L + 2));
@@ -400,19 +403,11 @@ int alg3_depth(double v, double c, const uint64_t* supp, int max_depth, int64_t 
 // max(1, ceil(R_b pi(k)^2 c^(2d))) (pi(k) for the basic allocation): the tail
 // estimator's variance and range are c^(2d) and c^d of Algorithm 2's.  Nodes with
 // din <= 1 already got no pairs from the allocation.  Then the offsets are rescanned.
-// Starts, on the side stream, the walks of every node that is not an Algorithm 3
-// candidate: their R(k) is final, and the walk spec keys a pair by (seed, k, r), so
-// splitting the nodes between two sampler launches changes no count.  The side
-// sampler takes two thirds of each SM, leaving room for the planning's kernels.
-esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& cand, double c, uint64_t seed,
-                             int* launches) {
-    ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand_ids, cand.data(), sizeof(int32_t) * cand.size(), cudaMemcpyHostToDevice,
-                                  g.stream), "upload candidates");
-    ESIM_CUDA_TRY(launch_mark(g, w.cand_ids, (int)cand.size(), w.cand), "mark candidates");
-    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 0, w.R2), "other nodes' R");
-    const int64_t nb = allocate_blocks(g.n);
-    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.off2, g.scan_part, nullptr, g.norm_part + nb, false), "other nodes' scan");
+// The sampler on the side stream after the work queued so far on g.stream: offsets off,
+// counts nm2, pair-steps to the status block's side counter; at most alg3_overlap
+// blocks per SM, leaving room for the planning's kernels.  Records side_ev[1] at its end.
+esim_status launch_side_walks(Graph& g, const Ws& w, const uint64_t* off, double c, uint64_t seed,
+                              const uint8_t* depth) {
     ESIM_CUDA_TRY(cudaEventRecord(g.side_ev[0], g.stream), "record");
     ESIM_CUDA_TRY(cudaStreamWaitEvent(g.side_stream, g.side_ev[0], 0), "side wait");
     Graph view = g;
@@ -423,40 +418,56 @@ esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& 
             if (!ev) ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
         cudaEventRecord(g.side_tev[0], g.side_stream);
     }
-    ESIM_CUDA_TRY(launch_sample(view, w.off2, c, seed, w.nm2, (uint64_t*)&g.status->pair_steps_side, nullptr),
-                  "other nodes' walk pairs");
+    ESIM_CUDA_TRY(launch_sample(view, off, c, seed, w.nm2, (uint64_t*)&g.status->pair_steps_side, depth),
+                  "side walk pairs");
     if (g.timing) cudaEventRecord(g.side_tev[1], g.side_stream);
     ESIM_CUDA_TRY(cudaEventRecord(g.side_ev[1], g.side_stream), "record");
+    return ESIM_OK;
+}
+
+// Starts, on the side stream, the walks of every node that is not an Algorithm 3
+// candidate: their R(k) is final, and the walk spec keys a pair by (seed, k, r), so
+// splitting the nodes between sampler launches changes no count.
+esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& cand, double c, uint64_t seed,
+                             int* launches) {
+    ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
+    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand_ids, cand.data(), sizeof(int32_t) * cand.size(), cudaMemcpyHostToDevice,
+                                  g.stream), "upload candidates");
+    ESIM_CUDA_TRY(launch_mark(g, w.cand_ids, (int)cand.size(), w.cand), "mark candidates");
+    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 0, w.R2), "other nodes' R");
+    const int64_t nb = allocate_blocks(g.n);
+    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.off2, g.scan_part, nullptr, g.norm_part + nb, false), "other nodes' scan");
+    esim_status st = launch_side_walks(g, w, w.off2, c, seed, nullptr);
+    if (st != ESIM_OK) return st;
     *launches += 6;
     return ESIM_OK;
 }
 
-// The walks of one planned candidate k on the early stream: its offsets alone (the other
-// nodes have none), counts added to nme, pair-steps to the status block.
-esim_status start_early_walks(Graph& g, const Ws& w, int32_t k, uint64_t R1, double c, uint64_t seed, bool started,
-                              int* launches) {
+// The walks of the candidates marked early (cand = 2) on the early stream, in one
+// launch: their plans are final, and they run while the first-meeting terms are computed.
+// Counts go to nme, pair-steps to the status block.
+esim_status start_early_walks(Graph& g, const Ws& w, double c, uint64_t seed, int* launches) {
+    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 2, w.R2), "early candidates' R");
+    const int64_t nb = allocate_blocks(g.n);
+    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.offe, g.scan_part, nullptr, g.norm_part + nb, false),
+                  "early candidates' scan");
+    ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.stream), "record");
+    ESIM_CUDA_TRY(cudaStreamWaitEvent(g.early_stream, g.early_ev, 0), "early wait");
     Graph view = g;
     view.stream = g.early_stream;
     view.sample_block_cap = g.alg3_overlap;
-    if (!started) ESIM_CUDA_TRY(cudaMemsetAsync(w.nme, 0, 8 * (size_t)g.n, g.early_stream), "reset counts");
-    ESIM_CUDA_TRY(launch_single_offsets(view, k, R1, w.offe), "one node's offsets");
-    const size_t ti = 2 * (size_t)g.early_launches;
     if (g.timing) {
-        while (g.early_tev.size() < ti + 2) {
+        while (g.early_tev.size() < 2) {
             cudaEvent_t ev = nullptr;
             ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
             g.early_tev.push_back(ev);
         }
-        cudaEventRecord(g.early_tev[ti], g.early_stream);
+        cudaEventRecord(g.early_tev[0], g.early_stream);
     }
-    ESIM_CUDA_TRY(launch_sample_segments(view, g.n, w.offe, c, seed, w.nme, nullptr, w.depth, 0, nullptr, false),
-                  "heavy candidate's walk pairs");
-    if (g.timing) cudaEventRecord(g.early_tev[ti + 1], g.early_stream);
-    ++g.early_launches;
-    const uint8_t two = 2;
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand + k, &two, 1, cudaMemcpyHostToDevice, g.stream), "mark early");
-    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "mark early");  // the host byte is a local
-    *launches += 2;
+    ESIM_CUDA_TRY(launch_sample(view, w.offe, c, seed, w.nme, nullptr, w.depth), "early candidates' walk pairs");
+    if (g.timing) cudaEventRecord(g.early_tev[1], g.early_stream);
+    g.early_launches = 1;
+    *launches += 3;
     return ESIM_OK;
 }
 
@@ -479,60 +490,86 @@ esim_status ensure_a3pws(Graph& g) {
     return ESIM_OK;
 }
 
-// zsum(k) = sum_{l <= depth(k)} Z_l(k) for every node (0 at depth 0), from a device depth
-// array: Z_1 = c/din(k) for depth 1, the closed form for depth 2 (alg3_paper.cu), and
-// Z_1..Z_d from alg3_first_meeting, one node at a time, beyond (and for depth-2 nodes
-// whose two-hop neighbourhood is too large for the closed form's table).  Returns the
-// number of nodes with depth >= 1 in *used.  Synchronises g.stream.
-esim_status alg3_zsums(Graph& g, const uint8_t* depth_dev, double c, double* zsum, int* launches, int* used_out) {
-    esim_status a3 = ensure_a3pws(g);
-    if (a3 != ESIM_OK) return a3;
+// zsum(k) = sum_{l <= depth(k)} Z_l(k) for the nodes of the given depths (every other
+// entry 0): Z_1 = c/din(k) for every node of depth 1 in depth_dev, the closed form of
+// depth 2 (alg3_paper.cu) for the nodes in d2, and Z_1..Z_d from alg3_first_meeting, one
+// node at a time, for the nodes in deep and for the depth-2 nodes whose two-hop
+// neighbourhood is too large for the closed form's table.  Synchronises g.stream.
+esim_status alg3_zsums_of(Graph& g, const uint8_t* depth_dev, const std::vector<int32_t>& d2,
+                          std::vector<std::pair<int32_t, int>> deep, double c, double* zsum, int* launches) {
     ESIM_CUDA_TRY(cudaMemsetAsync(zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
     ESIM_CUDA_TRY(alg3_paper_z1(g, depth_dev, c, zsum), "Algorithm 3 Z_1");
     *launches += 1;
+    if (!d2.empty()) {
+        const int cnt = (int)d2.size();
+        const size_t need = round256(4 * d2.size()) + 8 * d2.size();  // ids, then the gathered values
+        if (g.zstage_bytes < need) {
+            cudaStreamSynchronize(g.stream);
+            cudaFree(g.zstage);
+            g.zstage = nullptr;
+            g.zstage_bytes = 0;
+            const size_t want = round256(4 * (size_t)g.n) + 8 * (size_t)g.n;
+            if (cudaMalloc(&g.zstage, want) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ESIM_ENOMEM, "cudaMalloc(Algorithm 3 staging of " + std::to_string(want) + " bytes)");
+            }
+            g.zstage_bytes = want;
+        }
+        int32_t* stage_ids = (int32_t*)g.zstage;
+        double* stage_vals = (double*)((char*)g.zstage + round256(4 * d2.size()));
+        std::vector<double> v2((size_t)cnt);
+        ESIM_CUDA_TRY(cudaMemcpyAsync(stage_ids, d2.data(), sizeof(int32_t) * d2.size(), cudaMemcpyHostToDevice,
+                                      g.stream),
+                      "upload depth-2 nodes");
+        ESIM_CUDA_TRY(alg3_paper_z2(g, stage_ids, cnt, c, zsum), "Algorithm 3 Z_1 + Z_2");
+        ESIM_CUDA_TRY(alg3_gather_f64(g, stage_ids, cnt, zsum, stage_vals), "gather depth-2 terms");
+        ESIM_CUDA_TRY(cudaMemcpyAsync(v2.data(), stage_vals, sizeof(double) * d2.size(), cudaMemcpyDeviceToHost,
+                                      g.stream),
+                      "copy depth-2 terms");
+        ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depth-2 terms");  // d2 and v2 are locals
+        *launches += 2;
+        for (int i = 0; i < cnt; ++i)
+            if (v2[(size_t)i] != v2[(size_t)i]) deep.emplace_back(d2[(size_t)i], 2);  // NaN: too large
+    }
+    if (!deep.empty()) {
+        esim_status a3 = ensure_a3ws(g);
+        if (a3 != ESIM_OK) return a3;
+        std::vector<double> zs(deep.size());
+        for (size_t i = 0; i < deep.size(); ++i) {
+            const int d = deep[i].second;
+            double z[kAlg3MaxDepth] = {};
+            ESIM_CUDA_TRY(alg3_first_meeting(g, deep[i].first, d, c, g.a3ws, z, launches),
+                          "Algorithm 3 first meetings");
+            double sum = 0.0;
+            for (int j = 0; j < d; ++j) sum += z[j];
+            zs[i] = sum;
+            ESIM_CUDA_TRY(cudaMemcpyAsync(zsum + deep[i].first, &zs[i], sizeof(double), cudaMemcpyHostToDevice,
+                                          g.stream),
+                          "set zsum");
+        }
+        ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // zs is a local
+    }
+    return ESIM_OK;
+}
+
+// The same from a device depth array alone (every node): the host reads it back and
+// lists the nodes.  Returns the number of nodes with depth >= 1 in *used.
+esim_status alg3_zsums(Graph& g, const uint8_t* depth_dev, double c, double* zsum, int* launches, int* used_out) {
     std::vector<uint8_t> depth((size_t)g.n);
     ESIM_CUDA_TRY(cudaMemcpyAsync(depth.data(), depth_dev, (size_t)g.n, cudaMemcpyDeviceToHost, g.stream), "copy depth");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depths");
-    // depth 2: the closed form, one warp per node (ids staged in the bit-set area)
     std::vector<int32_t> d2;
-    for (int64_t k = 0; k < g.n; ++k)
-        if (depth[(size_t)k] == 2) d2.push_back((int32_t)k);
-    if (!d2.empty()) {
-        int32_t* ids = (int32_t*)g.a3pws;
-        ESIM_CUDA_TRY(cudaMemcpyAsync(ids, d2.data(), sizeof(int32_t) * d2.size(), cudaMemcpyHostToDevice, g.stream),
-                      "upload depth-2 nodes");
-        ESIM_CUDA_TRY(alg3_paper_z2(g, ids, (int)d2.size(), c, zsum), "Algorithm 3 Z_1 + Z_2");
-        *launches += 1;
-    }
-    std::vector<double> zs((size_t)g.n);
-    ESIM_CUDA_TRY(cudaMemcpyAsync(zs.data(), zsum, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToHost, g.stream),
-                  "copy zsum");
-    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 depth-2 terms");  // d2 and zs are locals
+    std::vector<std::pair<int32_t, int>> deep;
     int used = 0;
-    bool deep = false;
     for (int64_t k = 0; k < g.n; ++k) {
         const int d = depth[(size_t)k];
         if (d == 0) continue;
         ++used;
-        if (d == 1) continue;
-        if (d == 2 && zs[(size_t)k] == zs[(size_t)k]) continue;  // the closed form took it (NaN: too large)
-        if (!deep) {
-            a3 = ensure_a3ws(g);
-            if (a3 != ESIM_OK) return a3;
-            deep = true;
-        }
-        double z[kAlg3MaxDepth] = {};
-        ESIM_CUDA_TRY(alg3_first_meeting(g, k, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
-        double sum = 0.0;
-        for (int j = 0; j < d; ++j) sum += z[j];
-        zs[(size_t)k] = sum;
+        if (d == 2) d2.push_back((int32_t)k);
+        else if (d > 2) deep.emplace_back((int32_t)k, d);
     }
-    if (deep)
-        ESIM_CUDA_TRY(cudaMemcpyAsync(zsum, zs.data(), sizeof(double) * (size_t)g.n, cudaMemcpyHostToDevice, g.stream),
-                      "upload zsum");
-    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // zs is a local
     *used_out = used;
-    return ESIM_OK;
+    return alg3_zsums_of(g, depth_dev, d2, std::move(deep), c, zsum, launches);
 }
 
 // Algorithm 3 with the paper's adaptive depth: every node with R(k) > 0 (din >= 2; the
@@ -540,11 +577,24 @@ esim_status alg3_zsums(Graph& g, const uint8_t* depth_dev, double c, double* zsu
 // 2 R(k)/sqrt(c), at most alg3_max_depth levels (alg3_paper.cu); it keeps its R(k)
 // pairs, which move without the continuation draw for depth(k) steps; then the sums of
 // its exact Z (alg3_zsums).
-esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
+esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches, uint64_t seed, bool* side) {
     esim_status a3 = ensure_a3pws(g);
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(alg3_paper_depths(g, w.R, c, g.alg3_max_depth, g.a3pws, w.depth, launches),
                   "Algorithm 3 depths (explored edges)");
+    // Every node's walks are final now (the allocation's R(k) and offsets, the depths):
+    // with a side stream they all run there while the first-meeting sums are computed,
+    // and the main stream's candidate launch is empty (cand = 0 everywhere).
+    if (g.side_stream && g.alg3_overlap > 0) {
+        ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
+        esim_status st = launch_side_walks(g, w, w.off, c, seed, w.depth);
+        if (st != ESIM_OK) return st;
+        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.stream), "record");
+        g.early_launches = 0;
+        g.early_nodes = 0;
+        *side = true;
+        *launches += 1;
+    }
     int used = 0;
     a3 = alg3_zsums(g, w.depth, c, w.zsum, launches, &used);
     if (a3 != ESIM_OK) return a3;
@@ -555,11 +605,10 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches) {
 esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches, uint64_t seed, bool* side) {
     if (g.has_duplicates) return fail(ESIM_ENOTSUP, "Algorithm 3 needs a graph without repeated in-edges");
     *side = false;
-    if (g.alg3_rule == 0) return plan_alg3_paper(g, w, c, launches);
+    if (g.alg3_rule == 0) return plan_alg3_paper(g, w, c, launches, seed, side);
     esim_status a3 = ensure_a3ws(g);
     if (a3 != ESIM_OK) return a3;
     ESIM_CUDA_TRY(cudaMemsetAsync(w.depth, 0, (size_t)g.n, g.stream), "reset depth");
-    ESIM_CUDA_TRY(cudaMemsetAsync(w.zsum, 0, sizeof(double) * (size_t)g.n, g.stream), "reset zsum");
     const int K = (int)std::min<int64_t>(g.alg3_max_nodes, g.n);
     char* stage = (char*)g.topk_ws + topk_stage_offset(g.n);
     double* vals_d = (double*)stage;
@@ -572,7 +621,6 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     ESIM_CUDA_TRY(cudaMemcpyAsync(pis.data(), vals_d, sizeof(double) * K, cudaMemcpyDeviceToHost, g.stream), "copy pi");
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 node selection");
     const std::vector<uint32_t>& din = *g.din_host;
-    int used = 0;
     // candidates: the heaviest nodes with din >= 2 and enough Algorithm 2 pairs
     std::vector<int32_t> cand;
     std::vector<double> cand_v;
@@ -593,8 +641,8 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     // sampler judges the other nodes' pairs and the rescan below all of them.
     ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
     *side = false;
-    bool early_started = false;
     g.early_launches = 0;
+    g.early_nodes = 0;
     if (!cand.empty() && g.side_stream && g.alg3_overlap > 0) {
         esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
         if (ss != ESIM_OK) return ss;
@@ -605,40 +653,57 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     if (!cand.empty())
         ESIM_CUDA_TRY(alg3_supports(g, cand.data(), (int)cand.size(), levels, g.a3ws, supps.data(), launches),
                       "Algorithm 3 supports");
+    // The cost model picks each depth from the supports alone, so every plan is final
+    // before any first-meeting term is computed: R(k) and depth(k) go to the device at
+    // once, and the walks of the candidates with at least alg3_early_pairs pairs start
+    // on the early stream while the terms are computed.
+    std::vector<PlanEntry> plan;
+    std::vector<int32_t> d2;
+    std::vector<std::pair<int32_t, int>> deep;
+    int used = 0, n_early = 0;
     for (size_t ci = 0; ci < cand.size(); ++ci) {
         const int32_t kk = cand[ci];
         const double v = cand_v[ci];
         const uint64_t* supp = supps.data() + ci * (kAlg3MaxDepth + 1);
         const int d = alg3_depth(v, c, supp, g.alg3_max_depth, g.n, g.m, g.alg3_w_sweep, g.alg3_w_probe,
                                  g.alg3_w_launch);
-        if (d < 1) continue;
-        double z[kAlg3MaxDepth] = {};
-        ESIM_CUDA_TRY(alg3_first_meeting(g, kk, d, c, g.a3ws, z, launches), "Algorithm 3 first meetings");
-        double zs = 0.0;
-        for (int j = 0; j < d; ++j) zs += z[j];
-        double r = ceil(v * pow(c, (double)(2 * d)));
+        double r = d >= 1 ? ceil(v * pow(c, (double)(2 * d))) : ceil(v);
         if (r < 1.0) r = 1.0;
         if (r >= 1.8e19) r = 1.8e19;  // the rescan's budget check reports it
-        const uint64_t R1 = (uint64_t)r;
-        const uint8_t dd = (uint8_t)d;
-        ESIM_CUDA_TRY(cudaMemcpyAsync(w.R + kk, &R1, sizeof(uint64_t), cudaMemcpyHostToDevice, g.stream), "set R");
-        ESIM_CUDA_TRY(cudaMemcpyAsync(w.depth + kk, &dd, 1, cudaMemcpyHostToDevice, g.stream), "set depth");
-        ESIM_CUDA_TRY(cudaMemcpyAsync(w.zsum + kk, &zs, sizeof(double), cudaMemcpyHostToDevice, g.stream), "set zsum");
-        ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // host values above are locals
-        ++used;
-        if (*side && (double)R1 >= g.alg3_early_pairs) {
-            // this node's R(k) and depth are final: its walks start now, during the rest
-            // of the planning (the host synchronised the writes above)
-            esim_status es = start_early_walks(g, w, kk, R1, c, seed, early_started, launches);
+        PlanEntry e{};
+        e.k = kk;
+        e.depth = (uint8_t)std::max(0, d);
+        e.early = (uint8_t)(*side && r >= g.alg3_early_pairs ? 1 : 0);
+        e.R = (uint64_t)r;
+        if (!e.depth && !e.early) continue;
+        plan.push_back(e);
+        n_early += e.early;
+        if (d >= 1) ++used;
+        if (d == 2) d2.push_back(kk);
+        else if (d > 2) deep.emplace_back(kk, d);
+    }
+    if (!plan.empty()) {
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.plan, plan.data(), sizeof(PlanEntry) * plan.size(), cudaMemcpyHostToDevice,
+                                      g.stream),
+                      "upload the plan");
+        ESIM_CUDA_TRY(launch_plan_scatter(g, w.plan, (int)plan.size(), w.R, w.depth, w.cand), "scatter the plan");
+        *launches += 1;
+    }
+    g.early_launches = 0;
+    g.early_nodes = n_early;
+    if (*side) {
+        if (n_early > 0) {
+            esim_status es = start_early_walks(g, w, c, seed, launches);
             if (es != ESIM_OK) return es;
-            early_started = true;
         }
+        // the main stream waits for this event before it merges the counts (nme is read
+        // only for the early nodes)
+        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, n_early > 0 ? g.early_stream : g.stream), "record");
     }
+    ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // plan is a local
+    esim_status zs = alg3_zsums_of(g, w.depth, d2, std::move(deep), c, w.zsum, launches);
+    if (zs != ESIM_OK) return zs;
     g.last_alg3_nodes = used;
-    if (*side) {  // the early walks are done when this event is
-        if (!early_started) ESIM_CUDA_TRY(cudaMemsetAsync(w.nme, 0, 8 * (size_t)g.n, g.early_stream), "reset counts");
-        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.early_stream), "record");
-    }
     const int64_t nb = allocate_blocks(g.n);
     ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R, w.off, g.scan_part, nullptr, g.norm_part + nb), "Algorithm 3 rescan");
     *launches += 3;
@@ -803,6 +868,7 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     for (float& x : g.last_ms) x = 0.f;
     g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
     g.last_early = side_used ? g.early_launches : 0;
+    g.last_early_nodes = side_used ? g.early_nodes : 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
         cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
@@ -971,6 +1037,7 @@ esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, 
     for (float& x : g.last_ms) x = 0.f;
     g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
     g.last_early = 0;
+    g.last_early_nodes = 0;
     g.last_steps_side = 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
@@ -1424,6 +1491,7 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->pair_steps_side = g.last_steps_side;
     out->ms_sample_early = g.last_ms_early;
     out->early_launches = g.last_early;
+    out->early_nodes = g.last_early_nodes;
     out->alg3_nodes = g.last_alg3_nodes;
     out->hist_entries = g.last_hist_entries;
     out->workspace_bytes = g.last_ws_bytes;

@@ -93,6 +93,7 @@ struct Graph {
     cudaEvent_t early_ev = nullptr;
     std::vector<cudaEvent_t> early_tev;  // timing of the early launches (start, end pairs)
     int early_launches = 0;
+    int early_nodes = 0;
     cudaEvent_t side_tev[2] = {};        // timing of the side sampler (option timing)
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     int alg3_overlap = 4;                // side sampler blocks per SM during the planning (0: no overlap)
@@ -123,7 +124,10 @@ struct Graph {
     size_t a3ws_bytes = 0;
     void* a3pws = nullptr;        // the paper's depth rule: support bit sets and edge tables
     size_t a3pws_bytes = 0;
+    void* zstage = nullptr;       // Algorithm 3: depth-2 node ids and their gathered Z sums
+    size_t zstage_bytes = 0;
     int32_t last_alg3_nodes = 0;
+    int32_t last_early_nodes = 0;
     uint64_t last_hist_entries = 0;
     uint64_t last_ws_bytes = 0;
     // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
@@ -194,8 +198,17 @@ cudaError_t launch_mark(const Graph& g, const int32_t* ids, int count, uint8_t* 
 cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t* off, double c, uint64_t seed,
                                    uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr,
                                    int shared_B = 0, const uint64_t* rbase = nullptr, bool zero_counts = true);
-// off(i) = 0 for i <= k, R for i > k: the offsets of one node's R pairs
-cudaError_t launch_single_offsets(const Graph& g, int64_t k, uint64_t R, uint64_t* off);
+// One planned Algorithm 3 candidate: depth >= 1 sets R(k) and depth(k); early marks
+// cand(k) = 2 (its walks run during the rest of the planning)
+struct PlanEntry {
+    int32_t k;
+    uint8_t depth;
+    uint8_t early;
+    uint16_t pad;
+    uint64_t R;
+};
+cudaError_t launch_plan_scatter(const Graph& g, const PlanEntry* plan, int count, uint64_t* R, uint8_t* depth,
+                                uint8_t* cand);
 cudaError_t launch_dhat_segments(const Graph& g, int64_t nseg, const uint64_t* nonmeet, const uint64_t* off,
                                  double* dhat);
 // record = false: an auxiliary scan that leaves the status block (sum of R, budget) alone
@@ -249,6 +262,8 @@ cudaError_t alg3_paper_z1(const Graph& g, const uint8_t* depth, double c, double
 // zsum(k) = Z_1(k) + Z_2(k) for the listed nodes (device ids), by the closed form of depth 2;
 // NaN where the two-hop neighbourhood is too large for the kernel's table
 cudaError_t alg3_paper_z2(const Graph& g, const int32_t* ids, int count, double c, double* zsum);
+// dst[i] = src[ids[i]] for i < count (device arrays)
+cudaError_t alg3_gather_f64(const Graph& g, const int32_t* ids, int count, const double* src, double* dst);
 
 // topk.cu
 constexpr int kTopkMax = 4096;

@@ -408,9 +408,16 @@ __global__ void merge_counts_kernel(int64_t n, const uint8_t* __restrict__ cand,
     }
 }
 
-__global__ void single_offsets_kernel(int64_t n, int64_t k, uint64_t R, uint64_t* __restrict__ off) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
-        off[i] = i <= k ? 0ull : R;
+__global__ void plan_scatter_kernel(const PlanEntry* __restrict__ plan, int count, uint64_t* __restrict__ R,
+                                    uint8_t* __restrict__ depth, uint8_t* __restrict__ cand) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const PlanEntry e = plan[i];
+        if (e.depth) {
+            R[e.k] = e.R;
+            depth[e.k] = e.depth;
+        }
+        if (e.early) cand[e.k] = 2;
+    }
 }
 
 __global__ void mark_kernel(const int32_t* __restrict__ ids, int count, uint8_t* __restrict__ mark) {
@@ -434,8 +441,10 @@ cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint6
     return cudaGetLastError();
 }
 
-cudaError_t launch_single_offsets(const Graph& g, int64_t k, uint64_t R, uint64_t* off) {
-    single_offsets_kernel<<<eb_cap(g, g.n + 1), kBlock, 0, g.stream>>>(g.n, k, R, off);
+cudaError_t launch_plan_scatter(const Graph& g, const PlanEntry* plan, int count, uint64_t* R, uint8_t* depth,
+                                uint8_t* cand) {
+    if (count <= 0) return cudaSuccess;
+    plan_scatter_kernel<<<1, kBlock, 0, g.stream>>>(plan, count, R, depth, cand);
     return cudaGetLastError();
 }
 

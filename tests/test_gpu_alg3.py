@@ -83,6 +83,25 @@ def test_first_meeting_matches_lemma5(graph):
         assert np.max(np.abs(z - np.array(ref))) <= TOL
 
 
+def test_first_meeting_covers_both_last_level_forms(graph):
+    """The last probe level takes g_2 of each support node from a one-warp two-hop table
+    when the node's two-hop multiset fits (sum of din over its in-neighbours <= 512), else
+    from the dense probes; at the hub of the Chung-Lu graph, depth 3, both forms occur
+    among the support of h_1 = I(k), and Z still matches the oracle's Lemma 5."""
+    name, (n, rp, col), g = graph
+    if name != "chung_lu_20k":
+        pytest.skip("the hub graph covers both forms")
+    din = np.diff(rp)
+    k = int(np.argmax(din))
+    sup = col[rp[k]:rp[k + 1]]
+    e1 = np.array([int(din[col[rp[q]:rp[q + 1]]].sum()) for q in sup])
+    assert np.count_nonzero(e1 <= 512) > 0 and np.count_nonzero(e1 > 512) > 0
+    for d in (3, 4):
+        ref = a3.first_meeting_lemma5(n, rp, col, k, C, d)
+        z = g.alg3_first_meeting(k, d, C)
+        assert np.max(np.abs(z - np.array(ref))) <= TOL, (d, z, ref)
+
+
 def test_depth_sampler_bit_exact(torch_cuda, graph, oracle_walks):
     torch = torch_cuda
     name, (n, rp, col), g = graph
@@ -400,8 +419,9 @@ def test_alg3_cost_model_with_basic_allocation_and_fp32c(esim, oracle_walks):
 @pytest.mark.parametrize("overlap,early", [(0, 1e30), (4, 1e30), (4, 1.0), (2, 1.5e6)])
 def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, early):
     """Cost model: the walks split over the side stream (non-candidates), the early stream
-    (each planned candidate) and the main stream give the oracle's counts and scores on
-    the same plan."""
+    (the candidates with at least alg3_early_pairs pairs, one launch before the
+    first-meeting terms) and the main stream give the oracle's counts and scores on the
+    same plan."""
     n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
     g = esim.Graph(n, rp, col, alg3=1, alg3_rule=1, alg3_min_pairs=1e3, alg3_max_nodes=16, alg3_max_depth=6,
                    alg3_overlap=overlap, alg3_early_pairs=early)
@@ -415,11 +435,15 @@ def test_alg3_walk_overlap_gives_the_same_counts(esim, oracle_walks, overlap, ea
         st = g.stats()
         assert st["sum_R"] == int(q.R.sum()) and st["pair_steps"] == q.pair_steps
         assert np.max(np.abs(s - q.s)) <= TOL
-        if overlap and early <= 1.0:
-            assert st["early_launches"] == st["alg3_nodes"] > 0
+        if overlap and early <= 1.0:  # every candidate, exploited or not
+            assert st["early_launches"] == 1 and st["early_nodes"] >= st["alg3_nodes"] > 0
         if overlap and early == 1.5e6:  # exploited R(k) of these sources lie on both sides of 1.5e6
-            n_early = int(np.count_nonzero(q.R[q.depth > 0] >= early))
-            assert 0 < st["early_launches"] == n_early < st["alg3_nodes"]
+            planned = q.R[q.depth > 0]
+            n_early = int(np.count_nonzero(planned >= early))
+            assert st["early_launches"] == 1 and st["early_nodes"] >= n_early > 0
+            assert np.count_nonzero(planned < early) > 0
+        if not overlap or early > 1e20:
+            assert st["early_launches"] == 0 and st["early_nodes"] == 0
         checked += 1
     assert checked >= 2
     g.close()
