@@ -758,13 +758,12 @@ def main():
 
     # roofline of the dominant kernel (the walk-pair sampler): pair-steps per second against
     # the integer-issue limit of one Philox-4x32-10 block plus the step logic
-    # the sampler's launches: with Algorithm 3 one on the side stream (the other nodes' walks,
-    # overlapping the planning), one per heavy candidate on the early stream as soon as its
-    # plan is final, and one after the planning; achieved = pair-steps / the sum of the
-    # launches' durations (CUDA events on each launch's own stream)
+    # the sampler's launches: with Algorithm 3 one on the side stream (the walks whose plan is
+    # final, overlapping the planning) and one after the planning; achieved = pair-steps /
+    # the sum of the launches' durations (CUDA events on each launch's own stream)
     steps_total = sum(s["pair_steps"] for s in stats)
-    ms_sample = sum(s["ms_sample_kernel"] + s["ms_sample_side"] + s["ms_sample_early"] for s in stats)
-    sampler_launches = sum(1 + (1 if s["pair_steps_side"] else 0) + s["early_launches"] for s in stats)
+    ms_sample = sum(s["ms_sample_kernel"] + s["ms_sample_side"] for s in stats)
+    sampler_launches = sum(1 + (1 if s["pair_steps_side"] else 0) for s in stats)
     ms_phase = {p: sum(s[f"ms_{p}"] for s in stats) for p in ("forward", "allocate", "sample", "reverse", "topk")}
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))

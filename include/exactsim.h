@@ -94,22 +94,20 @@ typedef struct {
     int32_t reserved2;
     uint64_t hist_entries;    /* stored history entries: (L+1) n dense, kept entries sparse */
     uint64_t workspace_bytes; /* device bytes of the last query's workspace layout */
-    /* With Algorithm 3's cost-model rule the walks of the nodes that are not exploitation
-     * candidates run on a second stream while the candidates are planned, and the walks of
-     * the candidates with at least "alg3_early_pairs" pairs on a third, in one launch, as
-     * soon as every depth is chosen (before the first-meeting terms).  With the paper's
-     * rule every node's walks run on the second stream once the depths are known, while
-     * the first-meeting sums are computed.  ms_sample_kernel is the last sampler launch
-     * alone, ms_sample_side the side launch, ms_sample_early the early launch (all with
-     * option timing); early_launches is 0 or 1 and early_nodes the candidates it walked;
-     * pair_steps_side is the side launch's share of pair_steps, which counts every
-     * launch. */
+    /* With Algorithm 3 a second stream walks, in one sampler launch during the planning,
+     * the nodes whose R(k) and depth are final: under the cost-model rule every node that
+     * is not an exploitation candidate and the candidates with at least "alg3_early_pairs"
+     * pairs, once every depth is chosen (before the first-meeting terms); under the
+     * paper's rule every node, once the depths are known.  The other candidates walk on
+     * the main stream after the planning.  ms_sample_kernel is the main sampler launch
+     * alone and ms_sample_side the side launch (with option timing); pair_steps_side is
+     * the side launch's share of pair_steps, which counts every launch; side_candidates
+     * is the number of candidates the side launch walked. */
     float ms_sample_kernel;
     float ms_sample_side;
     uint64_t pair_steps_side;
-    float ms_sample_early;
-    int32_t early_launches;
-    int32_t early_nodes;  /* candidates whose walks ran in the early launch */
+    int32_t side_candidates;
+    int32_t reserved3;
 } esim_query_stats;
 
 /* ------------------------------------------------------------------ library */
@@ -201,12 +199,12 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_push_div"  a probe step pushes from its frontier while the frontier's in-edges are
  *                    at most (m+n)/alg3_push_div, else pulls over all rows (default 4);
  *                    both give the same integers
- *   "alg3_overlap"   sampler blocks per SM for the walks of the nodes that are not
- *                    candidates, run on a second stream during the planning (default 4;
- *                    0: all walks after the planning).  Counts do not depend on it.
+ *   "alg3_overlap"   sampler blocks per SM of the side launch, which walks the nodes
+ *                    whose plan is final on a second stream during the planning (default
+ *                    4; 0: all walks after the planning).  Counts do not depend on it.
  *   "alg3_early_pairs"  with "alg3_overlap" > 0, the candidates with at least this many
- *                    pairs (default 2^24) walk on a third stream, in one launch, as soon
- *                    as every depth is chosen, while the first-meeting terms are
+ *                    pairs (default 2^24) walk in the side launch, with the other nodes,
+ *                    as soon as every depth is chosen, while the first-meeting terms are
  *                    computed; the others after the planning.  Counts do not depend on it.
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch"  weights of the cost model, in
  *                    walk pair-steps: per entry of a single-vector sweep (default 4), per

@@ -35,9 +35,8 @@ class QueryStats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("alg3_nodes", ctypes.c_int32), ("reserved2", ctypes.c_int32),
                 ("hist_entries", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("ms_sample_kernel", ctypes.c_float), ("ms_sample_side", ctypes.c_float),
-                ("pair_steps_side", ctypes.c_uint64), ("ms_sample_early", ctypes.c_float),
-                ("early_launches", ctypes.c_int32),
-                ("early_nodes", ctypes.c_int32)]
+                ("pair_steps_side", ctypes.c_uint64), ("side_candidates", ctypes.c_int32),
+                ("reserved3", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved2"}

@@ -170,7 +170,6 @@ void release(Graph& g) {
     // caller's stream set by esim_set_stream is the caller's to drain)
     if (g.own_stream) cudaStreamSynchronize(g.own_stream);
     if (g.side_stream) cudaStreamSynchronize(g.side_stream);
-    if (g.early_stream) cudaStreamSynchronize(g.early_stream);
     free_csr(g.in);
     free_csr(g.out);
     cudaFree(g.inv_din);
@@ -194,10 +193,6 @@ void release(Graph& g) {
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : g.side_tev)
         if (ev) cudaEventDestroy(ev);
-    for (auto& ev : g.early_tev)
-        if (ev) cudaEventDestroy(ev);
-    if (g.early_stream) cudaStreamDestroy(g.early_stream);
-    if (g.early_ev) cudaEventDestroy(g.early_ev);
     g = Graph{};
 }
 
@@ -232,13 +227,11 @@ struct Ws {
     double* s;         // n
     uint8_t* depth;    // n  Algorithm 3 depth per node (0: Algorithm 2)
     double* zsum;      // n  Algorithm 3: sum of the exact Z_l(k)
-    uint8_t* cand;     // n  Algorithm 3 candidates (their walks wait for the plan)
-    uint64_t* R2;      // n  R of the other nodes, then of the candidates
-    uint64_t* off2;    // n+1  offsets of the other nodes' walks (read by the side stream)
+    uint8_t* cand;     // n  Algorithm 3: 0 other node, 1 candidate walked after the plan, 2 early candidate
+    uint64_t* R2;      // n  R of the side sampler's nodes, then of the other candidates
+    uint64_t* off2;    // n+1  offsets of the side sampler's walks (read by the side stream)
     uint64_t* offc;    // n+1  offsets of the candidates' walks
     uint64_t* nm2;     // n  counts of the other nodes
-    uint64_t* nme;     // n  counts of the candidates sampled during the planning
-    uint64_t* offe;    // n+1  offsets of their walks
     int32_t* cand_ids; // 4096
     PlanEntry* plan;   // 4096  the cost model's plan, staged for the scatter
     // sparse linearization (FP64): rolling pi^l, the running pi, the kept entries
@@ -300,8 +293,6 @@ size_t ws_layout(int64_t n_, int32_t L, int precision, char* base, Ws* w, uint64
     t.off2 = (uint64_t*)take(8 * (n + 1));
     t.offc = (uint64_t*)take(8 * (n + 1));
     t.nm2 = (uint64_t*)take(8 * n);
-    t.nme = (uint64_t*)take(8 * n);
-    t.offe = (uint64_t*)take(8 * (n + 1));
     t.cand_ids = (int32_t*)take(4 * 4096);
     t.plan = (PlanEntry*)take(sizeof(PlanEntry) * 4096);
     if (precision == 0 && sparse_cap > 0) {
@@ -426,48 +417,17 @@ esim_status launch_side_walks(Graph& g, const Ws& w, const uint64_t* off, double
 }
 
 // Starts, on the side stream, the walks of every node that is not an Algorithm 3
-// candidate: their R(k) is final, and the walk spec keys a pair by (seed, k, r), so
-// splitting the nodes between sampler launches changes no count.
-esim_status start_side_walks(Graph& g, const Ws& w, const std::vector<int32_t>& cand, double c, uint64_t seed,
-                             int* launches) {
-    ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
-    ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand_ids, cand.data(), sizeof(int32_t) * cand.size(), cudaMemcpyHostToDevice,
-                                  g.stream), "upload candidates");
-    ESIM_CUDA_TRY(launch_mark(g, w.cand_ids, (int)cand.size(), w.cand), "mark candidates");
-    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 0, w.R2), "other nodes' R");
+// candidate and of the early candidates (cand = 2), in one launch: their R(k) and depths
+// are final, and the walk spec keys a pair by (seed, k, r), so splitting the nodes
+// between sampler launches changes no count.  One launch, not one per group, so that
+// the planning's kernels keep their share of every SM.
+esim_status start_side_walks(Graph& g, const Ws& w, double c, uint64_t seed, int* launches) {
+    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, (1u << 0) | (1u << 2), w.R2), "side nodes' R");
     const int64_t nb = allocate_blocks(g.n);
-    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.off2, g.scan_part, nullptr, g.norm_part + nb, false), "other nodes' scan");
-    esim_status st = launch_side_walks(g, w, w.off2, c, seed, nullptr);
+    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.off2, g.scan_part, nullptr, g.norm_part + nb, false), "side nodes' scan");
+    esim_status st = launch_side_walks(g, w, w.off2, c, seed, w.depth);
     if (st != ESIM_OK) return st;
-    *launches += 6;
-    return ESIM_OK;
-}
-
-// The walks of the candidates marked early (cand = 2) on the early stream, in one
-// launch: their plans are final, and they run while the first-meeting terms are computed.
-// Counts go to nme, pair-steps to the status block.
-esim_status start_early_walks(Graph& g, const Ws& w, double c, uint64_t seed, int* launches) {
-    ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 2, w.R2), "early candidates' R");
-    const int64_t nb = allocate_blocks(g.n);
-    ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.offe, g.scan_part, nullptr, g.norm_part + nb, false),
-                  "early candidates' scan");
-    ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.stream), "record");
-    ESIM_CUDA_TRY(cudaStreamWaitEvent(g.early_stream, g.early_ev, 0), "early wait");
-    Graph view = g;
-    view.stream = g.early_stream;
-    view.sample_block_cap = g.alg3_overlap;
-    if (g.timing) {
-        while (g.early_tev.size() < 2) {
-            cudaEvent_t ev = nullptr;
-            ESIM_CUDA_TRY(cudaEventCreate(&ev), "cudaEventCreate");
-            g.early_tev.push_back(ev);
-        }
-        cudaEventRecord(g.early_tev[0], g.early_stream);
-    }
-    ESIM_CUDA_TRY(launch_sample(view, w.offe, c, seed, w.nme, nullptr, w.depth), "early candidates' walk pairs");
-    if (g.timing) cudaEventRecord(g.early_tev[1], g.early_stream);
-    g.early_launches = 1;
-    *launches += 3;
+    *launches += 5;
     return ESIM_OK;
 }
 
@@ -589,9 +549,7 @@ esim_status plan_alg3_paper(Graph& g, const Ws& w, double c, int* launches, uint
         ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
         esim_status st = launch_side_walks(g, w, w.off, c, seed, w.depth);
         if (st != ESIM_OK) return st;
-        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, g.stream), "record");
-        g.early_launches = 0;
-        g.early_nodes = 0;
+        g.side_candidates = 0;
         *side = true;
         *launches += 1;
     }
@@ -640,13 +598,15 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
     // Algorithm 2 counts (no other error can be raised before the walks); the side
     // sampler judges the other nodes' pairs and the rescan below all of them.
     ESIM_CUDA_TRY(cudaMemsetAsync((char*)g.status + offsetof(Status, err), 0, sizeof(int), g.stream), "reset budget");
-    *side = false;
-    g.early_launches = 0;
-    g.early_nodes = 0;
-    if (!cand.empty() && g.side_stream && g.alg3_overlap > 0) {
-        esim_status ss = start_side_walks(g, w, cand, c, seed, launches);
-        if (ss != ESIM_OK) return ss;
-        *side = true;
+    g.side_candidates = 0;
+    *side = !cand.empty() && g.side_stream && g.alg3_overlap > 0;
+    if (*side) {  // cand = 1 for the candidates (2 for the early ones below)
+        ESIM_CUDA_TRY(cudaMemsetAsync(w.cand, 0, (size_t)g.n, g.stream), "reset candidates");
+        ESIM_CUDA_TRY(cudaMemcpyAsync(w.cand_ids, cand.data(), sizeof(int32_t) * cand.size(), cudaMemcpyHostToDevice,
+                                      g.stream),
+                      "upload candidates");
+        ESIM_CUDA_TRY(launch_mark(g, w.cand_ids, (int)cand.size(), w.cand), "mark candidates");
+        *launches += 1;
     }
     const int levels = std::max(0, g.alg3_max_depth - 2);
     std::vector<uint64_t> supps(cand.size() * (kAlg3MaxDepth + 1), 0);
@@ -655,8 +615,8 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
                       "Algorithm 3 supports");
     // The cost model picks each depth from the supports alone, so every plan is final
     // before any first-meeting term is computed: R(k) and depth(k) go to the device at
-    // once, and the walks of the candidates with at least alg3_early_pairs pairs start
-    // on the early stream while the terms are computed.
+    // once, and the walks of the other nodes and of the candidates with at least
+    // alg3_early_pairs pairs start on the side stream while the terms are computed.
     std::vector<PlanEntry> plan;
     std::vector<int32_t> d2;
     std::vector<std::pair<int32_t, int>> deep;
@@ -689,16 +649,10 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         ESIM_CUDA_TRY(launch_plan_scatter(g, w.plan, (int)plan.size(), w.R, w.depth, w.cand), "scatter the plan");
         *launches += 1;
     }
-    g.early_launches = 0;
-    g.early_nodes = n_early;
+    g.side_candidates = n_early;
     if (*side) {
-        if (n_early > 0) {
-            esim_status es = start_early_walks(g, w, c, seed, launches);
-            if (es != ESIM_OK) return es;
-        }
-        // the main stream waits for this event before it merges the counts (nme is read
-        // only for the early nodes)
-        ESIM_CUDA_TRY(cudaEventRecord(g.early_ev, n_early > 0 ? g.early_stream : g.stream), "record");
+        esim_status ss = start_side_walks(g, w, c, seed, launches);
+        if (ss != ESIM_OK) return ss;
     }
     ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // plan is a local
     esim_status zs = alg3_zsums_of(g, w.depth, d2, std::move(deep), c, w.zsum, launches);
@@ -785,26 +739,22 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
         if (g.alg3) {
             esim_status a3 = plan_alg3(g, w, c, R_b, &extra_launches, seed, &side);
             if (a3 != ESIM_OK) {
-                if (side) {  // no walks left running into the next query
-                    cudaStreamSynchronize(g.side_stream);
-                    cudaStreamSynchronize(g.early_stream);
-                }
+                if (side) cudaStreamSynchronize(g.side_stream);  // no walks left running into the next query
                 return a3;
             }
         }
         if (g.timing) cudaEventRecord(g.ev[2], g.stream);
         if (side) {
-            // the candidates' walks here; the other nodes' counts come from the side stream
-            ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 1, w.R2), "candidates' R");
+            // the remaining candidates' walks here; the side stream's counts for the rest
+            ESIM_CUDA_TRY(launch_mask_R(g, w.R, w.cand, 1u << 1, w.R2), "candidates' R");
             ESIM_CUDA_TRY(launch_scan_R(g, g.n, w.R2, w.offc, g.scan_part, nullptr, g.norm_part + allocate_blocks(g.n),
                                         false),
                           "candidates' scan");
             if (g.timing) cudaEventRecord(g.ev[6], g.stream);
             ESIM_CUDA_TRY(launch_sample(g, w.offc, c, seed, w.nonmeet, nullptr, w.depth), "candidates' walk pairs");
             if (g.timing) cudaEventRecord(g.ev[7], g.stream);
-            ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.side_ev[1], 0), "wait for the other nodes' walks");
-            ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.early_ev, 0), "wait for the heavy candidates' walks");
-            ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nme, w.nonmeet), "merge counts");
+            ESIM_CUDA_TRY(cudaStreamWaitEvent(g.stream, g.side_ev[1], 0), "wait for the side walks");
+            ESIM_CUDA_TRY(launch_merge_counts(g, w.cand, w.nm2, w.nonmeet), "merge counts");
             extra_launches += 5;
         } else {
             if (g.timing) cudaEventRecord(g.ev[6], g.stream);
@@ -866,19 +816,13 @@ esim_status run_query(Graph& g, int64_t u, double c, double eps, uint64_t seed, 
     g.last_steps = hs.pair_steps + (side_used ? hs.pair_steps_side : 0ull);
     g.last_steps_side = side_used ? hs.pair_steps_side : 0ull;
     for (float& x : g.last_ms) x = 0.f;
-    g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
-    g.last_early = side_used ? g.early_launches : 0;
-    g.last_early_nodes = side_used ? g.early_nodes : 0;
+    g.last_ms_kernel = g.last_ms_side = 0.f;
+    g.last_side_candidates = side_used ? g.side_candidates : 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
         cudaEventElapsedTime(&g.last_ms[5], g.ev[0], g.ev[5]);
         cudaEventElapsedTime(&g.last_ms_kernel, g.ev[6], g.ev[7]);
         if (side_used) cudaEventElapsedTime(&g.last_ms_side, g.side_tev[0], g.side_tev[1]);
-        for (int i = 0; i < g.last_early; ++i) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, g.early_tev[2 * (size_t)i], g.early_tev[2 * (size_t)i + 1]);
-            g.last_ms_early += ms;
-        }
     }
     if (hs.err & kErrBudget)
         return fail(ESIM_EBUDGET, "sum of R(k) = " + std::to_string((double)hs.sum_R) + " exceeds the pair budget");
@@ -1035,9 +979,8 @@ esim_status run_batch(Graph& g, int32_t B, const int64_t* u, const double* eps, 
     g.last_sum_R = hs.sum_R;
     g.last_steps = hs.pair_steps;
     for (float& x : g.last_ms) x = 0.f;
-    g.last_ms_kernel = g.last_ms_side = g.last_ms_early = 0.f;
-    g.last_early = 0;
-    g.last_early_nodes = 0;
+    g.last_ms_kernel = g.last_ms_side = 0.f;
+    g.last_side_candidates = 0;
     g.last_steps_side = 0;
     if (g.timing) {
         for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&g.last_ms[i], g.ev[i], g.ev[i + 1]);
@@ -1295,9 +1238,7 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
               cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g.side_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&g.side_ev[0], cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&g.side_ev[1], cudaEventDisableTiming) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&g.early_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&g.early_ev, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&g.side_ev[1], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(g);
@@ -1489,9 +1430,7 @@ esim_status esim_last_stats(const esim_graph* h, esim_query_stats* out) {
     out->ms_sample_kernel = g.last_ms_kernel;
     out->ms_sample_side = g.last_ms_side;
     out->pair_steps_side = g.last_steps_side;
-    out->ms_sample_early = g.last_ms_early;
-    out->early_launches = g.last_early;
-    out->early_nodes = g.last_early_nodes;
+    out->side_candidates = g.last_side_candidates;
     out->alg3_nodes = g.last_alg3_nodes;
     out->hist_entries = g.last_hist_entries;
     out->workspace_bytes = g.last_ws_bytes;

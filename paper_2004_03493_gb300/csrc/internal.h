@@ -89,11 +89,7 @@ struct Graph {
     cudaStream_t stream = nullptr;
     cudaStream_t side_stream = nullptr;  // Algorithm 3: walks of the other nodes during the planning
     cudaEvent_t side_ev[2] = {};
-    cudaStream_t early_stream = nullptr; // Algorithm 3: walks of each planned heavy node during the rest
-    cudaEvent_t early_ev = nullptr;
-    std::vector<cudaEvent_t> early_tev;  // timing of the early launches (start, end pairs)
-    int early_launches = 0;
-    int early_nodes = 0;
+    int side_candidates = 0;             // Algorithm 3 candidates walked by the side sampler
     cudaEvent_t side_tev[2] = {};        // timing of the side sampler (option timing)
     int sample_block_cap = 0;            // sampler blocks per SM (0: as many as fit)
     int alg3_overlap = 4;                // side sampler blocks per SM during the planning (0: no overlap)
@@ -127,7 +123,7 @@ struct Graph {
     void* zstage = nullptr;       // Algorithm 3: depth-2 node ids and their gathered Z sums
     size_t zstage_bytes = 0;
     int32_t last_alg3_nodes = 0;
-    int32_t last_early_nodes = 0;
+    int32_t last_side_candidates = 0;
     uint64_t last_hist_entries = 0;
     uint64_t last_ws_bytes = 0;
     // batched queries: their own workspace, and the autotuned tile per width (W = 32, 64)
@@ -157,8 +153,6 @@ struct Graph {
     unsigned long long last_sum_R = 0, last_steps = 0;
     float last_ms[6] = {};
     float last_ms_kernel = 0.f, last_ms_side = 0.f;  // sampler launches alone (main, side)
-    float last_ms_early = 0.f;
-    int last_early = 0;
     unsigned long long last_steps_side = 0;
 };
 
@@ -186,11 +180,10 @@ cudaError_t launch_sample(const Graph& g, const uint64_t* off, double c, uint64_
                           uint64_t* pair_steps, const uint8_t* depth = nullptr);
 cudaError_t launch_dhat(const Graph& g, const uint64_t* nonmeet, const uint64_t* off, double* dhat);
 cudaError_t launch_fill(const Graph& g, int64_t n, double value, double* out);
-// R_out(k) = R(k) where keep(k) == want, else 0
-cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want, uint64_t* R_out);
-// counts(k) = side(k) where cand(k) == 0, early(k) where cand(k) == 2
-cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, const uint64_t* early,
-                                uint64_t* counts);
+// R_out(k) = R(k) where bit keep(k) of want_mask is set (keep(k) < 8), else 0
+cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want_mask, uint64_t* R_out);
+// counts(k) = side(k) where cand(k) != 1 (the nodes the side sampler walked)
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts);
 // cand(k) = 1 for the listed nodes
 cudaError_t launch_mark(const Graph& g, const int32_t* ids, int count, uint8_t* mark);
 // batches: nseg = B * n segments, segment q*n + k = node k of column q
@@ -199,7 +192,7 @@ cudaError_t launch_sample_segments(const Graph& g, int64_t nseg, const uint64_t*
                                    uint64_t* nonmeet, uint64_t* pair_steps, const uint8_t* depth = nullptr,
                                    int shared_B = 0, const uint64_t* rbase = nullptr, bool zero_counts = true);
 // One planned Algorithm 3 candidate: depth >= 1 sets R(k) and depth(k); early marks
-// cand(k) = 2 (its walks run during the rest of the planning)
+// cand(k) = 2 (its walks run on the side stream during the rest of the planning)
 struct PlanEntry {
     int32_t k;
     uint8_t depth;

@@ -394,18 +394,15 @@ __global__ void fill_kernel(int64_t n, double value, double* __restrict__ out) {
 }
 
 __global__ void mask_R_kernel(int64_t n, const uint64_t* __restrict__ R, const uint8_t* __restrict__ keep,
-                              uint8_t want, uint64_t* __restrict__ R_out) {
+                              uint8_t want_mask, uint64_t* __restrict__ R_out) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        R_out[k] = keep[k] == want ? R[k] : 0ull;
+        R_out[k] = ((want_mask >> keep[k]) & 1u) ? R[k] : 0ull;
 }
 
 __global__ void merge_counts_kernel(int64_t n, const uint8_t* __restrict__ cand, const uint64_t* __restrict__ side,
-                                    const uint64_t* __restrict__ early, uint64_t* __restrict__ counts) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t m = cand[k];
-        if (m == 0) counts[k] = side[k];
-        else if (m == 2) counts[k] = early[k];
-    }
+                                    uint64_t* __restrict__ counts) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (cand[k] != 1) counts[k] = side[k];
 }
 
 __global__ void plan_scatter_kernel(const PlanEntry* __restrict__ plan, int count, uint64_t* __restrict__ R,
@@ -430,14 +427,13 @@ static int eb_cap(const Graph& g, int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want, uint64_t* R_out) {
-    mask_R_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, R, keep, want, R_out);
+cudaError_t launch_mask_R(const Graph& g, const uint64_t* R, const uint8_t* keep, uint8_t want_mask, uint64_t* R_out) {
+    mask_R_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, R, keep, want_mask, R_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, const uint64_t* early,
-                                uint64_t* counts) {
-    merge_counts_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, cand, side, early, counts);
+cudaError_t launch_merge_counts(const Graph& g, const uint8_t* cand, const uint64_t* side, uint64_t* counts) {
+    merge_counts_kernel<<<eb_cap(g, g.n), kBlock, 0, g.stream>>>(g.n, cand, side, counts);
     return cudaGetLastError();
 }
 
