@@ -105,7 +105,7 @@ SIGNATURES = {
     "esim_server_get_stats": (_ST, [_P, ctypes.POINTER(ServerStats)]),
     "esim_server_destroy": (None, [_P]),
     "esim_alg3_first_meeting": (_ST, [_P, _I64, _I32, _D, _P]),
-    "esim_alg3_depth": (_I32, [_D, _D, _P, _I32, _I64, _I64, _D, _D, _D]),
+    "esim_alg3_depth": (_I32, [_D, _D, _P, _I32, _I64, _I64, _D, _D, _D, _D]),
     "esim_alg3_paper_depth": (_ST, [_P, _P, _D, _I32, _P]),
     "esim_alg3_zsum": (_ST, [_P, _P, _D, _P]),
     "esim_sample_depth": (_ST, [_P, _P, _P, _D, _U64, _P, _P]),
@@ -362,7 +362,7 @@ def esim_alg3_first_meeting(g: int, k: int, depth: int, c: float) -> np.ndarray:
 
 
 def esim_alg3_depth(v: float, c: float, supp, max_depth: int, n: int, m: int,
-                    weights=(4.0, 0.2, 524288.0)) -> int:
+                    weights=(4.0, 0.2, 524288.0, 0.0625)) -> int:
     """Algorithm 3's depth choice for one node (host arithmetic, no device)."""
     sp = np.ascontiguousarray(supp, dtype=np.uint64)
     return int(lib().esim_alg3_depth(float(v), float(c), sp.ctypes.data, int(max_depth), int(n), int(m),

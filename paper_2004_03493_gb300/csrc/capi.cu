@@ -344,30 +344,40 @@ esim_status ensure_a3ws(Graph& g) {
     return ESIM_OK;
 }
 
-// Algorithm 3's depth choice.  The paper grows l(k) until the explored edges reach
-// 2 R(k) / sqrt(c), the walk work they replace.  Here the exploitation is done with
-// dense sweeps, so the depth d of node k minimises an estimate of the GPU work, in
-// pair-steps of the sampler:
+// Algorithm 3's depth choice under option alg3_rule = 1.  The paper grows l(k) until the
+// explored edges reach 2 R(k) / sqrt(c), the walk work they replace.  Here the
+// exploitation is done with dense sweeps, so the depth d of node k minimises an
+// estimate of the GPU work, in walk pair-steps of the sampler:
 //   walks      R_d (d + 1/(1-c)),  R_d = max(1, ceil(v c^(2d)))  (v = R_b pi(k)^2)
-//   Lemma 5    2d-1 single-vector sweeps of m+n entries (h_1..h_d and the P~ sweeps),
-//              sum_{i=1}^{d-2} |supp h_i| (d-i) probe column-sweeps, and the launches;
+//   Lemma 5    2d-1 single-vector sweeps of m+n entries (h_1..h_d and the P~ sweeps);
+//              sum_{i=1}^{d-3} |supp h_i| (d-i) probe column-sweeps for the levels below
+//              the last; the last probe level (i = d-2, two steps, only its column sums)
+//              runs one warp per node over its two-hop neighbourhood and dense probes
+//              only for the nodes too large for that, charged as w_last 2 |supp h_{d-2}|
+//              column-sweeps; and the launches;
 // d = 0 is Algorithm 2 alone.  The weights (options alg3_w_sweep, alg3_w_probe,
-// alg3_w_launch: pair-steps per entry of a single sweep, per entry and column of a probe
-// sweep, and per launch) are calibrated by timing whole queries on GB300.
+// alg3_w_launch, alg3_w_last: pair-steps per entry of a single sweep, per entry and
+// column of a probe sweep, per launch, and the last level's share of a dense probe) are
+// calibrated by timing whole queries on GB300.
 double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int64_t m, double w_sweep,
-                 double w_probe, double w_launch) {
+                 double w_probe, double w_launch, double w_last) {
     double r = d == 0 ? ceil(v) : ceil(v * pow(c, (double)(2 * d)));
     if (r < 1.0) r = 1.0;
     double cost = r * ((double)d + 1.0 / (1.0 - c));
     if (d > 0) {
         const double edges = (double)(m + n);
         uint64_t probe = 0, launches = 3 * (uint64_t)(2 * d - 1);
-        for (int i = 1; i <= d - 2; ++i) {
+        for (int i = 1; i <= d - 3; ++i) {
             probe += supp[i] * (uint64_t)(d - i);
             launches += (supp[i] + 31) / 32 * (uint64_t)(3 * (d - i) + 2);
         }
+        double last = 0.0;
+        if (d >= 3) {
+            last = w_last * (2.0 * (double)supp[d - 2]);
+            launches += 2;
+        }
         cost += w_sweep * edges * (double)(2 * d - 1);
-        cost += w_probe * edges * (double)probe;
+        cost += w_probe * edges * ((double)probe + last);
         cost += w_launch * (double)launches;
     }
     return cost;
@@ -375,11 +385,11 @@ double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int
 
 // The depth of least estimated work, 0..max_depth (the first on ties).
 int alg3_depth(double v, double c, const uint64_t* supp, int max_depth, int64_t n, int64_t m, double w_sweep,
-               double w_probe, double w_launch) {
+               double w_probe, double w_launch, double w_last) {
     int d = 0;
-    double best = alg3_cost(0, v, c, supp, n, m, w_sweep, w_probe, w_launch);
+    double best = alg3_cost(0, v, c, supp, n, m, w_sweep, w_probe, w_launch, w_last);
     for (int dd = 1; dd <= max_depth; ++dd) {
-        const double cost = alg3_cost(dd, v, c, supp, n, m, w_sweep, w_probe, w_launch);
+        const double cost = alg3_cost(dd, v, c, supp, n, m, w_sweep, w_probe, w_launch, w_last);
         if (cost < best) {
             best = cost;
             d = dd;
@@ -626,7 +636,7 @@ esim_status plan_alg3(Graph& g, const Ws& w, double c, double R_b, int* launches
         const double v = cand_v[ci];
         const uint64_t* supp = supps.data() + ci * (kAlg3MaxDepth + 1);
         const int d = alg3_depth(v, c, supp, g.alg3_max_depth, g.n, g.m, g.alg3_w_sweep, g.alg3_w_probe,
-                                 g.alg3_w_launch);
+                                 g.alg3_w_launch, g.alg3_w_last);
         double r = d >= 1 ? ceil(v * pow(c, (double)(2 * d))) : ceil(v);
         if (r < 1.0) r = 1.0;
         if (r >= 1.8e19) r = 1.8e19;  // the rescan's budget check reports it
@@ -1322,6 +1332,9 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
     } else if (k == "alg3_min_pairs") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_min_pairs must be >= 0");
         g.alg3_min_pairs = value;
+    } else if (k == "alg3_w_last") {
+        if (!(value >= 0.0)) return fail(ESIM_EINVAL, "alg3_w_last must be >= 0");
+        g.alg3_w_last = value;
     } else if (k == "alg3_w_sweep" || k == "alg3_w_probe" || k == "alg3_w_launch") {
         if (!(value >= 0.0)) return fail(ESIM_EINVAL, k + " must be >= 0");
         (k == "alg3_w_sweep" ? g.alg3_w_sweep : k == "alg3_w_probe" ? g.alg3_w_probe : g.alg3_w_launch) = value;
@@ -1369,6 +1382,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_early_pairs") *value = g.alg3_early_pairs;
     else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
     else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
+    else if (k == "alg3_w_last") *value = g.alg3_w_last;
     else if (k == "alg3_w_launch") *value = g.alg3_w_launch;
     else if (k == "batch_tile") *value = g.batch_tile_force;
     else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];
@@ -1625,11 +1639,11 @@ esim_status esim_alg3_zsum(esim_graph* h, const uint8_t* depth, double c, double
 }
 
 int32_t esim_alg3_depth(double v, double c, const uint64_t* supp, int32_t max_depth, int64_t n, int64_t m,
-                        double w_sweep, double w_probe, double w_launch) {
+                        double w_sweep, double w_probe, double w_launch, double w_last) {
     if (!supp || !(c > 0.0 && c < 1.0) || max_depth < 0 || max_depth > kAlg3MaxDepth || n < 1 || m < 0 ||
-        !(v >= 0.0) || !(w_sweep >= 0.0) || !(w_probe >= 0.0) || !(w_launch >= 0.0))
+        !(v >= 0.0) || !(w_sweep >= 0.0) || !(w_probe >= 0.0) || !(w_launch >= 0.0) || !(w_last >= 0.0))
         return -1;
-    return alg3_depth(v, c, supp, max_depth, n, m, w_sweep, w_probe, w_launch);
+    return alg3_depth(v, c, supp, max_depth, n, m, w_sweep, w_probe, w_launch, w_last);
 }
 
 esim_status esim_sample_depth(esim_graph* h, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,

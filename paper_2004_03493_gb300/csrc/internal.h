@@ -114,6 +114,7 @@ struct Graph {
     double alg3_w_sweep = 4.0;
     double alg3_w_probe = 0.2;
     double alg3_w_launch = 524288.0;
+    double alg3_w_last = 0.0625;         // the last probe level's share of a dense probe
     bool has_duplicates = false;  // repeated in-edges (Algorithm 3 needs a simple graph)
     std::shared_ptr<std::vector<uint32_t>> din_host;  // in-degrees, for the exploitation plan
     void* a3ws = nullptr;         // Algorithm 3 scratch (FP64 vectors, dot partials)

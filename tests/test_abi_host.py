@@ -113,7 +113,7 @@ def test_alg3_cost_model_depth_is_the_documented_argmin(native):
         c = float(rng.choice([0.6, 0.8, 0.5]))
         max_depth = int(rng.integers(0, 17))
         weights = (float(rng.choice([4.0, 1.0])), float(rng.choice([0.2, 0.5, 0.05])),
-                   float(rng.choice([524288.0, 2.0 ** 16])))
+                   float(rng.choice([524288.0, 2.0 ** 16])), float(rng.choice([0.0625, 1.0, 0.0])))
         costs = [cp.cost(d, v, c, supp, n, m, *weights) for d in range(max_depth + 1)]
         want = min(range(max_depth + 1), key=lambda d: (costs[d], d))
         got = native.esim_alg3_depth(v, c, supp[:max(1, max_depth - 1)] + [0] * 2, max_depth, n, m, weights)
