@@ -196,6 +196,10 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_max_nodes" cost model: heaviest nodes (by pi) considered, 1..4096 (default 64)
  *   "alg3_min_pairs" cost model: smallest Algorithm 2 pair count worth considering (default 1e6)
  *   "alg3_max_depth" deepest exploitation, 1..16 (default 16)
+ *   "alg3_workers"   one-node Lemma 5 computations run at once, 1..16 (default 4): each
+ *                    extra worker has its own stream and Algorithm 3 workspace (about
+ *                    0.7 GB at n = 1e5, a few GB at n = 4e6; fewer workers when the device
+ *                    cannot hold them).  Results do not depend on it.
  *   "alg3_push_div"  a probe step pushes from its frontier while the frontier's in-edges are
  *                    at most (m+n)/alg3_push_div, else pulls over all rows (default 4);
  *                    both give the same integers

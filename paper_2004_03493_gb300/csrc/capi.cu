@@ -10,8 +10,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace esim;
@@ -164,12 +166,59 @@ esim_status upload_csr(int64_t n, const std::vector<uint32_t>& rp, const std::ve
     return ESIM_OK;
 }
 
+size_t partial_count(const Graph& g) {
+    return (size_t)std::max<int64_t>(1, std::max(std::max(g.in.nseg, g.out.nseg), std::max(g.in.tnseg, g.out.tnseg)));
+}
+
+void free_a3workers(Graph& g) {
+    for (auto& wk : g.a3workers) {
+        if (wk.stream) {
+            cudaStreamSynchronize(wk.stream);
+            cudaStreamDestroy(wk.stream);
+        }
+        cudaFree(wk.ws);
+        cudaFree(wk.partial);
+        cudaFree(wk.scan_part);
+        cudaFree(wk.norm_part);
+    }
+    g.a3workers.clear();
+    g.a3worker_ws_bytes = 0;
+}
+
+// Up to `extra` workers beside the query's stream; returns how many exist (fewer when
+// the device cannot hold more: the computation then uses fewer, never fails for it).
+int ensure_a3workers(Graph& g, int extra) {
+    const size_t need = alg3_workspace_bytes(g);
+    if (g.a3worker_ws_bytes < need) free_a3workers(g);
+    const int64_t nb = allocate_blocks(g.n);
+    while ((int)g.a3workers.size() < extra) {
+        Graph::A3Worker wk;
+        const bool ok = cudaStreamCreateWithFlags(&wk.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                        cudaMalloc(&wk.ws, need) == cudaSuccess && dev_alloc(&wk.partial, partial_count(g)) == cudaSuccess &&
+                        dev_alloc(&wk.scan_part, (size_t)nb) == cudaSuccess &&
+                        dev_alloc(&wk.norm_part, 2 * (size_t)nb) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (wk.stream) cudaStreamDestroy(wk.stream);
+            cudaFree(wk.ws);
+            cudaFree(wk.partial);
+            cudaFree(wk.scan_part);
+            cudaFree(wk.norm_part);
+            break;
+        }
+        g.a3workers.push_back(wk);
+        g.a3worker_ws_bytes = need;
+    }
+    return std::min<int>(extra, (int)g.a3workers.size());
+}
+
 void release(Graph& g) {
     cudaSetDevice(g.device);
     // no work of this handle may still use its buffers: its own streams drain first (a
     // caller's stream set by esim_set_stream is the caller's to drain)
     if (g.own_stream) cudaStreamSynchronize(g.own_stream);
     if (g.side_stream) cudaStreamSynchronize(g.side_stream);
+    free_a3workers(g);
     free_csr(g.in);
     free_csr(g.out);
     cudaFree(g.inv_din);
@@ -504,19 +553,56 @@ esim_status alg3_zsums_of(Graph& g, const uint8_t* depth_dev, const std::vector<
     if (!deep.empty()) {
         esim_status a3 = ensure_a3ws(g);
         if (a3 != ESIM_OK) return a3;
+        // Each node's Lemma 5 computation waits on the host between its levels (the next
+        // level's probe count); workers on their own streams take nodes from a shared
+        // counter, so one node's waits leave the GPU to the others.  A node's result does
+        // not depend on the worker that computes it.
+        const int want = std::max(1, std::min<int>(g.alg3_workers, (int)deep.size()));
+        const int nw = 1 + (want > 1 ? ensure_a3workers(g, want - 1) : 0);
         std::vector<double> zs(deep.size());
-        for (size_t i = 0; i < deep.size(); ++i) {
-            const int d = deep[i].second;
-            double z[kAlg3MaxDepth] = {};
-            ESIM_CUDA_TRY(alg3_first_meeting(g, deep[i].first, d, c, g.a3ws, z, launches),
-                          "Algorithm 3 first meetings");
-            double sum = 0.0;
-            for (int j = 0; j < d; ++j) sum += z[j];
-            zs[i] = sum;
+        std::atomic<size_t> next{0};
+        std::vector<cudaError_t> errs((size_t)nw, cudaSuccess);
+        std::vector<int> counts((size_t)nw, 0);
+        auto run = [&](int wi) {
+            Graph view = g;
+            void* ws = g.a3ws;
+            if (wi > 0) {
+                const Graph::A3Worker& wk = g.a3workers[(size_t)wi - 1];
+                if ((errs[(size_t)wi] = cudaSetDevice(g.device)) != cudaSuccess) return;
+                view.stream = wk.stream;
+                view.partial = wk.partial;
+                view.scan_part = wk.scan_part;
+                view.norm_part = wk.norm_part;
+                ws = wk.ws;
+            }
+            for (;;) {
+                const size_t i = next.fetch_add(1);
+                if (i >= deep.size()) return;
+                const int d = deep[i].second;
+                double z[kAlg3MaxDepth] = {};
+                const cudaError_t e = alg3_first_meeting(view, deep[i].first, d, c, ws, z, &counts[(size_t)wi]);
+                if (e != cudaSuccess) {
+                    errs[(size_t)wi] = e;
+                    next.store(deep.size());  // the others stop after their current node
+                    return;
+                }
+                double sum = 0.0;
+                for (int j = 0; j < d; ++j) sum += z[j];
+                zs[i] = sum;
+            }
+        };
+        std::vector<std::thread> threads;
+        for (int wi = 1; wi < nw; ++wi) threads.emplace_back(run, wi);
+        run(0);
+        for (auto& t : threads) t.join();
+        for (int wi = 0; wi < nw; ++wi) {
+            ESIM_CUDA_TRY(errs[(size_t)wi], "Algorithm 3 first meetings");
+            *launches += counts[(size_t)wi];
+        }
+        for (size_t i = 0; i < deep.size(); ++i)
             ESIM_CUDA_TRY(cudaMemcpyAsync(zsum + deep[i].first, &zs[i], sizeof(double), cudaMemcpyHostToDevice,
                                           g.stream),
                           "set zsum");
-        }
         ESIM_CUDA_TRY(cudaStreamSynchronize(g.stream), "Algorithm 3 plan");  // zs is a local
     }
     return ESIM_OK;
@@ -1239,8 +1325,7 @@ esim_status esim_load_graph(int64_t n, const int64_t* in_rowptr, const int32_t* 
         return st;
     }
     const int64_t nb = allocate_blocks(n);
-    const size_t npart = (size_t)std::max<int64_t>(
-        1, std::max(std::max(g.in.nseg, g.out.nseg), std::max(g.in.tnseg, g.out.tnseg)));
+    const size_t npart = partial_count(g);
     bool ok = dev_alloc(&g.status, 1) == cudaSuccess && cudaMallocHost((void**)&g.status_host, sizeof(Status)) == cudaSuccess &&
               dev_alloc(&g.partial, npart) == cudaSuccess && dev_alloc(&g.scan_part, (size_t)nb) == cudaSuccess &&
               dev_alloc(&g.norm_part, 2 * (size_t)nb) == cudaSuccess &&
@@ -1349,6 +1434,10 @@ esim_status esim_set_option(esim_graph* h, const char* key, double value) {
         if (!(value >= 0.0 && value <= 64.0) || value != floor(value))
             return fail(ESIM_EINVAL, "alg3_overlap must be an integer in [0, 64]");
         g.alg3_overlap = (int)value;
+    } else if (k == "alg3_workers") {
+        if (!(value >= 1.0 && value <= 16.0) || value != floor(value))
+            return fail(ESIM_EINVAL, "alg3_workers must be an integer in [1, 16]");
+        g.alg3_workers = (int)value;
     } else if (k == "alg3_max_nodes") {
         if (!(value >= 1.0 && value <= 4096.0)) return fail(ESIM_EINVAL, "alg3_max_nodes must be in [1, 4096]");
         g.alg3_max_nodes = (int)value;
@@ -1383,6 +1472,7 @@ esim_status esim_get_option(const esim_graph* h, const char* key, double* value)
     else if (k == "alg3_w_sweep") *value = g.alg3_w_sweep;
     else if (k == "alg3_w_probe") *value = g.alg3_w_probe;
     else if (k == "alg3_w_last") *value = g.alg3_w_last;
+    else if (k == "alg3_workers") *value = g.alg3_workers;
     else if (k == "alg3_w_launch") *value = g.alg3_w_launch;
     else if (k == "batch_tile") *value = g.batch_tile_force;
     else if (k == "batch_tile_fwd16") *value = g.batch_tile_fwd[0];

@@ -121,6 +121,18 @@ struct Graph {
     size_t a3ws_bytes = 0;
     void* a3pws = nullptr;        // the paper's depth rule: support bit sets and edge tables
     size_t a3pws_bytes = 0;
+    // Algorithm 3: extra workers for the one-node Lemma 5 computations, each with its own
+    // stream, workspace and sweep/scan scratch (worker 0 is the query's own stream)
+    struct A3Worker {
+        cudaStream_t stream = nullptr;
+        void* ws = nullptr;
+        double* partial = nullptr;
+        unsigned long long* scan_part = nullptr;
+        double* norm_part = nullptr;
+    };
+    std::vector<A3Worker> a3workers;
+    size_t a3worker_ws_bytes = 0;
+    int alg3_workers = 4;         // concurrent one-node Lemma 5 computations
     void* zstage = nullptr;       // Algorithm 3: depth-2 node ids and their gathered Z sums
     size_t zstage_bytes = 0;
     int32_t last_alg3_nodes = 0;

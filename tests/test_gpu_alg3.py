@@ -220,6 +220,30 @@ def test_zsum_step_matches_lemma5_sums(torch_cuda, esim, graph_name):
     g.close()
 
 
+def test_zsum_and_query_do_not_depend_on_the_workers(torch_cuda, esim):
+    """The deep nodes' Lemma 5 computations run on 1..alg3_workers streams at once; each
+    node's result is computed alone, so the zsum step and whole cost-model queries are
+    bit-identical for 1, 3 and 6 workers."""
+    torch = torch_cuda
+    n, rp, col = PAPER_GRAPHS["cl3000"]()
+    rng = np.random.default_rng(43)
+    depth = np.zeros(n, dtype=np.uint8)
+    picks = rng.choice(n, size=60, replace=False)
+    depth[picks] = rng.integers(3, 7, size=picks.size).astype(np.uint8)
+    g = esim.Graph(n, rp, col, alg3=1, alg3_rule=1, alg3_min_pairs=1e3, alg3_max_nodes=32, alg3_max_depth=6)
+    zs, qs = [], []
+    for workers in (1, 3, 6):
+        g.set_option("alg3_workers", workers)
+        zsum = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        g.alg3_zsum(_dev(torch, depth), C, zsum)
+        zs.append(zsum.cpu().numpy())
+        qs.append(g.query(5, C, 3e-3, 7))
+        assert g.stats()["alg3_nodes"] > 3
+    for z, q in zip(zs[1:], qs[1:]):
+        assert np.array_equal(z, zs[0]) and np.array_equal(q, qs[0])
+    g.close()
+
+
 @pytest.mark.parametrize("graph_name,kappa,eps", [
     ("er2000", 2000.0, 3e-3),
     ("cl3000", None, 3e-3),
