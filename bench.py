@@ -70,6 +70,11 @@ INSTR_PER_PAIR_STEP = 48.0
 # DRAM bytes of one sampler launch of the bench query, one-pass ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum; the graph once, it stays in L2)
 SAMPLER_TRAFFIC = 6.09e6
+# Algorithm 3 options of the timed configuration beyond the cost-model rule and depth 8:
+# the 128 heaviest nodes are candidates, the side sampler takes 5 blocks per SM during
+# the planning (chosen by timing the ten sources on GB300; the library defaults are 64
+# and 4)
+ALG3_OPTIONS = dict(alg3_max_nodes=128, alg3_overlap=5)
 # Accuracy of the timed configuration as tests/test_gpu_exceed.py measured it on GB300: the same
 # options (eps 1e-6, kappa 4, FP64, Algorithm 3 cost-model rule, depth <= 8) on the directed
 # Chung-Lu graph of the same recipe at n = 2e4, m = 2e5 (where the Power Method gives S), 100
@@ -633,9 +638,11 @@ def config_of(args, w):
     return {"workload": args.workload, "graph": w["kind"], "n": w["n"], "m": w["m"],
             "gamma": w.get("gamma"), "c": w["c"], "eps": w["eps"], "sources": w["sources"], "queries_per_step": 1,
             "top_k": w["k"], "kappa": args.kappa, "alloc": "pi^2 (Lemma 4)",
-            "dhat": ("Algorithm 3, the library's cost-model rule (alg3_rule 1): exact Z_1..Z_d for the 64 heaviest "
-                     "nodes at a cost-chosen d <= 8, max(1, ceil(R_b pi^2 c^(2d))) tail walk pairs; the others "
-                     "Algorithm 2" if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
+            "dhat": (f"Algorithm 3, the library's cost-model rule (alg3_rule 1): exact Z_1..Z_d for the "
+                     f"{ALG3_OPTIONS['alg3_max_nodes']} heaviest nodes at a cost-chosen d <= 8, "
+                     "max(1, ceil(R_b pi^2 c^(2d))) tail walk pairs; the others Algorithm 2"
+                     if getattr(args, "alg3", 0) else "Algorithm 2 (walk pairs)"),
+            "alg3_options": ALG3_OPTIONS if getattr(args, "alg3", 0) else None,
             "accuracy": ACCURACY,
             "l2": "flushed (512 MB write) before each timed step", "parallelism": f"replicas x{args.gpus}"}
 
@@ -700,7 +707,8 @@ def main():
     n, rp, col = make_graph(w)
     srcs = sources_for(w, rp, world, rank)
     c, eps, k = w["c"], w["eps"], w["k"]
-    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3, alg3_rule=1, alg3_max_depth=8)
+    g = esim.Graph(n, rp, col, kappa=args.kappa, timing=1, alg3=args.alg3, alg3_rule=1, alg3_max_depth=8,
+                   **ALG3_OPTIONS)
     stream = torch.cuda.Stream(device=dev)  # shared by the library's launches and the CUDA events
     g.set_stream(stream)
     ids = torch.empty(k, dtype=torch.int32, device=dev)

@@ -792,7 +792,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     if ((e = cudaMemsetAsync(ws.Zfx, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
-    bool cleared = false;  // the probe buffers start (and each group ends) all zero
+    int cleared = 0;  // probe blocks made zero so far (each group leaves its blocks zero)
     std::vector<double> cpow((size_t)depth + 1, 1.0);
     for (int j = 1; j <= depth; ++j) cpow[(size_t)j] = cpow[(size_t)j - 1] * c;
     const unsigned long long thr = (unsigned long long)(g.m + g.n) / (unsigned long long)std::max(1, g.alg3_push_div);
@@ -843,14 +843,15 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         const uint64_t nprobe = last ? (uint64_t)nbig : nsup;
         const int32_t* probe_ids = last ? ws.big_ids : ws.ids;
         const uint64_t per_group = (uint64_t)kProbeW * (uint64_t)ws.group;
-        if (nprobe > 0 && !cleared) {
-            const size_t gz = (size_t)ws.group;
-            if ((e = cudaMemsetAsync(ws.G.X[0], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-                (e = cudaMemsetAsync(ws.G.X[1], 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-                (e = cudaMemsetAsync(ws.G.Hn, 0, 8 * ws.G.nx * gz, g.stream)) != cudaSuccess ||
-                (e = cudaMemsetAsync(ws.G.mark, 0, 4 * n * gz, g.stream)) != cudaSuccess)
+        const int need_blocks = (int)std::min<uint64_t>((uint64_t)ws.group, (nprobe + kProbeW - 1) / kProbeW);
+        if (need_blocks > cleared) {  // blocks [cleared, need_blocks) of each buffer
+            const size_t b0 = (size_t)cleared, nbk = (size_t)(need_blocks - cleared);
+            if ((e = cudaMemsetAsync(ws.G.X[0] + b0 * ws.G.nx, 0, 8 * ws.G.nx * nbk, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.X[1] + b0 * ws.G.nx, 0, 8 * ws.G.nx * nbk, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.Hn + b0 * ws.G.nx, 0, 8 * ws.G.nx * nbk, g.stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(ws.G.mark + b0 * n, 0, 4 * n * nbk, g.stream)) != cudaSuccess)
                 return e;
-            cleared = true;
+            cleared = need_blocks;
         }
         for (uint64_t g0 = 0; g0 < nprobe; g0 += per_group) {
             const int cnt = (int)std::min<uint64_t>(per_group, nprobe - g0);

@@ -4,7 +4,7 @@ The timed workload (directed Chung-Lu n = 1e5, m = 1e6, gamma 2.1, eps = 1e-6) i
 of the Power Method's reach (S would take 80 GB), so this test takes the same recipe
 at n = 2e4, m = 2e5 (S: 3.2 GB, by the oracle's C Power Method to c^45 = 1e-10), and
 runs the benchmark's exact options: eps = 1e-6, kappa = 4, FP64, Algorithm 3 with the
-library's cost-model rule (alg3_rule 1, depth <= 8).  100 seeded queries cycle over five
+library's cost-model rule (alg3_rule 1, depth <= 8, 128 candidates).  100 seeded queries cycle over five
 seeded sources.  It asserts that no query's error exceeds eps, and prints the exceed
 rate and the error distribution (over all v, and over v != u) as one JSON line.
 
@@ -38,7 +38,8 @@ def test_exceed_rate_at_the_benchmark_settings():
     n, rp, col = synth.chung_lu(20_000, 200_000, gamma=2.1, seed=1)
     srcs = [int(x) for x in synth.random_sources(rp, 5, seed=7)]
     S = power.power_method_c(n, rp, col, C, iterations=power.power_iterations(C, 1e-10))
-    g = esim.Graph(n, rp, col, kappa=KAPPA, alg3=1, alg3_rule=1, alg3_max_depth=8)
+    g = esim.Graph(n, rp, col, kappa=KAPPA, alg3=1, alg3_rule=1, alg3_max_depth=8, alg3_max_nodes=128,
+                   alg3_overlap=5)
     errs, errs_off, pairs, nodes = [], [], [], []
     for seed in range(SEEDS):
         u = srcs[seed % len(srcs)]
