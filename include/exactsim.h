@@ -213,12 +213,12 @@ esim_status esim_set_stream(esim_graph* g, void* stream);
  *   "alg3_w_sweep", "alg3_w_probe", "alg3_w_launch", "alg3_w_last"  weights of the cost
  *                    model, in walk pair-steps: per entry of a single-vector sweep
  *                    (default 4), per entry and column of a 32-column probe sweep (0.2),
- *                    per kernel launch (2^19), and the last probe level's share of a dense
- *                    probe (1/16: one warp per node over its two-hop neighbourhood).  The
- *                    estimate of depth d is R_d (d + 1/(1-c)) walks plus
- *                    w_sweep (m+n)(2d-1) + w_probe (m+n) (sum_{i<=d-3} |supp h_i|(d-i) +
- *                    w_last 2 |supp h_{d-2}|) + w_launch (3(2d-1) +
- *                    sum_{i<=d-3} ceil(|supp h_i|/32)(3(d-i)+2) + 2 [d >= 3])
+ *                    per kernel launch (2^19), and the last two probe levels' share of a
+ *                    dense probe (1/16: one warp per node over its two- and three-hop
+ *                    neighbourhood).  The estimate of depth d is R_d (d + 1/(1-c)) walks
+ *                    plus w_sweep (m+n)(2d-1) + w_probe (m+n) (sum_{i<=d-4} |supp h_i|(d-i)
+ *                    + w_last sum_{i=max(1,d-3)}^{d-2} (d-i)|supp h_i|) + w_launch (3(2d-1)
+ *                    + sum_{i<=d-4} ceil(|supp h_i|/32)(3(d-i)+2) + 2 per level i >= d-3)
  *   "batch_tile"     -1: batched sweeps pick their tile by timing (default);
  *                    0, 1, 2: force 32, 16 or 8 lanes per row (results do not change)
  *   "precision"      0: FP64 sweeps (default);
@@ -388,8 +388,8 @@ esim_status esim_reverse_f32(esim_graph* g, const float* hist, int32_t L, double
 esim_status esim_alg3_first_meeting(esim_graph* g, int64_t k, int32_t depth, double c, double* z_out);
 /* Algorithm 3's depth choice for one node, host arithmetic only (no device): the d in
  * 0..max_depth (<= 16) of least estimated work R_d (d + 1/(1-c)) + w_sweep (m+n)(2d-1) +
- * w_probe (m+n) (sum_{i=1}^{d-3} supp[i](d-i) + w_last 2 supp[d-2] [d >= 3]) +
- * w_launch launches(d), R_d = max(1, ceil(v c^(2d))), v = R_b pi(k)^2 (R_b pi(k) for the
+ * w_probe (m+n) (sum_{i=1}^{d-4} supp[i](d-i) + w_last sum_{i=max(1,d-3)}^{d-2}
+ * (d-i) supp[i]) + w_launch launches(d), R_d = max(1, ceil(v c^(2d))), v = R_b pi(k)^2 (R_b pi(k) for the
  * basic allocation), supp[i] = |supp (P^T)^i(k, .)| for i = 0..max(0, max_depth-2); the
  * first on ties (the options "alg3_w_*" give the weights).  Option "alg3_rule" = 1
  * decides every candidate with it.  Returns -1 on invalid arguments. */

@@ -557,6 +557,117 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
     }
 }
 
+// The level below the last (probes of length 3 from the support of h_{d-3}) needs of each
+// node q' its second step's row terms, c^2 Zv(q') h_2^{q'}(q)^2 subtracted from level d-1,
+// and its third step's column sum g_3(q') = sum_q h_3^{q'}(q)^2.  One warp per node:
+// the two-hop table (twohop.cuh) holds H_2 over the two-hop neighbourhood; its entries
+// give the row terms (one integer atomic each, 58 fraction bits as the dense epilogue);
+// then x_2 = floor(H_2 / din) is pushed one more step into a second table, keyed by the
+// three-hop nodes, whose squares give g_3.  These are the dense probe's integers (the
+// same truncating divisions and sums); a row term is rounded to fixed point on its own
+// rather than after the dense step's sum over 32 columns, a difference of at most 2^-59
+// per term.  A node whose two- or three-hop multiset is too large for the tables is
+// appended to (big_ids, big_pos) for the dense probes, before it emits anything.
+constexpr int kG3Warps = 3;
+constexpr int kG3Table1 = 1024;  // two-hop slots per warp (12 KB)
+constexpr int kG3Table2 = 2048;  // three-hop slots per warp (24 KB)
+constexpr size_t kG3Smem = (size_t)kG3Warps * ((kG3Table1 + kG3Table2) * (sizeof(int32_t) + sizeof(unsigned long long)));
+
+__global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t* __restrict__ count_dev,
+                                                                 const int32_t* __restrict__ ids,
+                                                                 const uint32_t* __restrict__ rp,
+                                                                 const int32_t* __restrict__ col,
+                                                                 const unsigned long long* __restrict__ magic,
+                                                                 const double* __restrict__ zv_src, double c2,
+                                                                 long long* __restrict__ zfx_next,
+                                                                 unsigned long long* __restrict__ colsum,
+                                                                 int32_t* __restrict__ big_ids,
+                                                                 int32_t* __restrict__ big_pos,
+                                                                 unsigned int* __restrict__ nbig) {
+    extern __shared__ __align__(16) unsigned char g3_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long* V1 = (unsigned long long*)g3_smem + (size_t)wid * (kG3Table1 + kG3Table2);
+    unsigned long long* V2 = V1 + kG3Table1;
+    int32_t* K1 = (int32_t*)((unsigned long long*)g3_smem + (size_t)kG3Warps * (kG3Table1 + kG3Table2)) +
+                  (size_t)wid * (kG3Table1 + kG3Table2);
+    int32_t* K2 = K1 + kG3Table1;
+    const int64_t count = (int64_t)*count_dev;
+    const int64_t nw = (int64_t)gridDim.x * kG3Warps;
+    for (int64_t i = (int64_t)blockIdx.x * kG3Warps + wid; i < count; i += nw) {
+        const int32_t q = ids[i];
+        double T;
+        uint32_t dk;
+        const unsigned long long sq2 = twohop_sq_sum<kG3Table1>(q, rp, col, K1, V1, T, dk);
+        bool big = sq2 == kTwoHopTooLarge;
+        // the three-hop multiset: sum of din over the two-hop keys
+        unsigned long long e2 = 0;
+        if (!big && dk) {
+            for (int s = lane; s < kG3Table1; s += 32)
+                if (K1[s] >= 0) e2 += rp[K1[s] + 1] - rp[K1[s]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            big = e2 > (unsigned long long)(kG3Table2 / 2);
+        }
+        if (big) {
+            if (lane == 0) {
+                const unsigned int slot = atomicAdd(nbig, 1u);
+                big_ids[slot] = q;
+                big_pos[slot] = (int32_t)i;
+                colsum[i] = 0ull;
+            }
+            continue;
+        }
+        if (dk == 0) {  // no walk leaves q: no terms
+            if (lane == 0) colsum[i] = 0ull;
+            continue;
+        }
+        // row terms of the second step
+        const double coef = c2 * zv_src[q];
+        for (int s = lane; s < kG3Table1; s += 32) {
+            if (K1[s] < 0) continue;
+            const double h = (double)V1[s] * kInvOne;
+            const double t = coef * (h * h);
+            if (t != 0.0) atomicAdd((unsigned long long*)(zfx_next + K1[s]), (unsigned long long)(-__double2ll_rn(t * kZOne)));
+        }
+        // third step: H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a))
+        for (int s = lane; s < kG3Table2; s += 32) {
+            K2[s] = -1;
+            V2[s] = 0ull;
+        }
+        __syncwarp();
+        for (int s0 = 0; s0 < kG3Table1; s0 += 32) {
+            const int32_t a_mine = K1[s0 + lane];
+            unsigned live = __ballot_sync(0xffffffffu, a_mine >= 0 && V1[s0 + lane] != 0ull);
+            while (live) {
+                const int src = __ffs(live) - 1;
+                live &= live - 1;
+                const int32_t a = __shfl_sync(0xffffffffu, a_mine, src);
+                const uint32_t b2 = rp[a], e2r = rp[a + 1];
+                if (b2 == e2r) continue;
+                const unsigned long long x = div_by_magic(V1[s0 + src], e2r - b2, magic[a]);
+                if (!x) continue;
+                for (uint32_t p = b2 + lane; p < e2r; p += 32) {
+                    const int32_t r = col[p];
+                    uint32_t slot = ((uint32_t)r * 2654435761u) & (kG3Table2 - 1);
+                    for (;;) {  // at most half the slots are taken: a free or matching slot exists
+                        const int32_t prev = atomicCAS(&K2[slot], -1, r);
+                        if (prev == -1 || prev == r) break;
+                        slot = (slot + 1) & (kG3Table2 - 1);
+                    }
+                    atomicAdd(&V2[slot], x);
+                }
+            }
+        }
+        __syncwarp();
+        unsigned long long sq3 = 0;
+        for (int s = lane; s < kG3Table2; s += 32) sq3 += twohop_sq(V2[s]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq3 += __shfl_xor_sync(0xffffffffu, sq3, o);
+        if (lane == 0) colsum[i] = sq3;
+        __syncwarp();  // the tables are free for the warp's next node
+    }
+}
+
 // *zlast += sum_i (cl Zv(ids[i])) (colsum[i] 2^-63), i < count, in a fixed order: thread t
 // takes i = t, t + 1024, ... and a fixed tree adds the threads' partials.
 __global__ void __launch_bounds__(1024) probe_g2_total_kernel(const uint64_t* __restrict__ count_dev,
@@ -823,11 +934,22 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count += 5;
         const int steps = depth - j;
-        const bool last = steps == 2;  // these probes feed only Z_depth's total: g_2 per node
-        if (last) {
+        // the last two probe levels run one warp per node where its neighbourhood fits the
+        // tables: g_2 for the last, the row terms and g_3 for the one below it
+        const bool hashed = steps == 2 || steps == 3;
+        if (hashed) {
             if ((e = cudaMemsetAsync(ws.nbig, 0, sizeof(unsigned int), g.stream)) != cudaSuccess) return e;
-            probe_g2_kernel<<<(unsigned)(g.sm_count * 4), kG2Warps * 32, 0, g.stream>>>(
-                ws.off + n, ws.ids, g.in.rp, g.in.col, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+            if (steps == 2) {
+                probe_g2_kernel<<<(unsigned)(g.sm_count * 4), kG2Warps * 32, 0, g.stream>>>(
+                    ws.off + n, ws.ids, g.in.rp, g.in.col, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+            } else {
+                if ((e = cudaFuncSetAttribute(probe_g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kG3Smem)) != cudaSuccess)
+                    return e;
+                probe_g3_kernel<<<(unsigned)(g.sm_count * 2), kG3Warps * 32, kG3Smem, g.stream>>>(
+                    ws.off + n, ws.ids, g.in.rp, g.in.col, g.din_magic, zv, cpow[2], ws.Zfx + (size_t)(j + 2) * n,
+                    ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
         }
@@ -835,13 +957,13 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         unsigned int nbig = 0;
         if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
             return e;
-        if (last && (e = cudaMemcpyAsync(&nbig, ws.nbig, sizeof(unsigned int), cudaMemcpyDeviceToHost, g.stream)) !=
-                        cudaSuccess)
+        if (hashed && (e = cudaMemcpyAsync(&nbig, ws.nbig, sizeof(unsigned int), cudaMemcpyDeviceToHost, g.stream)) !=
+                          cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
-        // dense probes: every support node of a level below the last, the large ones of the last
-        const uint64_t nprobe = last ? (uint64_t)nbig : nsup;
-        const int32_t* probe_ids = last ? ws.big_ids : ws.ids;
+        // dense probes: every support node of the deeper levels, the large ones of the last two
+        const uint64_t nprobe = hashed ? (uint64_t)nbig : nsup;
+        const int32_t* probe_ids = hashed ? ws.big_ids : ws.ids;
         const uint64_t per_group = (uint64_t)kProbeW * (uint64_t)ws.group;
         const int need_blocks = (int)std::min<uint64_t>((uint64_t)ws.group, (nprobe + kProbeW - 1) / kProbeW);
         if (need_blocks > cleared) {  // blocks [cleared, need_blocks) of each buffer
@@ -875,13 +997,14 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                 if ((e = probe_step(g, ws, a, nb, &count)) != cudaSuccess) return e;
             }
             probe_end_kernel<<<dim3((unsigned)g.sm_count, (unsigned)nb), kBlock, 0, g.stream>>>(
-                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63, last ? ws.big_pos + g0 : nullptr,
-                last ? ws.g2 : nullptr);
+                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63, hashed ? ws.big_pos + g0 : nullptr,
+                hashed ? ws.g2 : nullptr);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
         }
-        if (last && nsup > 0) {
-            probe_g2_total_kernel<<<1, 1024, 0, g.stream>>>(ws.off + n, ws.ids, zv, cpow[2], ws.g2, ws.sums + 63);
+        if (hashed && nsup > 0) {
+            probe_g2_total_kernel<<<1, 1024, 0, g.stream>>>(ws.off + n, ws.ids, zv, cpow[(size_t)steps], ws.g2,
+                                                            ws.sums + 63);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
         }

@@ -399,11 +399,11 @@ esim_status ensure_a3ws(Graph& g) {
 // estimate of the GPU work, in walk pair-steps of the sampler:
 //   walks      R_d (d + 1/(1-c)),  R_d = max(1, ceil(v c^(2d)))  (v = R_b pi(k)^2)
 //   Lemma 5    2d-1 single-vector sweeps of m+n entries (h_1..h_d and the P~ sweeps);
-//              sum_{i=1}^{d-3} |supp h_i| (d-i) probe column-sweeps for the levels below
-//              the last; the last probe level (i = d-2, two steps, only its column sums)
-//              runs one warp per node over its two-hop neighbourhood and dense probes
-//              only for the nodes too large for that, charged as w_last 2 |supp h_{d-2}|
-//              column-sweeps; and the launches;
+//              sum_{i=1}^{d-4} |supp h_i| (d-i) probe column-sweeps for the deeper probe
+//              levels; the last two probe levels (i = d-2 and d-3, two and three steps)
+//              run one warp per node over its two- and three-hop neighbourhood and dense
+//              probes only for the nodes too large for that, charged as
+//              w_last (d-i) |supp h_i| column-sweeps; and the launches;
 // d = 0 is Algorithm 2 alone.  The weights (options alg3_w_sweep, alg3_w_probe,
 // alg3_w_launch, alg3_w_last: pair-steps per entry of a single sweep, per entry and
 // column of a probe sweep, per launch, and the last level's share of a dense probe) are
@@ -416,13 +416,13 @@ double alg3_cost(int d, double v, double c, const uint64_t* supp, int64_t n, int
     if (d > 0) {
         const double edges = (double)(m + n);
         uint64_t probe = 0, launches = 3 * (uint64_t)(2 * d - 1);
-        for (int i = 1; i <= d - 3; ++i) {
+        for (int i = 1; i <= d - 4; ++i) {
             probe += supp[i] * (uint64_t)(d - i);
             launches += (supp[i] + 31) / 32 * (uint64_t)(3 * (d - i) + 2);
         }
         double last = 0.0;
-        if (d >= 3) {
-            last = w_last * (2.0 * (double)supp[d - 2]);
+        for (int i = std::max(1, d - 3); i <= d - 2; ++i) {
+            last += w_last * ((double)(d - i) * (double)supp[i]);
             launches += 2;
         }
         cost += w_sweep * edges * (double)(2 * d - 1);

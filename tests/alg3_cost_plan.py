@@ -8,9 +8,9 @@ library's own host function ``esim_alg3_depth`` bit for bit.
 
 cost(d) of node k, in sampler pair-steps: R_d (d + 1/(1-c)) walk work, R_d =
 max(1, ceil(v c^(2d))), v = R_b pi(k)^2 (R_b pi(k) for the basic allocation), plus for
-d > 0 w_sweep (m+n)(2d-1) + w_probe (m+n) (sum_{i=1}^{d-3} |supp h_i|(d-i) +
-w_last 2 |supp h_{d-2}| [d >= 3]) + w_launch (3(2d-1) + sum_{i=1}^{d-3}
-ceil(|supp h_i|/32)(3(d-i)+2) + 2 [d >= 3]), h_i = (P^T)^i(k, .).
+d > 0 w_sweep (m+n)(2d-1) + w_probe (m+n) (sum_{i=1}^{d-4} |supp h_i|(d-i) +
+w_last sum_{i=max(1,d-3)}^{d-2} (d-i)|supp h_i|) + w_launch (3(2d-1) + sum_{i=1}^{d-4}
+ceil(|supp h_i|/32)(3(d-i)+2) + 2 per level i in max(1,d-3)..d-2), h_i = (P^T)^i(k, .).
 """
 from __future__ import annotations
 
@@ -33,12 +33,12 @@ def cost(d: int, v: float, c: float, supp, n: int, m: int, w_sweep: float = 4.0,
         edges = float(m + n)
         probe = 0
         launches = 3 * (2 * d - 1)
-        for i in range(1, d - 2):
+        for i in range(1, d - 3):
             probe += int(supp[i]) * (d - i)
             launches += (int(supp[i]) + 31) // 32 * (3 * (d - i) + 2)
         last = 0.0
-        if d >= 3:
-            last = w_last * (2.0 * float(supp[d - 2]))
+        for i in range(max(1, d - 3), d - 1):
+            last += w_last * (float(d - i) * float(supp[i]))
             launches += 2
         total += w_sweep * edges * float(2 * d - 1)
         total += w_probe * edges * (float(probe) + last)

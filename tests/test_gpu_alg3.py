@@ -102,6 +102,31 @@ def test_first_meeting_covers_both_last_level_forms(graph):
         assert np.max(np.abs(z - np.array(ref))) <= TOL, (d, z, ref)
 
 
+def test_first_meeting_hashed_levels_on_a_hub(esim):
+    """The last two probe levels run one warp per node where the neighbourhood fits the
+    tables (two-hop multiset <= 512 for both; three-hop multiset <= 1024 for the level
+    below the last), dense probes for the others.  At the hub of a Chung-Lu graph both
+    forms occur at both levels; Z_1..Z_d at depths 3..6 match the oracle's Lemma 5."""
+    n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
+    din = np.diff(rp).astype(np.int64)
+    k = int(np.argmax(din))
+
+    def multisets(q):
+        s1 = col[rp[q]:rp[q + 1]]
+        s2 = np.unique(np.concatenate([col[rp[a]:rp[a + 1]] for a in s1])) if len(s1) else s1
+        return int(din[s1].sum()), int(din[s2].sum())
+
+    sizes = np.array([multisets(int(q)) for q in col[rp[k]:rp[k + 1]]])  # the support of h_1
+    fits = (sizes[:, 0] <= 512) & (sizes[:, 1] <= 1024)
+    assert np.count_nonzero(fits) > 0 and np.count_nonzero(~fits) > 0
+    g = esim.Graph(n, rp, col)
+    ref = a3.first_meeting_lemma5(n, rp, col, k, C, 6)
+    for d in (3, 4, 5, 6):
+        z = g.alg3_first_meeting(k, d, C)
+        assert np.max(np.abs(z - np.array(ref[:d]))) <= TOL, (d, z, ref)
+    g.close()
+
+
 def test_depth_sampler_bit_exact(torch_cuda, graph, oracle_walks):
     torch = torch_cuda
     name, (n, rp, col), g = graph
