@@ -237,12 +237,13 @@ __device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigne
     }
     if (a.mode == 2) return twohop_sq(H);  // floor(H^2 / 2^63)
     if (a.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
+        // each column's term is rounded to fixed point on its own and the integers are
+        // added, so the result does not depend on which columns share a block
         const double h = (double)H * kInvOne;
-        double t = coef[lane] * (h * h);
+        long long t = __double2ll_rn(coef[lane] * (h * h) * kZOne);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0 && t != 0.0)
-            atomicAdd((unsigned long long*)(a.zfx + row), (unsigned long long)(-__double2ll_rn(t * kZOne)));
+        if (lane == 0 && t != 0) atomicAdd((unsigned long long*)(a.zfx + row), (unsigned long long)(-t));
     }
     return 0ull;
 }
@@ -564,10 +565,10 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
 // give the row terms (one integer atomic each, 58 fraction bits as the dense epilogue);
 // then x_2 = floor(H_2 / din) is pushed one more step into a second table, keyed by the
 // three-hop nodes, whose squares give g_3.  These are the dense probe's integers (the
-// same truncating divisions and sums); a row term is rounded to fixed point on its own
-// rather than after the dense step's sum over 32 columns, a difference of at most 2^-59
-// per term.  A node whose two- or three-hop multiset is too large for the tables is
-// appended to (big_ids, big_pos) for the dense probes, before it emits anything.
+// same truncating divisions and sums, each row term rounded to fixed point on its own),
+// so a node gives the same terms on either path.  A node whose two- or three-hop
+// multiset is too large for the tables is appended to (big_ids, big_pos) for the dense
+// probes, before it emits anything.
 constexpr int kG3Warps = 3;
 constexpr int kG3Table1 = 1024;  // two-hop slots per warp (12 KB)
 constexpr int kG3Table2 = 2048;  // three-hop slots per warp (24 KB)
@@ -626,8 +627,8 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
         for (int s = lane; s < kG3Table1; s += 32) {
             if (K1[s] < 0) continue;
             const double h = (double)V1[s] * kInvOne;
-            const double t = coef * (h * h);
-            if (t != 0.0) atomicAdd((unsigned long long*)(zfx_next + K1[s]), (unsigned long long)(-__double2ll_rn(t * kZOne)));
+            const long long t = __double2ll_rn(coef * (h * h) * kZOne);
+            if (t != 0) atomicAdd((unsigned long long*)(zfx_next + K1[s]), (unsigned long long)(-t));
         }
         // third step: H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a))
         for (int s = lane; s < kG3Table2; s += 32) {
