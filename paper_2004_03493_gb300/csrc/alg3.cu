@@ -119,20 +119,31 @@ __global__ void sq_scale_kernel(int64_t n, const double* __restrict__ v, const d
     }
 }
 
-// Probe terms of the levels below d are summed in signed fixed point with 58 fraction
-// bits (integer atomics: exact, order-free); a row's term is at most 32 in magnitude
-// and a level's total at most 1.
+// Probe terms of the levels below d are summed in signed two-word fixed point (integer
+// atomics: exact, order-free): each term t is split into the nearest multiple of 2^-58
+// (the hi word) and the remainder in units of 2^-98 (the lo word), so that no term is
+// lost however small it is and the result does not depend on the order of the terms.
+// A row's total over all columns is at most c^2 < 1 in magnitude, so the hi words do not
+// overflow; a lo term is at most 2^39 in magnitude.
 constexpr double kZOne = 288230376151711744.0;  // 2^58
+constexpr double kZLo = 1099511627776.0;        // 2^40: lo units per hi unit
+
+// t = (hi + lo 2^-40) 2^-58 to within 2^-99, for |t| < 1
+__device__ __forceinline__ void zacc_split(double t, long long& hi, long long& lo) {
+    const double s = t * kZOne;            // exact: a power-of-two scale
+    hi = __double2ll_rn(s);
+    lo = __double2ll_rn((s - (double)hi) * kZLo);  // s - hi is exact (|s - hi| <= 1/2)
+}
 
 // Zv_j = c^j h_j^2 - c T + (probe terms), T = P~ Zv_{j-1} (T = NULL at j = 1)
 __global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double* __restrict__ h,
-                                   const double* __restrict__ T, const long long* __restrict__ zfx,
-                                   double* __restrict__ zv) {
+                                   const double* __restrict__ T, const long long* __restrict__ zhi,
+                                   const long long* __restrict__ zlo, double* __restrict__ zv) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double hv = h[i];
         double z = cj * (hv * hv);
         if (T) z -= c * T[i];
-        zv[i] = z + (double)zfx[i] * (1.0 / kZOne);
+        zv[i] = z + ((double)zhi[i] * (1.0 / kZOne) + (double)zlo[i] * (1.0 / (kZOne * kZLo)));
     }
 }
 
@@ -222,7 +233,8 @@ struct ProbeStepArgs {
     int src;             // which X buffer holds x_s
     int mode;
     int last;            // no further step: x_{s+1} is not needed
-    long long* zfx;      // mode 1 target
+    long long* zfx;      // mode 1 target: hi words of the level
+    long long* zlo;      // and its lo words
     unsigned long long thr;
 };
 
@@ -240,10 +252,15 @@ __device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigne
         // each column's term is rounded to fixed point on its own and the integers are
         // added, so the result does not depend on which columns share a block
         const double h = (double)H * kInvOne;
-        long long t = __double2ll_rn(coef[lane] * (h * h) * kZOne);
+        long long hi, lo;
+        zacc_split(coef[lane] * (h * h), hi, lo);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0 && t != 0) atomicAdd((unsigned long long*)(a.zfx + row), (unsigned long long)(-t));
+        for (int o = 16; o > 0; o >>= 1) {
+            hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            lo += __shfl_xor_sync(0xffffffffu, lo, o);
+        }
+        if (lane == 0 && hi != 0) atomicAdd((unsigned long long*)(a.zfx + row), (unsigned long long)(-hi));
+        if (lane == 0 && lo != 0) atomicAdd((unsigned long long*)(a.zlo + row), (unsigned long long)(-lo));
     }
     return 0ull;
 }
@@ -562,7 +579,7 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
 // node q' its second step's row terms, c^2 Zv(q') h_2^{q'}(q)^2 subtracted from level d-1,
 // and its third step's column sum g_3(q') = sum_q h_3^{q'}(q)^2.  One warp per node:
 // the two-hop table (twohop.cuh) holds H_2 over the two-hop neighbourhood; its entries
-// give the row terms (one integer atomic each, 58 fraction bits as the dense epilogue);
+// give the row terms (two-word fixed point, as the dense epilogue);
 // then x_2 = floor(H_2 / din) is pushed one more step into a second table, keyed by the
 // three-hop nodes, whose squares give g_3.  These are the dense probe's integers (the
 // same truncating divisions and sums, each row term rounded to fixed point on its own),
@@ -580,7 +597,8 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
                                                                  const int32_t* __restrict__ col,
                                                                  const unsigned long long* __restrict__ magic,
                                                                  const double* __restrict__ zv_src, double c2,
-                                                                 long long* __restrict__ zfx_next,
+                                                                 long long* __restrict__ zhi_next,
+                                                                 long long* __restrict__ zlo_next,
                                                                  unsigned long long* __restrict__ colsum,
                                                                  int32_t* __restrict__ big_ids,
                                                                  int32_t* __restrict__ big_pos,
@@ -627,8 +645,10 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
         for (int s = lane; s < kG3Table1; s += 32) {
             if (K1[s] < 0) continue;
             const double h = (double)V1[s] * kInvOne;
-            const long long t = __double2ll_rn(coef * (h * h) * kZOne);
-            if (t != 0) atomicAdd((unsigned long long*)(zfx_next + K1[s]), (unsigned long long)(-t));
+            long long hi, lo;
+            zacc_split(coef * (h * h), hi, lo);
+            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + K1[s]), (unsigned long long)(-hi));
+            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + K1[s]), (unsigned long long)(-lo));
         }
         // third step: H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a))
         for (int s = lane; s < kG3Table2; s += 32) {
@@ -735,7 +755,7 @@ int group_size(int64_t n, int64_t m, int64_t nseg) {
 struct A3Ws {
     double* H;        // (D+1) n: h_0 .. h_D from k
     double* Zv;       // (D+1) n: Zv_1 .. Zv_D at rows 1..D (row 0 unused)
-    long long* Zfx;   // (D+1) n: fixed-point probe terms per level
+    long long* Zfx;   // 2 (D+1) n: fixed-point probe terms per level, hi words then lo words
     double* T;        // n: P~ Zv_{j-1}
     double* x;        // n: sweep input
     double* xa;       // n
@@ -768,7 +788,7 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     A3Ws w{};
     w.H = (double*)take(8 * (D + 1) * n);
     w.Zv = (double*)take(8 * (D + 1) * n);
-    w.Zfx = (long long*)take(8 * (D + 1) * n);
+    w.Zfx = (long long*)take(8 * 2 * (D + 1) * n);
     w.T = (double*)take(8 * n);
     w.x = (double*)take(8 * n);
     w.xa = (double*)take(8 * n);
@@ -901,7 +921,9 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     cudaError_t e = launch_walk_distributions(g, k, depth, ws.H, ws.xa, ws.xb);
     if (e != cudaSuccess) return e;
     count += 1 + depth * per_sweep;
-    if ((e = cudaMemsetAsync(ws.Zfx, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess)
+    long long* const zlo_base = ws.Zfx + (size_t)(kAlg3MaxDepth + 1) * n;
+    if ((e = cudaMemsetAsync(ws.Zfx, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(zlo_base, 0, sizeof(long long) * n * (size_t)(depth + 1), g.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(ws.sums, 0, sizeof(double) * 64, g.stream)) != cudaSuccess) return e;
     int cleared = 0;  // probe blocks made zero so far (each group leaves its blocks zero)
@@ -919,7 +941,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             T = ws.T;
         }
         zv_finalize_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, cpow[(size_t)j], c, ws.H + (size_t)j * n, T,
-                                                        ws.Zfx + (size_t)j * n, zv);
+                                                        ws.Zfx + (size_t)j * n, zlo_base + (size_t)j * n, zv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++count;
         if ((e = dsum(g, zv, 2, ws, ws.sums + j, &count)) != cudaSuccess) return e;
@@ -949,7 +971,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                     return e;
                 probe_g3_kernel<<<(unsigned)(g.sm_count * 2), kG3Warps * 32, kG3Smem, g.stream>>>(
                     ws.off + n, ws.ids, g.in.rp, g.in.col, g.din_magic, zv, cpow[2], ws.Zfx + (size_t)(j + 2) * n,
-                    ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+                    zlo_base + (size_t)(j + 2) * n, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
@@ -985,7 +1007,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
             ++count;
             for (int lp = 1; lp <= steps; ++lp) {
                 ProbeStepArgs a{g.in.rp, g.in.col, g.din_magic, lp - 1, (lp - 1) & 1, 0, lp == steps ? 1 : 0,
-                                ws.Zfx + (size_t)(j + lp) * n, thr};
+                                ws.Zfx + (size_t)(j + lp) * n, zlo_base + (size_t)(j + lp) * n, thr};
                 if (lp == steps) {
                     a.mode = 2;
                 } else if (lp >= 2) {
