@@ -80,7 +80,7 @@ ALG3_OPTIONS = dict(alg3_max_nodes=128, alg3_overlap=5)
 # Chung-Lu graph of the same recipe at n = 2e4, m = 2e5 (where the Power Method gives S), 100
 # seeds over five sources
 ACCURACY = {"measured_by": "tests/test_gpu_exceed.py", "graph": "chung_lu n=20000 m=200000 gamma=2.1",
-            "seeds": 100, "exceed_rate": 0.0, "max_err": 2.10e-7, "p50_err": 4.41e-8, "p99_err": 2.07e-7,
+            "seeds": 100, "exceed_rate": 0.0, "max_err": 2.09e-7, "p50_err": 4.34e-8, "p99_err": 2.07e-7,
             "eps": 1e-6}
 L2_FLUSH_BYTES = 512 << 20
 
