@@ -689,6 +689,183 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
     }
 }
 
+// Second tier of the last two probe levels: the nodes too large for a warp's tables get
+// a whole block (8 warps) and tables in most of its shared memory; warps take the outer
+// entries, lanes the inner ones, and the inserts and additions are the same integer
+// atomics, so a node gives the same integers on any tier.  Nodes still too large go on
+// to the dense probes.
+constexpr int kCtaThreads = 256;
+constexpr int kCta2Table = 16384;                   // last level: two-hop multiset <= 8192
+constexpr int kCta3Table1 = 4096, kCta3Table2 = 8192;  // level below: <= 2048 and <= 4096
+constexpr size_t kCta2Smem = (size_t)kCta2Table * (sizeof(int32_t) + sizeof(unsigned long long));
+constexpr size_t kCta3Smem = (size_t)(kCta3Table1 + kCta3Table2) * (sizeof(int32_t) + sizeof(unsigned long long));
+
+template <int kT>
+__device__ __forceinline__ void table_add(int32_t* K, unsigned long long* V, int32_t key, unsigned long long w) {
+    uint32_t slot = ((uint32_t)key * 2654435761u) & (kT - 1);
+    for (;;) {  // at most half the slots are taken: a free or matching slot exists
+        const int32_t prev = atomicCAS(&K[slot], -1, key);
+        if (prev == -1 || prev == key) break;
+        slot = (slot + 1) & (kT - 1);
+    }
+    atomicAdd(&V[slot], w);
+}
+
+// the block's total of v, in every thread
+__device__ __forceinline__ unsigned long long block_total(unsigned long long v, unsigned long long* red,
+                                                          unsigned long long* out) {
+    const unsigned long long r = block_sum(v, red);
+    if (threadIdx.x == 0) *out = r;
+    __syncthreads();
+    const unsigned long long t = *out;
+    __syncthreads();
+    return t;
+}
+
+// H_2 of node q over its two-hop neighbourhood into the block's table (all threads call
+// it; the table is cleared here).  Returns false, with the table untouched, when the
+// two-hop multiset exceeds half the slots.
+template <int kT>
+__device__ bool cta_two_hop(int32_t q, const uint32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t* K,
+                            unsigned long long* V, unsigned long long* red, unsigned long long* bc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kW = kCtaThreads / 32;
+    const uint32_t kb = rp[q], ke = rp[q + 1];
+    const uint32_t dk = ke - kb;
+    unsigned long long e1 = 0;
+    for (uint32_t p = kb + threadIdx.x; p < ke; p += kCtaThreads) e1 += rp[col[p] + 1] - rp[col[p]];
+    e1 = block_total(e1, red, bc);
+    if (dk == 0 || e1 > (unsigned long long)(kT / 2)) return false;
+    for (int s = threadIdx.x; s < kT; s += kCtaThreads) {
+        K[s] = -1;
+        V[s] = 0ull;
+    }
+    __syncthreads();
+    for (uint32_t p1 = kb + wid; p1 < ke; p1 += kW) {
+        const int32_t q1 = col[p1];
+        const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
+        if (b1 == e1r) continue;
+        const unsigned long long w = kTwoHopOne / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
+        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) table_add<kT>(K, V, col[p2], w);
+    }
+    __syncthreads();
+    return true;
+}
+
+// g_2 of the warp kernel's oversized nodes (list in_ids/in_pos, count *nin); the ones
+// still too large are appended to out_ids/out_pos.
+__global__ void __launch_bounds__(kCtaThreads) probe_g2_cta_kernel(const unsigned int* __restrict__ nin,
+                                                                   const int32_t* __restrict__ in_ids,
+                                                                   const int32_t* __restrict__ in_pos,
+                                                                   const uint32_t* __restrict__ rp,
+                                                                   const int32_t* __restrict__ col,
+                                                                   unsigned long long* __restrict__ colsum,
+                                                                   int32_t* __restrict__ out_ids,
+                                                                   int32_t* __restrict__ out_pos,
+                                                                   unsigned int* __restrict__ nout) {
+    extern __shared__ __align__(16) unsigned char cta_smem[];
+    unsigned long long* V = (unsigned long long*)cta_smem;
+    int32_t* K = (int32_t*)(V + kCta2Table);
+    __shared__ unsigned long long red[kCtaThreads / 32];
+    __shared__ unsigned long long bc;
+    const unsigned int count = *nin;
+    for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int32_t q = in_ids[i];
+        if (!cta_two_hop<kCta2Table>(q, rp, col, K, V, red, &bc)) {
+            if (threadIdx.x == 0) {
+                const unsigned int slot = atomicAdd(nout, 1u);
+                out_ids[slot] = q;
+                out_pos[slot] = in_pos[i];
+            }
+            continue;
+        }
+        unsigned long long sq = 0;
+        for (int s = threadIdx.x; s < kCta2Table; s += kCtaThreads) sq += twohop_sq(V[s]);
+        sq = block_sum(sq, red);
+        if (threadIdx.x == 0) colsum[in_pos[i]] = sq;
+        __syncthreads();  // the table is free for the block's next node
+    }
+}
+
+// the row terms and g_3 of the g_3 warp kernel's oversized nodes (as probe_g3_kernel)
+__global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigned int* __restrict__ nin,
+                                                                   const int32_t* __restrict__ in_ids,
+                                                                   const int32_t* __restrict__ in_pos,
+                                                                   const uint32_t* __restrict__ rp,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const unsigned long long* __restrict__ magic,
+                                                                   const double* __restrict__ zv_src, double c2,
+                                                                   long long* __restrict__ zhi_next,
+                                                                   long long* __restrict__ zlo_next,
+                                                                   unsigned long long* __restrict__ colsum,
+                                                                   int32_t* __restrict__ out_ids,
+                                                                   int32_t* __restrict__ out_pos,
+                                                                   unsigned int* __restrict__ nout) {
+    extern __shared__ __align__(16) unsigned char cta_smem[];
+    unsigned long long* V1 = (unsigned long long*)cta_smem;
+    unsigned long long* V2 = V1 + kCta3Table1;
+    int32_t* K1 = (int32_t*)(V2 + kCta3Table2);
+    int32_t* K2 = K1 + kCta3Table1;
+    __shared__ unsigned long long red[kCtaThreads / 32];
+    __shared__ unsigned long long bc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kW = kCtaThreads / 32;
+    const unsigned int count = *nin;
+    for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int32_t q = in_ids[i];
+        bool fits = cta_two_hop<kCta3Table1>(q, rp, col, K1, V1, red, &bc);
+        if (fits) {
+            unsigned long long e2 = 0;
+            for (int s = threadIdx.x; s < kCta3Table1; s += kCtaThreads)
+                if (K1[s] >= 0) e2 += rp[K1[s] + 1] - rp[K1[s]];
+            e2 = block_total(e2, red, &bc);
+            fits = e2 <= (unsigned long long)(kCta3Table2 / 2);
+        }
+        if (!fits) {
+            if (threadIdx.x == 0) {
+                const unsigned int slot = atomicAdd(nout, 1u);
+                out_ids[slot] = q;
+                out_pos[slot] = in_pos[i];
+            }
+            continue;
+        }
+        const double coef = c2 * zv_src[q];
+        for (int s = threadIdx.x; s < kCta3Table1; s += kCtaThreads) {
+            if (K1[s] < 0) continue;
+            const double h = (double)V1[s] * kInvOne;
+            long long hi, lo;
+            zacc_split(coef * (h * h), hi, lo);
+            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + K1[s]), (unsigned long long)(-hi));
+            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + K1[s]), (unsigned long long)(-lo));
+        }
+        for (int s = threadIdx.x; s < kCta3Table2; s += kCtaThreads) {
+            K2[s] = -1;
+            V2[s] = 0ull;
+        }
+        __syncthreads();
+        for (int s0 = wid * 32; s0 < kCta3Table1; s0 += kW * 32) {
+            const int32_t a_mine = K1[s0 + lane];
+            unsigned live = __ballot_sync(0xffffffffu, a_mine >= 0 && V1[s0 + lane] != 0ull);
+            while (live) {
+                const int src = __ffs(live) - 1;
+                live &= live - 1;
+                const int32_t a = __shfl_sync(0xffffffffu, a_mine, src);
+                const uint32_t b2 = rp[a], e2r = rp[a + 1];
+                if (b2 == e2r) continue;
+                const unsigned long long x = div_by_magic(V1[s0 + src], e2r - b2, magic[a]);
+                if (!x) continue;
+                for (uint32_t p = b2 + lane; p < e2r; p += 32) table_add<kCta3Table2>(K2, V2, col[p], x);
+            }
+        }
+        __syncthreads();
+        unsigned long long sq = 0;
+        for (int s = threadIdx.x; s < kCta3Table2; s += kCtaThreads) sq += twohop_sq(V2[s]);
+        sq = block_sum(sq, red);
+        if (threadIdx.x == 0) colsum[in_pos[i]] = sq;
+        __syncthreads();  // the tables are free for the block's next node
+    }
+}
+
 // *zlast += sum_i (cl Zv(ids[i])) (colsum[i] 2^-63), i < count, in a fixed order: thread t
 // takes i = t, t + 1024, ... and a fixed tree adds the threads' partials.
 __global__ void __launch_bounds__(1024) probe_g2_total_kernel(const uint64_t* __restrict__ count_dev,
@@ -771,7 +948,9 @@ struct A3Ws {
     unsigned long long* g2;  // n: column sums g_2 of the last probe level, by support position
     int32_t* big_ids;        // n: support nodes too large for the two-hop table
     int32_t* big_pos;        // n: their support positions
-    unsigned int* nbig;      // 1
+    unsigned int* nbig;      // 2: the warp tier's overflow count, then the block tier's
+    int32_t* big2_ids;       // n: nodes too large for the block tier too (dense probes)
+    int32_t* big2_pos;       // n
     ProbeGroup G;
     int group;        // probe blocks per launch
 };
@@ -805,6 +984,8 @@ size_t a3_layout(int64_t n_, int64_t m_, int64_t nseg, void* base, A3Ws* out) {
     w.big_ids = (int32_t*)take(4 * n);
     w.big_pos = (int32_t*)take(4 * n);
     w.nbig = (unsigned int*)take(256);
+    w.big2_ids = (int32_t*)take(4 * n);
+    w.big2_pos = (int32_t*)take(4 * n);
     const int G = group_size(n_, m_, nseg);
     const size_t gz = (size_t)G;
     w.group = G;
@@ -961,7 +1142,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         // tables: g_2 for the last, the row terms and g_3 for the one below it
         const bool hashed = steps == 2 || steps == 3;
         if (hashed) {
-            if ((e = cudaMemsetAsync(ws.nbig, 0, sizeof(unsigned int), g.stream)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(ws.nbig, 0, 2 * sizeof(unsigned int), g.stream)) != cudaSuccess) return e;
             if (steps == 2) {
                 probe_g2_kernel<<<(unsigned)(g.sm_count * 4), kG2Warps * 32, 0, g.stream>>>(
                     ws.off + n, ws.ids, g.in.rp, g.in.col, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
@@ -974,19 +1155,36 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                     zlo_base + (size_t)(j + 2) * n, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            ++count;
+            // the block tier takes the warp tier's overflow
+            if (steps == 2) {
+                if ((e = cudaFuncSetAttribute(probe_g2_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCta2Smem)) != cudaSuccess)
+                    return e;
+                probe_g2_cta_kernel<<<(unsigned)g.sm_count, kCtaThreads, kCta2Smem, g.stream>>>(
+                    ws.nbig, ws.big_ids, ws.big_pos, g.in.rp, g.in.col, ws.g2, ws.big2_ids, ws.big2_pos, ws.nbig + 1);
+            } else {
+                if ((e = cudaFuncSetAttribute(probe_g3_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCta3Smem)) != cudaSuccess)
+                    return e;
+                probe_g3_cta_kernel<<<(unsigned)g.sm_count, kCtaThreads, kCta3Smem, g.stream>>>(
+                    ws.nbig, ws.big_ids, ws.big_pos, g.in.rp, g.in.col, g.din_magic, zv, cpow[2],
+                    ws.Zfx + (size_t)(j + 2) * n, zlo_base + (size_t)(j + 2) * n, ws.g2, ws.big2_ids, ws.big2_pos,
+                    ws.nbig + 1);
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            count += 2;
         }
         uint64_t nsup = 0;
         unsigned int nbig = 0;
         if ((e = cudaMemcpyAsync(&nsup, ws.off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, g.stream)) != cudaSuccess)
             return e;
-        if (hashed && (e = cudaMemcpyAsync(&nbig, ws.nbig, sizeof(unsigned int), cudaMemcpyDeviceToHost, g.stream)) !=
-                          cudaSuccess)
+        if (hashed && (e = cudaMemcpyAsync(&nbig, ws.nbig + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                           g.stream)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess) return e;
         // dense probes: every support node of the deeper levels, the large ones of the last two
         const uint64_t nprobe = hashed ? (uint64_t)nbig : nsup;
-        const int32_t* probe_ids = hashed ? ws.big_ids : ws.ids;
+        const int32_t* probe_ids = hashed ? ws.big2_ids : ws.ids;
         const uint64_t per_group = (uint64_t)kProbeW * (uint64_t)ws.group;
         const int need_blocks = (int)std::min<uint64_t>((uint64_t)ws.group, (nprobe + kProbeW - 1) / kProbeW);
         if (need_blocks > cleared) {  // blocks [cleared, need_blocks) of each buffer
@@ -1020,7 +1218,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                 if ((e = probe_step(g, ws, a, nb, &count)) != cudaSuccess) return e;
             }
             probe_end_kernel<<<dim3((unsigned)g.sm_count, (unsigned)nb), kBlock, 0, g.stream>>>(
-                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63, hashed ? ws.big_pos + g0 : nullptr,
+                ws.G, ids, cnt, zv, cpow[(size_t)steps], ws.sums + 63, hashed ? ws.big2_pos + g0 : nullptr,
                 hashed ? ws.g2 : nullptr);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++count;
