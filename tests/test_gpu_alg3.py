@@ -85,9 +85,10 @@ def test_first_meeting_matches_lemma5(graph):
 
 def test_first_meeting_covers_both_last_level_forms(graph):
     """The last probe level takes g_2 of each support node from a one-warp two-hop table
-    when the node's two-hop multiset fits (sum of din over its in-neighbours <= 512), else
-    from the dense probes; at the hub of the Chung-Lu graph, depth 3, both forms occur
-    among the support of h_1 = I(k), and Z still matches the oracle's Lemma 5."""
+    when the node's two-hop multiset fits (sum of din over its in-neighbours <= 512), from
+    a one-block table when it is at most 8192, else from the dense probes; at the hub of
+    the Chung-Lu graph, depth 3, all three forms occur among the support of h_1 = I(k),
+    and Z still matches the oracle's Lemma 5."""
     name, (n, rp, col), g = graph
     if name != "chung_lu_20k":
         pytest.skip("the hub graph covers both forms")
@@ -95,7 +96,8 @@ def test_first_meeting_covers_both_last_level_forms(graph):
     k = int(np.argmax(din))
     sup = col[rp[k]:rp[k + 1]]
     e1 = np.array([int(din[col[rp[q]:rp[q + 1]]].sum()) for q in sup])
-    assert np.count_nonzero(e1 <= 512) > 0 and np.count_nonzero(e1 > 512) > 0
+    assert np.count_nonzero(e1 <= 512) > 0 and np.count_nonzero((e1 > 512) & (e1 <= 8192)) > 0
+    assert np.count_nonzero(e1 > 8192) > 0
     for d in (3, 4):
         ref = a3.first_meeting_lemma5(n, rp, col, k, C, d)
         z = g.alg3_first_meeting(k, d, C)
@@ -103,10 +105,11 @@ def test_first_meeting_covers_both_last_level_forms(graph):
 
 
 def test_first_meeting_hashed_levels_on_a_hub(esim):
-    """The last two probe levels run one warp per node where the neighbourhood fits the
-    tables (two-hop multiset <= 512 for both; three-hop multiset <= 1024 for the level
-    below the last), dense probes for the others.  At the hub of a Chung-Lu graph both
-    forms occur at both levels; Z_1..Z_d at depths 3..6 match the oracle's Lemma 5."""
+    """The last two probe levels run one warp per node where the neighbourhood fits its
+    tables (two-hop multiset <= 512; for the level below the last also three-hop
+    multiset <= 1024), one block per node where it fits the block's (<= 8192; <= 2048 and
+    <= 4096), dense probes for the others.  At the hub of a Chung-Lu graph all three forms
+    occur at the level below the last; Z_1..Z_d at depths 3..6 match the oracle's Lemma 5."""
     n, rp, col = synth.chung_lu(3000, 30000, gamma=2.1, seed=9)
     din = np.diff(rp).astype(np.int64)
     k = int(np.argmax(din))
@@ -117,8 +120,9 @@ def test_first_meeting_hashed_levels_on_a_hub(esim):
         return int(din[s1].sum()), int(din[s2].sum())
 
     sizes = np.array([multisets(int(q)) for q in col[rp[k]:rp[k + 1]]])  # the support of h_1
-    fits = (sizes[:, 0] <= 512) & (sizes[:, 1] <= 1024)
-    assert np.count_nonzero(fits) > 0 and np.count_nonzero(~fits) > 0
+    warp = (sizes[:, 0] <= 512) & (sizes[:, 1] <= 1024)
+    block = ~warp & (sizes[:, 0] <= 2048) & (sizes[:, 1] <= 4096)
+    assert np.count_nonzero(warp) > 0 and np.count_nonzero(block) > 0 and np.count_nonzero(~warp & ~block) > 0
     g = esim.Graph(n, rp, col)
     ref = a3.first_meeting_lemma5(n, rp, col, k, C, 6)
     for d in (3, 4, 5, 6):
