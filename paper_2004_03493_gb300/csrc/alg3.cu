@@ -543,8 +543,8 @@ __global__ void probe_end_kernel(ProbeGroup G, const int32_t* __restrict__ ids, 
 // probe's two steps); a node whose two-hop multiset is too large for the table is
 // appended to (big_ids, big_pos) for the dense probes, which write its column sum at
 // big_pos.  The order of the appends does not matter: each column sum is exact.
-constexpr int kG2Warps = 4;
-constexpr int kG2Table = 1024;  // slots per warp: 4 warps x 12 KB of shared memory
+constexpr int kG2Warps = 3;
+constexpr int kG2Table = 1024;  // slots per warp: 3 warps x 13 KB of shared memory
 
 __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t* __restrict__ count_dev,
                                                                  const int32_t* __restrict__ ids,
@@ -556,15 +556,25 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
                                                                  unsigned int* __restrict__ nbig) {
     __shared__ int32_t key[kG2Warps][kG2Table];
     __shared__ unsigned long long val[kG2Warps][kG2Table];
+    __shared__ uint16_t used[kG2Warps][kG2Table / 2];
+    __shared__ unsigned int nused[kG2Warps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SlotTable<kG2Table> tb{key[wid], val[wid], used[wid], &nused[wid]};
+    tb.clear_all(lane, 32);
+    __syncwarp();
     const int64_t count = (int64_t)*count_dev;
     const int64_t nw = (int64_t)gridDim.x * kG2Warps;
     for (int64_t i = (int64_t)blockIdx.x * kG2Warps + wid; i < count; i += nw) {
         double T;
         uint32_t dk;
-        const unsigned long long sq = twohop_sq_sum<kG2Table>(ids[i], rp, col, key[wid], val[wid], T, dk);
+        const bool large = twohop_build<kG2Table>(ids[i], rp, col, tb, T, dk) == kTwoHopTooLarge;
+        unsigned long long sq = 0;
+        if (!large) {
+            sq = warp_sq_sum(tb);
+            twohop_release(tb);
+        }
         if (lane != 0) continue;
-        if (sq == kTwoHopTooLarge) {
+        if (large) {
             const unsigned int slot = atomicAdd(nbig, 1u);
             big_ids[slot] = ids[i];
             big_pos[slot] = (int32_t)i;
@@ -586,10 +596,51 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
 // so a node gives the same terms on either path.  A node whose two- or three-hop
 // multiset is too large for the tables is appended to (big_ids, big_pos) for the dense
 // probes, before it emits anything.
-constexpr int kG3Warps = 3;
-constexpr int kG3Table1 = 1024;  // two-hop slots per warp (12 KB)
-constexpr int kG3Table2 = 2048;  // three-hop slots per warp (24 KB)
-constexpr size_t kG3Smem = (size_t)kG3Warps * ((kG3Table1 + kG3Table2) * (sizeof(int32_t) + sizeof(unsigned long long)));
+constexpr int kG3Warps = 4;
+constexpr int kG3Table1 = 1024;  // two-hop slots per warp
+constexpr int kG3Table2 = 1024;  // three-hop slots per warp
+constexpr size_t kG3WarpBytes = (size_t)(kG3Table1 + kG3Table2) * (sizeof(int32_t) + sizeof(unsigned long long)) +
+                                (size_t)(kG3Table1 + kG3Table2) / 2 * sizeof(uint16_t) + 16;
+constexpr size_t kG3Smem = (size_t)kG3Warps * kG3WarpBytes;
+
+// the shared memory of one warp: values, keys, used-slot lists, counts
+template <int kT1, int kT2>
+__device__ __forceinline__ void carve_tables(unsigned char* base, SlotTable<kT1>& t1, SlotTable<kT2>& t2) {
+    t1.V = (unsigned long long*)base;
+    t2.V = t1.V + kT1;
+    t1.K = (int32_t*)(t2.V + kT2);
+    t2.K = t1.K + kT1;
+    t1.U = (uint16_t*)(t2.K + kT2);
+    t2.U = t1.U + kT1 / 2;
+    t1.n = (unsigned int*)(((uintptr_t)(t2.U + kT2 / 2) + 7) & ~(uintptr_t)7);
+    t2.n = t1.n + 1;
+}
+
+// The third step of a node from its two-hop table t1 into t2 (all lanes of the warp):
+// H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a)).
+template <int kT1, int kT2>
+__device__ void warp_third_step(const SlotTable<kT1>& t1, SlotTable<kT2>& t2, const uint32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const unsigned long long* __restrict__ magic) {
+    const int lane = threadIdx.x & 31;
+    const unsigned int cnt = *t1.n;
+    for (unsigned int i0 = 0; i0 < cnt; i0 += 32) {
+        const unsigned int i = i0 + (unsigned int)lane;
+        const int slot_mine = i < cnt ? (int)t1.U[i] : -1;
+        unsigned live = __ballot_sync(0xffffffffu, slot_mine >= 0);
+        while (live) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1;
+            const int slot = __shfl_sync(0xffffffffu, slot_mine, src);
+            const int32_t a = t1.K[slot];
+            const uint32_t b2 = rp[a], e2r = rp[a + 1];
+            if (b2 == e2r) continue;
+            const unsigned long long x = div_by_magic(t1.V[slot], e2r - b2, magic[a]);
+            if (!x) continue;
+            for (uint32_t p = b2 + lane; p < e2r; p += 32) t2.add(col[p], x);
+        }
+    }
+    __syncwarp();
+}
 
 __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t* __restrict__ count_dev,
                                                                  const int32_t* __restrict__ ids,
@@ -605,29 +656,33 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
                                                                  unsigned int* __restrict__ nbig) {
     extern __shared__ __align__(16) unsigned char g3_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long* V1 = (unsigned long long*)g3_smem + (size_t)wid * (kG3Table1 + kG3Table2);
-    unsigned long long* V2 = V1 + kG3Table1;
-    int32_t* K1 = (int32_t*)((unsigned long long*)g3_smem + (size_t)kG3Warps * (kG3Table1 + kG3Table2)) +
-                  (size_t)wid * (kG3Table1 + kG3Table2);
-    int32_t* K2 = K1 + kG3Table1;
+    SlotTable<kG3Table1> t1;
+    SlotTable<kG3Table2> t2;
+    carve_tables(g3_smem + (size_t)wid * kG3WarpBytes, t1, t2);
+    t1.clear_all(lane, 32);
+    t2.clear_all(lane, 32);
+    __syncwarp();
     const int64_t count = (int64_t)*count_dev;
     const int64_t nw = (int64_t)gridDim.x * kG3Warps;
     for (int64_t i = (int64_t)blockIdx.x * kG3Warps + wid; i < count; i += nw) {
         const int32_t q = ids[i];
         double T;
         uint32_t dk;
-        const unsigned long long sq2 = twohop_sq_sum<kG3Table1>(q, rp, col, K1, V1, T, dk);
-        bool big = sq2 == kTwoHopTooLarge;
-        // the three-hop multiset: sum of din over the two-hop keys
-        unsigned long long e2 = 0;
-        if (!big && dk) {
-            for (int s = lane; s < kG3Table1; s += 32)
-                if (K1[s] >= 0) e2 += rp[K1[s] + 1] - rp[K1[s]];
+        const bool built = twohop_build<kG3Table1>(q, rp, col, t1, T, dk) != kTwoHopTooLarge;
+        bool big = !built;
+        if (built && dk) {  // the three-hop multiset: sum of din over the two-hop keys
+            const unsigned int cnt = *t1.n;
+            unsigned long long e2 = 0;
+            for (unsigned int u = (unsigned int)lane; u < cnt; u += 32) {
+                const int32_t a = t1.K[t1.U[u]];
+                e2 += rp[a + 1] - rp[a];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
             big = e2 > (unsigned long long)(kG3Table2 / 2);
         }
         if (big) {
+            if (built) twohop_release(t1);
             if (lane == 0) {
                 const unsigned int slot = atomicAdd(nbig, 1u);
                 big_ids[slot] = q;
@@ -642,50 +697,20 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
         }
         // row terms of the second step
         const double coef = c2 * zv_src[q];
-        for (int s = lane; s < kG3Table1; s += 32) {
-            if (K1[s] < 0) continue;
-            const double h = (double)V1[s] * kInvOne;
+        const unsigned int cnt1 = *t1.n;
+        for (unsigned int u = (unsigned int)lane; u < cnt1; u += 32) {
+            const int slot = t1.U[u];
+            const double h = (double)t1.V[slot] * kInvOne;
             long long hi, lo;
             zacc_split(coef * (h * h), hi, lo);
-            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + K1[s]), (unsigned long long)(-hi));
-            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + K1[s]), (unsigned long long)(-lo));
+            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + t1.K[slot]), (unsigned long long)(-hi));
+            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + t1.K[slot]), (unsigned long long)(-lo));
         }
-        // third step: H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a))
-        for (int s = lane; s < kG3Table2; s += 32) {
-            K2[s] = -1;
-            V2[s] = 0ull;
-        }
-        __syncwarp();
-        for (int s0 = 0; s0 < kG3Table1; s0 += 32) {
-            const int32_t a_mine = K1[s0 + lane];
-            unsigned live = __ballot_sync(0xffffffffu, a_mine >= 0 && V1[s0 + lane] != 0ull);
-            while (live) {
-                const int src = __ffs(live) - 1;
-                live &= live - 1;
-                const int32_t a = __shfl_sync(0xffffffffu, a_mine, src);
-                const uint32_t b2 = rp[a], e2r = rp[a + 1];
-                if (b2 == e2r) continue;
-                const unsigned long long x = div_by_magic(V1[s0 + src], e2r - b2, magic[a]);
-                if (!x) continue;
-                for (uint32_t p = b2 + lane; p < e2r; p += 32) {
-                    const int32_t r = col[p];
-                    uint32_t slot = ((uint32_t)r * 2654435761u) & (kG3Table2 - 1);
-                    for (;;) {  // at most half the slots are taken: a free or matching slot exists
-                        const int32_t prev = atomicCAS(&K2[slot], -1, r);
-                        if (prev == -1 || prev == r) break;
-                        slot = (slot + 1) & (kG3Table2 - 1);
-                    }
-                    atomicAdd(&V2[slot], x);
-                }
-            }
-        }
-        __syncwarp();
-        unsigned long long sq3 = 0;
-        for (int s = lane; s < kG3Table2; s += 32) sq3 += twohop_sq(V2[s]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq3 += __shfl_xor_sync(0xffffffffu, sq3, o);
+        warp_third_step(t1, t2, rp, col, magic);
+        const unsigned long long sq3 = warp_sq_sum(t2);
         if (lane == 0) colsum[i] = sq3;
-        __syncwarp();  // the tables are free for the warp's next node
+        twohop_release(t2);
+        twohop_release(t1);
     }
 }
 
@@ -695,21 +720,13 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
 // atomics, so a node gives the same integers on any tier.  Nodes still too large go on
 // to the dense probes.
 constexpr int kCtaThreads = 256;
-constexpr int kCta2Table = 16384;                   // last level: two-hop multiset <= 8192
+constexpr int kCtaWarps = kCtaThreads / 32;
+constexpr int kCta2Table = 16384;                      // last level: two-hop multiset <= 8192
 constexpr int kCta3Table1 = 4096, kCta3Table2 = 8192;  // level below: <= 2048 and <= 4096
-constexpr size_t kCta2Smem = (size_t)kCta2Table * (sizeof(int32_t) + sizeof(unsigned long long));
-constexpr size_t kCta3Smem = (size_t)(kCta3Table1 + kCta3Table2) * (sizeof(int32_t) + sizeof(unsigned long long));
-
-template <int kT>
-__device__ __forceinline__ void table_add(int32_t* K, unsigned long long* V, int32_t key, unsigned long long w) {
-    uint32_t slot = ((uint32_t)key * 2654435761u) & (kT - 1);
-    for (;;) {  // at most half the slots are taken: a free or matching slot exists
-        const int32_t prev = atomicCAS(&K[slot], -1, key);
-        if (prev == -1 || prev == key) break;
-        slot = (slot + 1) & (kT - 1);
-    }
-    atomicAdd(&V[slot], w);
-}
+constexpr size_t kCta2Smem = (size_t)kCta2Table * (sizeof(int32_t) + sizeof(unsigned long long)) +
+                             (size_t)kCta2Table / 2 * sizeof(uint16_t) + 16;
+constexpr size_t kCta3Smem = (size_t)(kCta3Table1 + kCta3Table2) * (sizeof(int32_t) + sizeof(unsigned long long)) +
+                             (size_t)(kCta3Table1 + kCta3Table2) / 2 * sizeof(uint16_t) + 16;
 
 // the block's total of v, in every thread
 __device__ __forceinline__ unsigned long long block_total(unsigned long long v, unsigned long long* red,
@@ -722,31 +739,35 @@ __device__ __forceinline__ unsigned long long block_total(unsigned long long v, 
     return t;
 }
 
-// H_2 of node q over its two-hop neighbourhood into the block's table (all threads call
-// it; the table is cleared here).  Returns false, with the table untouched, when the
-// two-hop multiset exceeds half the slots.
+// frees a block's table for its next node (all threads)
 template <int kT>
-__device__ bool cta_two_hop(int32_t q, const uint32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t* K,
-                            unsigned long long* V, unsigned long long* red, unsigned long long* bc) {
+__device__ void block_release(SlotTable<kT>& tb) {
+    __syncthreads();
+    tb.reset(threadIdx.x, kCtaThreads);
+    __syncthreads();
+    if (threadIdx.x == 0) *tb.n = 0u;
+    __syncthreads();
+}
+
+// H_2 of node q over its two-hop neighbourhood into the block's table (all threads call
+// it; the table is free on entry).  Returns false, with the table untouched, when din(q) is
+// 0 or the two-hop multiset exceeds half the slots.
+template <int kT>
+__device__ bool cta_two_hop(int32_t q, const uint32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            SlotTable<kT>& tb, unsigned long long* red, unsigned long long* bc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kW = kCtaThreads / 32;
     const uint32_t kb = rp[q], ke = rp[q + 1];
     const uint32_t dk = ke - kb;
     unsigned long long e1 = 0;
     for (uint32_t p = kb + threadIdx.x; p < ke; p += kCtaThreads) e1 += rp[col[p] + 1] - rp[col[p]];
     e1 = block_total(e1, red, bc);
     if (dk == 0 || e1 > (unsigned long long)(kT / 2)) return false;
-    for (int s = threadIdx.x; s < kT; s += kCtaThreads) {
-        K[s] = -1;
-        V[s] = 0ull;
-    }
-    __syncthreads();
-    for (uint32_t p1 = kb + wid; p1 < ke; p1 += kW) {
+    for (uint32_t p1 = kb + wid; p1 < ke; p1 += kCtaWarps) {
         const int32_t q1 = col[p1];
         const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
         if (b1 == e1r) continue;
         const unsigned long long w = kTwoHopOne / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
-        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) table_add<kT>(K, V, col[p2], w);
+        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) tb.add(col[p2], w);
     }
     __syncthreads();
     return true;
@@ -764,14 +785,20 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g2_cta_kernel(const unsigne
                                                                    int32_t* __restrict__ out_pos,
                                                                    unsigned int* __restrict__ nout) {
     extern __shared__ __align__(16) unsigned char cta_smem[];
-    unsigned long long* V = (unsigned long long*)cta_smem;
-    int32_t* K = (int32_t*)(V + kCta2Table);
-    __shared__ unsigned long long red[kCtaThreads / 32];
+    SlotTable<kCta2Table> tb;
+    tb.V = (unsigned long long*)cta_smem;
+    tb.K = (int32_t*)(tb.V + kCta2Table);
+    tb.U = (uint16_t*)(tb.K + kCta2Table);
+    tb.n = (unsigned int*)(((uintptr_t)(tb.U + kCta2Table / 2) + 7) & ~(uintptr_t)7);
+    __shared__ unsigned long long red[kCtaWarps];
     __shared__ unsigned long long bc;
     const unsigned int count = *nin;
+    if (blockIdx.x >= count) return;
+    tb.clear_all(threadIdx.x, kCtaThreads);
+    __syncthreads();
     for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
         const int32_t q = in_ids[i];
-        if (!cta_two_hop<kCta2Table>(q, rp, col, K, V, red, &bc)) {
+        if (!cta_two_hop<kCta2Table>(q, rp, col, tb, red, &bc)) {
             if (threadIdx.x == 0) {
                 const unsigned int slot = atomicAdd(nout, 1u);
                 out_ids[slot] = q;
@@ -779,11 +806,10 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g2_cta_kernel(const unsigne
             }
             continue;
         }
-        unsigned long long sq = 0;
-        for (int s = threadIdx.x; s < kCta2Table; s += kCtaThreads) sq += twohop_sq(V[s]);
+        unsigned long long sq = tb.sq_part(threadIdx.x, kCtaThreads);
         sq = block_sum(sq, red);
         if (threadIdx.x == 0) colsum[in_pos[i]] = sq;
-        __syncthreads();  // the table is free for the block's next node
+        block_release(tb);
     }
 }
 
@@ -802,26 +828,33 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigne
                                                                    int32_t* __restrict__ out_pos,
                                                                    unsigned int* __restrict__ nout) {
     extern __shared__ __align__(16) unsigned char cta_smem[];
-    unsigned long long* V1 = (unsigned long long*)cta_smem;
-    unsigned long long* V2 = V1 + kCta3Table1;
-    int32_t* K1 = (int32_t*)(V2 + kCta3Table2);
-    int32_t* K2 = K1 + kCta3Table1;
-    __shared__ unsigned long long red[kCtaThreads / 32];
+    SlotTable<kCta3Table1> t1;
+    SlotTable<kCta3Table2> t2;
+    carve_tables(cta_smem, t1, t2);
+    __shared__ unsigned long long red[kCtaWarps];
     __shared__ unsigned long long bc;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kW = kCtaThreads / 32;
     const unsigned int count = *nin;
+    if (blockIdx.x >= count) return;
+    t1.clear_all(threadIdx.x, kCtaThreads);
+    t2.clear_all(threadIdx.x, kCtaThreads);
+    __syncthreads();
     for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
         const int32_t q = in_ids[i];
-        bool fits = cta_two_hop<kCta3Table1>(q, rp, col, K1, V1, red, &bc);
-        if (fits) {
+        const bool built = cta_two_hop<kCta3Table1>(q, rp, col, t1, red, &bc);
+        bool fits = built;
+        if (built) {
+            const unsigned int cnt = *t1.n;
             unsigned long long e2 = 0;
-            for (int s = threadIdx.x; s < kCta3Table1; s += kCtaThreads)
-                if (K1[s] >= 0) e2 += rp[K1[s] + 1] - rp[K1[s]];
+            for (unsigned int u = threadIdx.x; u < cnt; u += kCtaThreads) {
+                const int32_t a = t1.K[t1.U[u]];
+                e2 += rp[a + 1] - rp[a];
+            }
             e2 = block_total(e2, red, &bc);
             fits = e2 <= (unsigned long long)(kCta3Table2 / 2);
         }
         if (!fits) {
+            if (built) block_release(t1);
             if (threadIdx.x == 0) {
                 const unsigned int slot = atomicAdd(nout, 1u);
                 out_ids[slot] = q;
@@ -830,39 +863,38 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigne
             continue;
         }
         const double coef = c2 * zv_src[q];
-        for (int s = threadIdx.x; s < kCta3Table1; s += kCtaThreads) {
-            if (K1[s] < 0) continue;
-            const double h = (double)V1[s] * kInvOne;
+        const unsigned int cnt1 = *t1.n;
+        for (unsigned int u = threadIdx.x; u < cnt1; u += kCtaThreads) {
+            const int slot = t1.U[u];
+            const double h = (double)t1.V[slot] * kInvOne;
             long long hi, lo;
             zacc_split(coef * (h * h), hi, lo);
-            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + K1[s]), (unsigned long long)(-hi));
-            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + K1[s]), (unsigned long long)(-lo));
+            if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + t1.K[slot]), (unsigned long long)(-hi));
+            if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + t1.K[slot]), (unsigned long long)(-lo));
         }
-        for (int s = threadIdx.x; s < kCta3Table2; s += kCtaThreads) {
-            K2[s] = -1;
-            V2[s] = 0ull;
-        }
-        __syncthreads();
-        for (int s0 = wid * 32; s0 < kCta3Table1; s0 += kW * 32) {
-            const int32_t a_mine = K1[s0 + lane];
-            unsigned live = __ballot_sync(0xffffffffu, a_mine >= 0 && V1[s0 + lane] != 0ull);
+        // third step: warps take 32-entry chunks of the two-hop list, lanes the in-neighbours
+        for (unsigned int i0 = (unsigned int)wid * 32; i0 < cnt1; i0 += kCtaWarps * 32) {
+            const unsigned int u = i0 + (unsigned int)lane;
+            const int slot_mine = u < cnt1 ? (int)t1.U[u] : -1;
+            unsigned live = __ballot_sync(0xffffffffu, slot_mine >= 0);
             while (live) {
                 const int src = __ffs(live) - 1;
                 live &= live - 1;
-                const int32_t a = __shfl_sync(0xffffffffu, a_mine, src);
+                const int slot = __shfl_sync(0xffffffffu, slot_mine, src);
+                const int32_t a = t1.K[slot];
                 const uint32_t b2 = rp[a], e2r = rp[a + 1];
                 if (b2 == e2r) continue;
-                const unsigned long long x = div_by_magic(V1[s0 + src], e2r - b2, magic[a]);
+                const unsigned long long x = div_by_magic(t1.V[slot], e2r - b2, magic[a]);
                 if (!x) continue;
-                for (uint32_t p = b2 + lane; p < e2r; p += 32) table_add<kCta3Table2>(K2, V2, col[p], x);
+                for (uint32_t p = b2 + lane; p < e2r; p += 32) t2.add(col[p], x);
             }
         }
         __syncthreads();
-        unsigned long long sq = 0;
-        for (int s = threadIdx.x; s < kCta3Table2; s += kCtaThreads) sq += twohop_sq(V2[s]);
+        unsigned long long sq = t2.sq_part(threadIdx.x, kCtaThreads);
         sq = block_sum(sq, red);
         if (threadIdx.x == 0) colsum[in_pos[i]] = sq;
-        __syncthreads();  // the tables are free for the block's next node
+        block_release(t2);
+        block_release(t1);
     }
 }
 

@@ -160,8 +160,8 @@ __global__ void paper_z1_kernel(int64_t n, const uint8_t* __restrict__ depth, co
 // One warp per node builds h_2 over the two-hop neighbourhood and sums its squares in
 // 63-bit fixed point (twohop.cuh).  A node whose two-hop multiset exceeds half the table
 // gets NaN and is left to the one-node Lemma 5 path.
-constexpr int kD2Warps = 4;
-constexpr int kD2Table = 1024;  // slots per warp (power of two): 4 warps x 12 KB of shared memory
+constexpr int kD2Warps = 3;
+constexpr int kD2Table = 1024;  // slots per warp (power of two): 3 warps x 13 KB of shared memory
 
 __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, const int32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ rp,
@@ -169,16 +169,26 @@ __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, cons
                                                                  double* __restrict__ zsum) {
     __shared__ int32_t key[kD2Warps][kD2Table];
     __shared__ unsigned long long val[kD2Warps][kD2Table];
+    __shared__ uint16_t used[kD2Warps][kD2Table / 2];
+    __shared__ unsigned int nused[kD2Warps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SlotTable<kD2Table> tb{key[wid], val[wid], used[wid], &nused[wid]};
+    tb.clear_all(lane, 32);
+    __syncwarp();
     const int nw = gridDim.x * kD2Warps;
     for (int i = blockIdx.x * kD2Warps + wid; i < count; i += nw) {
         const int32_t k = ids[i];
         double T;
         uint32_t dk;
-        const unsigned long long sq = twohop_sq_sum<kD2Table>(k, rp, col, key[wid], val[wid], T, dk);
+        const bool large = twohop_build<kD2Table>(k, rp, col, tb, T, dk) == kTwoHopTooLarge;
+        unsigned long long sq = 0;
+        if (!large) {
+            sq = warp_sq_sum(tb);
+            twohop_release(tb);
+        }
         if (lane != 0) continue;
         if (dk == 0) zsum[k] = 0.0;  // no in-neighbour: the walks stop at once and never meet
-        else if (sq == kTwoHopTooLarge) zsum[k] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: one-node path
+        else if (large) zsum[k] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: the one-node path
         else {
             const double S2 = (double)sq * (1.0 / 9223372036854775808.0);
             const double inv = 1.0 / (double)dk;

@@ -10,6 +10,10 @@
 // the table exact and independent of the lanes' order.  The result is
 //   sum_q floor(H_2(q)^2 / 2^63)
 // in the same fixed point.
+//
+// A table keeps the list of the slots it has used, so that its sums, its scans and its
+// reset touch those slots only: a node costs in proportion to its neighbourhood, not to
+// the table.  Between nodes every slot is free (key -1, value 0) and the list is empty.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,15 +29,68 @@ __device__ __forceinline__ unsigned long long twohop_sq(unsigned long long H) {
     return (__umul64hi(H, H) << 1) | ((H * H) >> 63);
 }
 
-// All 32 lanes of a warp call it with the same k; K and V are the warp's kTable slots
-// (kTable a power of two).  Returns the sum above (0 when din(k) = 0), or
-// kTwoHopTooLarge when the two-hop multiset (sum of din(q') over q' in I(k)) exceeds
-// half the slots.  T receives sum over q' in I(k) with din(q') > 0 of 1/din(q') (FP64,
-// fixed lane order) and dk din(k), in every lane.
-template <int kTable>
-__device__ unsigned long long twohop_sq_sum(int32_t k, const uint32_t* __restrict__ rp,
-                                            const int32_t* __restrict__ col, int32_t* K, unsigned long long* V,
-                                            double& T, uint32_t& dk) {
+// A hash table of kT slots (a power of two) in shared memory, shared by the threads of one
+// warp (or of one block: the callers synchronise accordingly).  K: keys (-1 free), V:
+// fixed-point values, U: the used slots in insertion order (kT / 2 entries), n: their
+// count.  Callers insert at most kT / 2 distinct keys.
+template <int kT>
+struct SlotTable {
+    int32_t* K;
+    unsigned long long* V;
+    uint16_t* U;
+    unsigned int* n;
+
+    // every slot free and the list empty; threads t of nthreads share the work
+    __device__ void clear_all(int t, int nthreads) {
+        for (int s = t; s < kT; s += nthreads) {
+            K[s] = -1;
+            V[s] = 0ull;
+        }
+        if (t == 0) *n = 0u;
+    }
+
+    __device__ __forceinline__ void add(int32_t key, unsigned long long w) {
+        uint32_t slot = ((uint32_t)key * 2654435761u) & (kT - 1);
+        for (;;) {  // at most half the slots are taken: a free or matching slot exists
+            const int32_t prev = atomicCAS(&K[slot], -1, key);
+            if (prev == -1) {
+                U[atomicAdd(n, 1u)] = (uint16_t)slot;
+                break;
+            }
+            if (prev == key) break;
+            slot = (slot + 1) & (kT - 1);
+        }
+        atomicAdd(&V[slot], w);
+    }
+
+    // this thread's share of sum over used slots of floor(V^2 / 2^63)
+    __device__ unsigned long long sq_part(int t, int nthreads) const {
+        const unsigned int cnt = *n;
+        unsigned long long s = 0;
+        for (unsigned int i = (unsigned int)t; i < cnt; i += (unsigned int)nthreads) s += twohop_sq(V[U[i]]);
+        return s;
+    }
+
+    // frees the used slots (the callers synchronise before and after)
+    __device__ void reset(int t, int nthreads) {
+        const unsigned int cnt = *n;
+        for (unsigned int i = (unsigned int)t; i < cnt; i += (unsigned int)nthreads) {
+            K[U[i]] = -1;
+            V[U[i]] = 0ull;
+        }
+    }
+};
+
+// All 32 lanes of a warp call it with the same k; tb is the warp's table, free on entry.
+// Builds H_2 of node k and returns 0, or returns kTwoHopTooLarge (table untouched) when
+// the two-hop multiset (sum of din(q') over q' in I(k)) exceeds half the slots.  T
+// receives sum over q' in I(k) with din(q') > 0 of 1/din(q') (FP64, fixed lane order)
+// and dk din(k), in every lane.  The caller reads the table, then frees it with
+// twohop_release.
+template <int kT>
+__device__ unsigned long long twohop_build(int32_t k, const uint32_t* __restrict__ rp,
+                                           const int32_t* __restrict__ col, SlotTable<kT>& tb, double& T,
+                                           uint32_t& dk) {
     const int lane = threadIdx.x & 31;
     const uint32_t kb = rp[k], ke = rp[k + 1];
     dk = ke - kb;
@@ -51,35 +108,35 @@ __device__ unsigned long long twohop_sq_sum(int32_t k, const uint32_t* __restric
         e1 += __shfl_xor_sync(0xffffffffu, e1, o);
         T += __shfl_xor_sync(0xffffffffu, T, o);
     }
-    if (e1 > (unsigned long long)(kTable / 2)) return kTwoHopTooLarge;
-    for (int s = lane; s < kTable; s += 32) {
-        K[s] = -1;
-        V[s] = 0ull;
-    }
-    __syncwarp();
+    if (e1 > (unsigned long long)(kT / 2)) return kTwoHopTooLarge;
     for (uint32_t p1 = kb; p1 < ke; ++p1) {  // q' in I(k), then its in-neighbours across the lanes
         const int32_t q1 = col[p1];
         const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
         if (b1 == e1r) continue;
         const unsigned long long w = kTwoHopOne / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
-        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) {
-            const int32_t q = col[p2];
-            uint32_t slot = ((uint32_t)q * 2654435761u) & (kTable - 1);
-            for (;;) {  // at most half the slots are taken: a free or matching slot exists
-                const int32_t prev = atomicCAS(&K[slot], -1, q);
-                if (prev == -1 || prev == q) break;
-                slot = (slot + 1) & (kTable - 1);
-            }
-            atomicAdd(&V[slot], w);
-        }
+        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) tb.add(col[p2], w);
     }
     __syncwarp();
-    unsigned long long sq = 0;
-    for (int s = lane; s < kTable; s += 32) sq += twohop_sq(V[s]);
+    return 0ull;
+}
+
+// sum over the warp's table of floor(H^2 / 2^63), in every lane
+template <int kT>
+__device__ unsigned long long warp_sq_sum(const SlotTable<kT>& tb) {
+    unsigned long long sq = tb.sq_part(threadIdx.x & 31, 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    __syncwarp();  // the table is free for the warp's next node
     return sq;
+}
+
+// frees the warp's table for its next node
+template <int kT>
+__device__ void twohop_release(SlotTable<kT>& tb) {
+    __syncwarp();
+    tb.reset(threadIdx.x & 31, 32);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) *tb.n = 0u;
+    __syncwarp();
 }
 
 }  // namespace esim
