@@ -159,25 +159,6 @@ __global__ void zv_finalize_kernel(int64_t n, double cj, double c, const double*
 constexpr unsigned long long kOne = 1ull << 63;
 constexpr double kInvOne = 1.0 / 9223372036854775808.0;  // 2^-63
 
-// floor(H / d) for 1 <= d < 2^32, with M = floor((2^64 - 1) / d) precomputed per node
-// (Graph::din_magic): the high word of H M never exceeds the quotient and falls short of
-// it by at most two, which the remainder corrects.  The GPU has no 64-bit integer divide;
-// this replaces its long software sequence by a multiply-high and a few adds.
-__host__ __device__ __forceinline__ unsigned long long div_by_magic(unsigned long long H, uint32_t d,
-                                                                     unsigned long long M) {
-    if (d == 1u) return H;
-#ifdef __CUDA_ARCH__
-    unsigned long long q = __umul64hi(H, M);
-#else
-    unsigned long long q = (unsigned long long)(((unsigned __int128)H * M) >> 64);
-#endif
-    unsigned long long r = H - q * d;
-    while (r >= d) {
-        ++q;
-        r -= d;
-    }
-    return q;
-}
 
 
 // Direction-optimising steps.  A block starts from 32 single nodes, so its first
@@ -245,7 +226,7 @@ __device__ __forceinline__ unsigned long long probe_row_out(int64_t row, unsigne
                                                             const double* coef) {
     if (!a.last) {
         const uint32_t d = __ldg(a.in_rp + row + 1) - __ldg(a.in_rp + row);
-        xnext[(size_t)row * kProbeW + lane] = (d && H) ? div_by_magic(H, d, __ldg(a.magic + row)) : 0ull;
+        xnext[(size_t)row * kProbeW + lane] = (d && H) ? floor_div_magic(H, d, __ldg(a.magic + row)) : 0ull;
     }
     if (a.mode == 2) return twohop_sq(H);  // floor(H^2 / 2^63)
     if (a.mode == 1 && __any_sync(0xffffffffu, H != 0ull)) {
@@ -550,6 +531,7 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
                                                                  const int32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ rp,
                                                                  const int32_t* __restrict__ col,
+                                                                 const unsigned long long* __restrict__ magic,
                                                                  unsigned long long* __restrict__ colsum,
                                                                  int32_t* __restrict__ big_ids,
                                                                  int32_t* __restrict__ big_pos,
@@ -558,6 +540,7 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
     __shared__ unsigned long long val[kG2Warps][kG2Table];
     __shared__ uint16_t used[kG2Warps][kG2Table / 2];
     __shared__ unsigned int nused[kG2Warps];
+    __shared__ PushScratch scratch[kG2Warps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SlotTable<kG2Table> tb{key[wid], val[wid], used[wid], &nused[wid]};
     tb.clear_all(lane, 32);
@@ -567,7 +550,7 @@ __global__ void __launch_bounds__(kG2Warps * 32) probe_g2_kernel(const uint64_t*
     for (int64_t i = (int64_t)blockIdx.x * kG2Warps + wid; i < count; i += nw) {
         double T;
         uint32_t dk;
-        const bool large = twohop_build<kG2Table>(ids[i], rp, col, tb, T, dk) == kTwoHopTooLarge;
+        const bool large = twohop_build<kG2Table>(ids[i], rp, col, magic, tb, scratch[wid], T, dk) == kTwoHopTooLarge;
         unsigned long long sq = 0;
         if (!large) {
             sq = warp_sq_sum(tb);
@@ -600,7 +583,7 @@ constexpr int kG3Warps = 4;
 constexpr int kG3Table1 = 1024;  // two-hop slots per warp
 constexpr int kG3Table2 = 1024;  // three-hop slots per warp
 constexpr size_t kG3WarpBytes = (size_t)(kG3Table1 + kG3Table2) * (sizeof(int32_t) + sizeof(unsigned long long)) +
-                                (size_t)(kG3Table1 + kG3Table2) / 2 * sizeof(uint16_t) + 16;
+                                (size_t)(kG3Table1 + kG3Table2) / 2 * sizeof(uint16_t) + 16 + sizeof(PushScratch);
 constexpr size_t kG3Smem = (size_t)kG3Warps * kG3WarpBytes;
 
 // the shared memory of one warp: values, keys, used-slot lists, counts
@@ -620,26 +603,15 @@ __device__ __forceinline__ void carve_tables(unsigned char* base, SlotTable<kT1>
 // H_3(r) = sum over two-hop keys a with r in I(a) of floor(H_2(a) / din(a)).
 template <int kT1, int kT2>
 __device__ void warp_third_step(const SlotTable<kT1>& t1, SlotTable<kT2>& t2, const uint32_t* __restrict__ rp,
-                                const int32_t* __restrict__ col, const unsigned long long* __restrict__ magic) {
+                                const int32_t* __restrict__ col, const unsigned long long* __restrict__ magic,
+                                PushScratch& sc) {
     const int lane = threadIdx.x & 31;
     const unsigned int cnt = *t1.n;
     for (unsigned int i0 = 0; i0 < cnt; i0 += 32) {
         const unsigned int i = i0 + (unsigned int)lane;
-        const int slot_mine = i < cnt ? (int)t1.U[i] : -1;
-        unsigned live = __ballot_sync(0xffffffffu, slot_mine >= 0);
-        while (live) {
-            const int src = __ffs(live) - 1;
-            live &= live - 1;
-            const int slot = __shfl_sync(0xffffffffu, slot_mine, src);
-            const int32_t a = t1.K[slot];
-            const uint32_t b2 = rp[a], e2r = rp[a + 1];
-            if (b2 == e2r) continue;
-            const unsigned long long x = div_by_magic(t1.V[slot], e2r - b2, magic[a]);
-            if (!x) continue;
-            for (uint32_t p = b2 + lane; p < e2r; p += 32) t2.add(col[p], x);
-        }
+        const int slot = i < cnt ? (int)t1.U[i] : -1;
+        push_batch(slot >= 0 ? t1.K[slot] : -1, slot >= 0 ? t1.V[slot] : 0ull, rp, col, magic, t2, sc);
     }
-    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t* __restrict__ count_dev,
@@ -658,7 +630,9 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SlotTable<kG3Table1> t1;
     SlotTable<kG3Table2> t2;
-    carve_tables(g3_smem + (size_t)wid * kG3WarpBytes, t1, t2);
+    unsigned char* mine = g3_smem + (size_t)wid * kG3WarpBytes;
+    PushScratch& sc = *(PushScratch*)mine;
+    carve_tables(mine + sizeof(PushScratch), t1, t2);
     t1.clear_all(lane, 32);
     t2.clear_all(lane, 32);
     __syncwarp();
@@ -668,7 +642,7 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
         const int32_t q = ids[i];
         double T;
         uint32_t dk;
-        const bool built = twohop_build<kG3Table1>(q, rp, col, t1, T, dk) != kTwoHopTooLarge;
+        const bool built = twohop_build<kG3Table1>(q, rp, col, magic, t1, sc, T, dk) != kTwoHopTooLarge;
         bool big = !built;
         if (built && dk) {  // the three-hop multiset: sum of din over the two-hop keys
             const unsigned int cnt = *t1.n;
@@ -706,7 +680,7 @@ __global__ void __launch_bounds__(kG3Warps * 32) probe_g3_kernel(const uint64_t*
             if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + t1.K[slot]), (unsigned long long)(-hi));
             if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + t1.K[slot]), (unsigned long long)(-lo));
         }
-        warp_third_step(t1, t2, rp, col, magic);
+        warp_third_step(t1, t2, rp, col, magic, sc);
         const unsigned long long sq3 = warp_sq_sum(t2);
         if (lane == 0) colsum[i] = sq3;
         twohop_release(t2);
@@ -754,7 +728,8 @@ __device__ void block_release(SlotTable<kT>& tb) {
 // 0 or the two-hop multiset exceeds half the slots.
 template <int kT>
 __device__ bool cta_two_hop(int32_t q, const uint32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                            SlotTable<kT>& tb, unsigned long long* red, unsigned long long* bc) {
+                            const unsigned long long* __restrict__ magic, SlotTable<kT>& tb, PushScratch* sc,
+                            unsigned long long* red, unsigned long long* bc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t kb = rp[q], ke = rp[q + 1];
     const uint32_t dk = ke - kb;
@@ -762,12 +737,10 @@ __device__ bool cta_two_hop(int32_t q, const uint32_t* __restrict__ rp, const in
     for (uint32_t p = kb + threadIdx.x; p < ke; p += kCtaThreads) e1 += rp[col[p] + 1] - rp[col[p]];
     e1 = block_total(e1, red, bc);
     if (dk == 0 || e1 > (unsigned long long)(kT / 2)) return false;
-    for (uint32_t p1 = kb + wid; p1 < ke; p1 += kCtaWarps) {
-        const int32_t q1 = col[p1];
-        const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
-        if (b1 == e1r) continue;
-        const unsigned long long w = kTwoHopOne / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
-        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) tb.add(col[p2], w);
+    const unsigned long long x0 = floor_div_magic(kTwoHopOne, dk, magic[q]);
+    for (uint32_t base = kb + (uint32_t)wid * 32; base < ke; base += kCtaWarps * 32) {  // warp-uniform
+        const uint32_t p = base + (uint32_t)lane;
+        push_batch(p < ke ? col[p] : -1, x0, rp, col, magic, tb, sc[wid]);
     }
     __syncthreads();
     return true;
@@ -780,6 +753,7 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g2_cta_kernel(const unsigne
                                                                    const int32_t* __restrict__ in_pos,
                                                                    const uint32_t* __restrict__ rp,
                                                                    const int32_t* __restrict__ col,
+                                                                   const unsigned long long* __restrict__ magic,
                                                                    unsigned long long* __restrict__ colsum,
                                                                    int32_t* __restrict__ out_ids,
                                                                    int32_t* __restrict__ out_pos,
@@ -792,13 +766,14 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g2_cta_kernel(const unsigne
     tb.n = (unsigned int*)(((uintptr_t)(tb.U + kCta2Table / 2) + 7) & ~(uintptr_t)7);
     __shared__ unsigned long long red[kCtaWarps];
     __shared__ unsigned long long bc;
+    __shared__ PushScratch sc[kCtaWarps];
     const unsigned int count = *nin;
     if (blockIdx.x >= count) return;
     tb.clear_all(threadIdx.x, kCtaThreads);
     __syncthreads();
     for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
         const int32_t q = in_ids[i];
-        if (!cta_two_hop<kCta2Table>(q, rp, col, tb, red, &bc)) {
+        if (!cta_two_hop<kCta2Table>(q, rp, col, magic, tb, sc, red, &bc)) {
             if (threadIdx.x == 0) {
                 const unsigned int slot = atomicAdd(nout, 1u);
                 out_ids[slot] = q;
@@ -833,6 +808,7 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigne
     carve_tables(cta_smem, t1, t2);
     __shared__ unsigned long long red[kCtaWarps];
     __shared__ unsigned long long bc;
+    __shared__ PushScratch sc[kCtaWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned int count = *nin;
     if (blockIdx.x >= count) return;
@@ -841,7 +817,7 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigne
     __syncthreads();
     for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
         const int32_t q = in_ids[i];
-        const bool built = cta_two_hop<kCta3Table1>(q, rp, col, t1, red, &bc);
+        const bool built = cta_two_hop<kCta3Table1>(q, rp, col, magic, t1, sc, red, &bc);
         bool fits = built;
         if (built) {
             const unsigned int cnt = *t1.n;
@@ -872,22 +848,11 @@ __global__ void __launch_bounds__(kCtaThreads) probe_g3_cta_kernel(const unsigne
             if (hi != 0) atomicAdd((unsigned long long*)(zhi_next + t1.K[slot]), (unsigned long long)(-hi));
             if (lo != 0) atomicAdd((unsigned long long*)(zlo_next + t1.K[slot]), (unsigned long long)(-lo));
         }
-        // third step: warps take 32-entry chunks of the two-hop list, lanes the in-neighbours
+        // third step: warps take 32-entry chunks of the two-hop list (warp-uniform bounds)
         for (unsigned int i0 = (unsigned int)wid * 32; i0 < cnt1; i0 += kCtaWarps * 32) {
             const unsigned int u = i0 + (unsigned int)lane;
-            const int slot_mine = u < cnt1 ? (int)t1.U[u] : -1;
-            unsigned live = __ballot_sync(0xffffffffu, slot_mine >= 0);
-            while (live) {
-                const int src = __ffs(live) - 1;
-                live &= live - 1;
-                const int slot = __shfl_sync(0xffffffffu, slot_mine, src);
-                const int32_t a = t1.K[slot];
-                const uint32_t b2 = rp[a], e2r = rp[a + 1];
-                if (b2 == e2r) continue;
-                const unsigned long long x = div_by_magic(t1.V[slot], e2r - b2, magic[a]);
-                if (!x) continue;
-                for (uint32_t p = b2 + lane; p < e2r; p += 32) t2.add(col[p], x);
-            }
+            const int slot = u < cnt1 ? (int)t1.U[u] : -1;
+            push_batch(slot >= 0 ? t1.K[slot] : -1, slot >= 0 ? t1.V[slot] : 0ull, rp, col, magic, t2, sc[wid]);
         }
         __syncthreads();
         unsigned long long sq = t2.sq_part(threadIdx.x, kCtaThreads);
@@ -1176,8 +1141,8 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         if (hashed) {
             if ((e = cudaMemsetAsync(ws.nbig, 0, 2 * sizeof(unsigned int), g.stream)) != cudaSuccess) return e;
             if (steps == 2) {
-                probe_g2_kernel<<<(unsigned)(g.sm_count * 4), kG2Warps * 32, 0, g.stream>>>(
-                    ws.off + n, ws.ids, g.in.rp, g.in.col, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
+                probe_g2_kernel<<<(unsigned)(g.sm_count * 5), kG2Warps * 32, 0, g.stream>>>(
+                    ws.off + n, ws.ids, g.in.rp, g.in.col, g.din_magic, ws.g2, ws.big_ids, ws.big_pos, ws.nbig);
             } else {
                 if ((e = cudaFuncSetAttribute(probe_g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kG3Smem)) != cudaSuccess)
@@ -1193,7 +1158,8 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
                                               (int)kCta2Smem)) != cudaSuccess)
                     return e;
                 probe_g2_cta_kernel<<<(unsigned)g.sm_count, kCtaThreads, kCta2Smem, g.stream>>>(
-                    ws.nbig, ws.big_ids, ws.big_pos, g.in.rp, g.in.col, ws.g2, ws.big2_ids, ws.big2_pos, ws.nbig + 1);
+                    ws.nbig, ws.big_ids, ws.big_pos, g.in.rp, g.in.col, g.din_magic, ws.g2, ws.big2_ids, ws.big2_pos,
+                    ws.nbig + 1);
             } else {
                 if ((e = cudaFuncSetAttribute(probe_g3_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kCta3Smem)) != cudaSuccess)

@@ -165,12 +165,14 @@ constexpr int kD2Table = 1024;  // slots per warp (power of two): 3 warps x 13 K
 
 __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, const int32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ rp,
-                                                                 const int32_t* __restrict__ col, double c,
-                                                                 double* __restrict__ zsum) {
+                                                                 const int32_t* __restrict__ col,
+                                                                 const unsigned long long* __restrict__ magic,
+                                                                 double c, double* __restrict__ zsum) {
     __shared__ int32_t key[kD2Warps][kD2Table];
     __shared__ unsigned long long val[kD2Warps][kD2Table];
     __shared__ uint16_t used[kD2Warps][kD2Table / 2];
     __shared__ unsigned int nused[kD2Warps];
+    __shared__ PushScratch scratch[kD2Warps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SlotTable<kD2Table> tb{key[wid], val[wid], used[wid], &nused[wid]};
     tb.clear_all(lane, 32);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kD2Warps * 32) paper_z2_kernel(int count, cons
         const int32_t k = ids[i];
         double T;
         uint32_t dk;
-        const bool large = twohop_build<kD2Table>(k, rp, col, tb, T, dk) == kTwoHopTooLarge;
+        const bool large = twohop_build<kD2Table>(k, rp, col, magic, tb, scratch[wid], T, dk) == kTwoHopTooLarge;
         unsigned long long sq = 0;
         if (!large) {
             sq = warp_sq_sum(tb);
@@ -298,7 +300,7 @@ cudaError_t alg3_paper_z2(const Graph& g, const int32_t* ids, int count, double 
     if (count <= 0) return cudaSuccess;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + kD2Warps - 1) / kD2Warps,
                                                                    (int64_t)g.sm_count * 8));
-    paper_z2_kernel<<<blocks, kD2Warps * 32, 0, g.stream>>>(count, ids, g.in.rp, g.in.col, c, zsum);
+    paper_z2_kernel<<<blocks, kD2Warps * 32, 0, g.stream>>>(count, ids, g.in.rp, g.in.col, g.din_magic, c, zsum);
     return cudaGetLastError();
 }
 

@@ -81,16 +81,76 @@ struct SlotTable {
     }
 };
 
+// Per-warp scratch of push_batch.
+struct PushScratch {
+    uint32_t excl[32];
+    uint32_t beg[32];
+    unsigned long long w[32];
+};
+
+// floor(H / d) for 1 <= d < 2^32, with M = floor((2^64 - 1) / d) (0 for d = 1): the high
+// word of H M never exceeds the quotient and falls short of it by at most two, which the
+// remainder corrects.
+__device__ __forceinline__ unsigned long long floor_div_magic(unsigned long long H, uint32_t d, unsigned long long M) {
+    if (d == 1u) return H;
+    unsigned long long q = __umul64hi(H, M);
+    unsigned long long r = H - q * d;
+    while (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
+
+// All 32 lanes: lane l brings node a_l (-1 for none) and a numerator num_l; every q in
+// I(a_l) receives floor(num_l / din(a_l)) in tb.  The (node, in-neighbour) entries of the
+// 32 nodes are spread over the lanes (prefix sums of the lengths, then a five-step search
+// for each entry's node), so the loads do not wait on one another.
+template <class Table>
+__device__ void push_batch(int32_t a, unsigned long long num, const uint32_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, const unsigned long long* __restrict__ magic, Table& tb,
+                           PushScratch& sc) {
+    const int lane = threadIdx.x & 31;
+    uint32_t b = 0, len = 0;
+    unsigned long long w = 0;
+    if (a >= 0 && num) {
+        b = rp[a];
+        len = rp[a + 1] - b;
+        if (len) w = floor_div_magic(num, len, magic[a]);
+        if (!w) len = 0;
+    }
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    sc.excl[lane] = incl - len;
+    sc.beg[lane] = b;
+    sc.w[lane] = w;
+    __syncwarp();
+    for (uint32_t f = (uint32_t)lane; f < total; f += 32) {
+        int src = 0;  // the last lane whose entries start at or before f: it owns f
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (sc.excl[src + step] <= f) src += step;
+        tb.add(col[sc.beg[src] + (f - sc.excl[src])], sc.w[src]);
+    }
+    __syncwarp();
+}
+
 // All 32 lanes of a warp call it with the same k; tb is the warp's table, free on entry.
 // Builds H_2 of node k and returns 0, or returns kTwoHopTooLarge (table untouched) when
 // the two-hop multiset (sum of din(q') over q' in I(k)) exceeds half the slots.  T
 // receives sum over q' in I(k) with din(q') > 0 of 1/din(q') (FP64, fixed lane order)
 // and dk din(k), in every lane.  The caller reads the table, then frees it with
-// twohop_release.
+// twohop_release.  magic: floor((2^64 - 1) / din) per node (0 where din <= 1).
 template <int kT>
 __device__ unsigned long long twohop_build(int32_t k, const uint32_t* __restrict__ rp,
-                                           const int32_t* __restrict__ col, SlotTable<kT>& tb, double& T,
-                                           uint32_t& dk) {
+                                           const int32_t* __restrict__ col,
+                                           const unsigned long long* __restrict__ magic, SlotTable<kT>& tb,
+                                           PushScratch& sc, double& T, uint32_t& dk) {
     const int lane = threadIdx.x & 31;
     const uint32_t kb = rp[k], ke = rp[k + 1];
     dk = ke - kb;
@@ -109,14 +169,12 @@ __device__ unsigned long long twohop_build(int32_t k, const uint32_t* __restrict
         T += __shfl_xor_sync(0xffffffffu, T, o);
     }
     if (e1 > (unsigned long long)(kT / 2)) return kTwoHopTooLarge;
-    for (uint32_t p1 = kb; p1 < ke; ++p1) {  // q' in I(k), then its in-neighbours across the lanes
-        const int32_t q1 = col[p1];
-        const uint32_t b1 = rp[q1], e1r = rp[q1 + 1];
-        if (b1 == e1r) continue;
-        const unsigned long long w = kTwoHopOne / ((unsigned long long)dk * (unsigned long long)(e1r - b1));
-        for (uint32_t p2 = b1 + lane; p2 < e1r; p2 += 32) tb.add(col[p2], w);
+    // every q1 in I(k) holds h_1(q1) = x_0 = floor(2^63 / din(k)) and pushes floor(x_0 / din(q1))
+    const unsigned long long x0 = floor_div_magic(kTwoHopOne, dk, magic[k]);
+    for (uint32_t base = kb; base < ke; base += 32) {
+        const uint32_t p = base + (uint32_t)lane;
+        push_batch(p < ke ? col[p] : -1, x0, rp, col, magic, tb, sc);
     }
-    __syncwarp();
     return 0ull;
 }
 
