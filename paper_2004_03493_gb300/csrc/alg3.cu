@@ -4,8 +4,9 @@
 // tail walk pairs.
 //
 // Notation: h_l = (P^T)^l(k, .), the distribution of a non-stop walk from k after l
-// steps (dense FP64, by pull sweeps over the out-edge CSR with no decay); Zv_l the
-// vector Z_l(k, .) of Lemma 5; P~ the transition matrix with squared entries.
+// steps (FP64 storage; pull sweeps over the out-edge CSR with no decay, on the warp-tile
+// kernel with two-float sums); Zv_l the vector Z_l(k, .) of Lemma 5; P~ the transition
+// matrix with squared entries.
 // Lemma 5 reads, for each target level j,
 //   Zv_j = c^j h_j^2 - c P~ Zv_{j-1} - sum_{l'=2}^{j-1} c^{l'} sum_{q'} Zv_{j-l'}(q') ((P^T)^{l'}(q', .))^2
 // (the l' = 1 term is one squared-weight sweep, because (P^T)(q', q)^2 = 1/din(q')^2
@@ -15,11 +16,16 @@
 // block's x = h/din to h_next = P x; its epilogue subtracts
 // sum_col c^{l'} Zv_i(q'_col) h^{q'_col}_{l'}(q)^2 from Zv_{i+l'}(q) for a level below
 // d, or adds h^2 to per-column sums for level d itself (only Z_d's total is needed).
-// Z_j = sum_q Zv_j(q) by fixed-order block partials.  Every accumulation that
-// crosses blocks or threads is an integer one, so the result is deterministic.
+// The last two probe levels run one warp (or one block) per node over hash tables of
+// its two- and three-hop neighbourhood instead, with the same integers.
+// Z_j = sum_q Zv_j(q) by fixed-order block partials.  Every accumulation that crosses
+// blocks or threads is an integer one or has a fixed order, so the result is
+// deterministic.
 #include "common.cuh"
 #include "internal.h"
 #include "twohop.cuh"
+#include "f2conv.cuh"
+#include "twofloat.cuh"
 
 #include <math.h>
 
@@ -110,12 +116,13 @@ __global__ void scatter_ids_kernel(int64_t n, const uint64_t* __restrict__ flag,
         if (flag[i]) ids[off[i]] = (int32_t)i;
 }
 
-// x = v / din^2: the input of the squared-transition sweep P~ v
+// x = v / din^2 as a two-float: the input of the squared-transition sweep P~ v
 __global__ void sq_scale_kernel(int64_t n, const double* __restrict__ v, const double* __restrict__ inv_din,
-                                double* __restrict__ x) {
+                                float2* __restrict__ x) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double w = inv_din[i];
-        x[i] = v[i] * (w * w);
+        const f2 t = double_to_f2_bits(v[i] * (w * w));
+        x[i] = make_float2(t.hi, t.lo);
     }
 }
 
@@ -1093,7 +1100,7 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
     A3Ws ws;
     a3_layout(g.n, g.m, g.out.nseg, wsp, &ws);
     const size_t n = (size_t)g.n;
-    const int per_sweep = 1 + (g.out.nlong > 0 ? 1 : 0);
+    const int per_sweep = 1 + (g.out.tnlong > 0 ? 1 : 0);  // tile kernel, long rows
     const int eb = eblocks(g, g.n);
     int count = 0;
     cudaError_t e = launch_walk_distributions(g, k, depth, ws.H, ws.xa, ws.xb);
@@ -1112,9 +1119,10 @@ cudaError_t alg3_first_meeting(const Graph& g, int64_t k, int depth, double c, v
         double* zv = ws.Zv + (size_t)j * n;
         const double* T = nullptr;
         if (j >= 2) {  // T = P~ Zv_{j-1}
-            sq_scale_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.Zv + (size_t)(j - 1) * n, g.inv_din, ws.x);
+            float2* x2 = reinterpret_cast<float2*>(ws.x);  // n 8-byte entries
+            sq_scale_kernel<<<eb, kBlock, 0, g.stream>>>(g.n, ws.Zv + (size_t)(j - 1) * n, g.inv_din, x2);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = launch_pull_sum(g, ws.x, ws.T)) != cudaSuccess) return e;
+            if ((e = launch_pull_sum(g, x2, ws.T)) != cudaSuccess) return e;
             count += 1 + per_sweep;
             T = ws.T;
         }

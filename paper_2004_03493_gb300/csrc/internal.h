@@ -175,7 +175,7 @@ cudaError_t launch_reverse(const Graph& g, const double* hist, int32_t L, double
                            double* sa, double* sb);
 cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb);
 cudaError_t launch_walk_distributions(const Graph& g, int64_t u, int steps, double* H, double* xa, double* xb);
-cudaError_t launch_pull_sum(const Graph& g, const double* x, double* out);
+cudaError_t launch_pull_sum(const Graph& g, const float2* x, double* out);
 cudaError_t launch_reverse32(const Graph& g, const float* hist, int32_t L, double c, const double* dhat,
                              double* s_out, float2* w, float2* sa, float2* sb);
 cudaError_t launch_forward_sparse(const Graph& g, int64_t u, double c, int32_t L, double theta, const SparseHist& h,

@@ -659,28 +659,34 @@ cudaError_t launch_reverse_sparse(const Graph& g, const SparseHist& h, int32_t L
 }
 
 // Algorithm 3 helpers: h_l = (P^T)^l(u, .), the distribution of a non-stop walk from
-// u (no decay, no stop), for l = 0..steps, into H[(steps+1) * n] (FP64).
+// u (no decay, no stop), for l = 0..steps, into H[(steps+1) * n] (FP64 storage), on the
+// warp-tile kernel in the FP64 form's two-float arithmetic (x_l = h_l / din as two-floats
+// in xa/xb, n 8-byte entries each).
 cudaError_t launch_walk_distributions(const Graph& g, int64_t u, int steps, double* H, double* xa, double* xb) {
-    forward_init_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, 1.0, g.inv_din, H, xa);
+    const uint32_t din_u = (*g.din_host)[(size_t)u];
+    const f2 x0 = din_u ? host_f2(1.0 / (double)din_u) : f2{0.f, 0.f};
+    float2* x[2] = {reinterpret_cast<float2*>(xa), reinterpret_cast<float2*>(xb)};
+    forward_init_d_kernel<<<elementwise_blocks(g, g.n), kBlock, 0, g.stream>>>(g.n, u, 1.0, x0.hi, x0.lo, H, x[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    double* x[2] = {xa, xb};
+    const f2 one{1.f, 0.f};
     for (int l = 1; l <= steps; ++l) {
-        ForwardOp op{1.0, g.inv_din, H + (size_t)l * (size_t)g.n, x[l & 1]};
-        e = sweep_level<Pol64>(g, g.out, x[(l - 1) & 1], op);
+        ForwardOpD op{one, g.in.rp, H + (size_t)l * (size_t)g.n, x[l & 1]};
+        e = sweep_level<Pol2f>(g, g.out, x[(l - 1) & 1], op);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-struct PlainOp {
+struct PlainOpD {
     double* __restrict__ out;
-    __device__ __forceinline__ void operator()(int64_t row, double acc) const { out[row] = acc; }
+    __device__ __forceinline__ void operator()(int64_t row, f2 acc) const { out[row] = f2_to_double_bits(acc); }
 };
 
-// out(i) = sum_{j in Out(i)} x(j): the pull product over out-edges without weights.
-cudaError_t launch_pull_sum(const Graph& g, const double* x, double* out) {
-    return sweep_level<Pol64>(g, g.out, x, PlainOp{out});
+// out(i) = sum_{j in Out(i)} x(j): the pull product over out-edges without weights, x as
+// two-floats, the sums in two-float, out in FP64.
+cudaError_t launch_pull_sum(const Graph& g, const float2* x, double* out) {
+    return sweep_level<Pol2f>(g, g.out, x, PlainOpD{out});
 }
 
 cudaError_t launch_forward32(const Graph& g, int64_t u, double c, int32_t L, float* hist, float* xa, float* xb) {
