@@ -410,10 +410,10 @@ esim_status esim_alg3_paper_depth(esim_graph* g, const uint64_t* R, double c, in
  * d = depth[k] (device uint8[n], 0..16), 0 where d = 0; zsum is device double[n].  Depth 1
  * is c/din(k); depth 2 uses Lemma 5's closed form over the two-hop neighbourhood (one warp
  * per node, 63-bit fixed point); deeper nodes, and depth-2 nodes with more than 512
- * two-hop entries, run esim_alg3_first_meeting's kernels one node at a time.  The query
- * with option "alg3_rule" = 0 uses this for the depths esim_alg3_paper_depth gives.
- * Synchronous.  Needs a graph without repeated in-edges (else ESIM_ENOTSUP); ESIM_ENOTSUP
- * also for n > 131072 (the work space is the depth rule's). */
+ * two-hop entries, run esim_alg3_first_meeting's kernels, "alg3_workers" nodes at a time.
+ * The query with option "alg3_rule" = 0 uses this for the depths esim_alg3_paper_depth
+ * gives, and the cost-model rule for its plan.  Synchronous.  Needs a graph without
+ * repeated in-edges (else ESIM_ENOTSUP); ESIM_ENOMEM, ESIM_ECUDA. */
 esim_status esim_alg3_zsum(esim_graph* g, const uint8_t* depth, double c, double* zsum);
 esim_status esim_sample_depth(esim_graph* g, const uint64_t* off, const uint8_t* depth, double c, uint64_t seed,
                               uint64_t* counts, uint64_t* pair_steps);

@@ -341,6 +341,16 @@ def test_alg3_paper_rule_refuses_graphs_beyond_its_bit_sets(esim):
     g.set_option("alg3_rule", 1)  # the cost model has no such limit
     s = g.query(0, C, 1e-2, 0)
     assert abs(s[0] - (1 - C) * (1 - C ** (esim.esim_levels(C, 1e-2) + 1)) / (1 - C)) < 1e-12
+    # nor has the exact part for given depths: on a cycle (one in-neighbour each) the two
+    # walks meet at step 1, so Z_1 = c and the deeper terms are 0
+    import torch
+    depth = np.zeros(n, dtype=np.uint8)
+    depth[:6] = np.arange(1, 7)
+    depth[n - 1] = 3
+    zsum = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    g.alg3_zsum(torch.from_numpy(depth).cuda(), C, zsum)
+    z = zsum.cpu().numpy()
+    assert np.allclose(z[depth > 0], C, rtol=0, atol=1e-15) and np.all(z[depth == 0] == 0.0)
     g.close()
 
 
